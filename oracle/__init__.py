@@ -1,0 +1,262 @@
+"""FP64 CPU oracle of the 3DGS-ReLoc relocalization hot path.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its binding) never imports this package.
+
+The arithmetic lives in ``reloc_oracle.c`` (plain C, IEEE FP64, OpenMP over
+candidate views); this module compiles it with gcc on first use and wraps it
+with numpy-facing functions.  Every function cites the passage of the paper it
+follows in the C source.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "reloc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# record layout (mirrors the enum in reloc_oracle.c)
+REC_FIELDS = ["visible", "u", "v", "depth", "cov_a", "cov_b", "cov_c", "con_a", "con_b", "con_c",
+              "rx", "ry", "r", "g", "b", "opacity", "tx0", "ty0", "tx1", "ty1",
+              "det_undil", "det", "tcx", "tcy"]
+F = {k: i for i, k in enumerate(REC_FIELDS)}
+
+FLAG_POWER, FLAG_ALPHA, FLAG_T, FLAG_DEPTH = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math) into oracle/_build/."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                               "-Wall", "-Wno-misleading-indentation", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, fp, i64p = C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int64)
+            u8p, u32p, u64p, i32p = (C.POINTER(C.c_uint8), C.POINTER(C.c_uint32),
+                                     C.POINTER(C.c_uint64), C.POINTER(C.c_int32))
+            L.or_rec_stride.restype = C.c_int
+            L.or_max_threads.restype = C.c_int
+            L.or_quat_to_rot.argtypes = [dp, dp]
+            L.or_sh_basis.argtypes = [C.c_int, dp, dp]
+            L.or_project.argtypes = [fp, fp, fp, fp, fp, C.c_int, C.c_int64, dp, dp, dp, dp]
+            L.or_render.argtypes = [dp, C.c_int64, dp, dp, dp, dp, dp, u8p, C.c_int]
+            L.or_render.restype = C.c_int64
+            L.or_ncc.argtypes = [dp, dp, C.c_int64, C.POINTER(C.c_int)]
+            L.or_ncc.restype = C.c_double
+            L.or_argmax.argtypes = [dp, C.c_int]
+            L.or_argmax.restype = C.c_int
+            L.or_grid_poses.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp]
+            L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, i64p, i64p]
+            L.or_block_select.restype = C.c_int64
+            L.or_tile_bits.argtypes = [C.c_int]
+            L.or_tile_bits.restype = C.c_int
+            L.or_tile_keys.argtypes = [C.c_int, C.c_int64, u8p, u32p, i32p, C.c_int, C.c_int, u64p, u32p]
+            L.or_tile_keys.restype = C.c_int64
+            L.or_tile_ranges.argtypes = [u64p, C.c_int64, C.c_int, C.c_int, i64p]
+            L.or_stable_sort_u64.argtypes = [u64p, u32p, C.c_int64]
+            L.or_insertion_sort_u64.argtypes = [u64p, u32p, C.c_int64]
+            L.or_render_views.argtypes = [fp, fp, fp, fp, fp, C.c_int, C.c_int64, dp, C.c_int, dp, dp,
+                                          dp, dp, C.POINTER(C.c_int), dp, dp, dp, u8p, i64p]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ---------------------------------------------------------------------------
+# parameters
+# ---------------------------------------------------------------------------
+
+DEFAULT_PARAMS = dict(near=0.2, fov_clamp=1.3, eps2d=0.3, alpha_min=1.0 / 255.0, alpha_max=0.99,
+                      t_min=1e-4, cut=3.0, tile_w=16, tile_h=16,
+                      flag_power=1e-4, flag_alpha=1e-4, flag_t=1e-3, flag_depth=1e-6)
+_PORDER = ["near", "fov_clamp", "eps2d", "alpha_min", "alpha_max", "t_min", "cut", "tile_w", "tile_h",
+           "flag_power", "flag_alpha", "flag_t", "flag_depth"]
+
+
+def params(**over) -> np.ndarray:
+    d = dict(DEFAULT_PARAMS)
+    for k, v in over.items():
+        if k not in d:
+            raise KeyError(k)
+        d[k] = v
+    out = np.zeros(16)
+    for i, k in enumerate(_PORDER):
+        out[i] = d[k]
+    return out
+
+
+def camvec(cam) -> np.ndarray:
+    return np.array([cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy], dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# wrappers
+# ---------------------------------------------------------------------------
+
+def quat_to_rot(q) -> np.ndarray:
+    R = np.zeros(9)
+    lib().or_quat_to_rot(_p(_c(q, np.float64), C.c_double), _p(R, C.c_double))
+    return R.reshape(3, 3)
+
+
+def sh_basis(deg: int, d) -> np.ndarray:
+    Y = np.zeros((deg + 1) ** 2)
+    lib().or_sh_basis(deg, _p(_c(d, np.float64), C.c_double), _p(Y, C.c_double))
+    return Y
+
+
+def _gauss_ptrs(g):
+    return (_c(g.mean, np.float32), _c(g.scale, np.float32), _c(g.quat, np.float32),
+            _c(g.opacity, np.float32), _c(g.sh, np.float32))
+
+
+def project(g, pose, cam, prm=None) -> np.ndarray:
+    """Project every Gaussian of ``g`` for one world-to-camera pose.
+    Returns an (N, len(REC_FIELDS)) float64 record array (fields in F)."""
+    prm = params() if prm is None else prm
+    m, s, q, o, sh = _gauss_ptrs(g)
+    recs = np.zeros((g.n, lib().or_rec_stride()))
+    lib().or_project(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
+                     _p(sh, C.c_float), g.sh_degree, g.n, _p(_c(pose, np.float64), C.c_double),
+                     _p(camvec(cam), C.c_double), _p(_c(prm, np.float64), C.c_double), _p(recs, C.c_double))
+    return recs
+
+
+def render_records(recs, cam, prm=None, brute=False):
+    """Composite projected records (index order = tie order).
+    Returns dict(rgb (3,H,W), depth (H,W), alpha (H,W), flags (H,W) u8, n_eval)."""
+    prm = params() if prm is None else prm
+    recs = _c(recs, np.float64)
+    H, W = cam.height, cam.width
+    rgb = np.zeros((3, H, W)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
+    flags = np.zeros((H, W), np.uint8)
+    ne = lib().or_render(_p(recs, C.c_double), recs.shape[0], _p(camvec(cam), C.c_double),
+                         _p(_c(prm, np.float64), C.c_double), _p(rgb, C.c_double), _p(depth, C.c_double),
+                         _p(alpha, C.c_double), _p(flags, C.c_uint8), 1 if brute else 0)
+    return dict(rgb=rgb, depth=depth, alpha=alpha, flags=flags, n_eval=int(ne))
+
+
+def render(g, pose, cam, prm=None, brute=False):
+    prm = params() if prm is None else prm
+    return render_records(project(g, pose, cam, prm), cam, prm, brute)
+
+
+def render_views(g, poses, cam, prm=None, query=None, images=True, flags=True):
+    """Render V views (OpenMP over views); NCC against ``query`` if given.
+    Returns dict(scores, degenerate, rgb, depth, alpha, flags, counts)."""
+    prm = params() if prm is None else prm
+    poses = _c(poses, np.float64).reshape(-1, 16)
+    V = poses.shape[0]
+    H, W = cam.height, cam.width
+    m, s, q, o, sh = _gauss_ptrs(g)
+    out = dict(counts=np.zeros((V, 3), np.int64))
+    if images:
+        out["rgb"] = np.zeros((V, 3, H, W)); out["depth"] = np.zeros((V, H, W)); out["alpha"] = np.zeros((V, H, W))
+    if flags:
+        out["flags"] = np.zeros((V, H, W), np.uint8)
+    qd = None
+    if query is not None:
+        qd = _c(query, np.float64).reshape(-1)
+        out["scores"] = np.zeros(V); out["degenerate"] = np.zeros(V, np.int32)
+    lib().or_render_views(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
+                          _p(sh, C.c_float), g.sh_degree, g.n, _p(poses, C.c_double), V,
+                          _p(camvec(cam), C.c_double), _p(_c(prm, np.float64), C.c_double),
+                          _p(qd, C.c_double), _p(out.get("scores"), C.c_double),
+                          _p(out.get("degenerate"), C.c_int), _p(out.get("rgb"), C.c_double),
+                          _p(out.get("depth"), C.c_double), _p(out.get("alpha"), C.c_double),
+                          _p(out.get("flags"), C.c_uint8), _p(out["counts"], C.c_int64))
+    return out
+
+
+def ncc(a, b):
+    a = _c(a, np.float64).reshape(-1)
+    b = _c(b, np.float64).reshape(-1)
+    dg = C.c_int(0)
+    val = lib().or_ncc(_p(a, C.c_double), _p(b, C.c_double), a.size, C.byref(dg))
+    return val, bool(dg.value)
+
+
+def argmax(scores) -> int:
+    s = _c(scores, np.float64)
+    return int(lib().or_argmax(_p(s, C.c_double), s.size))
+
+
+def grid_poses(seed_pose, nx, ny, nyaw, step_xy, step_yaw_deg) -> np.ndarray:
+    out = np.zeros((nx * ny * nyaw, 16))
+    lib().or_grid_poses(_p(_c(seed_pose, np.float64).reshape(16), C.c_double), nx, ny, nyaw,
+                        step_xy, step_yaw_deg, _p(out, C.c_double))
+    return out.reshape(-1, 4, 4)
+
+
+def block_select(means, block_size, cx, cy, radius):
+    """Original indices of the Gaussians in every block whose centre is within
+    ``radius`` of (cx, cy), ordered by block key then index; and the block count."""
+    m = _c(means, np.float32)
+    n = m.shape[0]
+    idx = np.zeros(n, np.int64)
+    nb = C.c_int64(0)
+    cnt = lib().or_block_select(_p(m, C.c_float), n, block_size, cx, cy, radius, _p(idx, C.c_int64),
+                                C.byref(nb))
+    return idx[:cnt], int(nb.value)
+
+
+def tile_bits(n_tiles: int) -> int:
+    return int(lib().or_tile_bits(n_tiles))
+
+
+def tile_keys(vis, dbits, rect, ntx, nty):
+    """vis (V,N) u8, dbits (V,N) u32, rect (V,N,4) i32 -> (keys u64, vals u32) in emission order."""
+    vis = _c(vis, np.uint8); dbits = _c(dbits, np.uint32); rect = _c(rect, np.int32)
+    V, N = vis.shape
+    L = lib()
+    cnt = L.or_tile_keys(V, N, _p(vis, C.c_uint8), _p(dbits, C.c_uint32), _p(rect, C.c_int32), ntx, nty,
+                         None, None)
+    keys = np.zeros(cnt, np.uint64); vals = np.zeros(cnt, np.uint32)
+    L.or_tile_keys(V, N, _p(vis, C.c_uint8), _p(dbits, C.c_uint32), _p(rect, C.c_int32), ntx, nty,
+                   _p(keys, C.c_uint64), _p(vals, C.c_uint32))
+    return keys, vals
+
+
+def stable_sort(keys, vals, insertion=False):
+    k = _c(keys, np.uint64).copy(); v = _c(vals, np.uint32).copy()
+    fn = lib().or_insertion_sort_u64 if insertion else lib().or_stable_sort_u64
+    fn(_p(k, C.c_uint64), _p(v, C.c_uint32), k.size)
+    return k, v
+
+
+def tile_ranges(keys, n_views, n_tiles):
+    k = _c(keys, np.uint64)
+    r = np.zeros((n_views, n_tiles, 2), np.int64)
+    lib().or_tile_ranges(_p(k, C.c_uint64), k.size, n_views, n_tiles, _p(r, C.c_int64))
+    return r
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())

@@ -1,0 +1,592 @@
+/*
+ * reloc_oracle.c -- FP64 CPU oracle of the 3DGS-ReLoc relocalization hot path
+ * (Jiang, Pandey, Saripalli, "3DGS-ReLoc", arXiv 2403.11367).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path.
+ *
+ * What it computes, in the paper's order:
+ *   - Gaussian parameterisation g = [mu, S, R, c, o] with Sigma = R S S^T R^T
+ *     and R = q2R(q)                                             (Sec. III-A)
+ *   - world-to-camera transform and pinhole projection m(mu)     (Eq. proj)
+ *   - EWA footprint covariance Sigma^c = J W Sigma W^T J^T, 2x2  (Eq. foot_conv)
+ *   - footprint q_i = o_i G(x - mu_hat)                          (Eq. footprint)
+ *   - front-to-back colour compositing, Max's model              (Sec. III-A, Eq. 1)
+ *   - depth compositing with z_i = camera-space depth            (Sec. III-A, depth eq.)
+ *   - normalised cross-correlation                               (Sec. III-C.1, Eq. ncc)
+ *   - block (2D voxel) selection around a coarse pose            (Sec. III-B.2, III-C.1)
+ *   - argmax over the candidate grid                             (Sec. III-C.1)
+ * plus an integer replay of the tile|depth key build and stable sort so the
+ * GPU's keys and tile lists can be compared bit for bit.
+ *
+ * Readings taken where the paper is silent or garbled (each one is a
+ * parameter or a documented rule below):
+ *   - the 1/(|J^-1||W^-1|) factor of Eq. footprint is dropped (W is rigid;
+ *     the unnormalised kernel keeps alpha <= o <= 1);
+ *   - mu_hat is the projected mean (first two components of m(mu));
+ *   - inclusion: pixel centre x is inside iff d^T Sigma'^-1 d <= cut^2 (cut = 3);
+ *   - alpha = min(alpha_max, o exp(power)); skipped if alpha < alpha_min;
+ *   - transmittance stop: if T (1 - alpha) < t_min the Gaussian is not added
+ *     and the pixel is finished;
+ *   - Sigma' gets eps (px^2) added to its diagonal; J uses tx/tz, ty/tz
+ *     clamped to +-fov_clamp * tan(half FOV);
+ *   - cull if tz <= near, det(Sigma') <= 0 or the 3-sigma box misses the image;
+ *   - SH degree 0 is plain RGB; degree >= 1 is max(0, sum c_lm Y_lm(dir) + 0.5)
+ *     with real orthonormal SH (Condon-Shortley phase), dir = mu - camera centre;
+ *   - depth order: ascending camera depth, ties by Gaussian index;
+ *   - NCC over all 3*H*W samples as one vector with one mean each.
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC (no fast-math: IEEE FP64 throughout).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ---- parameter vector (double[16]) --------------------------------------- */
+enum {
+    P_NEAR = 0, P_FOV_CLAMP, P_EPS2D, P_ALPHA_MIN, P_ALPHA_MAX, P_T_MIN, P_CUT,
+    P_TILE_W, P_TILE_H,
+    P_FLAG_POWER, P_FLAG_ALPHA, P_FLAG_T, P_FLAG_DEPTH,
+    P_COUNT = 16
+};
+
+/* ---- camera vector (double[6]): width, height, fx, fy, cx, cy ------------- */
+enum { C_W = 0, C_H, C_FX, C_FY, C_CX, C_CY };
+
+/* ---- projected record (double[OR_REC]) ------------------------------------ */
+enum {
+    R_VISIBLE = 0, R_U, R_V, R_DEPTH,
+    R_COV_A, R_COV_B, R_COV_C,           /* Sigma' (dilated): [[a, b], [b, c]] */
+    R_CON_A, R_CON_B, R_CON_C,           /* inverse of Sigma'                  */
+    R_RX, R_RY,                          /* cut * sqrt(Sigma'_xx), ... (px)    */
+    R_RED, R_GREEN, R_BLUE, R_OPACITY,
+    R_TX0, R_TY0, R_TX1, R_TY1,          /* inclusive tile rectangle           */
+    R_DET_UNDIL, R_DET, R_TCX, R_TCY,    /* undilated det, det, camera x, y    */
+    OR_REC
+};
+
+int or_rec_stride(void) { return OR_REC; }
+int or_param_count(void) { return P_COUNT; }
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ========================================================================= */
+/* Rotation from a quaternion (w, x, y, z), normalised first.  Sec. III-A.   */
+/* ========================================================================= */
+void or_quat_to_rot(const double qin[4], double R[9])
+{
+    double n = sqrt(qin[0] * qin[0] + qin[1] * qin[1] + qin[2] * qin[2] + qin[3] * qin[3]);
+    double w = qin[0] / n, x = qin[1] / n, y = qin[2] / n, z = qin[3] / n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* ========================================================================= */
+/* Real orthonormal spherical harmonics, any degree, from their definition:   */
+/*   Y_l0  = K_l0 P_l^0(z)                                                   */
+/*   Y_lm  = sqrt2 K_lm cos(m phi) P_l^m(z)     (m > 0)                      */
+/*   Y_l-m = sqrt2 K_lm sin(m phi) P_l^m(z)     (m > 0)                      */
+/*   K_lm  = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)                               */
+/* with P_l^m the associated Legendre functions including (-1)^m.  For a unit */
+/* direction, cos(m phi) sin^m(theta) = Re((x+iy)^m) and likewise Im for sin, */
+/* so P_l^m / sin^m(theta) is a polynomial in z obtained by the usual         */
+/* three-term recurrence.  Output index: l*l + l + m.                         */
+/* ========================================================================= */
+static double factorial(int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; }
+
+void or_sh_basis(int deg, const double d[3], double *Y)
+{
+    double re[8], im[8];          /* (x + i y)^m */
+    re[0] = 1; im[0] = 0;
+    for (int m = 1; m <= deg; ++m) {
+        re[m] = re[m - 1] * d[0] - im[m - 1] * d[1];
+        im[m] = re[m - 1] * d[1] + im[m - 1] * d[0];
+    }
+    double z = d[2];
+    for (int m = 0; m <= deg; ++m) {
+        /* Ptilde_m^m = (-1)^m (2m-1)!! */
+        double pmm = 1;
+        for (int i = 1; i <= m; ++i) pmm *= -(2.0 * i - 1);
+        double p_prev2 = 0, p_prev = 0;
+        for (int l = m; l <= deg; ++l) {
+            double p;
+            if (l == m) p = pmm;
+            else if (l == m + 1) p = z * (2 * m + 1) * pmm;
+            else p = ((2 * l - 1) * z * p_prev - (l + m - 1) * p_prev2) / (l - m);
+            p_prev2 = p_prev; p_prev = p;
+            double K = sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - m) / factorial(l + m));
+            if (m == 0) {
+                Y[l * l + l] = K * p;
+            } else {
+                Y[l * l + l + m] = sqrt(2.0) * K * re[m] * p;
+                Y[l * l + l - m] = sqrt(2.0) * K * im[m] * p;
+            }
+        }
+    }
+}
+
+/* ========================================================================= */
+/* Projection of one Gaussian for one camera (Eqs. proj, foot_conv).          */
+/* ========================================================================= */
+static void project_one(const float *mean, const float *scale, const float *quat, float opac,
+                        const float *sh, int sh_deg, const double *Wm, const double *cam,
+                        const double *p, double *rec)
+{
+    memset(rec, 0, sizeof(double) * OR_REC);
+    const double Rw[9] = {Wm[0], Wm[1], Wm[2], Wm[4], Wm[5], Wm[6], Wm[8], Wm[9], Wm[10]};
+    const double tw[3] = {Wm[3], Wm[7], Wm[11]};
+    const double mu[3] = {mean[0], mean[1], mean[2]};
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = Rw[3 * i] * mu[0] + Rw[3 * i + 1] * mu[1] + Rw[3 * i + 2] * mu[2] + tw[i];
+    rec[R_DEPTH] = t[2];
+    rec[R_TCX] = t[0];
+    rec[R_TCY] = t[1];
+    if (!(t[2] > p[P_NEAR])) return;
+
+    /* 3D covariance Sigma = (R S)(R S)^T */
+    double q[4] = {quat[0], quat[1], quat[2], quat[3]}, R[9], M[9], S3[9];
+    or_quat_to_rot(q, R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * (double)scale[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S3[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+
+    /* Jacobian of the pinhole projection at t (FOV clamp applied in J only) */
+    const double fx = cam[C_FX], fy = cam[C_FY];
+    double limx = p[P_FOV_CLAMP] * (0.5 * cam[C_W]) / fx;
+    double limy = p[P_FOV_CLAMP] * (0.5 * cam[C_H]) / fy;
+    double xz = t[0] / t[2], yz = t[1] / t[2];
+    if (xz < -limx) xz = -limx; if (xz > limx) xz = limx;
+    if (yz < -limy) yz = -limy; if (yz > limy) yz = limy;
+    double J[6] = {fx / t[2], 0, -fx * xz / t[2],
+                   0, fy / t[2], -fy * yz / t[2]};
+    /* T = J W_R  (2x3);  Sigma' = T Sigma T^T */
+    double T[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = J[3 * i] * Rw[j] + J[3 * i + 1] * Rw[3 + j] + J[3 * i + 2] * Rw[6 + j];
+    double TS[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            TS[3 * i + j] = T[3 * i] * S3[j] + T[3 * i + 1] * S3[3 + j] + T[3 * i + 2] * S3[6 + j];
+    double c00 = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2];
+    double c01 = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    double c11 = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5];
+    rec[R_DET_UNDIL] = c00 * c11 - c01 * c01;
+    double a = c00 + p[P_EPS2D], b = c01, c = c11 + p[P_EPS2D];
+    double det = a * c - b * b;
+    rec[R_COV_A] = a; rec[R_COV_B] = b; rec[R_COV_C] = c; rec[R_DET] = det;
+    if (!(det > 0)) return;
+    rec[R_CON_A] = c / det; rec[R_CON_B] = -b / det; rec[R_CON_C] = a / det;
+
+    /* projected mean m(mu) */
+    double u = fx * t[0] / t[2] + cam[C_CX];
+    double v = fy * t[1] / t[2] + cam[C_CY];
+    double rx = p[P_CUT] * sqrt(a), ry = p[P_CUT] * sqrt(c);
+    rec[R_U] = u; rec[R_V] = v; rec[R_RX] = rx; rec[R_RY] = ry;
+
+    /* conservative tile rectangle of the cut-sigma box */
+    const int width = (int)cam[C_W], height = (int)cam[C_H];
+    const int tw_ = (int)p[P_TILE_W], th_ = (int)p[P_TILE_H];
+    const int ntx = (width + tw_ - 1) / tw_, nty = (height + th_ - 1) / th_;
+    double xlo = u - rx, xhi = u + rx, ylo = v - ry, yhi = v + ry;
+    if (xhi < 0 || xlo >= width || yhi < 0 || ylo >= height) return;
+    int tx0 = (int)floor(xlo / tw_), tx1 = (int)floor(xhi / tw_);
+    int ty0 = (int)floor(ylo / th_), ty1 = (int)floor(yhi / th_);
+    if (tx0 < 0) tx0 = 0; if (ty0 < 0) ty0 = 0;
+    if (tx1 > ntx - 1) tx1 = ntx - 1; if (ty1 > nty - 1) ty1 = nty - 1;
+    rec[R_TX0] = tx0; rec[R_TY0] = ty0; rec[R_TX1] = tx1; rec[R_TY1] = ty1;
+
+    /* colour */
+    if (sh_deg == 0) {
+        rec[R_RED] = sh[0]; rec[R_GREEN] = sh[1]; rec[R_BLUE] = sh[2];
+    } else {
+        /* camera centre C = -R_w^T t_w;  dir = normalise(mu - C) */
+        double C[3];
+        for (int i = 0; i < 3; ++i) C[i] = -(Rw[i] * tw[0] + Rw[3 + i] * tw[1] + Rw[6 + i] * tw[2]);
+        double d[3] = {mu[0] - C[0], mu[1] - C[1], mu[2] - C[2]};
+        double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] /= nd; d[1] /= nd; d[2] /= nd;
+        double Y[64];
+        or_sh_basis(sh_deg, d, Y);
+        int K = (sh_deg + 1) * (sh_deg + 1);
+        for (int ch = 0; ch < 3; ++ch) {
+            double s = 0;
+            for (int k = 0; k < K; ++k) s += (double)sh[3 * k + ch] * Y[k];
+            s += 0.5;
+            rec[R_RED + ch] = s > 0 ? s : 0;
+        }
+    }
+    rec[R_OPACITY] = opac;
+    rec[R_VISIBLE] = 1;
+}
+
+/* Project n Gaussians for one camera pose W (row-major 4x4, world-to-camera). */
+void or_project(const float *means, const float *scales, const float *quats, const float *opac,
+                const float *sh, int sh_deg, int64_t n, const double *W, const double *cam,
+                const double *params, double *recs)
+{
+    const int K = (sh_deg + 1) * (sh_deg + 1);
+    for (int64_t i = 0; i < n; ++i)
+        project_one(means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], sh + (int64_t)3 * K * i,
+                    sh_deg, W, cam, params, recs + (int64_t)OR_REC * i);
+}
+
+/* ========================================================================= */
+/* Stable merge sorts.                                                        */
+/* ========================================================================= */
+static void msort_by_double(int64_t *idx, int64_t *tmp, int64_t n, const double *key)
+{
+    if (n < 2) return;
+    int64_t h = n / 2;
+    msort_by_double(idx, tmp, h, key);
+    msort_by_double(idx + h, tmp, n - h, key);
+    int64_t i = 0, j = h, k = 0;
+    while (i < h && j < n) {
+        if (key[idx[j]] < key[idx[i]]) tmp[k++] = idx[j++];   /* equal: left first */
+        else tmp[k++] = idx[i++];
+    }
+    while (i < h) tmp[k++] = idx[i++];
+    while (j < n) tmp[k++] = idx[j++];
+    memcpy(idx, tmp, sizeof(int64_t) * n);
+}
+
+static void msort_u64(uint64_t *k, uint32_t *v, uint64_t *tk, uint32_t *tv, int64_t n)
+{
+    if (n < 2) return;
+    int64_t h = n / 2;
+    msort_u64(k, v, tk, tv, h);
+    msort_u64(k + h, v + h, tk, tv, n - h);
+    int64_t i = 0, j = h, o = 0;
+    while (i < h && j < n) {
+        if (k[j] < k[i]) { tk[o] = k[j]; tv[o++] = v[j++]; }
+        else { tk[o] = k[i]; tv[o++] = v[i++]; }
+    }
+    while (i < h) { tk[o] = k[i]; tv[o++] = v[i++]; }
+    while (j < n) { tk[o] = k[j]; tv[o++] = v[j++]; }
+    memcpy(k, tk, sizeof(uint64_t) * n);
+    memcpy(v, tv, sizeof(uint32_t) * n);
+}
+
+void or_stable_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n)
+{
+    if (n < 2) return;
+    uint64_t *tk = (uint64_t *)malloc(sizeof(uint64_t) * n);
+    uint32_t *tv = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    msort_u64(keys, vals, tk, tv, n);
+    free(tk); free(tv);
+}
+
+/* O(n^2) insertion sort: the plain definition of a stable sort (pins the above). */
+void or_insertion_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n)
+{
+    for (int64_t i = 1; i < n; ++i) {
+        uint64_t k = keys[i]; uint32_t v = vals[i];
+        int64_t j = i - 1;
+        while (j >= 0 && keys[j] > k) { keys[j + 1] = keys[j]; vals[j + 1] = vals[j]; --j; }
+        keys[j + 1] = k; vals[j + 1] = v;
+    }
+}
+
+/* ========================================================================= */
+/* Front-to-back compositing of RGB and depth (Sec. III-A).                   */
+/* recs: projected records of n Gaussians (index order = tie order).          */
+/* brute != 0: every pixel tests every visible Gaussian (pins the splat form). */
+/* flags bit 1: footprint boundary, 2: alpha-skip boundary, 4: stop boundary, */
+/*       8: depth near-tie between consecutive contributors.                  */
+/* ========================================================================= */
+typedef struct { double T, r, g, b, d; double last_z; int done, any; } pix_state;
+
+static inline void composite(pix_state *s, const double *rc, double px, double py,
+                             const double *p, uint8_t *flag, int64_t *n_eval)
+{
+    if (s->done) return;
+    double dx = px - rc[R_U], dy = py - rc[R_V];
+    double power = -0.5 * (rc[R_CON_A] * dx * dx + rc[R_CON_C] * dy * dy) - rc[R_CON_B] * dx * dy;
+    double lim = -0.5 * p[P_CUT] * p[P_CUT];
+    if (fabs(power - lim) <= p[P_FLAG_POWER] * fabs(lim)) *flag |= 1;
+    if (power < lim) return;
+    (*n_eval)++;
+    double raw = rc[R_OPACITY] * exp(power);
+    double alpha = raw < p[P_ALPHA_MAX] ? raw : p[P_ALPHA_MAX];
+    if (fabs(raw - p[P_ALPHA_MIN]) <= p[P_FLAG_ALPHA] * p[P_ALPHA_MIN]) *flag |= 2;
+    if (alpha < p[P_ALPHA_MIN]) return;
+    double tn = s->T * (1 - alpha);
+    if (fabs(tn - p[P_T_MIN]) <= p[P_FLAG_T] * p[P_T_MIN]) *flag |= 4;
+    if (tn < p[P_T_MIN]) { s->done = 1; return; }
+    double z = rc[R_DEPTH];
+    if (s->any && fabs(z - s->last_z) <= p[P_FLAG_DEPTH] * fabs(z)) *flag |= 8;
+    double w = alpha * s->T;
+    s->r += rc[R_RED] * w; s->g += rc[R_GREEN] * w; s->b += rc[R_BLUE] * w;
+    s->d += z * w;
+    s->T = tn; s->last_z = z; s->any = 1;
+}
+
+int64_t or_render(const double *recs, int64_t n, const double *cam, const double *p,
+                  double *rgb, double *depth, double *alpha, uint8_t *flags, int brute)
+{
+    const int W = (int)cam[C_W], H = (int)cam[C_H];
+    const int64_t npx = (int64_t)W * H;
+    int64_t nvis = 0;
+    for (int64_t i = 0; i < n; ++i) nvis += recs[OR_REC * i + R_VISIBLE] != 0;
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (nvis + 1));
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (nvis + 1));
+    double *zkey = (double *)malloc(sizeof(double) * (n + 1));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        zkey[i] = recs[OR_REC * i + R_DEPTH];
+        if (recs[OR_REC * i + R_VISIBLE] != 0) order[k++] = i;
+    }
+    msort_by_double(order, tmp, nvis, zkey);   /* depth ascending, ties by index */
+
+    pix_state *st = (pix_state *)calloc(npx, sizeof(pix_state));
+    uint8_t *fl = (uint8_t *)calloc(npx, 1);
+    for (int64_t q = 0; q < npx; ++q) st[q].T = 1;
+    int64_t n_eval = 0;
+    if (brute) {
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int64_t j = 0; j < nvis; ++j)
+                    composite(&st[(int64_t)y * W + x], recs + OR_REC * order[j], x + 0.5, y + 0.5, p,
+                              &fl[(int64_t)y * W + x], &n_eval);
+    } else {
+        for (int64_t j = 0; j < nvis; ++j) {
+            const double *rc = recs + OR_REC * order[j];
+            /* every pixel whose centre can lie inside the cut-sigma ellipse */
+            int x0 = (int)floor(rc[R_U] - rc[R_RX] - 1), x1 = (int)ceil(rc[R_U] + rc[R_RX]);
+            int y0 = (int)floor(rc[R_V] - rc[R_RY] - 1), y1 = (int)ceil(rc[R_V] + rc[R_RY]);
+            if (x0 < 0) x0 = 0; if (y0 < 0) y0 = 0;
+            if (x1 > W - 1) x1 = W - 1; if (y1 > H - 1) y1 = H - 1;
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x)
+                    composite(&st[(int64_t)y * W + x], rc, x + 0.5, y + 0.5, p,
+                              &fl[(int64_t)y * W + x], &n_eval);
+        }
+    }
+    for (int64_t q = 0; q < npx; ++q) {
+        if (rgb) { rgb[q] = st[q].r; rgb[npx + q] = st[q].g; rgb[2 * npx + q] = st[q].b; }
+        if (depth) depth[q] = st[q].d;
+        if (alpha) alpha[q] = 1 - st[q].T;
+        if (flags) flags[q] = fl[q];
+    }
+    free(st); free(fl); free(order); free(tmp); free(zkey);
+    return n_eval;
+}
+
+/* ========================================================================= */
+/* NCC (Eq. ncc), two-pass: means first, then centred sums.                   */
+/* Returns 0 and sets *degenerate when either centred sum of squares is       */
+/* <= 1e-12 * n (zero-variance image: NCC undefined).                         */
+/* ========================================================================= */
+double or_ncc(const double *a, const double *b, int64_t n, int *degenerate)
+{
+    double ma = 0, mb = 0;
+    for (int64_t i = 0; i < n; ++i) { ma += a[i]; mb += b[i]; }
+    ma /= n; mb /= n;
+    double sab = 0, saa = 0, sbb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double da = a[i] - ma, db = b[i] - mb;
+        sab += da * db; saa += da * da; sbb += db * db;
+    }
+    if (degenerate) *degenerate = 0;
+    if (saa <= 1e-12 * n || sbb <= 1e-12 * n) { if (degenerate) *degenerate = 1; return 0; }
+    return sab / (sqrt(saa) * sqrt(sbb));
+}
+
+/* Argmax with the lowest index on ties. */
+int or_argmax(const double *s, int n)
+{
+    int best = 0;
+    for (int i = 1; i < n; ++i) if (s[i] > s[best]) best = i;
+    return best;
+}
+
+/* ========================================================================= */
+/* Candidate grid around a coarse pose (Sec. III-C.1; Sec. IV-A grid).        */
+/* Offsets (dx, dy) in the world ground plane and a yaw about world z through */
+/* the camera centre; height, pitch and roll are the seed's.                  */
+/* Candidate index = ix + nx * (iy + ny * iyaw); offsets centred on zero.     */
+/* ========================================================================= */
+void or_grid_poses(const double *seed, int nx, int ny, int nyaw, double step_xy,
+                   double step_yaw_deg, double *out)
+{
+    const double R[9] = {seed[0], seed[1], seed[2], seed[4], seed[5], seed[6], seed[8], seed[9], seed[10]};
+    const double t[3] = {seed[3], seed[7], seed[11]};
+    double C[3];
+    for (int i = 0; i < 3; ++i) C[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);
+    for (int iyaw = 0; iyaw < nyaw; ++iyaw)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                int k = ix + nx * (iy + ny * iyaw);
+                double dx = (ix - 0.5 * (nx - 1)) * step_xy;
+                double dy = (iy - 0.5 * (ny - 1)) * step_xy;
+                double psi = (iyaw - 0.5 * (nyaw - 1)) * step_yaw_deg * M_PI / 180.0;
+                /* camera-to-world rotation Rcw' = Rz(psi) R^T, so R' = R Rz(psi)^T */
+                double Rz[9] = {cos(psi), -sin(psi), 0, sin(psi), cos(psi), 0, 0, 0, 1};
+                double Rn[9];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        Rn[3 * i + j] = R[3 * i] * Rz[3 * j] + R[3 * i + 1] * Rz[3 * j + 1] + R[3 * i + 2] * Rz[3 * j + 2];
+                double Cn[3] = {C[0] + dx, C[1] + dy, C[2]};
+                double *o = out + 16 * k;
+                for (int i = 0; i < 3; ++i) {
+                    o[4 * i] = Rn[3 * i]; o[4 * i + 1] = Rn[3 * i + 1]; o[4 * i + 2] = Rn[3 * i + 2];
+                    o[4 * i + 3] = -(Rn[3 * i] * Cn[0] + Rn[3 * i + 1] * Cn[1] + Rn[3 * i + 2] * Cn[2]);
+                }
+                o[12] = 0; o[13] = 0; o[14] = 0; o[15] = 1;
+            }
+}
+
+/* ========================================================================= */
+/* 2D voxel blocks (Sec. III-B.2): block (floor(x/B), floor(y/B)); the map is */
+/* ordered by block key (bx, by) ascending, Gaussians of a block in index     */
+/* order.  Selection (Sec. III-C.1): every block whose centre lies within     */
+/* radius of (cx, cy), by a plain distance scan.  Writes the selected          */
+/* Gaussians' original indices in that order; returns their count.            */
+/* ========================================================================= */
+typedef struct { int64_t bx, by, idx; } blk_item;
+static int cmp_blk(const void *a, const void *b)
+{
+    const blk_item *x = (const blk_item *)a, *y = (const blk_item *)b;
+    if (x->bx != y->bx) return x->bx < y->bx ? -1 : 1;
+    if (x->by != y->by) return x->by < y->by ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);   /* index order inside a block */
+}
+
+int64_t or_block_select(const float *means, int64_t n, double B, double cx, double cy, double radius,
+                        int64_t *out_idx, int64_t *out_nblocks)
+{
+    blk_item *it = (blk_item *)malloc(sizeof(blk_item) * (n + 1));
+    for (int64_t i = 0; i < n; ++i) {
+        it[i].bx = (int64_t)floor(means[3 * i] / B);
+        it[i].by = (int64_t)floor(means[3 * i + 1] / B);
+        it[i].idx = i;
+    }
+    qsort(it, n, sizeof(blk_item), cmp_blk);
+    int64_t cnt = 0, nb = 0;
+    for (int64_t i = 0; i < n;) {
+        int64_t j = i;
+        while (j < n && it[j].bx == it[i].bx && it[j].by == it[i].by) ++j;
+        double ccx = (it[i].bx + 0.5) * B, ccy = (it[i].by + 0.5) * B;
+        double dd = sqrt((ccx - cx) * (ccx - cx) + (ccy - cy) * (ccy - cy));
+        if (dd <= radius) {
+            ++nb;
+            for (int64_t k = i; k < j; ++k) { if (out_idx) out_idx[cnt] = it[k].idx; ++cnt; }
+        }
+        i = j;
+    }
+    if (out_nblocks) *out_nblocks = nb;
+    free(it);
+    return cnt;
+}
+
+/* ========================================================================= */
+/* Tile|depth key replay (integer logic only).  Inputs per (view, Gaussian):  */
+/* visibility, float32 depth bit pattern and inclusive tile rectangle, as the */
+/* GPU recorded them.  Emits one (key, value) per covered tile in view-major, */
+/* Gaussian-index order:                                                      */
+/*   key = view << (32 + tile_bits) | tile << 32 | depth_bits, value = index  */
+/* tile = ty * ntx + tx; tile_bits = bits needed for ntx*nty - 1.             */
+/* keys == NULL: count only.                                                  */
+/* ========================================================================= */
+int or_tile_bits(int n_tiles)
+{
+    int b = 0;
+    while ((1LL << b) < n_tiles) ++b;
+    return b;
+}
+
+int64_t or_tile_keys(int n_views, int64_t n, const uint8_t *vis, const uint32_t *dbits,
+                     const int32_t *rect, int ntx, int nty, uint64_t *keys, uint32_t *vals)
+{
+    int tb = or_tile_bits(ntx * nty);
+    int64_t o = 0;
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t q = (int64_t)v * n + i;
+            if (!vis[q]) continue;
+            const int32_t *r = rect + 4 * q;
+            for (int ty = r[1]; ty <= r[3]; ++ty)
+                for (int tx = r[0]; tx <= r[2]; ++tx) {
+                    if (keys) {
+                        uint64_t tile = (uint64_t)(ty * ntx + tx);
+                        keys[o] = ((uint64_t)v << (32 + tb)) | (tile << 32) | (uint64_t)dbits[q];
+                        vals[o] = (uint32_t)i;
+                    }
+                    ++o;
+                }
+        }
+    return o;
+}
+
+/* [begin, end) of every (view, tile) in a sorted key list; empty = [0, 0). */
+void or_tile_ranges(const uint64_t *keys, int64_t n, int n_views, int n_tiles, int64_t *ranges)
+{
+    int tb = or_tile_bits(n_tiles);
+    memset(ranges, 0, sizeof(int64_t) * 2 * (int64_t)n_views * n_tiles);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t vt = keys[i] >> 32;
+        int64_t v = (int64_t)(vt >> tb), t = (int64_t)(vt & ((1ULL << tb) - 1));
+        int64_t slot = v * n_tiles + t;
+        if (i == 0 || (keys[i - 1] >> 32) != vt) ranges[2 * slot] = i;
+        if (i == n - 1 || (keys[i + 1] >> 32) != vt) ranges[2 * slot + 1] = i + 1;
+    }
+}
+
+/* ========================================================================= */
+/* Whole views: project + composite + NCC for V poses, in parallel over views. */
+/* query: 3*H*W doubles or NULL (then scores are not computed).               */
+/* Optional outputs (NULL = skip): images per view, flags, and counts per     */
+/* view {n_visible, n_instances (tile rectangle sizes), n_eval}.             */
+/* ========================================================================= */
+void or_render_views(const float *means, const float *scales, const float *quats, const float *opac,
+                     const float *sh, int sh_deg, int64_t n, const double *poses, int n_views,
+                     const double *cam, const double *p, const double *query,
+                     double *scores, int *degenerate, double *rgb, double *depth, double *alpha,
+                     uint8_t *flags, int64_t *counts)
+{
+    const int W = (int)cam[C_W], H = (int)cam[C_H];
+    const int64_t npx = (int64_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int v = 0; v < n_views; ++v) {
+        double *recs = (double *)malloc(sizeof(double) * OR_REC * (n + 1));
+        or_project(means, scales, quats, opac, sh, sh_deg, n, poses + 16 * v, cam, p, recs);
+        double *img = rgb ? rgb + 3 * npx * v : (double *)malloc(sizeof(double) * 3 * npx);
+        int64_t ne = or_render(recs, n, cam, p, img, depth ? depth + npx * v : NULL,
+                               alpha ? alpha + npx * v : NULL, flags ? flags + npx * v : NULL, 0);
+        if (counts) {
+            int64_t nv = 0, ni = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                const double *r = recs + OR_REC * i;
+                if (r[R_VISIBLE] == 0) continue;
+                ++nv;
+                ni += (int64_t)(r[R_TX1] - r[R_TX0] + 1) * (int64_t)(r[R_TY1] - r[R_TY0] + 1);
+            }
+            counts[3 * v] = nv; counts[3 * v + 1] = ni; counts[3 * v + 2] = ne;
+        }
+        if (query && scores) {
+            int dg = 0;
+            scores[v] = or_ncc(img, query, 3 * npx, &dg);
+            if (degenerate) degenerate[v] = dg;
+        }
+        if (!rgb) free(img);
+        free(recs);
+    }
+}
