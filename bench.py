@@ -1,0 +1,327 @@
+"""Benchmark of the relocalization hot path (render candidates + NCC + argmax).
+
+Workload (one "step" = one query through the whole path): the driving-scale
+street -- 2M Gaussians, SH degree 3, FP32 attributes, 20 m blocks; each query
+selects the blocks within 40 m of its coarse pose (~280k Gaussians), renders
+64 candidate poses (4 x 4 x 4 grid, 0.5 m / 2 deg) at 1408x376, scores each
+against the query image by NCC, takes the argmax and exports the winner's RGB
+and depth.  Metric: candidate views rendered + NCC-scored per second.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the slow plain restatement of
+the method) on the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica on its own
+queries (the path has no exchange step: "replicas only"), value = all ranks'
+candidates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate views rendered+NCC-scored/s at 1408x376"
+UNIT = "candidates/s"
+N_GAUSS = 2_000_000
+GRID = (4, 4, 4, 0.5, 2.0)
+RADIUS = 40.0
+N_QUERIES = 4
+FLOPS_PER_EVAL = 24          # FP32 ops per included (pixel, Gaussian) pair (plus one exp)
+WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
+            "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (every 200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(rank: int = 0):
+    import scenegen as sg
+    g = sg.street_gaussians(N_GAUSS, seed=11, sh_degree=3)
+    cam = sg.street_camera()
+    hidden, seeds = sg.street_queries(N_QUERIES * (rank + 1), seed=12)
+    hidden, seeds = hidden[N_QUERIES * rank:], seeds[N_QUERIES * rank:]
+    return g, cam, hidden, seeds
+
+
+# ---------------------------------------------------------------- oracle ----
+
+def oracle_sample(g, cam, hidden, seeds, n_cand: int, query_index: int = 0, with_counts=True):
+    """Oracle (FP64, OpenMP over views) on n_cand candidates of one query:
+    block select, render, NCC.  Returns (seconds, threads, counts)."""
+    import numpy as np
+
+    import oracle
+    import scenegen as sg
+    oracle.build()
+    h, s = hidden[query_index], seeds[query_index]
+    seed_pose = sg.pose_from_xyz_yaw(*s)
+    t0 = time.perf_counter()
+    idx, nb = oracle.block_select(g.mean, 20.0, s[0], s[1], RADIUS)
+    sub = g.subset(idx)
+    q = oracle.render(sub, sg.pose_from_xyz_yaw(*h), cam)["rgb"] + sg.image_noise(13 + query_index, cam.height,
+                                                                                    cam.width)
+    t1 = time.perf_counter()
+    poses = oracle.grid_poses(seed_pose, *GRID)[:n_cand]
+    out = oracle.render_views(sub, poses, cam, query=q, images=False, flags=False)
+    oracle.argmax(out["scores"])
+    t2 = time.perf_counter()
+    return t2 - t1, oracle.max_threads(), out["counts"], t1 - t0, np.asarray(out["scores"])
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g, cam, hidden, seeds = make_workload(0)
+    n_cand = 16
+    for _ in range(args.warmup):
+        oracle_sample(g, cam, hidden, seeds, n_cand, 0)
+    total, cores = 0.0, 1
+    for k in range(args.steps):
+        dt, cores, *_ = oracle_sample(g, cam, hidden, seeds, n_cand, k % N_QUERIES)
+        total += dt
+    value = n_cand * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded street scene standing in for KITTI-360)",
+            "config": {"workload": WORKLOAD, "sample": f"{n_cand} of 64 candidates per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_cand} of the 64 candidates of one query per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours ---
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2403_11367_gb300.build import build
+    build()
+    from paper_2403_11367_gb300 import reloc as R
+    import scenegen as sg
+
+    g, cam, hidden, seeds = make_workload(rank)
+    ctx = R.Context(R.reloc_default_config(), device=local)
+    ctx.load_map(g)
+    V = GRID[0] * GRID[1] * GRID[2]
+    H, W = cam.height, cam.width
+    stream = torch.cuda.current_stream(dev)
+
+    # query images: rendered on the GPU at the hidden pose (+ seeded noise)
+    queries, seed_poses = [], []
+    n_runs = max(len(ctx.select_block(s_[0], s_[1], RADIUS)[0]) for s_ in seeds[:N_QUERIES])
+    for qi in range(N_QUERIES):
+        runs, _, _ = ctx.select_block(hidden[qi][0], hidden[qi][1], RADIUS)
+        img = torch.empty((1, 3, H, W), device=dev)
+        ctx.render(runs, sg.pose_from_xyz_yaw(*hidden[qi])[None], cam, rgb=img)
+        img = img[0] + torch.tensor(sg.image_noise(13 + qi, H, W), device=dev)
+        queries.append(img.contiguous())
+        seed_poses.append(sg.pose_from_xyz_yaw(*seeds[qi]))
+    brgb = torch.empty((3, H, W), device=dev)
+    bdep = torch.empty((H, W), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step(k):
+        res, _ = ctx.localize(queries[k % N_QUERIES], seed_poses[k % N_QUERIES], RADIUS, GRID, cam, brgb, bdep,
+                              stream=stream, want_scores=False)
+        return res
+
+    for k in range(args.warmup):
+        step(k)
+    ctx.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    best = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            res = step(k)
+            ev[k][1].record(stream)
+            launches += ctx.last_counts().kernel_launches
+            best.append(res.best_index)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    stage_ms, stage_calls = ctx.stage_times()
+    counts = ctx.last_counts()
+    ctx.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * V * args.steps / (total_ms / 1e3)
+
+    # e2e: the host-buffer entry point, pinned host query and winner buffers
+    qh = [q.cpu().pin_memory() for q in queries]
+    rgb_h = torch.empty((3, H, W), pin_memory=True)
+    dep_h = torch.empty((H, W), pin_memory=True)
+    for k in range(2):
+        ctx.localize_host(qh[k % N_QUERIES], seed_poses[k % N_QUERIES], RADIUS, GRID, cam, rgb_h, dep_h, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e2e_s = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        ctx.localize_host(qh[k % N_QUERIES], seed_poses[k % N_QUERIES], RADIUS, GRID, cam, rgb_h, dep_h,
+                          stream=stream)
+        e2e_s += time.perf_counter() - a
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    clocks = clk.summary()
+    blend_ms = stage_ms["blend"] / max(1, stage_calls["blend"])
+    # algorithmic work of the blend: included (pixel, Gaussian) pairs, counted
+    # exactly by the oracle for the same views (cpu_baseline leg below)
+    cpu_s, cores, ocounts, _, _ = oracle_sample(g, cam, hidden, seeds, 16, 0)
+    n_eval_per_view = float(ocounts[:, 2].mean())
+    flops = n_eval_per_view * V * FLOPS_PER_EVAL
+    sm_clock = clocks.get("sm_mhz") or 2070.0
+    peak = fp32_peak_tflops(2070.0)
+    achieved = flops / (blend_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded street scene standing in for KITTI-360)",
+        "config": {"workload": WORKLOAD, "queries": N_QUERIES, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas{world}"},
+        "queries_per_s": world * args.steps / (total_ms / 1e3),
+        "e2e": {"value": world * V * args.steps / e2e_s, "unit": UNIT,
+                # query image + candidate view parameters + block runs in; winner RGB + depth
+                # + per-view counts/scores + flags out
+                "h2d_bytes_per_step": 3 * H * W * 4 + 64 * V + 16 * (n_runs + 1),
+                "d2h_bytes_per_step": 4 * H * W * 4 + 20 * V + 24},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_blend", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                     "work": f"{n_eval_per_view:.4g} included pixel-Gaussian pairs/view x {V} views x "
+                             f"{FLOPS_PER_EVAL} flop (oracle count)",
+                     "launch_ms": blend_ms},
+        "stage_ms": {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()},
+        "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
+        "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},
+        "clocks": clocks,
+        "peaks": {"hbm_gbs": _peaks().get("hbm_gbs"), "bf16_tflops": _peaks().get("bf16_tflops")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

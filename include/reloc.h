@@ -1,0 +1,242 @@
+/*
+ * reloc.h -- C ABI of the GB300 relocalization hot path of 3DGS-ReLoc
+ * (arXiv 2403.11367): load a Gaussian map, pick the 2D-voxel block near a
+ * coarse pose, render RGB and depth of many candidate poses, score each
+ * against the query by normalised cross-correlation and return the best view
+ * with its depth (Sec. III-C.1, "Initial ReLocalization").
+ *
+ * Conventions (every call):
+ *   - A pose is a row-major 4x4 world-to-camera matrix W (the paper's W_t,
+ *     Sec. III-A) in double; camera axes are x right, y down, z forward.
+ *   - Images are planar float32 [C][H][W] (C = 3 for RGB), values in [0, 1].
+ *     Depth and accumulated alpha are float32 [H][W].
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; all
+ *     other pointers are host pointers owned by the caller.  The library owns
+ *     only its context, the device copy of the map and its workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that return host results synchronise that stream before
+ *     returning; reloc_render also synchronises (it checks workspace capacity).
+ *   - Every call returns a reloc_status; nothing aborts and no C++ exception
+ *     crosses the ABI.  On error, reloc_last_error() gives a message for the
+ *     calling thread.  The map and workspace stay valid after an error.
+ *   - Thread safety: a context is used by one host thread at a time.
+ */
+#ifndef RELOC_H
+#define RELOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int reloc_status;
+enum {
+    RELOC_OK = 0,
+    RELOC_EINVAL = 1,     /* bad argument (null pointer, size, config)          */
+    RELOC_ENOMEM = 2,     /* host or device allocation failed                   */
+    RELOC_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed        */
+    RELOC_ETIMEOUT = 4,   /* a bounded device wait gave up                      */
+    RELOC_ENOMAP = 5,     /* no map loaded                                      */
+    RELOC_ENUMERIC = 6,   /* non-finite pose or intrinsics                      */
+    RELOC_EOVERFLOW = 7   /* workspace capacity exceeded and could not grow     */
+};
+
+enum { RELOC_FP32 = 0, RELOC_FP16 = 1, RELOC_BF16 = 2 };   /* map attribute storage */
+
+/* Every constant of the path, explicit.  reloc_default_config() fills the
+ * values given in the comments. */
+typedef struct reloc_config {
+    int32_t tile_w, tile_h;    /* blend tile, pixels: 16 x 16 (8x8, 32x8 allowed)      */
+    float near_plane;          /* cull if camera depth <= near: 0.2 m                  */
+    float fov_clamp;           /* J uses tx/tz clamped to +-fov_clamp*tan(half FOV): 1.3 */
+    float eps2d;               /* low-pass dilation added to Sigma' diagonal: 0.3 px^2 */
+    float alpha_min;           /* skip a Gaussian at a pixel if alpha < this: 1/255    */
+    float alpha_max;           /* alpha clamp: 0.99                                    */
+    float t_min;               /* stop a pixel when T (1 - alpha) < this: 1e-4         */
+    float cut;                 /* footprint radius in sigmas (inclusion d'S^-1 d <= cut^2): 3 */
+    float det_fp64;            /* invert Sigma' in FP64 when its det < this: 1e-6 px^4 */
+    double block_size;         /* 2D voxel block edge: 20 m                            */
+    int64_t inst_capacity;     /* initial tile-instance capacity per view: 1<<20       */
+    int32_t reserved[8];
+} reloc_config;
+
+typedef struct reloc_camera {
+    int32_t width, height;     /* pixels (1 .. 16383)                                  */
+    double fx, fy, cx, cy;     /* pinhole intrinsics, pixels; pixel centres at +0.5    */
+} reloc_camera;
+
+/* Host map, one row per Gaussian g_i = [mu, S, R, c, o] (Sec. III-A). */
+typedef struct reloc_gaussians_host {
+    const float *mean;         /* [n][3] world position, metres                        */
+    const float *scale;        /* [n][3] activated standard deviations, metres (> 0)   */
+    const float *quat;         /* [n][4] rotation (w, x, y, z); normalised on use      */
+    const float *opacity;      /* [n]    in [0, 1]                                     */
+    const float *sh;           /* [n][K][3], K = (deg+1)^2; degree 0 = plain RGB       */
+} reloc_gaussians_host;
+
+/* A contiguous run [begin, end) of the block-ordered map (reloc_map_order). */
+typedef struct reloc_range { int64_t begin, end; } reloc_range;
+
+/* Candidate grid around a coarse pose (Sec. III-C.1; Sec. IV-A uses 2 m, 10 deg):
+ * offsets (dx, dy) in the world ground plane and a yaw about world z through
+ * the camera centre, all centred on zero; height, pitch and roll are the
+ * coarse pose's.  Candidate index = ix + nx * (iy + ny * iyaw). */
+typedef struct reloc_grid {
+    int32_t nx, ny, nyaw;
+    double step_xy;            /* metres  */
+    double step_yaw_deg;       /* degrees */
+} reloc_grid;
+
+typedef struct reloc_result {
+    int32_t best_index;        /* argmax of NCC, lowest index on ties (-1: none)       */
+    int32_t n_candidates;
+    double best_score;         /* NCC of the best candidate                            */
+    double best_pose[16];      /* its world-to-camera pose                             */
+    int64_t n_gauss;           /* Gaussians in the selected block subset               */
+    int32_t n_blocks;          /* blocks selected                                      */
+    int32_t degenerate;        /* 1 if the best render or the query has zero variance  */
+} reloc_result;
+
+/* Work counts of the last render/score/localize call (sums over views). */
+typedef struct reloc_counts {
+    int64_t n_views;
+    int64_t n_gauss;           /* subset size                                           */
+    int64_t n_visible;         /* (view, Gaussian) pairs that survived the cull         */
+    int64_t n_instances;       /* (view, tile, Gaussian) entries sorted                 */
+    int64_t inst_stride;       /* per-view instance capacity used                       */
+    int32_t retries;           /* capacity grow-and-retry rounds taken                  */
+    int32_t kernel_launches;   /* CUDA kernels the call launched (all attempts)         */
+} reloc_counts;
+
+/* Stage indices of reloc_stage_times(). */
+enum {
+    RELOC_STAGE_CULL = 0,      /* block subset gather (K1)                              */
+    RELOC_STAGE_PROJECT,       /* EWA projection + SH (K2)                              */
+    RELOC_STAGE_DEPTH_SORT,    /* visibility compaction + depth radix sort             */
+    RELOC_STAGE_EMIT,          /* scan of tile counts + tile|depth instance emission (K3) */
+    RELOC_STAGE_TILE_SORT,     /* stable tile radix sort (K4)                          */
+    RELOC_STAGE_RANGES,        /* tile ranges (K5)                                      */
+    RELOC_STAGE_BLEND,         /* blend + fused NCC partials (K6, K7 partials)          */
+    RELOC_STAGE_SCORE,         /* NCC finalise + argmax + winner export (K7, K8)        */
+    RELOC_STAGE_COUNT
+};
+
+typedef struct reloc_ctx reloc_ctx;
+
+/* Library version string (static storage). */
+const char *reloc_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *reloc_last_error(void);
+
+/* Fill cfg with the defaults listed in reloc_config. */
+void reloc_default_config(reloc_config *cfg);
+
+/* Create a context on CUDA device `device` (that device becomes current for
+ * the calling thread).  cfg NULL = defaults.  Errors: EINVAL (bad config:
+ * tile sizes not in {8,16,32}x{8,16,32} or tile_w*tile_h > 512, non-positive
+ * constants), ECUDA (no such device), ENOMEM. */
+reloc_status reloc_create(const reloc_config *cfg, int device, reloc_ctx **out);
+
+/* Free the context and all device memory it owns.  NULL is a no-op. */
+reloc_status reloc_destroy(reloc_ctx *ctx);
+
+/* Load (or replace) the map: partition into 2D voxel blocks of
+ * cfg.block_size (Sec. III-B.2: block = (floor(x/B), floor(y/B)); the map is
+ * reordered by block key (bx, by), index order inside a block), build the
+ * KD-tree over block centres, and copy the attributes to the device as SoA
+ * in `precision` (RELOC_FP32, RELOC_FP16 or RELOC_BF16 for scale, rotation,
+ * opacity and SH; means stay FP32).  sh_degree in 0..3.  The host arrays are
+ * read during the call only.  Errors: EINVAL, ENOMEM, ECUDA. */
+reloc_status reloc_load_map(reloc_ctx *ctx, const reloc_gaussians_host *g, int64_t n,
+                            int sh_degree, int precision);
+
+/* Block order: order_out[p] = original index of the Gaussian at block-ordered
+ * position p (n entries, host).  Errors: ENOMAP, EINVAL. */
+reloc_status reloc_map_order(reloc_ctx *ctx, int64_t *order_out);
+
+/* Select every block whose centre lies within `radius` metres of (x, y)
+ * (Sec. III-C.1, submap retrieval; KD-tree range query, Sec. III-B.2).  Writes
+ * up to max_ranges merged runs of the block-ordered map in ascending block-key
+ * order to ranges_out (host), their number to *n_ranges, the Gaussian count
+ * to *n_gauss and the block count to *n_blocks (any of the three may be
+ * NULL).  EINVAL if more than max_ranges runs are needed (*n_ranges then
+ * holds the number needed). */
+reloc_status reloc_select_block(reloc_ctx *ctx, double x, double y, double radius,
+                                reloc_range *ranges_out, int max_ranges, int *n_ranges,
+                                int64_t *n_gauss, int *n_blocks);
+
+/* Render n_views poses (host, [n_views][16]) of the subset given by `ranges`
+ * (host, n_ranges runs; the subset's Gaussian order -- the tie order of equal
+ * depths -- is the concatenation of the runs).  Writes, for each view v,
+ * rgb_dev[v][3][H][W], depth_dev[v][H][W] (Sec. III-A depth compositing,
+ * unnormalised) and alpha_dev[v][H][W] = 1 - T; any of the three may be NULL.
+ * 1 <= n_views <= 4096.  Errors: EINVAL, ENOMAP, ENUMERIC, ECUDA, EOVERFLOW. */
+reloc_status reloc_render(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                          const double *poses, int n_views, const reloc_camera *cam,
+                          float *rgb_dev, float *depth_dev, float *alpha_dev, void *stream);
+
+/* Render as reloc_render and score each view against query_dev ([3][H][W],
+ * device) with NCC (Eq. ncc) over all 3*H*W samples; writes scores_host
+ * [n_views] (NCC, 0 for a zero-variance image) and, if not NULL,
+ * degenerate_host[n_views] (1 = zero variance).  Images are not exported. */
+reloc_status reloc_score(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                         const double *poses, int n_views, const reloc_camera *cam,
+                         const float *query_dev, double *scores_host, int *degenerate_host,
+                         void *stream);
+
+/* The whole initial relocalization of one query (Sec. III-C.1): select the
+ * blocks within `radius` of the coarse pose's camera centre, build the
+ * candidate grid around the coarse pose, render every candidate, score it
+ * against query_dev by NCC, take the argmax (lowest index on ties) and export
+ * the winner's RGB [3][H][W], depth [H][W] and alpha [H][W] to the *_dev
+ * buffers (each may be NULL).  scores_host[n_candidates] may be NULL.
+ * Errors: EINVAL, ENOMAP, ENUMERIC, ECUDA, EOVERFLOW. */
+reloc_status reloc_localize(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose,
+                            double radius, const reloc_grid *grid, const reloc_camera *cam,
+                            reloc_result *out, double *scores_host, float *best_rgb_dev,
+                            float *best_depth_dev, float *best_alpha_dev, void *stream);
+
+/* reloc_localize for callers holding HOST buffers: copies query_host
+ * ([3][H][W]) to the device and the winner's RGB/depth back to best_rgb_host
+ * ([3][H][W]) and best_depth_host ([H][W]) (either may be NULL), through the
+ * context's own device buffers, on `stream`.  Pinned host memory makes the
+ * copies asynchronous. */
+reloc_status reloc_localize_host(reloc_ctx *ctx, const float *query_host, const double *coarse_pose,
+                                 double radius, const reloc_grid *grid, const reloc_camera *cam,
+                                 reloc_result *out, float *best_rgb_host, float *best_depth_host,
+                                 void *stream);
+
+/* Work counts of the last render/score/localize call. */
+reloc_status reloc_last_counts(reloc_ctx *ctx, reloc_counts *out);
+
+/* Stage timing with CUDA events on the call's stream: enable (1) or disable
+ * (0) and reset the accumulators.  reloc_stage_times writes, for each stage
+ * s < RELOC_STAGE_COUNT, the accumulated milliseconds ms_out[s] and the
+ * number of timed calls calls_out[s] since the last reset (either may be NULL). */
+reloc_status reloc_set_profiling(reloc_ctx *ctx, int enabled);
+reloc_status reloc_stage_times(reloc_ctx *ctx, double *ms_out, int64_t *calls_out);
+
+/* Copy intermediate results of the LAST render/score/localize call, for
+ * parity checks (device pointers, any may be NULL; sizes from reloc_last_counts):
+ *   records_dev [n_views][n_gauss][12] float: u, v, depth, opacity,
+ *                conic a, b, c, 0, red, green, blue, 0   (valid where visible)
+ *   rects_dev   [n_views][n_gauss][4] int32: tile rectangle tx0, ty0, tx1, ty1
+ *                inclusive; all -1 where not visible
+ *   inst_tiles_dev / inst_gauss_dev [n_views][inst_stride] uint32: the sorted
+ *                tile list of each view (tile id, Gaussian subset index);
+ *                entries past the view's count are undefined
+ *   inst_count_host [n_views] int64: instances per view
+ *   ranges_dev  [n_views][n_tiles][2] int32: [begin, end) of each tile in the
+ *                view's sorted list (relative to the view), empty = [0, 0).
+ * Synchronises `stream`. */
+reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rects_dev,
+                                uint32_t *inst_tiles_dev, uint32_t *inst_gauss_dev,
+                                int64_t *inst_count_host, int32_t *ranges_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RELOC_H */

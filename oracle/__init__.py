@@ -58,7 +58,7 @@ def lib():
             L.or_quat_to_rot.argtypes = [dp, dp]
             L.or_sh_basis.argtypes = [C.c_int, dp, dp]
             L.or_project.argtypes = [fp, fp, fp, fp, fp, C.c_int, C.c_int64, dp, dp, dp, dp]
-            L.or_render.argtypes = [dp, C.c_int64, dp, dp, dp, dp, dp, u8p, C.c_int]
+            L.or_render.argtypes = [dp, C.c_int64, dp, dp, dp, dp, dp, u8p, dp, C.c_int]
             L.or_render.restype = C.c_int64
             L.or_ncc.argtypes = [dp, dp, C.c_int64, C.POINTER(C.c_int)]
             L.or_ncc.restype = C.c_double
@@ -76,7 +76,7 @@ def lib():
             L.or_stable_sort_u64.argtypes = [u64p, u32p, C.c_int64]
             L.or_insertion_sort_u64.argtypes = [u64p, u32p, C.c_int64]
             L.or_render_views.argtypes = [fp, fp, fp, fp, fp, C.c_int, C.c_int64, dp, C.c_int, dp, dp,
-                                          dp, dp, C.POINTER(C.c_int), dp, dp, dp, u8p, i64p]
+                                          dp, dp, C.POINTER(C.c_int), dp, dp, dp, u8p, dp, i64p]
             _lib = L
     return _lib
 
@@ -95,9 +95,10 @@ def _c(a, dt):
 
 DEFAULT_PARAMS = dict(near=0.2, fov_clamp=1.3, eps2d=0.3, alpha_min=1.0 / 255.0, alpha_max=0.99,
                       t_min=1e-4, cut=3.0, tile_w=16, tile_h=16,
-                      flag_power=1e-4, flag_alpha=1e-4, flag_t=1e-3, flag_depth=1e-6)
+                      flag_power=1e-5, flag_alpha=1e-5, flag_t=1e-3, flag_depth=1e-6, flag_sig=1e-5,
+                      flag_pos=2e-4)
 _PORDER = ["near", "fov_clamp", "eps2d", "alpha_min", "alpha_max", "t_min", "cut", "tile_w", "tile_h",
-           "flag_power", "flag_alpha", "flag_t", "flag_depth"]
+           "flag_power", "flag_alpha", "flag_t", "flag_depth", "flag_sig", "flag_pos"]
 
 
 def params(**over) -> np.ndarray:
@@ -151,16 +152,18 @@ def project(g, pose, cam, prm=None) -> np.ndarray:
 
 def render_records(recs, cam, prm=None, brute=False):
     """Composite projected records (index order = tie order).
-    Returns dict(rgb (3,H,W), depth (H,W), alpha (H,W), flags (H,W) u8, n_eval)."""
+    Returns dict(rgb (3,H,W), depth (H,W), alpha (H,W), flags (H,W) u8,
+    bound (H,W): first-order bound of what a flagged decision can move, n_eval)."""
     prm = params() if prm is None else prm
     recs = _c(recs, np.float64)
     H, W = cam.height, cam.width
     rgb = np.zeros((3, H, W)); depth = np.zeros((H, W)); alpha = np.zeros((H, W))
     flags = np.zeros((H, W), np.uint8)
+    bound = np.zeros((H, W))
     ne = lib().or_render(_p(recs, C.c_double), recs.shape[0], _p(camvec(cam), C.c_double),
                          _p(_c(prm, np.float64), C.c_double), _p(rgb, C.c_double), _p(depth, C.c_double),
-                         _p(alpha, C.c_double), _p(flags, C.c_uint8), 1 if brute else 0)
-    return dict(rgb=rgb, depth=depth, alpha=alpha, flags=flags, n_eval=int(ne))
+                         _p(alpha, C.c_double), _p(flags, C.c_uint8), _p(bound, C.c_double), 1 if brute else 0)
+    return dict(rgb=rgb, depth=depth, alpha=alpha, flags=flags, bound=bound, n_eval=int(ne))
 
 
 def render(g, pose, cam, prm=None, brute=False):
@@ -181,6 +184,7 @@ def render_views(g, poses, cam, prm=None, query=None, images=True, flags=True):
         out["rgb"] = np.zeros((V, 3, H, W)); out["depth"] = np.zeros((V, H, W)); out["alpha"] = np.zeros((V, H, W))
     if flags:
         out["flags"] = np.zeros((V, H, W), np.uint8)
+        out["bound"] = np.zeros((V, H, W))
     qd = None
     if query is not None:
         qd = _c(query, np.float64).reshape(-1)
@@ -191,7 +195,8 @@ def render_views(g, poses, cam, prm=None, query=None, images=True, flags=True):
                           _p(qd, C.c_double), _p(out.get("scores"), C.c_double),
                           _p(out.get("degenerate"), C.c_int), _p(out.get("rgb"), C.c_double),
                           _p(out.get("depth"), C.c_double), _p(out.get("alpha"), C.c_double),
-                          _p(out.get("flags"), C.c_uint8), _p(out["counts"], C.c_int64))
+                          _p(out.get("flags"), C.c_uint8), _p(out.get("bound"), C.c_double),
+                          _p(out["counts"], C.c_int64))
     return out
 
 

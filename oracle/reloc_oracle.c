@@ -55,7 +55,7 @@
 enum {
     P_NEAR = 0, P_FOV_CLAMP, P_EPS2D, P_ALPHA_MIN, P_ALPHA_MAX, P_T_MIN, P_CUT,
     P_TILE_W, P_TILE_H,
-    P_FLAG_POWER, P_FLAG_ALPHA, P_FLAG_T, P_FLAG_DEPTH,
+    P_FLAG_POWER, P_FLAG_ALPHA, P_FLAG_T, P_FLAG_DEPTH, P_FLAG_SIG, P_FLAG_POS,
     P_COUNT = 16
 };
 
@@ -309,38 +309,80 @@ void or_insertion_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n)
 /* Front-to-back compositing of RGB and depth (Sec. III-A).                   */
 /* recs: projected records of n Gaussians (index order = tie order).          */
 /* brute != 0: every pixel tests every visible Gaussian (pins the splat form). */
-/* flags bit 1: footprint boundary, 2: alpha-skip boundary, 4: stop boundary, */
-/*       8: depth near-tie between consecutive contributors.                  */
+/*                                                                            */
+/* Flags mark pixels where an FP32 evaluation may take a different branch     */
+/* than this FP64 one AND the branch matters.  A decision taken the other way */
+/* at a footprint or alpha-skip edge moves the pixel by at most ~2 alpha T;   */
+/* swapping two consecutive contributors of near-equal depth moves colour by  */
+/* T_prev alpha_prev alpha |c - c_prev| (depth and alpha are unchanged); so a */
+/* band hit is flagged only when that effect reaches P_FLAG_SIG.  The band   */
+/* of the footprint test is P_FLAG_POWER |lim| plus the change of the power   */
+/* under a shift of P_FLAG_POS pixels of the projected mean (its gradient).   */
+/*   bit 1: footprint boundary, 2: alpha-skip boundary, 4: stop boundary,     */
+/*   8: depth near-tie between consecutive contributors (or the stopper).     */
 /* ========================================================================= */
-typedef struct { double T, r, g, b, d; double last_z; int done, any; } pix_state;
+typedef struct {
+    double T, r, g, b, d;
+    double last_z, last_T, last_a, last_c[3];
+    int done, any;
+} pix_state;
 
 static inline void composite(pix_state *s, const double *rc, double px, double py,
-                             const double *p, uint8_t *flag, int64_t *n_eval)
+                             const double *p, uint8_t *flag, double *bnd, int64_t *n_eval)
 {
     if (s->done) return;
     double dx = px - rc[R_U], dy = py - rc[R_V];
     double power = -0.5 * (rc[R_CON_A] * dx * dx + rc[R_CON_C] * dy * dy) - rc[R_CON_B] * dx * dy;
     double lim = -0.5 * p[P_CUT] * p[P_CUT];
-    if (fabs(power - lim) <= p[P_FLAG_POWER] * fabs(lim)) *flag |= 1;
+    const double sig = p[P_FLAG_SIG];
+    const double gx = rc[R_CON_A] * dx + rc[R_CON_B] * dy, gy = rc[R_CON_B] * dx + rc[R_CON_C] * dy;
+    const double band = p[P_FLAG_POWER] * fabs(lim) + p[P_FLAG_POS] * (fabs(gx) + fabs(gy));
+    if (fabs(power - lim) <= band) {
+        /* including or dropping this Gaussian moves the pixel by <= 2 alpha T */
+        double e = 2 * s->T * fmin(p[P_ALPHA_MAX], rc[R_OPACITY] * exp(power));
+        if (e >= sig) { *flag |= 1; *bnd += e; }
+    }
     if (power < lim) return;
     (*n_eval)++;
     double raw = rc[R_OPACITY] * exp(power);
     double alpha = raw < p[P_ALPHA_MAX] ? raw : p[P_ALPHA_MAX];
-    if (fabs(raw - p[P_ALPHA_MIN]) <= p[P_FLAG_ALPHA] * p[P_ALPHA_MIN]) *flag |= 2;
+    if (fabs(raw - p[P_ALPHA_MIN]) <= (p[P_FLAG_ALPHA] + band) * p[P_ALPHA_MIN]) {
+        double e = 2 * s->T * raw;
+        if (e >= sig) { *flag |= 2; *bnd += e; }
+    }
     if (alpha < p[P_ALPHA_MIN]) return;
     double tn = s->T * (1 - alpha);
-    if (fabs(tn - p[P_T_MIN]) <= p[P_FLAG_T] * p[P_T_MIN]) *flag |= 4;
-    if (tn < p[P_T_MIN]) { s->done = 1; return; }
+    /* stopping one Gaussian earlier or later moves the pixel by <= T */
+    if (fabs(tn - p[P_T_MIN]) <= p[P_FLAG_T] * p[P_T_MIN]) { *flag |= 4; *bnd += s->T; }
     double z = rc[R_DEPTH];
-    if (s->any && fabs(z - s->last_z) <= p[P_FLAG_DEPTH] * fabs(z)) *flag |= 8;
+    const double col[3] = {rc[R_RED], rc[R_GREEN], rc[R_BLUE]};
+    int tie = s->any && fabs(z - s->last_z) <= p[P_FLAG_DEPTH] * fabs(z);
+    if (tn < p[P_T_MIN]) {
+        if (tie) {
+            double e = 2 * s->last_T * fmax(s->last_a, alpha);
+            if (e >= sig) { *flag |= 8; *bnd += e; }
+        }
+        s->done = 1;
+        return;
+    }
+    if (tie) {
+        /* swapping two consecutive contributors changes colour by exactly
+           T_prev alpha_prev alpha (c - c_prev); T afterwards is unchanged */
+        double dc = 0;
+        for (int k = 0; k < 3; ++k) dc = fmax(dc, fabs(col[k] - s->last_c[k]));
+        double e = s->last_T * s->last_a * alpha * dc;
+        if (e >= sig) { *flag |= 8; *bnd += e; }
+    }
     double w = alpha * s->T;
-    s->r += rc[R_RED] * w; s->g += rc[R_GREEN] * w; s->b += rc[R_BLUE] * w;
+    s->r += col[0] * w; s->g += col[1] * w; s->b += col[2] * w;
     s->d += z * w;
+    s->last_T = s->T; s->last_a = alpha;
+    s->last_c[0] = col[0]; s->last_c[1] = col[1]; s->last_c[2] = col[2];
     s->T = tn; s->last_z = z; s->any = 1;
 }
 
 int64_t or_render(const double *recs, int64_t n, const double *cam, const double *p,
-                  double *rgb, double *depth, double *alpha, uint8_t *flags, int brute)
+                  double *rgb, double *depth, double *alpha, uint8_t *flags, double *bound, int brute)
 {
     const int W = (int)cam[C_W], H = (int)cam[C_H];
     const int64_t npx = (int64_t)W * H;
@@ -358,6 +400,7 @@ int64_t or_render(const double *recs, int64_t n, const double *cam, const double
 
     pix_state *st = (pix_state *)calloc(npx, sizeof(pix_state));
     uint8_t *fl = (uint8_t *)calloc(npx, 1);
+    double *bd = (double *)calloc(npx, sizeof(double));
     for (int64_t q = 0; q < npx; ++q) st[q].T = 1;
     int64_t n_eval = 0;
     if (brute) {
@@ -365,7 +408,7 @@ int64_t or_render(const double *recs, int64_t n, const double *cam, const double
             for (int x = 0; x < W; ++x)
                 for (int64_t j = 0; j < nvis; ++j)
                     composite(&st[(int64_t)y * W + x], recs + OR_REC * order[j], x + 0.5, y + 0.5, p,
-                              &fl[(int64_t)y * W + x], &n_eval);
+                              &fl[(int64_t)y * W + x], &bd[(int64_t)y * W + x], &n_eval);
     } else {
         for (int64_t j = 0; j < nvis; ++j) {
             const double *rc = recs + OR_REC * order[j];
@@ -377,7 +420,7 @@ int64_t or_render(const double *recs, int64_t n, const double *cam, const double
             for (int y = y0; y <= y1; ++y)
                 for (int x = x0; x <= x1; ++x)
                     composite(&st[(int64_t)y * W + x], rc, x + 0.5, y + 0.5, p,
-                              &fl[(int64_t)y * W + x], &n_eval);
+                              &fl[(int64_t)y * W + x], &bd[(int64_t)y * W + x], &n_eval);
         }
     }
     for (int64_t q = 0; q < npx; ++q) {
@@ -385,8 +428,9 @@ int64_t or_render(const double *recs, int64_t n, const double *cam, const double
         if (depth) depth[q] = st[q].d;
         if (alpha) alpha[q] = 1 - st[q].T;
         if (flags) flags[q] = fl[q];
+        if (bound) bound[q] = bd[q];
     }
-    free(st); free(fl); free(order); free(tmp); free(zkey);
+    free(st); free(fl); free(bd); free(order); free(tmp); free(zkey);
     return n_eval;
 }
 
@@ -560,7 +604,7 @@ void or_render_views(const float *means, const float *scales, const float *quats
                      const float *sh, int sh_deg, int64_t n, const double *poses, int n_views,
                      const double *cam, const double *p, const double *query,
                      double *scores, int *degenerate, double *rgb, double *depth, double *alpha,
-                     uint8_t *flags, int64_t *counts)
+                     uint8_t *flags, double *bound, int64_t *counts)
 {
     const int W = (int)cam[C_W], H = (int)cam[C_H];
     const int64_t npx = (int64_t)W * H;
@@ -570,7 +614,8 @@ void or_render_views(const float *means, const float *scales, const float *quats
         or_project(means, scales, quats, opac, sh, sh_deg, n, poses + 16 * v, cam, p, recs);
         double *img = rgb ? rgb + 3 * npx * v : (double *)malloc(sizeof(double) * 3 * npx);
         int64_t ne = or_render(recs, n, cam, p, img, depth ? depth + npx * v : NULL,
-                               alpha ? alpha + npx * v : NULL, flags ? flags + npx * v : NULL, 0);
+                               alpha ? alpha + npx * v : NULL, flags ? flags + npx * v : NULL,
+                               bound ? bound + npx * v : NULL, 0);
         if (counts) {
             int64_t nv = 0, ni = 0;
             for (int64_t i = 0; i < n; ++i) {

@@ -1,0 +1,270 @@
+// project.cu -- K1 block-subset gather and K2 EWA projection + SH colour.
+//
+// K2 follows Sec. III-A of 3DGS-ReLoc: t = W mu (world-to-camera), pinhole
+// projection m(mu) (Eq. proj), footprint covariance Sigma' = J W Sigma W^T J^T
+// (Eq. foot_conv) with Sigma = R S S^T R^T, and the colour c_i (plain RGB, or
+// real SH evaluated along the viewing ray).  One thread owns one Gaussian: it
+// loads the attributes once (coalesced SoA loads) and projects them into every
+// candidate view, so the map bytes are read once per call however many
+// candidates there are.
+#include "internal.cuh"
+
+namespace reloc {
+
+// ---------------------------------------------------------------- K1 ------
+
+__global__ void k_gather_subset(const int64_t *__restrict__ run_begin, const int64_t *__restrict__ run_off,
+                                int n_runs, int64_t S, uint32_t *__restrict__ gidx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    int lo = 0, hi = n_runs - 1;             // last run with run_off[r] <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (run_off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    gidx[i] = (uint32_t)(run_begin[lo] + (i - run_off[lo]));
+}
+
+cudaError_t launch_gather_subset(const int64_t *run_begin, const int64_t *run_off, int n_runs, int64_t S,
+                                 uint32_t *gidx, cudaStream_t st)
+{
+    if (S <= 0) return cudaSuccess;
+    k_gather_subset<<<(unsigned)ceil_div(S, 256), 256, 0, st>>>(run_begin, run_off, n_runs, S, gidx);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- K2 ------
+
+template <typename T> __device__ __forceinline__ float ldattr(const T *p);
+template <> __device__ __forceinline__ float ldattr<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldattr<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float ldattr<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+// Real orthonormal SH basis (Condon-Shortley phase) up to degree DEG for a
+// unit direction, as explicit polynomials; normalisation constants are
+// sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) (times sqrt 2 for m != 0) folded with the
+// polynomial coefficients.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
+{
+    Y[0] = 0.28209479177387814f;
+    if (DEG >= 1) {
+        Y[1] = -0.48860251190291987f * y;
+        Y[2] = 0.48860251190291987f * z;
+        Y[3] = -0.48860251190291987f * x;
+    }
+    if (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -0.5900435899266435f * y * (3.f * xx - yy);
+            Y[10] = 2.890611442640554f * x * y * z;
+            Y[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);
+            Y[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);
+            Y[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+constexpr int PROJ_THREADS = 128;
+constexpr int PROJ_VIEW_BATCH = 128;
+
+template <typename T, int DEG>
+__global__ void __launch_bounds__(PROJ_THREADS)
+k_project(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
+          const T *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, int64_t S,
+          const ViewParams *__restrict__ views, int V, CamParams cam, float4 *__restrict__ rec,
+          uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles, uint32_t *__restrict__ dkey)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ ViewParams s_view[PROJ_VIEW_BATCH];
+
+    const int64_t i = (int64_t)blockIdx.x * PROJ_THREADS + threadIdx.x;
+    const bool active = i < S;
+
+    // ---- per-Gaussian quantities, loaded and formed once ------------------
+    float mu0 = 0, mu1 = 0, mu2 = 0, opac = 0;
+    float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
+    float sh[3 * K];
+    if (active) {
+        const int64_t g = gidx[i];
+        mu0 = __ldg(mx + g); mu1 = __ldg(my + g); mu2 = __ldg(mz + g);
+        float s0 = ldattr(attr + (ATTR_SCALE + 0) * n_map + g);
+        float s1 = ldattr(attr + (ATTR_SCALE + 1) * n_map + g);
+        float s2 = ldattr(attr + (ATTR_SCALE + 2) * n_map + g);
+        float qw = ldattr(attr + (ATTR_QUAT + 0) * n_map + g);
+        float qx = ldattr(attr + (ATTR_QUAT + 1) * n_map + g);
+        float qy = ldattr(attr + (ATTR_QUAT + 2) * n_map + g);
+        float qz = ldattr(attr + (ATTR_QUAT + 3) * n_map + g);
+        opac = ldattr(attr + ATTR_OPAC * n_map + g);
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) sh[k] = ldattr(attr + (int64_t)(ATTR_SH + k) * n_map + g);
+        // rotation from the normalised quaternion
+        float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
+        float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
+        float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
+        // M = R S, Sigma = M M^T
+        float m00 = r00 * s0, m01 = r01 * s1, m02 = r02 * s2;
+        float m10 = r10 * s0, m11 = r11 * s1, m12 = r12 * s2;
+        float m20 = r20 * s0, m21 = r21 * s1, m22 = r22 * s2;
+        S00 = m00 * m00 + m01 * m01 + m02 * m02;
+        S01 = m00 * m10 + m01 * m11 + m02 * m12;
+        S02 = m00 * m20 + m01 * m21 + m02 * m22;
+        S11 = m10 * m10 + m11 * m11 + m12 * m12;
+        S12 = m10 * m20 + m11 * m21 + m12 * m22;
+        S22 = m20 * m20 + m21 * m21 + m22 * m22;
+    }
+    const float cut2 = cam.cut;
+    const float inv_tw = 1.0f / cam.tile_w, inv_th = 1.0f / cam.tile_h;
+
+    for (int vb = 0; vb < V; vb += PROJ_VIEW_BATCH) {
+        const int nb = min(PROJ_VIEW_BATCH, V - vb);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nb * 16; k += PROJ_THREADS)
+            reinterpret_cast<float *>(s_view)[k] = reinterpret_cast<const float *>(views + vb)[k];
+        __syncthreads();
+        if (!active) continue;
+        for (int vv = 0; vv < nb; ++vv) {
+            const ViewParams &P = s_view[vv];
+            const int v = vb + vv;
+            const int64_t o = (int64_t)v * S + i;
+            // camera-space position t = R (mu - c)
+            float d0 = (mu0 - P.c_hi[0]) - P.c_lo[0];
+            float d1 = (mu1 - P.c_hi[1]) - P.c_lo[1];
+            float d2 = (mu2 - P.c_hi[2]) - P.c_lo[2];
+            float tx = P.R[0] * d0 + P.R[1] * d1 + P.R[2] * d2;
+            float ty = P.R[3] * d0 + P.R[4] * d1 + P.R[5] * d2;
+            float tz = P.R[6] * d0 + P.R[7] * d1 + P.R[8] * d2;
+            uint32_t nt = 0;
+            uint2 rc = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+            if (tz > cam.near_plane) {
+                // Jacobian of the projection (FOV clamp in J only)
+                float xz = fminf(fmaxf(tx / tz, -cam.limx), cam.limx);
+                float yz = fminf(fmaxf(ty / tz, -cam.limy), cam.limy);
+                float j00 = cam.fx / tz, j02 = -cam.fx * xz / tz;
+                float j11 = cam.fy / tz, j12 = -cam.fy * yz / tz;
+                // T = J R_w (2x3)
+                float t00 = j00 * P.R[0] + j02 * P.R[6], t01 = j00 * P.R[1] + j02 * P.R[7], t02 = j00 * P.R[2] + j02 * P.R[8];
+                float t10 = j11 * P.R[3] + j12 * P.R[6], t11 = j11 * P.R[4] + j12 * P.R[7], t12 = j11 * P.R[5] + j12 * P.R[8];
+                // Sigma' = T Sigma T^T
+                float u0 = t00 * S00 + t01 * S01 + t02 * S02;
+                float u1 = t00 * S01 + t01 * S11 + t02 * S12;
+                float u2 = t00 * S02 + t01 * S12 + t02 * S22;
+                float w0 = t10 * S00 + t11 * S01 + t12 * S02;
+                float w1 = t10 * S01 + t11 * S11 + t12 * S12;
+                float w2 = t10 * S02 + t11 * S12 + t12 * S22;
+                float ca = u0 * t00 + u1 * t01 + u2 * t02 + cam.eps2d;
+                float cb = u0 * t10 + u1 * t11 + u2 * t12;
+                float cc = w0 * t10 + w1 * t11 + w2 * t12 + cam.eps2d;
+                float det = ca * cc - cb * cb;
+                float ia, ib, ic;
+                bool ok;
+                if (det < cam.det_fp64) {
+                    // near-degenerate footprint: form Sigma' and its inverse in FP64
+                    double T0[3] = {(double)t00, (double)t01, (double)t02};
+                    double T1[3] = {(double)t10, (double)t11, (double)t12};
+                    double Sg[9] = {S00, S01, S02, S01, S11, S12, S02, S12, S22};
+                    double A = 0, B = 0, Cc = 0;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            A += T0[r] * Sg[3 * r + c] * T0[c];
+                            B += T0[r] * Sg[3 * r + c] * T1[c];
+                            Cc += T1[r] * Sg[3 * r + c] * T1[c];
+                        }
+                    A += cam.eps2d; Cc += cam.eps2d;
+                    double dd = A * Cc - B * B;
+                    ok = dd > 0;
+                    ia = (float)(Cc / dd); ib = (float)(-B / dd); ic = (float)(A / dd);
+                    ca = (float)A; cc = (float)Cc;
+                } else {
+                    ok = det > 0;
+                    ia = cc / det; ib = -cb / det; ic = ca / det;
+                }
+                if (ok) {
+                    float u = cam.fx * tx / tz + cam.cx;
+                    float vpx = cam.fy * ty / tz + cam.cy;
+                    float rx = cut2 * sqrtf(ca), ry = cut2 * sqrtf(cc);
+                    float xlo = u - rx, xhi = u + rx, ylo = vpx - ry, yhi = vpx + ry;
+                    if (!(xhi < 0.f || xlo >= (float)cam.width || yhi < 0.f || ylo >= (float)cam.height)) {
+                        int x0 = max(0, (int)floorf(xlo * inv_tw));
+                        int x1 = min(cam.ntx - 1, (int)floorf(xhi * inv_tw));
+                        int y0 = max(0, (int)floorf(ylo * inv_th));
+                        int y1 = min(cam.nty - 1, (int)floorf(yhi * inv_th));
+                        nt = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+                        rc = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+                        float cr, cg, cbl;
+                        if (DEG == 0) {
+                            cr = sh[0]; cg = sh[1]; cbl = sh[2];
+                        } else {
+                            float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                            float Y[K];
+                            sh_basis<DEG>(d0 * inv, d1 * inv, d2 * inv, Y);
+                            cr = 0.5f; cg = 0.5f; cbl = 0.5f;
+#pragma unroll
+                            for (int k = 0; k < K; ++k) {
+                                cr += sh[3 * k] * Y[k];
+                                cg += sh[3 * k + 1] * Y[k];
+                                cbl += sh[3 * k + 2] * Y[k];
+                            }
+                            cr = fmaxf(cr, 0.f); cg = fmaxf(cg, 0.f); cbl = fmaxf(cbl, 0.f);
+                        }
+                        float4 *rp = rec + 3 * o;
+                        rp[0] = make_float4(u, vpx, tz, opac);
+                        rp[1] = make_float4(ia, ib, ic, 0.f);
+                        rp[2] = make_float4(cr, cg, cbl, 0.f);
+                    }
+                }
+            }
+            rect[o] = rc;
+            ntiles[o] = nt;
+            dkey[o] = nt ? __float_as_uint(tz) : 0xFFFFFFFFu;
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t project_t(const float *mx, const float *my, const float *mz, const T *attr, int sh_degree,
+                             int64_t n_map, const uint32_t *gidx, int64_t S, const ViewParams *views, int V,
+                             const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles, uint32_t *dkey,
+                             cudaStream_t st)
+{
+    dim3 grid((unsigned)ceil_div(S, PROJ_THREADS));
+    switch (sh_degree) {
+    case 0: k_project<T, 0><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
+    case 1: k_project<T, 1><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
+    case 2: k_project<T, 2><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
+    case 3: k_project<T, 3><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const float *mx, const float *my, const float *mz, const void *attr, int precision,
+                           int sh_degree, int64_t n_map, const uint32_t *gidx, int64_t S, const ViewParams *views,
+                           int V, const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles,
+                           uint32_t *dkey, cudaStream_t st)
+{
+    if (S <= 0) return cudaSuccess;
+    switch (precision) {
+    case 0: return project_t(mx, my, mz, (const float *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
+    case 1: return project_t(mx, my, mz, (const __half *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
+    case 2: return project_t(mx, my, mz, (const __nv_bfloat16 *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace reloc

@@ -1,0 +1,277 @@
+"""Python binding of the C ABI in include/reloc.h (ctypes; marshalling only).
+
+Every function here forwards to the CUDA library ``_lib/libreloc.so``.
+There is no fallback: if the library is missing or fails to load, importing
+this module raises.  Device buffers are passed as torch CUDA tensors (their
+data pointers) and the stream as torch's current stream handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libreloc.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOMAP, ENUMERIC, EOVERFLOW = range(8)
+FP32, FP16, BF16 = 0, 1, 2
+STAGES = ["cull", "project", "depth_sort", "emit", "tile_sort", "ranges", "blend", "score"]
+
+
+class RelocError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"reloc status {status}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_plane", C.c_float),
+                ("fov_clamp", C.c_float), ("eps2d", C.c_float), ("alpha_min", C.c_float),
+                ("alpha_max", C.c_float), ("t_min", C.c_float), ("cut", C.c_float), ("det_fp64", C.c_float),
+                ("block_size", C.c_double), ("inst_capacity", C.c_int64), ("reserved", C.c_int32 * 8)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double)]
+
+
+class GaussiansHost(C.Structure):
+    _fields_ = [("mean", C.POINTER(C.c_float)), ("scale", C.POINTER(C.c_float)),
+                ("quat", C.POINTER(C.c_float)), ("opacity", C.POINTER(C.c_float)),
+                ("sh", C.POINTER(C.c_float))]
+
+
+class Range(C.Structure):
+    _fields_ = [("begin", C.c_int64), ("end", C.c_int64)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nyaw", C.c_int32), ("step_xy", C.c_double),
+                ("step_yaw_deg", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("best_index", C.c_int32), ("n_candidates", C.c_int32), ("best_score", C.c_double),
+                ("best_pose", C.c_double * 16), ("n_gauss", C.c_int64), ("n_blocks", C.c_int32),
+                ("degenerate", C.c_int32)]
+
+
+class Counts(C.Structure):
+    _fields_ = [("n_views", C.c_int64), ("n_gauss", C.c_int64), ("n_visible", C.c_int64),
+                ("n_instances", C.c_int64), ("inst_stride", C.c_int64), ("retries", C.c_int32),
+                ("kernel_launches", C.c_int32)]
+
+
+# exported symbols and their signatures (name -> (restype, argtypes))
+_vp, _dp, _fp, _ip, _i64p, _u32p, _i32p = (C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_uint32),
+                                           C.POINTER(C.c_int32))
+SIGNATURES = {
+    "reloc_version": (C.c_char_p, []),
+    "reloc_last_error": (C.c_char_p, []),
+    "reloc_default_config": (None, [C.POINTER(Config)]),
+    "reloc_create": (C.c_int, [C.POINTER(Config), C.c_int, C.POINTER(_vp)]),
+    "reloc_destroy": (C.c_int, [_vp]),
+    "reloc_load_map": (C.c_int, [_vp, C.POINTER(GaussiansHost), C.c_int64, C.c_int, C.c_int]),
+    "reloc_map_order": (C.c_int, [_vp, _i64p]),
+    "reloc_select_block": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.POINTER(Range), C.c_int, _ip,
+                                     _i64p, _ip]),
+    "reloc_render": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp, _vp, _vp,
+                               _vp]),
+    "reloc_score": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp, _dp, _ip,
+                              _vp]),
+    "reloc_localize": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera), C.POINTER(Result),
+                                 _dp, _vp, _vp, _vp, _vp]),
+    "reloc_localize_host": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera),
+                                      C.POINTER(Result), _vp, _vp, _vp]),
+    "reloc_last_counts": (C.c_int, [_vp, C.POINTER(Counts)]),
+    "reloc_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
+    "reloc_export_debug": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64p, _vp, _vp]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libreloc.so not built ({LIB_PATH}); run paper_2403_11367_gb300/build.py "
+                          "or __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != OK:
+        raise RelocError(status, lib.reloc_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _poses(poses):
+    p = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1, 16)
+    return p, p.ctypes.data_as(_dp), p.shape[0]
+
+
+def camera(cam) -> Camera:
+    return Camera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy))
+
+
+def reloc_version() -> str:
+    return lib.reloc_version().decode()
+
+
+def reloc_default_config(**over) -> Config:
+    cfg = Config()
+    lib.reloc_default_config(C.byref(cfg))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """Owns one reloc_ctx.  Method names follow the C ABI without the prefix."""
+
+    def __init__(self, cfg: Config | None = None, device: int = 0):
+        self._h = _vp()
+        _check(lib.reloc_create(C.byref(cfg) if cfg is not None else None, device, C.byref(self._h)))
+        self.n = 0
+
+    def close(self):
+        if self._h:
+            lib.reloc_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- map ------------------------------------------------------------------
+    def load_map(self, g, precision: int = FP32):
+        self._keep = [_f32(g.mean), _f32(g.scale), _f32(g.quat), _f32(g.opacity), _f32(g.sh)]
+        m, s, q, o, sh = self._keep
+        gh = GaussiansHost(*(a.ctypes.data_as(_fp) for a in (m, s, q, o, sh)))
+        _check(lib.reloc_load_map(self._h, C.byref(gh), g.n, g.sh_degree, precision))
+        self._keep = None
+        self.n = g.n
+
+    def map_order(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int64)
+        _check(lib.reloc_map_order(self._h, out.ctypes.data_as(_i64p)))
+        return out
+
+    def select_block(self, x, y, radius, max_ranges=4096):
+        rng = (Range * max_ranges)()
+        nr, ng, nb = C.c_int(0), C.c_int64(0), C.c_int(0)
+        _check(lib.reloc_select_block(self._h, x, y, radius, rng, max_ranges, C.byref(nr), C.byref(ng),
+                                      C.byref(nb)))
+        return [(rng[i].begin, rng[i].end) for i in range(nr.value)], int(ng.value), int(nb.value)
+
+    @staticmethod
+    def _ranges(ranges):
+        arr = (Range * max(1, len(ranges)))(*[Range(int(b), int(e)) for b, e in ranges])
+        return arr, len(ranges)
+
+    # -- hot path ---------------------------------------------------------------
+    def render(self, ranges, poses, cam, rgb=None, depth=None, alpha=None, stream=None):
+        ra, nr = self._ranges(ranges)
+        p, pp, V = _poses(poses)
+        c = camera(cam)
+        _check(lib.reloc_render(self._h, ra, nr, pp, V, C.byref(c), _ptr(rgb), _ptr(depth), _ptr(alpha),
+                                _stream(stream)))
+
+    def score(self, ranges, poses, cam, query, stream=None):
+        ra, nr = self._ranges(ranges)
+        p, pp, V = _poses(poses)
+        c = camera(cam)
+        sc = np.zeros(V)
+        dg = np.zeros(V, np.int32)
+        _check(lib.reloc_score(self._h, ra, nr, pp, V, C.byref(c), _ptr(query), sc.ctypes.data_as(_dp),
+                               dg.ctypes.data_as(_ip), _stream(stream)))
+        return sc, dg
+
+    def localize(self, query, coarse_pose, radius, grid, cam, best_rgb=None, best_depth=None, best_alpha=None,
+                 stream=None, want_scores=True):
+        cp = np.ascontiguousarray(coarse_pose, np.float64).reshape(16)
+        g = Grid(*grid) if not isinstance(grid, Grid) else grid
+        c = camera(cam)
+        res = Result()
+        V = g.nx * g.ny * g.nyaw
+        sc = np.zeros(V) if want_scores else None
+        _check(lib.reloc_localize(self._h, _ptr(query), cp.ctypes.data_as(_dp), radius, C.byref(g), C.byref(c),
+                                  C.byref(res), sc.ctypes.data_as(_dp) if sc is not None else None,
+                                  _ptr(best_rgb), _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
+        return res, sc
+
+    def localize_host(self, query_host, coarse_pose, radius, grid, cam, best_rgb_host=None, best_depth_host=None,
+                      stream=None):
+        """Host buffers: query_host / best_* are numpy float32 or pinned CPU torch tensors."""
+        cp = np.ascontiguousarray(coarse_pose, np.float64).reshape(16)
+        g = Grid(*grid) if not isinstance(grid, Grid) else grid
+        c = camera(cam)
+        res = Result()
+
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous():
+                    raise ValueError("host buffers must be contiguous CPU tensors")
+                return C.c_void_p(a.data_ptr())
+            if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be contiguous float32")
+            return C.c_void_p(a.ctypes.data)
+        _check(lib.reloc_localize_host(self._h, hp(query_host), cp.ctypes.data_as(_dp), radius, C.byref(g),
+                                       C.byref(c), C.byref(res), hp(best_rgb_host), hp(best_depth_host),
+                                       _stream(stream)))
+        return res
+
+    # -- introspection ------------------------------------------------------------
+    def last_counts(self) -> Counts:
+        c = Counts()
+        _check(lib.reloc_last_counts(self._h, C.byref(c)))
+        return c
+
+    def set_profiling(self, enabled: bool):
+        _check(lib.reloc_set_profiling(self._h, 1 if enabled else 0))
+
+    def stage_times(self):
+        ms = np.zeros(len(STAGES))
+        calls = np.zeros(len(STAGES), np.int64)
+        _check(lib.reloc_stage_times(self._h, ms.ctypes.data_as(_dp), calls.ctypes.data_as(_i64p)))
+        return dict(zip(STAGES, ms)), dict(zip(STAGES, calls))
+
+    def export_debug(self, records=None, rects=None, inst_tiles=None, inst_gauss=None, ranges=None, n_views=None,
+                     stream=None):
+        cnt = np.zeros(max(1, n_views or 1), np.int64)
+        _check(lib.reloc_export_debug(self._h, _ptr(records), _ptr(rects), _ptr(inst_tiles), _ptr(inst_gauss),
+                                      cnt.ctypes.data_as(_i64p), _ptr(ranges), _stream(stream)))
+        return cnt

@@ -1,0 +1,364 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded
+synthetic scenes.  Each test states its bar; the helpers in parity.py hold the
+tolerances and the bit-exact tile-list replay."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from parity import TOL_NCC, compare_images, replay_tile_lists, z_ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_11367_gb300.build import build
+    build()
+    from paper_2403_11367_gb300 import reloc
+    return reloc
+
+
+def make_ctx(R, g, precision=0, **cfg):
+    ctx = R.Context(R.reloc_default_config(**cfg))
+    ctx.load_map(g, precision)
+    return ctx
+
+
+def full_range(ctx):
+    return [(0, ctx.n)]
+
+
+def gpu_render(ctx, ranges, poses, cam):
+    V = len(poses)
+    dev = torch.device("cuda:0")
+    rgb = torch.empty((V, 3, cam.height, cam.width), device=dev)
+    depth = torch.empty((V, cam.height, cam.width), device=dev)
+    alpha = torch.empty((V, cam.height, cam.width), device=dev)
+    ctx.render(ranges, poses, cam, rgb, depth, alpha)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy().astype(np.float64), depth.cpu().numpy().astype(np.float64), \
+        alpha.cpu().numpy().astype(np.float64)
+
+
+def ordered(ctx, g):
+    """The map in the library's block order (the subset order the GPU uses)."""
+    return g.subset(ctx.map_order())
+
+
+def export(ctx, V, S, cam, tile=(16, 16)):
+    dev = torch.device("cuda:0")
+    c = ctx.last_counts()
+    rec = torch.empty((V, S, 12), device=dev)
+    rect = torch.empty((V, S, 4), dtype=torch.int32, device=dev)
+    it = torch.empty((V, c.inst_stride), dtype=torch.int32, device=dev)
+    ig = torch.empty((V, c.inst_stride), dtype=torch.int32, device=dev)
+    ntx = (cam.width + tile[0] - 1) // tile[0]
+    nty = (cam.height + tile[1] - 1) // tile[1]
+    rg = torch.empty((V, ntx * nty, 2), dtype=torch.int32, device=dev)
+    cnt = ctx.export_debug(rec, rect, it, ig, rg, n_views=V)
+    return (rec.cpu().numpy(), rect.cpu().numpy(), it.cpu().numpy().view(np.uint32),
+            ig.cpu().numpy().view(np.uint32), cnt, rg.cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return sg.tiny_scene()
+
+
+# ------------------------------------------------------------------ tiny ----
+
+def test_render_tiny_matches_oracle(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    g = ordered(ctx, tiny.gaussians)
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), tiny.candidate_poses, tiny.camera)
+    ref = oracle.render_views(g, tiny.candidate_poses, tiny.camera)
+    st = compare_images(rgb, depth, alpha, ref, z_ref(g, tiny.candidate_poses, tiny.camera))
+    print("tiny render", st)
+    assert st["flagged"] < 0.02
+    c = ctx.last_counts()
+    assert c.n_visible == ref["counts"][:, 0].sum()
+
+
+def test_tile_lists_bit_exact_tiny(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    V, S = len(tiny.candidate_poses), tiny.gaussians.n
+    gpu_render(ctx, full_range(ctx), tiny.candidate_poses, tiny.camera)
+    rec, rect, it, ig, cnt, rg = export(ctx, V, S, tiny.camera)
+    n = replay_tile_lists(rec, rect, it, ig, cnt, rg, tiny.camera.width, tiny.camera.height, 16, 16)
+    assert n == ctx.last_counts().n_instances
+
+
+def test_projection_records_match_oracle(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    g = ordered(ctx, tiny.gaussians)
+    V, S = 4, g.n
+    poses = tiny.candidate_poses[:V]
+    gpu_render(ctx, full_range(ctx), poses, tiny.camera)
+    rec, rect, *_ = export(ctx, V, S, tiny.camera)
+    F = oracle.F
+    n_boundary = 0
+    for v in range(V):
+        ref = oracle.project(g, poses[v], tiny.camera)
+        gv = rect[v, :, 0] >= 0
+        ov = ref[:, F["visible"]] == 1
+        n_boundary += int((gv != ov).sum())
+        both = gv & ov
+        np.testing.assert_allclose(rec[v, both, 0], ref[both, F["u"]], atol=2e-4)
+        np.testing.assert_allclose(rec[v, both, 1], ref[both, F["v"]], atol=2e-4)
+        np.testing.assert_allclose(rec[v, both, 2], ref[both, F["depth"]], rtol=1e-6)
+        np.testing.assert_allclose(rec[v, both, 3], ref[both, F["opacity"]], rtol=0, atol=0)
+        for k, name in ((4, "con_a"), (5, "con_b"), (6, "con_c")):
+            scale = np.sqrt(np.abs(ref[both, F["con_a"]] * ref[both, F["con_c"]]))
+            assert np.max(np.abs(rec[v, both, k] - ref[both, F[name]]) / scale) < 1e-4
+        np.testing.assert_allclose(rec[v, both, 8:11], ref[both][:, [F["r"], F["g"], F["b"]]], atol=1e-6)
+        # tile rectangles: identical unless an edge is within 1e-3 px of a tile line
+        rr = ref[both][:, [F["tx0"], F["ty0"], F["tx1"], F["ty1"]]].astype(np.int32)
+        diff = np.any(rect[v, both] != rr, axis=1)
+        if diff.any():
+            u, vv = ref[both, F["u"]][diff], ref[both, F["v"]][diff]
+            rx, ry = ref[both, F["rx"]][diff], ref[both, F["ry"]][diff]
+            edges = np.stack([u - rx, u + rx, vv - ry, vv + ry], 1) / 16.0
+            assert np.all(np.min(np.abs(edges - np.round(edges)), axis=1) * 16 < 1e-3)
+    assert n_boundary <= 2
+
+
+def test_scores_and_argmax_tiny(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    g = ordered(ctx, tiny.gaussians)
+    q = oracle.render(g, tiny.hidden_pose, tiny.camera)["rgb"] + tiny.query_noise
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda:0").contiguous()
+    sc, dg = ctx.score(full_range(ctx), tiny.candidate_poses, tiny.camera, qd)
+    ref = oracle.render_views(g, tiny.candidate_poses, tiny.camera, query=q.astype(np.float32),
+                              images=False, flags=False)
+    err = np.abs(sc - ref["scores"]).max()
+    print("tiny ncc max err", err)
+    assert err <= TOL_NCC
+    assert not dg.any()
+    top = np.sort(ref["scores"])[::-1]
+    if top[0] - top[1] > TOL_NCC:
+        assert int(np.argmax(sc)) == oracle.argmax(ref["scores"])
+
+
+def test_localize_tiny_grid(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians, block_size=5.0)
+    g = ordered(ctx, tiny.gaussians)
+    q = (oracle.render(g, tiny.hidden_pose, tiny.camera)["rgb"] + tiny.query_noise).astype(np.float32)
+    qd = torch.tensor(q, device="cuda:0").contiguous()
+    cam = tiny.camera
+    brgb = torch.empty((3, cam.height, cam.width), device="cuda:0")
+    bdep = torch.empty((cam.height, cam.width), device="cuda:0")
+    bal = torch.empty((cam.height, cam.width), device="cuda:0")
+    radius = 12.0
+    res, sc = ctx.localize(qd, tiny.seed_pose, radius, (3, 3, 3, 0.5, 3.0), cam, brgb, bdep, bal)
+    # oracle: same blocks, same grid, full sweep
+    seed_c = -tiny.seed_pose[:3, :3].T @ tiny.seed_pose[:3, 3]
+    idx, nb = oracle.block_select(tiny.gaussians.mean, 5.0, seed_c[0], seed_c[1], radius)
+    assert res.n_blocks == nb and res.n_gauss == len(idx)
+    sub = tiny.gaussians.subset(idx)
+    poses = oracle.grid_poses(tiny.seed_pose, 3, 3, 3, 0.5, 3.0)
+    ref = oracle.render_views(sub, poses, cam, query=q)
+    assert np.abs(sc - ref["scores"]).max() <= TOL_NCC
+    best = oracle.argmax(ref["scores"])
+    top = np.sort(ref["scores"])[::-1]
+    if top[0] - top[1] > TOL_NCC:
+        assert res.best_index == best
+    k = res.best_index
+    assert np.allclose(np.array(res.best_pose).reshape(4, 4), poses[k], atol=1e-12)
+    one = {key: ref[key][k:k + 1] for key in ("rgb", "depth", "alpha", "flags", "bound")}
+    compare_images(brgb.cpu().numpy()[None].astype(np.float64), bdep.cpu().numpy()[None].astype(np.float64),
+                   bal.cpu().numpy()[None].astype(np.float64), one, z_ref(sub, poses, cam))
+
+
+def test_block_select_matches_oracle(R):
+    g = sg.street_gaussians(60_000, seed=4, sh_degree=0)
+    ctx = make_ctx(R, g)
+    order = ctx.map_order()
+    for (x, y, r) in [(0.0, 0.0, 40.0), (-150.0, 3.0, 30.0), (249.0, -7.0, 55.0), (0.0, 0.0, 0.0)]:
+        runs, ng, nb = ctx.select_block(x, y, r)
+        got = np.concatenate([order[b:e] for b, e in runs]) if runs else np.zeros(0, np.int64)
+        idx, nbo = oracle.block_select(g.mean, 20.0, x, y, r)
+        assert nb == nbo and ng == len(idx)
+        assert np.array_equal(got, idx)
+
+
+# ------------------------------------------------------------ edge cases ----
+
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (16, 16), (8, 16)])
+def test_ragged_image_and_tile_shapes(R, tiny, tile):
+    cam = sg.Camera(101, 37, 40.0, 40.0, 50.5, 18.5)
+    ctx = make_ctx(R, tiny.gaussians, tile_w=tile[0], tile_h=tile[1])
+    g = ordered(ctx, tiny.gaussians)
+    poses = tiny.candidate_poses[:3]
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), poses, cam)
+    prm = oracle.params(tile_w=tile[0], tile_h=tile[1])
+    ref = oracle.render_views(g, poses, cam, prm)
+    compare_images(rgb, depth, alpha, ref, z_ref(g, poses, cam))
+    rec, rect, it, ig, cnt, rg = export(ctx, 3, g.n, cam, tile)
+    replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, tile[0], tile[1])
+
+
+def test_no_dilation_uses_fp64_inverse(R, tiny):
+    # eps2d = 0: tiny footprints have det(Sigma') < 1e-6 and take the FP64 path
+    ctx = make_ctx(R, tiny.gaussians, eps2d=0.0)
+    g = ordered(ctx, tiny.gaussians)
+    poses = tiny.candidate_poses[:2]
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), poses, tiny.camera)
+    ref = oracle.render_views(g, poses, tiny.camera, oracle.params(eps2d=0.0))
+    compare_images(rgb, depth, alpha, ref, z_ref(g, poses, tiny.camera))
+
+
+def test_empty_subset_and_nothing_visible(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    rgb, depth, alpha = gpu_render(ctx, [], tiny.candidate_poses[:2], tiny.camera)
+    assert not rgb.any() and not depth.any() and not alpha.any()
+    q = torch.rand((3, tiny.camera.height, tiny.camera.width), device="cuda:0")
+    sc, dg = ctx.score([], tiny.candidate_poses[:2], tiny.camera, q)
+    assert np.all(sc == 0) and np.all(dg == 1)
+    # camera looking away from every Gaussian
+    away = sg.pose_from_xyz_yaw(0.0, -14.0, 2.0, -math.pi / 2)
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), away[None], tiny.camera)
+    ref = oracle.render_views(ordered(ctx, tiny.gaussians), away[None], tiny.camera)
+    assert ref["counts"][0, 0] == ctx.last_counts().n_visible
+    compare_images(rgb, depth, alpha, ref, 30.0)
+
+
+def test_single_view_single_gaussian(R):
+    g = sg.Gaussians(np.array([[0.0, 0.0, 5.0]], np.float32), np.full((1, 3), 0.3, np.float32),
+                     np.array([[1, 0, 0, 0]], np.float32), np.array([0.8], np.float32),
+                     np.array([[[0.2, 0.5, 0.9]]], np.float32), 0)
+    cam = sg.Camera(64, 48, 50.0, 50.0, 32.0, 24.0)
+    ctx = make_ctx(R, g)
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), np.eye(4)[None], cam)
+    ref = oracle.render_views(g, np.eye(4)[None], cam)
+    compare_images(rgb, depth, alpha, ref, 5.0)
+
+
+def test_overflow_grow_and_retry_is_exact(R, tiny):
+    a = make_ctx(R, tiny.gaussians)
+    b = make_ctx(R, tiny.gaussians, inst_capacity=64)
+    ra = gpu_render(a, full_range(a), tiny.candidate_poses, tiny.camera)
+    rb = gpu_render(b, full_range(b), tiny.candidate_poses, tiny.camera)
+    assert b.last_counts().retries >= 1
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x, y)
+
+
+def test_repeat_calls_are_deterministic(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    q = torch.rand((3, tiny.camera.height, tiny.camera.width), device="cuda:0", generator=None)
+    s1, _ = ctx.score(full_range(ctx), tiny.candidate_poses, tiny.camera, q)
+    s2, _ = ctx.score(full_range(ctx), tiny.candidate_poses, tiny.camera, q)
+    assert np.array_equal(s1, s2)
+
+
+def test_invalid_arguments_fail_cleanly(R, tiny):
+    ctx = make_ctx(R, tiny.gaussians)
+    with pytest.raises(R.RelocError) as e:
+        ctx.render([(0, tiny.gaussians.n + 5)], tiny.candidate_poses[:1], tiny.camera)
+    assert e.value.status == R.EINVAL
+    bad = tiny.candidate_poses[:1].copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(R.RelocError) as e:
+        ctx.render(full_range(ctx), bad, tiny.camera)
+    assert e.value.status == R.ENUMERIC
+    empty = R.Context()
+    with pytest.raises(R.RelocError) as e:
+        empty.render([], tiny.candidate_poses[:1], tiny.camera)
+    assert e.value.status == R.ENOMAP
+    # the context still works after errors
+    gpu_render(ctx, full_range(ctx), tiny.candidate_poses[:1], tiny.camera)
+
+
+# --------------------------------------------------------- street scenes ----
+
+@pytest.fixture(scope="module")
+def street_small():
+    return sg.street_gaussians(150_000, seed=11, sh_degree=3)
+
+
+def test_street_sh3_reduced_camera(R, street_small):
+    # 704x188 (half resolution, ragged 16-px tiles in y), SH degree 3
+    cam = sg.street_camera(704, 188, 276.0)
+    hidden, seeds = sg.street_queries(2, seed=12)
+    ctx = make_ctx(R, street_small)
+    runs, ng, nb = ctx.select_block(seeds[0][0], seeds[0][1], 40.0)
+    order = ctx.map_order()
+    sub = street_small.subset(np.concatenate([order[b:e] for b, e in runs]))
+    poses = sg.street_grid_poses(seeds[0], 2, 2, 2, 0.5, 2.0)
+    rgb, depth, alpha = gpu_render(ctx, runs, poses, cam)
+    ref = oracle.render_views(sub, poses, cam)
+    st = compare_images(rgb, depth, alpha, ref, z_ref(sub, poses, cam))
+    print("street sh3 704x188", st)
+    rec, rect, it, ig, cnt, rg = export(ctx, len(poses), ng, cam)
+    replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_half_precision_storage(R, street_small, precision):
+    """FP16/BF16 attribute storage (means FP32): parity with the oracle fed the
+    same rounded attributes; the error against the unrounded map is reported."""
+    cam = sg.street_camera(704, 188, 276.0)
+    hidden, seeds = sg.street_queries(2, seed=12)
+    ctx = make_ctx(R, street_small, precision)
+    runs, ng, nb = ctx.select_block(seeds[0][0], seeds[0][1], 40.0)
+    order = ctx.map_order()
+    sub = street_small.subset(np.concatenate([order[b:e] for b, e in runs]))
+    dt = torch.float16 if precision == 1 else torch.bfloat16
+
+    def rnd(a):
+        return torch.tensor(a).to(dt).float().numpy()
+    subr = sg.Gaussians(sub.mean, rnd(sub.scale), rnd(sub.quat), rnd(sub.opacity), rnd(sub.sh), sub.sh_degree)
+    poses = sg.street_grid_poses(seeds[0], 2, 1, 1, 0.5, 2.0)
+    rgb, depth, alpha = gpu_render(ctx, runs, poses, cam)
+    ref = oracle.render_views(subr, poses, cam)
+    st = compare_images(rgb, depth, alpha, ref, z_ref(subr, poses, cam))
+    full = oracle.render_views(sub, poses, cam, flags=False)
+    print("precision", precision, st, "vs unrounded map: rgb max",
+          float(np.abs(rgb - full["rgb"]).max()), "mean", float(np.abs(rgb - full["rgb"]).mean()))
+
+
+def test_street_full_size_sampled(R):
+    """The driving configuration as the benchmark runs it: 2M Gaussians, 20 m
+    blocks, 40 m radius, 1408x376, 64 candidates (4x4x4 grid, 0.5 m / 2 deg).
+    Sampled views are rendered by the oracle pixel for pixel; every NCC score
+    is checked against the oracle's full sweep."""
+    g = sg.street_gaussians(2_000_000, seed=11, sh_degree=3)
+    cam = sg.street_camera()
+    hidden, seeds = sg.street_queries(1, seed=12)
+    ctx = make_ctx(R, g)
+    order = ctx.map_order()
+    seed_pose = sg.pose_from_xyz_yaw(*seeds[0])
+    runs, ng, nb = ctx.select_block(seeds[0][0], seeds[0][1], 40.0)
+    sub = g.subset(np.concatenate([order[b:e] for b, e in runs]))
+    q = (oracle.render(sub, sg.pose_from_xyz_yaw(*hidden[0]), cam)["rgb"]
+         + sg.image_noise(13, cam.height, cam.width)).astype(np.float32)
+    qd = torch.tensor(q, device="cuda:0")
+    brgb = torch.empty((3, cam.height, cam.width), device="cuda:0")
+    bdep = torch.empty((cam.height, cam.width), device="cuda:0")
+    bal = torch.empty((cam.height, cam.width), device="cuda:0")
+    res, sc = ctx.localize(qd, seed_pose, 40.0, (4, 4, 4, 0.5, 2.0), cam, brgb, bdep, bal)
+    poses = oracle.grid_poses(seed_pose, 4, 4, 4, 0.5, 2.0)
+    ref = oracle.render_views(sub, poses, cam, query=q, images=False, flags=False)
+    err = np.abs(sc - ref["scores"]).max()
+    print("full-size ncc max err", err, "best", res.best_index, oracle.argmax(ref["scores"]))
+    assert err <= TOL_NCC
+    top = np.sort(ref["scores"])[::-1]
+    if top[0] - top[1] > TOL_NCC:
+        assert res.best_index == oracle.argmax(ref["scores"])
+    k = res.best_index
+    one = oracle.render_views(sub, poses[k:k + 1], cam)
+    st = compare_images(brgb.cpu().numpy()[None].astype(np.float64), bdep.cpu().numpy()[None].astype(np.float64),
+                        bal.cpu().numpy()[None].astype(np.float64), one, z_ref(sub, poses[k:k + 1], cam))
+    print("full-size winner image", st)
+    # two more sampled views through reloc_render
+    pick = [0, 63]
+    rgb, depth, alpha = gpu_render(ctx, runs, poses[pick], cam)
+    two = oracle.render_views(sub, poses[pick], cam)
+    print("full-size sampled views", compare_images(rgb, depth, alpha, two, z_ref(sub, poses[pick], cam)))
