@@ -236,6 +236,32 @@ reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rec
                                 uint32_t *inst_tiles_dev, uint32_t *inst_gauss_dev,
                                 int64_t *inst_count_host, int32_t *ranges_dev, void *stream);
 
+/* NCC of already-rendered images against a query, without allocating.
+ * The paper has no counterpart: this entry point is for callers that must not
+ * allocate device memory after start-up -- e.g. a real-time relocalization
+ * loop whose memory is reserved up front (cudaMalloc/cudaFree may synchronise
+ * the whole device and take milliseconds) or a process whose device memory
+ * belongs to another framework's pool.  It computes what the scoring stage of
+ * reloc_score computes (Eq. ncc over all 3*H*W samples, FP64 sums, 0 and
+ * degenerate = 1 for a zero-variance image) for images the caller rendered.
+ *   images_dev      [n_views][3][height][width] float32, device, caller-owned
+ *   query_dev       [3][height][width] float32, device, caller-owned
+ *   scores_dev      [n_views] double, device, written (caller-owned)
+ *   degenerate_dev  [n_views] int, device, written (may be NULL)
+ * Its only scratch is a fixed 393,728-byte device array inside the library,
+ * held by every GPU that loads the library until the process exits; no
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on a device looks up that array's device address (with the device
+ * current) and should come before any stream capture.  Asynchronous on
+ * `stream`.  All calls share the one array: calls that overlap on the GPU
+ * race and must be ordered by the caller.  Errors: EINVAL (NULL pointer,
+ * n_views outside 1..RELOC_NOALLOC_MAX_VIEWS, image size outside 1..16383),
+ * ECUDA. */
+#define RELOC_NOALLOC_MAX_VIEWS 512
+reloc_status reloc_ncc_images_noalloc(const float *images_dev, int n_views, int height, int width,
+                                      const float *query_dev, double *scores_dev, int *degenerate_dev,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

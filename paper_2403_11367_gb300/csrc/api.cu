@@ -145,6 +145,8 @@ struct reloc_ctx {
 
 // ============================================================ small pieces ==
 
+int reloc::reloc_internal_fail(int st, const char *msg) { return fail(st, "%s", msg); }
+
 static const char *kVersion = "gs-reloc-gb300 0.1 (sm_103a)";
 
 extern "C" const char *reloc_version(void) { return kVersion; }

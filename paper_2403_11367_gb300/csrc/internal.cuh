@@ -117,4 +117,7 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, in
 // K8: argmax (lowest index on ties) -> best[0] = index, best_score[0].
 cudaError_t launch_argmax(const double *scores, int V, int *best, double *best_score, cudaStream_t st);
 
+// Record msg as the calling thread's last error; returns st.
+int reloc_internal_fail(int st, const char *msg);
+
 }  // namespace reloc

@@ -91,7 +91,9 @@ SIGNATURES = {
     "reloc_set_profiling": (C.c_int, [_vp, C.c_int]),
     "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
     "reloc_export_debug": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64p, _vp, _vp]),
+    "reloc_ncc_images_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
 }
+NOALLOC_MAX_VIEWS = 512
 
 
 def _load():
@@ -145,6 +147,15 @@ def camera(cam) -> Camera:
 
 def reloc_version() -> str:
     return lib.reloc_version().decode()
+
+
+def reloc_ncc_images_noalloc(images, query, scores_out, degenerate_out=None, stream=None):
+    """NCC of rendered images [V,3,H,W] against query [3,H,W] into scores_out
+    [V] (float64) and degenerate_out [V] (int32), all CUDA tensors; the library
+    allocates nothing for this call (see include/reloc.h)."""
+    V, _, H, W = images.shape
+    _check(lib.reloc_ncc_images_noalloc(_ptr(images), V, H, W, _ptr(query), _ptr(scores_out),
+                                        _ptr(degenerate_out), _stream(stream)))
 
 
 def reloc_default_config(**over) -> Config:
