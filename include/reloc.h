@@ -59,7 +59,8 @@ typedef struct reloc_config {
     float det_fp64;            /* invert Sigma' in FP64 when its det < this: 1e-6 px^4 */
     double block_size;         /* 2D voxel block edge: 20 m                            */
     int64_t inst_capacity;     /* initial tile-instance capacity per view: 1<<20       */
-    int32_t reserved[8];
+    int32_t blend_rpl;         /* blend: records staged per lane per warp step (1, 2): 1 */
+    int32_t reserved[7];
 } reloc_config;
 
 typedef struct reloc_camera {
@@ -222,7 +223,8 @@ reloc_status reloc_stage_times(reloc_ctx *ctx, double *ms_out, int64_t *calls_ou
 /* Copy intermediate results of the LAST render/score/localize call, for
  * parity checks (device pointers, any may be NULL; sizes from reloc_last_counts):
  *   records_dev [n_views][n_gauss][12] float: u, v, depth, opacity,
- *                conic a, b, c, 0, red, green, blue, 0   (valid where visible)
+ *                conic a, b, c, Sigma'_xx, red, green, blue, Sigma'_yy
+                (conic = inverse of the dilated Sigma'; valid where visible)
  *   rects_dev   [n_views][n_gauss][4] int32: tile rectangle tx0, ty0, tx1, ty1
  *                inclusive; all -1 where not visible
  *   inst_tiles_dev / inst_gauss_dev [n_views][inst_stride] uint32: the sorted

@@ -168,6 +168,7 @@ extern "C" void reloc_default_config(reloc_config *cfg)
     cfg->det_fp64 = 1e-6f;
     cfg->block_size = 20.0;
     cfg->inst_capacity = 1 << 20;
+    cfg->blend_rpl = 1;
 }
 
 static bool tile_ok(int w, int h)
@@ -181,7 +182,7 @@ static reloc_status check_config(const reloc_config &c)
     if (!tile_ok(c.tile_w, c.tile_h)) return fail(RELOC_EINVAL, "tile %dx%d not supported", c.tile_w, c.tile_h);
     if (!(c.near_plane > 0) || !(c.fov_clamp > 0) || !(c.eps2d >= 0) || !(c.alpha_min > 0) ||
         !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1) || !(c.t_min > 0) || !(c.t_min < 1) || !(c.cut > 0) ||
-        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 1)
+        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 1 || c.blend_rpl < 1 || c.blend_rpl > 2)
         return fail(RELOC_EINVAL, "invalid constant in reloc_config");
     return RELOC_OK;
 }
@@ -406,6 +407,7 @@ static reloc_status make_cam(const reloc_ctx *ctx, const reloc_camera *cam, CamP
     cp.alpha_min = c.alpha_min;
     cp.alpha_max = c.alpha_max;
     cp.t_min = c.t_min;
+    cp.blend_rpl = c.blend_rpl;
     return RELOC_OK;
 }
 

@@ -39,6 +39,7 @@ struct CamParams {
     float fx, fy, cx, cy, limx, limy;
     float near_plane, eps2d, cut, det_fp64;
     float alpha_min, alpha_max, t_min;
+    int blend_rpl;     // records per lane per warp step in K6 (1 or 2)
 };
 
 // Stable LSD radix sort over view-strided segments (sort.cu).

@@ -224,8 +224,8 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
                         }
                         float4 *rp = rec + 3 * o;
                         rp[0] = make_float4(u, vpx, tz, opac);
-                        rp[1] = make_float4(ia, ib, ic, 0.f);
-                        rp[2] = make_float4(cr, cg, cbl, 0.f);
+                        rp[1] = make_float4(ia, ib, ic, ca);
+                        rp[2] = make_float4(cr, cg, cbl, cc);
                     }
                 }
             }

@@ -66,97 +66,233 @@ cudaError_t launch_query_stats(const float *query, int64_t n, double *block_scra
 }
 
 // ------------------------------------------------------------------ K6 -----
-// One CTA per (view, tile), one thread per pixel.  Records of the tile's
-// sorted list are staged through shared memory in batches of one record per
-// thread; the CTA stops early once every pixel's transmittance has run out.
+// One CTA per (view, tile).  Each thread owns two vertically adjacent pixels,
+// so a warp covers a TW x (64/TW) pixel block, and the warps of a tile run
+// independently (no barrier until the NCC epilogue).  A warp walks the tile's
+// sorted list RPL*32 records at a time: each lane loads its records (the
+// tile's warps read the same records, so after the first they hit L1),
+// derives the power threshold below which a record cannot contribute --
+// max(-cut^2/2, ln(alpha_min / o) - 1e-3), the margin covering the float
+// logarithm and exponential -- and keeps the record if the ellipse
+// {power >= threshold}, widened by 1%, meets the warp's pixel block (exact
+// ellipse-rectangle test: the least value of the quadratic form over the
+// block).  A ballot compacts the kept records, in list order,
+// into the warp's shared-memory slots, and the warp blends only those; a
+// pixel below a record's threshold also skips the exponential.  Both tests
+// only drop pairs the exact per-pixel tests would drop, so the result is that
+// of testing every pixel of the tile against every record of its list.  A
+// warp stops once all its pixels' transmittance has run out.
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH)
+// Packed FP32 pairs (two pixels per thread): one 64-bit register holds
+// (low = pixel row y, high = pixel row y + 1); fma/mul/add.rn.f32x2 operate on
+// both halves with IEEE round-to-nearest, like two scalar instructions.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Minimum over the rectangle [x0,x1] x [y0,y1] (offsets from the ellipse
+// centre) of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 for a positive-definite
+// conic: 0 if the centre is inside, else the least of the four edge minima
+// (each a clamped 1D quadratic).
+__device__ __forceinline__ float quad_min_rect(float a, float b, float c, float x0, float x1, float y0, float y1)
+{
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
+    auto edge_x = [&](float dx) {      // dx fixed, dy free in [y0, y1]
+        const float dy = fminf(fmaxf(-b * dx / c, y0), y1);
+        return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
+    };
+    auto edge_y = [&](float dy) {      // dy fixed, dx free in [x0, x1]
+        const float dx = fminf(fmaxf(-b * dy / a, x0), x1);
+        return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
+    };
+    return fminf(fminf(edge_x(x0), edge_x(x1)), fminf(edge_y(y0), edge_y(y1)));
+}
+
+template <int TW, int TH, int RPL>
+__global__ void __launch_bounds__(TW *TH / 2)
 k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ inst_gauss, int64_t inst_stride,
         const int2 *__restrict__ ranges, CamParams cam, const float *__restrict__ query, double *__restrict__ partials,
         float *__restrict__ rgb, float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
         const int *__restrict__ overflow)
 {
-    constexpr int NT = TW * TH;
+    constexpr int NT = TW * TH / 2;          // threads
     constexpr int NW = NT / 32;
-    __shared__ float4 s_a[NT];   // u, v, depth, opacity
-    __shared__ float4 s_b[NT];   // conic a, b, c
-    __shared__ float4 s_c[NT];   // red, green, blue
+    constexpr int WROWS = 64 / TW;           // pixel rows per warp
+    constexpr int CH = 32 * RPL;             // records per warp step
+    static_assert(NT % 32 == 0 && TH % 2 == 0, "tile shape");
+    __shared__ float4 s_rec[NW][3][CH];      // per warp: u v o z | conic a b c thr | rgb
     __shared__ double s_red[3][NW];
 
     const int tile = blockIdx.x;
     const int v = view_sel ? *view_sel : (int)blockIdx.y;
     const int out_v = view_sel ? 0 : (int)blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * TW + (int)(threadIdx.x % TW);
-    const int py = ty * TH + (int)(threadIdx.x / TW);
-    const bool inside = px < cam.width && py < cam.height;
-    const float fxp = (float)px + 0.5f, fyp = (float)py + 0.5f;
+    const int py0 = ty * TH + 2 * (int)(threadIdx.x / TW);
+    const int py1 = py0 + 1;
+    const bool in0 = px < cam.width && py0 < cam.height;
+    const bool in1 = px < cam.width && py1 < cam.height;
+    const float fxp = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
+    // pixel-centre extent of this warp's block
+    const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
+    const float wy0 = (float)(ty * TH + warp * WROWS) + 0.5f, wy1 = wy0 + (float)(WROWS - 1);
 
     int2 r = make_int2(0, 0);
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + (int64_t)v * inst_stride;
     const float4 *vrec = rec + (int64_t)v * S * 3;
     const float lim = -0.5f * cam.cut * cam.cut;
+    const float lamin = __logf(cam.alpha_min);
+    float4(*const sw)[CH] = s_rec[warp];
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    bool done = !inside;
-    for (int b = r.x; b < r.y; b += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const int j = b + (int)threadIdx.x;
-        if (j < r.y) {
-            const float4 *p = vrec + 3 * (int64_t)list[j];
-            s_a[threadIdx.x] = p[0];
-            s_b[threadIdx.x] = p[1];
-            s_c[threadIdx.x] = p[2];
+    // pixel pair state: transmittance, colour, depth (low = row y, high = y + 1)
+    float T0 = 1.f, T1 = 1.f;
+    f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, D2 = 0ull;
+    bool done0 = !in0, done1 = !in1;
+    const f32x2 FY2 = pk(fy0, fy1);
+
+    // software pipeline: list indices two steps ahead, records one step ahead
+    uint32_t gnext[RPL];
+    float4 qa[RPL], qb[RPL], qc[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int j0 = r.x + q * 32 + lane, j1 = j0 + CH;
+        if (j0 < r.y) {
+            const float4 *p = vrec + 3 * (int64_t)__ldg(list + j0);
+            qa[q] = __ldg(p); qb[q] = __ldg(p + 1); qc[q] = __ldg(p + 2);
         }
-        __syncthreads();
-        const int cnt = min(NT, r.y - b);
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const float4 a = s_a[k];
-                const float4 cb = s_b[k];
-                const float dx = fxp - a.x, dy = fyp - a.y;
-                const float power = -0.5f * (cb.x * dx * dx + cb.z * dy * dy) - cb.y * dx * dy;
-                if (power < lim) continue;
-                const float al = fminf(cam.alpha_max, a.w * __expf(power));
-                if (al < cam.alpha_min) continue;
-                const float tn = T * (1.f - al);
-                if (tn < cam.t_min) { done = true; break; }
-                const float w = al * T;
-                const float4 c = s_c[k];
-                C0 += c.x * w;
-                C1 += c.y * w;
-                C2 += c.z * w;
-                D += a.z * w;
-                T = tn;
+        gnext[q] = j1 < r.y ? __ldg(list + j1) : 0u;
+    }
+    for (int b = r.x; b < r.y; b += CH) {
+        if (__all_sync(0xffffffffu, done0 && done1)) break;
+        unsigned keep[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int j = b + q * 32 + lane;
+            bool hit = false;
+            const float4 pa = qa[q], pb = qb[q], pc = qc[q];
+            // issue the next step's loads before working on this one
+            const int jn = j + CH, jnn = j + 2 * CH;
+            if (jn < r.y) {
+                const float4 *p = vrec + 3 * (int64_t)gnext[q];
+                qa[q] = __ldg(p); qb[q] = __ldg(p + 1); qc[q] = __ldg(p + 2);
+            }
+            gnext[q] = jnn < r.y ? __ldg(list + jnn) : 0u;
+            if (j < r.y) {
+                // pa: u v z o | pb: conic a b c, Sigma'_xx | pc: rgb, Sigma'_yy
+                const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
+                if (thr < 0.f) {
+                    // keep iff the ellipse {power >= thr} (widened 1%) meets the block
+                    const float qmin = quad_min_rect(pb.x, pb.y, pb.z, wx0 - pa.x, wx1 - pa.x, wy0 - pa.y, wy1 - pa.y);
+                    hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
+                }
+                if (hit) {
+                    // power(dx, dy) = dx (A dx + B dy) + C dy^2
+                    sw[0][q * 32 + lane] = make_float4(pa.x, pa.y, pa.w, pa.z);
+                    sw[1][q * 32 + lane] = make_float4(-0.5f * pb.x, -pb.y, -0.5f * pb.z, thr);
+                    sw[2][q * 32 + lane] = pc;
+                }
+            }
+            keep[q] = __ballot_sync(0xffffffffu, hit);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            unsigned m = keep[q];
+            while (m) {
+                const int k = q * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                const float4 a = sw[0][k];       // u, v, opacity, depth
+                const float4 cb = sw[1][k];      // A = -a/2, B = -b, C = -c/2, threshold
+                // power(dx, dy) = dx (A dx + B dy) + C dy^2 for both rows
+                const float dx = fxp - a.x;
+                const f32x2 dy2 = add2(FY2, pk(-a.y, -a.y));
+                const f32x2 Cdy2 = mul2(pk(cb.z, cb.z), dy2);
+                const f32x2 t2 = fma2(pk(cb.y, cb.y), dy2, pk(cb.x * dx, cb.x * dx));
+                const f32x2 p2 = fma2(Cdy2, dy2, mul2(pk(dx, dx), t2));
+                float p0, p1;
+                upk(p2, p0, p1);
+                const bool t0 = !done0 && p0 >= cb.w;
+                const bool t1 = !done1 && p1 >= cb.w;
+                if (!(t0 || t1)) continue;
+                // both pixels without branches: alpha, stop test, weights
+                const float al0 = fminf(cam.alpha_max, a.z * __expf(p0));
+                const float al1 = fminf(cam.alpha_max, a.z * __expf(p1));
+                const bool ok0 = t0 && al0 >= cam.alpha_min;
+                const bool ok1 = t1 && al1 >= cam.alpha_min;
+                const float tn0 = T0 * (1.f - al0), tn1 = T1 * (1.f - al1);
+                const bool st0 = ok0 && tn0 < cam.t_min, st1 = ok1 && tn1 < cam.t_min;
+                const bool ad0 = ok0 && !st0, ad1 = ok1 && !st1;
+                const f32x2 w2 = pk(ad0 ? al0 * T0 : 0.f, ad1 ? al1 * T1 : 0.f);
+                const float4 c = sw[2][k];
+                R2 = fma2(pk(c.x, c.x), w2, R2);
+                G2 = fma2(pk(c.y, c.y), w2, G2);
+                B2 = fma2(pk(c.z, c.z), w2, B2);
+                D2 = fma2(pk(a.w, a.w), w2, D2);
+                T0 = ad0 ? tn0 : T0;
+                T1 = ad1 ? tn1 : T1;
+                done0 = done0 || st0;
+                done1 = done1 || st1;
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 
+    float R0, R1, G0, G1, B0, B1, D0, D1;
+    upk(R2, R0, R1);
+    upk(G2, G0, G1);
+    upk(B2, B0, B1);
+    upk(D2, D0, D1);
     const int64_t HW = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)py * cam.width + px;
-    if (inside) {
-        if (rgb) {
-            float *o = rgb + (int64_t)out_v * 3 * HW;
-            o[pix] = C0;
-            o[HW + pix] = C1;
-            o[2 * HW + pix] = C2;
-        }
-        if (depth) depth[(int64_t)out_v * HW + pix] = D;
-        if (alpha) alpha[(int64_t)out_v * HW + pix] = 1.f - T;
+    const int64_t pix0 = (int64_t)py0 * cam.width + px, pix1 = pix0 + cam.width;
+    if (rgb) {
+        float *o = rgb + (int64_t)out_v * 3 * HW;
+        if (in0) { o[pix0] = R0; o[HW + pix0] = G0; o[2 * HW + pix0] = B0; }
+        if (in1) { o[pix1] = R1; o[HW + pix1] = G1; o[2 * HW + pix1] = B1; }
+    }
+    if (depth) {
+        if (in0) depth[(int64_t)out_v * HW + pix0] = D0;
+        if (in1) depth[(int64_t)out_v * HW + pix1] = D1;
+    }
+    if (alpha) {
+        if (in0) alpha[(int64_t)out_v * HW + pix0] = 1.f - T0;
+        if (in1) alpha[(int64_t)out_v * HW + pix1] = 1.f - T1;
     }
     if (partials) {
-        float sr = C0 + C1 + C2;
-        float srr = C0 * C0 + C1 * C1 + C2 * C2;
+        // pixels outside the image have zero colour and contribute nothing
+        float sr = R0 + G0 + B0 + R1 + G1 + B1;
+        float srr = R0 * R0 + G0 * G0 + B0 * B0 + R1 * R1 + G1 * G1 + B1 * B1;
         float srq = 0.f;
-        if (inside) srq = C0 * __ldg(query + pix) + C1 * __ldg(query + HW + pix) + C2 * __ldg(query + 2 * HW + pix);
+        if (in0) srq += R0 * __ldg(query + pix0) + G0 * __ldg(query + HW + pix0) + B0 * __ldg(query + 2 * HW + pix0);
+        if (in1) srq += R1 * __ldg(query + pix1) + G1 * __ldg(query + HW + pix1) + B1 * __ldg(query + 2 * HW + pix1);
         sr = warp_sum_f(sr);
         srr = warp_sum_f(srr);
         srq = warp_sum_f(srq);
-        const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) { s_red[0][w] = sr; s_red[1][w] = srr; s_red[2][w] = srq; }
+        if (lane == 0) { s_red[0][warp] = sr; s_red[1][warp] = srr; s_red[2][warp] = srq; }
         __syncthreads();
         if (threadIdx.x < 3) {
             double acc = 0;
@@ -167,15 +303,15 @@ k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ 
     }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int RPL>
 static cudaError_t blend_t(const float4 *rec, int64_t S, const uint32_t *inst_gauss, int64_t inst_stride,
                            const int2 *ranges, int V, const CamParams &cam, const float *query, double *partials,
                            float *rgb, float *depth, float *alpha, const int *view_sel, const int *overflow,
                            cudaStream_t st)
 {
     dim3 grid(cam.n_tiles, view_sel ? 1 : V);
-    k_blend<TW, TH><<<grid, TW * TH, 0, st>>>(rec, S, inst_gauss, inst_stride, ranges, cam, query, partials, rgb,
-                                              depth, alpha, view_sel, overflow);
+    k_blend<TW, TH, RPL><<<grid, TW * TH / 2, 0, st>>>(rec, S, inst_gauss, inst_stride, ranges, cam, query, partials,
+                                                      rgb, depth, alpha, view_sel, overflow);
     return cudaGetLastError();
 }
 
@@ -184,16 +320,22 @@ cudaError_t launch_blend(const float4 *rec, int64_t S, const uint32_t *inst_gaus
                          float *rgb, float *depth, float *alpha, const int *view_sel, const int *overflow,
                          cudaStream_t st)
 {
-#define RELOC_BLEND_CASE(W_, H_)                                                                                 \
-    if (cam.tile_w == W_ && cam.tile_h == H_)                                                                   \
-        return blend_t<W_, H_>(rec, S, inst_gauss, inst_stride, ranges, V, cam, query, partials, rgb, depth, alpha, \
-                               view_sel, overflow, st);
-    RELOC_BLEND_CASE(16, 16)
-    RELOC_BLEND_CASE(8, 8)
-    RELOC_BLEND_CASE(32, 8)
-    RELOC_BLEND_CASE(16, 8)
-    RELOC_BLEND_CASE(8, 16)
-    RELOC_BLEND_CASE(32, 16)
+#define RELOC_BLEND_CASE(W_, H_, R_)                                                                             \
+    if (cam.tile_w == W_ && cam.tile_h == H_ && cam.blend_rpl == R_)                                            \
+        return blend_t<W_, H_, R_>(rec, S, inst_gauss, inst_stride, ranges, V, cam, query, partials, rgb, depth, \
+                                   alpha, view_sel, overflow, st);
+    RELOC_BLEND_CASE(16, 16, 1)
+    RELOC_BLEND_CASE(16, 16, 2)
+    RELOC_BLEND_CASE(8, 8, 1)
+    RELOC_BLEND_CASE(8, 8, 2)
+    RELOC_BLEND_CASE(32, 8, 1)
+    RELOC_BLEND_CASE(32, 8, 2)
+    RELOC_BLEND_CASE(16, 8, 1)
+    RELOC_BLEND_CASE(16, 8, 2)
+    RELOC_BLEND_CASE(8, 16, 1)
+    RELOC_BLEND_CASE(8, 16, 2)
+    RELOC_BLEND_CASE(32, 16, 1)
+    RELOC_BLEND_CASE(32, 16, 2)
 #undef RELOC_BLEND_CASE
     return cudaErrorInvalidValue;
 }

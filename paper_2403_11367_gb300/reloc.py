@@ -30,7 +30,8 @@ class Config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_plane", C.c_float),
                 ("fov_clamp", C.c_float), ("eps2d", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("t_min", C.c_float), ("cut", C.c_float), ("det_fp64", C.c_float),
-                ("block_size", C.c_double), ("inst_capacity", C.c_int64), ("reserved", C.c_int32 * 8)]
+                ("block_size", C.c_double), ("inst_capacity", C.c_int64), ("blend_rpl", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class Camera(C.Structure):
