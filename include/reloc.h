@@ -58,7 +58,8 @@ typedef struct reloc_config {
     float cut;                 /* footprint radius in sigmas (inclusion d'S^-1 d <= cut^2): 3 */
     float det_fp64;            /* invert Sigma' in FP64 when its det < this: 1e-6 px^4 */
     double block_size;         /* 2D voxel block edge: 20 m                            */
-    int64_t inst_capacity;     /* initial tile-instance capacity per view: 1<<20       */
+    int64_t inst_capacity;     /* tile instances per view to start with; 0 = from the
+                                  subset size (learned ratio): 0                       */
     int32_t blend_rpl;         /* blend: records staged per lane per warp step (1, 2): 1 */
     int32_t reserved[7];
 } reloc_config;
@@ -209,6 +210,38 @@ reloc_status reloc_localize_host(reloc_ctx *ctx, const float *query_host, const 
                                  double radius, const reloc_grid *grid, const reloc_camera *cam,
                                  reloc_result *out, float *best_rgb_host, float *best_depth_host,
                                  void *stream);
+
+/* One query of a batch (Sec. III-C.1 applied to many queries at once). */
+typedef struct reloc_query {
+    const float *query_dev;    /* [3][H][W] device image of the query (caller-owned)   */
+    double coarse_pose[16];    /* world-to-camera coarse pose                          */
+    double radius;             /* block-selection radius around its camera centre, m   */
+    reloc_grid grid;           /* candidate grid (counts may differ between queries)   */
+} reloc_query;
+
+/* reloc_localize for n_queries queries at once, each with its own subset and
+ * candidate count.  Every stage runs as one launch over all (query, candidate)
+ * views of a sub-batch; sub-batches are formed so that their workspace stays
+ * within the memory budget of reloc_set_batch_options, and (use_graph) the
+ * launches of the whole call are captured and replayed as one CUDA graph.
+ * results[n_queries] (host) as reloc_localize; scores_host, if not NULL,
+ * receives every candidate's NCC in query order (sum of candidate counts);
+ * best_rgb_dev [n_queries][3][H][W] and best_depth_dev [n_queries][H][W]
+ * (device, may be NULL) receive the winners.  Results equal those of
+ * n_queries separate reloc_localize calls.  Errors: as reloc_localize. */
+reloc_status reloc_localize_batch(reloc_ctx *ctx, const reloc_query *queries, int n_queries,
+                                  const reloc_camera *cam, reloc_result *results, double *scores_host,
+                                  float *best_rgb_dev, float *best_depth_dev, void *stream);
+
+typedef struct reloc_batch_options {
+    int32_t use_graph;         /* capture each batch call in one CUDA graph: 1          */
+    int32_t reserved0;
+    int64_t mem_budget;        /* workspace bytes per sub-batch (>= 64 MiB): 16 GiB     */
+    int32_t reserved[8];
+} reloc_batch_options;
+
+/* Set the batch options of the context.  Errors: EINVAL. */
+reloc_status reloc_set_batch_options(reloc_ctx *ctx, const reloc_batch_options *opt);
 
 /* Work counts of the last render/score/localize call. */
 reloc_status reloc_last_counts(reloc_ctx *ctx, reloc_counts *out);

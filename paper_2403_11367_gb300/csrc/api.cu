@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -102,14 +103,6 @@ struct PinBuf {
     }
 };
 
-// pinned readback block written at the end of every call
-struct Readback {
-    int overflow;
-    int best;
-    unsigned long long need;
-    double best_score;
-};
-
 }  // namespace
 
 struct reloc_ctx {
@@ -122,23 +115,30 @@ struct reloc_ctx {
     DevBuf mean, attr;
     std::vector<int64_t> order;
     BlockIndex blocks;
-    // workspace
-    DevBuf gidx, runs, views, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, nvis, hist1, chunk_sums;
-    DevBuf ikA, ivA, ikB, ivB, ninst, hist2, ranges, partials, qpart, qstats, scores, degen, best, best_score, flags;
+    // workspace (sized for the largest sub-batch of a call)
+    DevBuf gidx, tables, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums;
+    DevBuf ikA, ivA, ikB, ivB, hist2, ranges, partials, qpart, qstats;
+    // per-call results (all views / queries of the call)
+    DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
     DevBuf hq, hrgb, hdepth;
     PinBuf pin;
-    int64_t inst_stride = 0;
-    // last call
+    double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
+    // batch options
+    int use_graph = 1;
+    int64_t mem_budget = (int64_t)16 << 30;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // last call (debug export covers its first sub-batch)
     int last_V = 0;
     int64_t last_S = 0;
     CamParams last_cam{};
     bool last_valid = false;
     bool last_final_b = false;      // final instance lists live in ikB/ivB
-    std::vector<int64_t> last_ninst;
+    std::vector<int64_t> last_ninst, last_io_off, last_vd_off;
     reloc_counts counts{};
     // profiling
     bool prof = false;
-    cudaEvent_t ev[RELOC_STAGE_COUNT + 1] = {};
+    std::vector<cudaEvent_t> ev;    // (RELOC_STAGE_COUNT + 1) per sub-batch
     double stage_ms[RELOC_STAGE_COUNT] = {};
     int64_t stage_calls[RELOC_STAGE_COUNT] = {};
 };
@@ -167,7 +167,7 @@ extern "C" void reloc_default_config(reloc_config *cfg)
     cfg->cut = 3.0f;
     cfg->det_fp64 = 1e-6f;
     cfg->block_size = 20.0;
-    cfg->inst_capacity = 1 << 20;
+    cfg->inst_capacity = 0;
     cfg->blend_rpl = 1;
 }
 
@@ -182,7 +182,7 @@ static reloc_status check_config(const reloc_config &c)
     if (!tile_ok(c.tile_w, c.tile_h)) return fail(RELOC_EINVAL, "tile %dx%d not supported", c.tile_w, c.tile_h);
     if (!(c.near_plane > 0) || !(c.fov_clamp > 0) || !(c.eps2d >= 0) || !(c.alpha_min > 0) ||
         !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1) || !(c.t_min > 0) || !(c.t_min < 1) || !(c.cut > 0) ||
-        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 1 || c.blend_rpl < 1 || c.blend_rpl > 2)
+        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 0 || c.blend_rpl < 1 || c.blend_rpl > 2)
         return fail(RELOC_EINVAL, "invalid constant in reloc_config");
     return RELOC_OK;
 }
@@ -202,13 +202,12 @@ extern "C" reloc_status reloc_create(const reloc_config *cfg, int device, reloc_
     if (!ctx) return fail(RELOC_ENOMEM, "host allocation failed");
     ctx->cfg = c;
     ctx->device = device;
-    ctx->inst_stride = c.inst_capacity;
-    for (auto &e : ctx->ev) {
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaGetLastError();
-            reloc_destroy(ctx);
-            return fail(RELOC_ECUDA, "cudaEventCreate failed");
-        }
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        reloc_destroy(ctx);
+        return fail(RELOC_ECUDA, "stream/event creation failed");
     }
     *out = ctx;
     return RELOC_OK;
@@ -218,15 +217,19 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
 {
     if (!ctx) return RELOC_OK;
     cudaSetDevice(ctx->device);
-    DevBuf *bufs[] = {&ctx->mean, &ctx->attr, &ctx->gidx, &ctx->runs, &ctx->views, &ctx->rec, &ctx->rect,
-                      &ctx->ntiles, &ctx->dkey, &ctx->k1a, &ctx->v1a, &ctx->k1b, &ctx->v1b, &ctx->nvis,
-                      &ctx->hist1, &ctx->chunk_sums, &ctx->ikA, &ctx->ivA, &ctx->ikB, &ctx->ivB, &ctx->ninst,
-                      &ctx->hist2, &ctx->ranges, &ctx->partials, &ctx->qpart, &ctx->qstats, &ctx->scores,
-                      &ctx->degen, &ctx->best, &ctx->best_score, &ctx->flags, &ctx->hq, &ctx->hrgb, &ctx->hdepth};
+    DevBuf *bufs[] = {&ctx->mean, &ctx->attr, &ctx->gidx, &ctx->tables, &ctx->rec, &ctx->rect, &ctx->ntiles,
+                      &ctx->dkey, &ctx->k1a, &ctx->v1a, &ctx->k1b, &ctx->v1b, &ctx->hist1, &ctx->chunk_sums,
+                      &ctx->ikA, &ctx->ivA, &ctx->ikB, &ctx->ivB, &ctx->hist2, &ctx->ranges, &ctx->partials,
+                      &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
+                      &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
+                      &ctx->hdepth};
     for (DevBuf *b : bufs) b->release();
     ctx->pin.release();
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return RELOC_OK;
 }
@@ -411,159 +414,231 @@ static reloc_status make_cam(const reloc_ctx *ctx, const reloc_camera *cam, CamP
     return RELOC_OK;
 }
 
-static reloc_status make_views(const double *poses, int V, std::vector<ViewParams> &vp)
+static reloc_status make_view(const double *W, int v, ViewParams &P)
 {
-    vp.resize(V);
-    for (int v = 0; v < V; ++v) {
-        const double *W = poses + 16 * v;
-        for (int k = 0; k < 16; ++k)
-            if (!std::isfinite(W[k])) return fail(RELOC_ENUMERIC, "non-finite pose %d", v);
-        ViewParams &P = vp[v];
-        memset(&P, 0, sizeof P);
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) P.R[3 * r + c] = (float)W[4 * r + c];
-        for (int i = 0; i < 3; ++i) {
-            const double C = -(W[i] * W[3] + W[4 + i] * W[7] + W[8 + i] * W[11]);
-            P.c_hi[i] = (float)C;
-            P.c_lo[i] = (float)(C - (double)P.c_hi[i]);
-        }
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(W[k])) return fail(RELOC_ENUMERIC, "non-finite pose %d", v);
+    memset(&P, 0, sizeof P);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) P.R[3 * r + c] = (float)W[4 * r + c];
+    for (int i = 0; i < 3; ++i) {
+        const double C = -(W[i] * W[3] + W[4 + i] * W[7] + W[8 + i] * W[11]);
+        P.c_hi[i] = (float)C;
+        P.c_lo[i] = (float)(C - (double)P.c_hi[i]);
     }
     return RELOC_OK;
 }
 
-struct CallOut {
-    const float *query = nullptr;    // device; scores computed if non-null
-    float *rgb = nullptr, *depth = nullptr, *alpha = nullptr;          // all views
-    bool export_best = false;
-    float *brgb = nullptr, *bdepth = nullptr, *balpha = nullptr;       // winner
-    double *scores_host = nullptr;
-    int *degen_host = nullptr;
-    int best = -1;
-    double best_score = 0;
+// One query of a call: its Gaussian subset (block-ordered runs) and views.
+struct QuerySpec {
+    std::vector<reloc_range> runs;
+    int64_t S = 0;
+    int V = 0;
+    std::vector<double> poses;      // V x 16, world-to-camera
+    const float *img = nullptr;     // device query image ([3][H][W]) or null
+    int n_blocks = 0;
 };
 
-static void stage_mark(reloc_ctx *ctx, int s, cudaStream_t st)
+// What a call produces.  Per-view device outputs use the call's global view
+// index, per-query outputs its query index.
+struct CallOut {
+    float *rgb = nullptr, *depth = nullptr, *alpha = nullptr;     // [V][...]
+    bool score = false;                                         // NCC (needs query images)
+    bool argmax = false;                                        // per query argmax
+    float *brgb = nullptr, *bdepth = nullptr, *balpha = nullptr; // winners [Q][...]
+    std::vector<double> scores;
+    std::vector<int> degen, best;
+    std::vector<double> best_score;
+};
+
+// A run of consecutive queries whose workspace fits the memory budget.
+struct SubBatch {
+    int q0 = 0, q1 = 0, v0 = 0, v1 = 0;
+    int64_t S_tot = 0, VS = 0, VI = 0;
+    int c1 = 0, ce = 0, c2 = 0, pblk = 0, n_runs = 0;
+    std::vector<int32_t> view_q, c1_base, ce_base, c2_base, q_view, q_pblk;
+    std::vector<int64_t> vd_off, io_off, q_gsub, run_begin, run_off;
+    std::vector<ViewParams> views;
+    std::vector<const float *> q_img;
+    size_t tab_off = 0, tab_bytes = 0;
+    Layout L{};
+    const int64_t *d_run_begin = nullptr, *d_run_off = nullptr;
+    const ViewParams *d_views = nullptr;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int64_t inst_cap(const reloc_ctx *ctx, int64_t S, int64_t override_cap)
 {
-    if (ctx->prof) cudaEventRecord(ctx->ev[s], st);
+    int64_t c = override_cap > 0 ? override_cap
+                                 : (ctx->cfg.inst_capacity > 0 ? ctx->cfg.inst_capacity
+                                                               : (int64_t)(ctx->inst_ratio * (double)S) + 4096);
+    return ceil_div(c, SORT_CHUNK) * SORT_CHUNK;
 }
 
-static reloc_status run_views(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges, const double *poses, int V,
-                              const reloc_camera *cam, cudaStream_t st, CallOut &o)
+static int64_t query_bytes(int64_t S, int V, int64_t cap, int n_tiles)
 {
-    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
-    if (V < 1 || V > 4096) return fail(RELOC_EINVAL, "n_views %d not in 1..4096", V);
-    if (!poses) return fail(RELOC_EINVAL, "poses is NULL");
-    if (n_ranges < 0 || (n_ranges > 0 && !ranges)) return fail(RELOC_EINVAL, "bad ranges");
-    int64_t S = 0;
-    for (int r = 0; r < n_ranges; ++r) {
-        if (ranges[r].begin < 0 || ranges[r].end < ranges[r].begin || ranges[r].end > ctx->n)
-            return fail(RELOC_EINVAL, "range %d [%lld, %lld) outside the map", r, (long long)ranges[r].begin,
-                        (long long)ranges[r].end);
-        S += ranges[r].end - ranges[r].begin;
-    }
-    if (S > (int64_t)UINT32_MAX / 4) return fail(RELOC_EINVAL, "subset too large");
-    CamParams cp;
-    CKS(make_cam(ctx, cam, cp));
-    std::vector<ViewParams> vp;
-    CKS(make_views(poses, V, vp));
-    CK(cudaSetDevice(ctx->device));
-    ctx->last_valid = false;
+    return (int64_t)V * (S * 80 + cap * 16 + (int64_t)n_tiles * 32 + 1024) + S * 4 + 4096;
+}
 
-    const int64_t HW = (int64_t)cp.width * cp.height;
-    const int64_t S1 = S > 0 ? S : 1;
-    // ---- workspace --------------------------------------------------------
-    const size_t VS = (size_t)V * S1;
-    CKS(ctx->gidx.ensure(4 * S1));
-    CKS(ctx->runs.ensure(16 * (size_t)(n_ranges + 1)));
-    CKS(ctx->views.ensure(sizeof(ViewParams) * V));
-    CKS(ctx->rec.ensure(48 * VS));
-    CKS(ctx->rect.ensure(8 * VS));
-    CKS(ctx->ntiles.ensure(4 * VS));
-    CKS(ctx->dkey.ensure(4 * VS));
-    CKS(ctx->k1a.ensure(4 * VS));
-    CKS(ctx->v1a.ensure(4 * VS));
-    CKS(ctx->k1b.ensure(4 * VS));
-    CKS(ctx->v1b.ensure(4 * VS));
-    CKS(ctx->nvis.ensure(4 * (size_t)V));
-    CKS(ctx->hist1.ensure(4 * (size_t)radix_hist_words(V, S1)));
-    CKS(ctx->chunk_sums.ensure(4 * (size_t)emit_chunk_words(V, S1)));
-    CKS(ctx->ninst.ensure(4 * (size_t)V));
-    CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
-    CKS(ctx->partials.ensure(24 * (size_t)V * cp.n_tiles));
-    CKS(ctx->qpart.ensure(16 * 256));
-    CKS(ctx->qstats.ensure(16));
-    CKS(ctx->scores.ensure(8 * (size_t)V));
-    CKS(ctx->degen.ensure(4 * (size_t)V));
-    CKS(ctx->best.ensure(16));
-    CKS(ctx->best_score.ensure(16));
-    CKS(ctx->flags.ensure(64));
-    const size_t pin_need = sizeof(Readback) + 16 * (size_t)(n_ranges + 1) + sizeof(ViewParams) * V +
-                            (8 + 4 + 4 + 4) * (size_t)V + 64;
-    CKS(ctx->pin.ensure(pin_need));
-
-    // ---- uploads (pinned staging) -----------------------------------------
-    char *pin = (char *)ctx->pin.p;
-    Readback *rb = (Readback *)pin;
-    int64_t *h_runs = (int64_t *)(pin + sizeof(Readback));
-    ViewParams *h_views = (ViewParams *)(h_runs + 2 * (n_ranges + 1));
-    double *h_scores = (double *)(h_views + V);
-    int *h_degen = (int *)(h_scores + V);
-    uint32_t *h_nvis = (uint32_t *)(h_degen + V);
-    uint32_t *h_ninst = h_nvis + V;
-    {
-        int64_t off = 0;
-        for (int r = 0; r < n_ranges; ++r) {
-            h_runs[r] = ranges[r].begin;
-            h_runs[n_ranges + 1 + r] = off;
-            off += ranges[r].end - ranges[r].begin;
+// Split the call into sub-batches and build each one's host tables.
+static void plan_batches(const reloc_ctx *ctx, const std::vector<QuerySpec> &qs, const std::vector<int64_t> &caps,
+                         const CamParams &cp, std::vector<SubBatch> &out)
+{
+    out.clear();
+    const int Q = (int)qs.size();
+    int q = 0, vglob = 0;
+    while (q < Q) {
+        SubBatch sb;
+        sb.q0 = q;
+        sb.v0 = vglob;
+        int64_t bytes = 0;
+        while (q < Q) {
+            const int64_t b = query_bytes(qs[q].S, qs[q].V, caps[q], cp.n_tiles);
+            if (q > sb.q0 && bytes + b > ctx->mem_budget) break;
+            bytes += b;
+            vglob += qs[q].V;
+            ++q;
         }
-        h_runs[n_ranges] = 0;
-        h_runs[n_ranges + 1 + n_ranges] = off;
+        sb.q1 = q;
+        sb.v1 = vglob;
+        const int nq = sb.q1 - sb.q0, nv = sb.v1 - sb.v0;
+        sb.vd_off.assign(nv + 1, 0);
+        sb.io_off.assign(nv + 1, 0);
+        sb.c1_base.assign(nv + 1, 0);
+        sb.ce_base.assign(nv + 1, 0);
+        sb.c2_base.assign(nv + 1, 0);
+        sb.view_q.assign(nv, 0);
+        sb.q_gsub.assign(nq + 1, 0);
+        sb.q_view.assign(nq + 1, 0);
+        sb.q_pblk.assign(nq + 1, 0);
+        sb.q_img.assign(nq, nullptr);
+        sb.views.resize(nv);
+        sb.run_off.push_back(0);
+        int v = 0;
+        for (int k = 0; k < nq; ++k) {
+            const QuerySpec &Qs = qs[sb.q0 + k];
+            const int64_t cap = inst_cap(ctx, Qs.S, caps[sb.q0 + k]);
+            sb.q_gsub[k + 1] = sb.q_gsub[k] + Qs.S;
+            sb.q_view[k + 1] = sb.q_view[k] + Qs.V;
+            sb.q_pblk[k + 1] = sb.q_pblk[k] + (int32_t)ceil_div(Qs.S, PROJ_THREADS);
+            sb.q_img[k] = Qs.img;
+            for (auto &r : Qs.runs) {
+                sb.run_begin.push_back(r.begin);
+                sb.run_off.push_back(sb.run_off.back() + (r.end - r.begin));
+            }
+            for (int j = 0; j < Qs.V; ++j, ++v) {
+                sb.view_q[v] = k;
+                make_view(Qs.poses.data() + 16 * j, v, sb.views[v]);
+                sb.vd_off[v + 1] = sb.vd_off[v] + Qs.S;
+                sb.io_off[v + 1] = sb.io_off[v] + cap;
+                sb.c1_base[v + 1] = sb.c1_base[v] + (int32_t)ceil_div(Qs.S, SORT_CHUNK);
+                sb.ce_base[v + 1] = sb.ce_base[v] + (int32_t)ceil_div(Qs.S, EMIT_CHUNK);
+                sb.c2_base[v + 1] = sb.c2_base[v] + (int32_t)ceil_div(cap, SORT_CHUNK);
+            }
+        }
+        sb.S_tot = sb.q_gsub[nq];
+        sb.VS = sb.vd_off[nv];
+        sb.VI = sb.io_off[nv];
+        sb.c1 = sb.c1_base[nv];
+        sb.ce = sb.ce_base[nv];
+        sb.c2 = sb.c2_base[nv];
+        sb.pblk = sb.q_pblk[nq];
+        sb.n_runs = (int)sb.run_begin.size();
+        if (sb.run_begin.empty()) sb.run_begin.push_back(0);
+        // table bytes (each array 256-aligned)
+        size_t t = 0;
+        t += align256(4 * (size_t)nv) + 2 * align256(8 * (size_t)(nv + 1)) + 3 * align256(4 * (size_t)(nv + 1));
+        t += align256(8 * (size_t)(nq + 1)) + 2 * align256(4 * (size_t)(nq + 1)) + align256(8 * (size_t)nq);
+        t += align256(8 * sb.run_begin.size()) + align256(8 * sb.run_off.size()) + align256(sizeof(ViewParams) * nv);
+        sb.tab_bytes = t;
+        out.push_back(std::move(sb));
     }
-    memcpy(h_views, vp.data(), sizeof(ViewParams) * V);
-    CK(cudaMemcpyAsync(ctx->runs.p, h_runs, 16 * (size_t)(n_ranges + 1), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->views.p, h_views, sizeof(ViewParams) * V, cudaMemcpyHostToDevice, st));
-    const int64_t *d_run_begin = ctx->runs.as<int64_t>();
-    const int64_t *d_run_off = d_run_begin + n_ranges + 1;
+}
 
+// Write a sub-batch's tables into host staging at base + sb.tab_off and set
+// its device pointers relative to dev.
+static void stage_tables(SubBatch &sb, char *host, char *dev)
+{
+    size_t o = sb.tab_off;
+    auto put = [&](const void *src, size_t bytes) -> char * {
+        memcpy(host + o, src, bytes);
+        char *d = dev + o;
+        o += align256(bytes);
+        return d;
+    };
+    const int nq = sb.q1 - sb.q0, nv = sb.v1 - sb.v0;
+    sb.L.Q = nq;
+    sb.L.V = nv;
+    sb.L.view_q = (const int32_t *)put(sb.view_q.data(), 4 * (size_t)nv);
+    sb.L.vd_off = (const int64_t *)put(sb.vd_off.data(), 8 * (size_t)(nv + 1));
+    sb.L.io_off = (const int64_t *)put(sb.io_off.data(), 8 * (size_t)(nv + 1));
+    sb.L.c1_base = (const int32_t *)put(sb.c1_base.data(), 4 * (size_t)(nv + 1));
+    sb.L.ce_base = (const int32_t *)put(sb.ce_base.data(), 4 * (size_t)(nv + 1));
+    sb.L.c2_base = (const int32_t *)put(sb.c2_base.data(), 4 * (size_t)(nv + 1));
+    sb.L.q_gsub = (const int64_t *)put(sb.q_gsub.data(), 8 * (size_t)(nq + 1));
+    sb.L.q_view = (const int32_t *)put(sb.q_view.data(), 4 * (size_t)(nq + 1));
+    sb.L.q_pblk = (const int32_t *)put(sb.q_pblk.data(), 4 * (size_t)(nq + 1));
+    sb.L.q_img = (const float *const *)put(sb.q_img.data(), 8 * (size_t)nq);
+    sb.d_run_begin = (const int64_t *)put(sb.run_begin.data(), 8 * sb.run_begin.size());
+    sb.d_run_off = (const int64_t *)put(sb.run_off.data(), 8 * sb.run_off.size());
+    sb.d_views = (const ViewParams *)put(sb.views.data(), sizeof(ViewParams) * (size_t)nv);
+}
+
+static void stage_mark(reloc_ctx *ctx, int sbi, int s, cudaStream_t st, bool capturing)
+{
+    if (ctx->prof && !capturing) cudaEventRecord(ctx->ev[(size_t)sbi * (RELOC_STAGE_COUNT + 1) + s], st);
+}
+
+// Enqueue every kernel of one sub-batch on st.  Returns the launch count.
+static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, const CamParams &cp, const CallOut &o,
+                                     cudaStream_t st, bool capturing, int &launches, bool &final_b)
+{
+    const int64_t HW = (int64_t)cp.width * cp.height;
+    const Layout &L = sb.L;
     int *d_overflow = ctx->flags.as<int>();
-    unsigned long long *d_need = (unsigned long long *)(ctx->flags.as<char>() + 8);
+    uint32_t *nvis = ctx->nvis.as<uint32_t>() + sb.v0;
+    uint32_t *ninst = ctx->ninst.as<uint32_t>() + sb.v0;
 
-    // ---- K1 + K2 + depth sort (done once per call) ------------------------
-    stage_mark(ctx, RELOC_STAGE_CULL, st);
-    int launches = 0;
-    if (S > 0) { CK(launch_gather_subset(d_run_begin, d_run_off, n_ranges, S, ctx->gidx.as<uint32_t>(), st)); launches += 1; }
-    stage_mark(ctx, RELOC_STAGE_PROJECT, st);
-    if (S > 0) launches += 1;
-    if (S > 0)
+    stage_mark(ctx, sbi, RELOC_STAGE_CULL, st, capturing);
+    if (sb.S_tot > 0) {
+        CK(launch_gather_subset(sb.d_run_begin, sb.d_run_off, sb.n_runs, sb.S_tot, ctx->gidx.as<uint32_t>(), st));
+        launches += 1;
+    }
+    stage_mark(ctx, sbi, RELOC_STAGE_PROJECT, st, capturing);
+    if (sb.pblk > 0) {
         CK(launch_project(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n, ctx->mean.as<float>() + 2 * ctx->n,
-                          ctx->attr.p, ctx->precision, ctx->sh_degree, ctx->n, ctx->gidx.as<uint32_t>(), S,
-                          ctx->views.as<ViewParams>(), V, cp, ctx->rec.as<float4>(), ctx->rect.as<uint2>(),
-                          ctx->ntiles.as<uint32_t>(), ctx->dkey.as<uint32_t>(), st));
-    stage_mark(ctx, RELOC_STAGE_DEPTH_SORT, st);
-    CK(cudaMemsetAsync(ctx->nvis.p, 0, 4 * (size_t)V, st));
-    if (S > 0) {
+                          ctx->attr.p, ctx->precision, ctx->sh_degree, ctx->n, ctx->gidx.as<uint32_t>(), L, sb.pblk,
+                          sb.d_views, cp, ctx->rec.as<float4>(), ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(),
+                          ctx->dkey.as<uint32_t>(), st));
+        launches += 1;
+    }
+    stage_mark(ctx, sbi, RELOC_STAGE_DEPTH_SORT, st, capturing);
+    CK(cudaMemsetAsync(nvis, 0, 4 * (size_t)L.V, st));
+    CK(cudaMemsetAsync(ninst, 0, 4 * (size_t)L.V, st));
+    if (sb.c1 > 0) {
         RadixPass p{};
-        p.V = V;
-        p.stride = S;
-        p.cps = (int)ceil_div(S, SORT_CHUNK);
+        p.seg_off = L.vd_off;
+        p.chunk_base = L.c1_base;
+        p.n_seg = L.V;
+        p.total_chunks = sb.c1;
         p.hist = ctx->hist1.as<uint32_t>();
         p.mask = 0xFF;
         uint32_t *ka = ctx->k1a.as<uint32_t>(), *va = ctx->v1a.as<uint32_t>();
         uint32_t *kb = ctx->k1b.as<uint32_t>(), *vb = ctx->v1b.as<uint32_t>();
-        // pass 0: dense (view, Gaussian) arrays, invisible pairs dropped
+        // pass 0: dense (view, Gaussian) arrays; culled pairs are dropped
         p.keys_in = ctx->dkey.as<uint32_t>();
         p.vals_in = nullptr;
         p.filt = ctx->ntiles.as<uint32_t>();
         p.len = nullptr;
         p.keys_out = ka;
         p.vals_out = va;
-        p.len_out = ctx->nvis.as<uint32_t>();
+        p.len_out = nvis;
         p.shift = 0;
         CK(launch_radix_pass(p, st));
         launches += 3;
         p.filt = nullptr;
-        p.len = ctx->nvis.as<uint32_t>();
+        p.len = nvis;
         p.len_out = nullptr;
         for (int pass = 1; pass < 4; ++pass) {
             p.shift = 8 * pass;
@@ -575,159 +650,327 @@ static reloc_status run_views(reloc_ctx *ctx, const reloc_range *ranges, int n_r
             launches += 3;
         }
     }
-    const uint32_t *sorted_g = ctx->v1b.as<uint32_t>();   // after 4 passes
-
-    // ---- instance stages (re-run if the instance workspace overflows) -----
-    int retries = 0;
-    for (;;) {
-        const int64_t IS = ctx->inst_stride;
-        const size_t VI = (size_t)V * IS;
-        CKS(ctx->ikA.ensure(4 * VI));
-        CKS(ctx->ivA.ensure(4 * VI));
-        CKS(ctx->ikB.ensure(4 * VI));
-        CKS(ctx->ivB.ensure(4 * VI));
-        CKS(ctx->hist2.ensure(4 * (size_t)radix_hist_words(V, IS)));
-        CK(cudaMemsetAsync(ctx->flags.p, 0, 64, st));
-        CK(cudaMemsetAsync(ctx->ninst.p, 0, 4 * (size_t)V, st));
-        stage_mark(ctx, RELOC_STAGE_EMIT, st);
-        if (S > 0) launches += 3;
-        if (S > 0)
-            CK(launch_emit(sorted_g, ctx->nvis.as<uint32_t>(), ctx->ntiles.as<uint32_t>(), ctx->rect.as<uint2>(), S, V,
-                           cp.ntx, IS, ctx->chunk_sums.as<uint32_t>(), ctx->ikA.as<uint32_t>(),
-                           ctx->ivA.as<uint32_t>(), ctx->ninst.as<uint32_t>(), d_need, d_overflow, st));
-        stage_mark(ctx, RELOC_STAGE_TILE_SORT, st);
-        bool final_b = false;
-        if (S > 0 && cp.tile_bits > 0) {
-            RadixPass p{};
-            p.V = V;
-            p.stride = IS;
-            p.cps = (int)ceil_div(IS, SORT_CHUNK);
-            p.hist = ctx->hist2.as<uint32_t>();
-            p.len = ctx->ninst.as<uint32_t>();
-            const int b1 = cp.tile_bits <= 8 ? cp.tile_bits : (cp.tile_bits + 1) / 2;
-            const int b2 = cp.tile_bits - b1;
-            p.keys_in = ctx->ikA.as<uint32_t>();
-            p.vals_in = ctx->ivA.as<uint32_t>();
-            p.keys_out = ctx->ikB.as<uint32_t>();
-            p.vals_out = ctx->ivB.as<uint32_t>();
-            p.shift = 0;
-            p.mask = (1u << b1) - 1;
+    stage_mark(ctx, sbi, RELOC_STAGE_EMIT, st, capturing);
+    if (sb.ce > 0) {
+        CK(launch_emit(ctx->v1b.as<uint32_t>(), nvis, ctx->ntiles.as<uint32_t>(), ctx->rect.as<uint2>(), L, sb.ce,
+                       cp.ntx, ctx->chunk_sums.as<uint32_t>(), ctx->ikA.as<uint32_t>(), ctx->ivA.as<uint32_t>(), ninst,
+                       d_overflow, st));
+        launches += 3;
+    }
+    stage_mark(ctx, sbi, RELOC_STAGE_TILE_SORT, st, capturing);
+    final_b = false;
+    if (sb.c2 > 0 && sb.ce > 0 && cp.tile_bits > 0) {
+        RadixPass p{};
+        p.seg_off = L.io_off;
+        p.chunk_base = L.c2_base;
+        p.n_seg = L.V;
+        p.total_chunks = sb.c2;
+        p.hist = ctx->hist2.as<uint32_t>();
+        p.len = ninst;
+        const int b1 = cp.tile_bits <= 8 ? cp.tile_bits : (cp.tile_bits + 1) / 2;
+        const int b2 = cp.tile_bits - b1;
+        p.keys_in = ctx->ikA.as<uint32_t>();
+        p.vals_in = ctx->ivA.as<uint32_t>();
+        p.keys_out = ctx->ikB.as<uint32_t>();
+        p.vals_out = ctx->ivB.as<uint32_t>();
+        p.shift = 0;
+        p.mask = (1u << b1) - 1;
+        CK(launch_radix_pass(p, st));
+        launches += 3;
+        final_b = true;
+        if (b2 > 0) {
+            p.keys_in = ctx->ikB.as<uint32_t>();
+            p.vals_in = ctx->ivB.as<uint32_t>();
+            p.keys_out = ctx->ikA.as<uint32_t>();
+            p.vals_out = ctx->ivA.as<uint32_t>();
+            p.shift = b1;
+            p.mask = (1u << b2) - 1;
             CK(launch_radix_pass(p, st));
             launches += 3;
-            final_b = true;
-            if (b2 > 0) {
-                p.keys_in = ctx->ikB.as<uint32_t>();
-                p.vals_in = ctx->ivB.as<uint32_t>();
-                p.keys_out = ctx->ikA.as<uint32_t>();
-                p.vals_out = ctx->ivA.as<uint32_t>();
-                p.shift = b1;
-                p.mask = (1u << b2) - 1;
-                CK(launch_radix_pass(p, st));
-                launches += 3;
-                final_b = false;
-            }
+            final_b = false;
         }
-        const uint32_t *ftile = final_b ? ctx->ikB.as<uint32_t>() : ctx->ikA.as<uint32_t>();
-        const uint32_t *fgauss = final_b ? ctx->ivB.as<uint32_t>() : ctx->ivA.as<uint32_t>();
-        ctx->last_final_b = final_b;
-        stage_mark(ctx, RELOC_STAGE_RANGES, st);
+    }
+    const uint32_t *ftile = final_b ? ctx->ikB.as<uint32_t>() : ctx->ikA.as<uint32_t>();
+    const uint32_t *fgauss = final_b ? ctx->ivB.as<uint32_t>() : ctx->ivA.as<uint32_t>();
+    stage_mark(ctx, sbi, RELOC_STAGE_RANGES, st, capturing);
+    CK(launch_ranges(ftile, ninst, L, cp.n_tiles, ctx->ranges.as<int2>(), d_overflow, st));
+    launches += 1;
+    stage_mark(ctx, sbi, RELOC_STAGE_BLEND, st, capturing);
+    if (o.score) {
+        CK(launch_query_stats(L, 3 * HW, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
+        launches += 2;
+    }
+    CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
+                    o.score ? ctx->partials.as<double>() : nullptr, o.rgb ? o.rgb + (int64_t)sb.v0 * 3 * HW : nullptr,
+                    o.depth ? o.depth + (int64_t)sb.v0 * HW : nullptr, o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr,
+                    nullptr, 0, d_overflow, st));
+    launches += 1;
+    stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
+    if (o.score) {
+        CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, cp.n_tiles, 3 * HW,
+                               ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0, st));
         launches += 1;
-        CK(launch_ranges(ftile, ctx->ninst.as<uint32_t>(), IS, V, cp.n_tiles, ctx->ranges.as<int2>(), d_overflow, st));
-        stage_mark(ctx, RELOC_STAGE_BLEND, st);
-        if (o.query) launches += 2;
-        if (o.query) CK(launch_query_stats(o.query, 3 * HW, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
-        launches += 1;
-        CK(launch_blend(ctx->rec.as<float4>(), S1, fgauss, IS, ctx->ranges.as<int2>(), V, cp, o.query,
-                        o.query ? ctx->partials.as<double>() : nullptr, o.rgb, o.depth, o.alpha, nullptr, d_overflow,
-                        st));
-        stage_mark(ctx, RELOC_STAGE_SCORE, st);
-        if (o.query) {
+        if (o.argmax) {
+            int *vsel = ctx->view_sel.as<int>() + sb.q0;
+            CK(launch_argmax(ctx->scores.as<double>() + sb.v0, L, ctx->best.as<int>() + sb.q0,
+                             ctx->best_score.as<double>() + sb.q0, vsel, st));
             launches += 1;
-            CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), V, cp.n_tiles, 3 * HW,
-                                   ctx->scores.as<double>(), ctx->degen.as<int>(), st));
-            if (o.export_best) {
+            if (o.brgb || o.bdepth || o.balpha) {
+                const int nq = sb.q1 - sb.q0;
+                CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
+                                o.brgb ? o.brgb + (int64_t)sb.q0 * 3 * HW : nullptr,
+                                o.bdepth ? o.bdepth + (int64_t)sb.q0 * HW : nullptr,
+                                o.balpha ? o.balpha + (int64_t)sb.q0 * HW : nullptr, vsel, nq, d_overflow, st));
                 launches += 1;
-                CK(launch_argmax(ctx->scores.as<double>(), V, ctx->best.as<int>(), ctx->best_score.as<double>(), st));
-                if (o.brgb || o.bdepth || o.balpha) launches += 1;
-                if (o.brgb || o.bdepth || o.balpha)
-                    CK(launch_blend(ctx->rec.as<float4>(), S1, fgauss, IS, ctx->ranges.as<int2>(), V, cp, nullptr,
-                                    nullptr, o.brgb, o.bdepth, o.balpha, ctx->best.as<int>(), d_overflow, st));
             }
         }
-        stage_mark(ctx, RELOC_STAGE_COUNT, st);
-        // ---- readback -----------------------------------------------------
-        CK(cudaMemcpyAsync(&rb->overflow, d_overflow, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&rb->need, d_need, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_nvis, ctx->nvis.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_ninst, ctx->ninst.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
-        if (o.query) {
-            CK(cudaMemcpyAsync(h_scores, ctx->scores.p, 8 * (size_t)V, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(h_degen, ctx->degen.p, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
-            if (o.export_best) {
-                CK(cudaMemcpyAsync(&rb->best, ctx->best.p, 4, cudaMemcpyDeviceToHost, st));
-                CK(cudaMemcpyAsync(&rb->best_score, ctx->best_score.p, 8, cudaMemcpyDeviceToHost, st));
+    }
+    stage_mark(ctx, sbi, RELOC_STAGE_COUNT, st, capturing);
+    return RELOC_OK;
+}
+
+static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const reloc_camera *cam, cudaStream_t ust,
+                              CallOut &o, bool allow_graph)
+{
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    const int Q = (int)qs.size();
+    if (Q < 1) return fail(RELOC_EINVAL, "no queries");
+    int64_t Vtot = 0;
+    for (auto &q : qs) {
+        if (q.V < 1 || q.V > 4096) return fail(RELOC_EINVAL, "a query has %d views (1..4096 allowed)", q.V);
+        if (o.score && !q.img) return fail(RELOC_EINVAL, "query image is NULL");
+        Vtot += q.V;
+        q.S = 0;
+        for (auto &r : q.runs) {
+            if (r.begin < 0 || r.end < r.begin || r.end > ctx->n)
+                return fail(RELOC_EINVAL, "range [%lld, %lld) outside the map", (long long)r.begin, (long long)r.end);
+            q.S += r.end - r.begin;
+        }
+        if (q.S > (int64_t)UINT32_MAX / 4) return fail(RELOC_EINVAL, "subset too large");
+        for (int j = 0; j < q.V; ++j)
+            for (int k = 0; k < 16; ++k)
+                if (!std::isfinite(q.poses[16 * j + k])) return fail(RELOC_ENUMERIC, "non-finite pose %d", j);
+    }
+    if (Vtot > (1 << 24)) return fail(RELOC_EINVAL, "too many views in one call");
+    CamParams cp;
+    CKS(make_cam(ctx, cam, cp));
+    CK(cudaSetDevice(ctx->device));
+    ctx->last_valid = false;
+    const int64_t HW = (int64_t)cp.width * cp.height;
+    const bool graph = allow_graph && ctx->use_graph;
+
+    std::vector<int64_t> caps(Q, 0);
+    std::vector<SubBatch> sbs;
+    int retries = 0, launches = 0;
+    bool final_b = false;
+    for (;;) {
+        plan_batches(ctx, qs, caps, cp, sbs);
+        // ---- workspace: the largest sub-batch --------------------------------
+        int64_t S_tot = 1, VS = 1, VI = 1, c1 = 1, ce = 1, c2 = 1, V = 1, Qm = 1;
+        size_t tab = 0;
+        for (auto &sb : sbs) {
+            S_tot = std::max(S_tot, sb.S_tot);
+            VS = std::max(VS, sb.VS);
+            VI = std::max(VI, sb.VI);
+            c1 = std::max<int64_t>(c1, sb.c1);
+            ce = std::max<int64_t>(ce, sb.ce);
+            c2 = std::max<int64_t>(c2, sb.c2);
+            V = std::max<int64_t>(V, sb.v1 - sb.v0);
+            Qm = std::max<int64_t>(Qm, sb.q1 - sb.q0);
+            sb.tab_off = tab;
+            tab += sb.tab_bytes;
+        }
+        CKS(ctx->gidx.ensure(4 * (size_t)S_tot));
+        CKS(ctx->rec.ensure(48 * (size_t)VS));
+        CKS(ctx->rect.ensure(8 * (size_t)VS));
+        CKS(ctx->ntiles.ensure(4 * (size_t)VS));
+        CKS(ctx->dkey.ensure(4 * (size_t)VS));
+        CKS(ctx->k1a.ensure(4 * (size_t)VS));
+        CKS(ctx->v1a.ensure(4 * (size_t)VS));
+        CKS(ctx->k1b.ensure(4 * (size_t)VS));
+        CKS(ctx->v1b.ensure(4 * (size_t)VS));
+        CKS(ctx->hist1.ensure(4 * (size_t)RADIX * c1));
+        CKS(ctx->chunk_sums.ensure(4 * (size_t)ce));
+        CKS(ctx->ikA.ensure(4 * (size_t)VI));
+        CKS(ctx->ivA.ensure(4 * (size_t)VI));
+        CKS(ctx->ikB.ensure(4 * (size_t)VI));
+        CKS(ctx->ivB.ensure(4 * (size_t)VI));
+        CKS(ctx->hist2.ensure(4 * (size_t)RADIX * c2));
+        CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
+        CKS(ctx->partials.ensure(24 * (size_t)V * cp.n_tiles));
+        CKS(ctx->qpart.ensure(16 * 152 * (size_t)Qm));
+        CKS(ctx->qstats.ensure(16 * (size_t)Qm));
+        CKS(ctx->nvis.ensure(4 * (size_t)Vtot));
+        CKS(ctx->ninst.ensure(4 * (size_t)Vtot));
+        CKS(ctx->scores.ensure(8 * (size_t)Vtot));
+        CKS(ctx->degen.ensure(4 * (size_t)Vtot));
+        CKS(ctx->best.ensure(4 * (size_t)Q));
+        CKS(ctx->best_score.ensure(8 * (size_t)Q));
+        CKS(ctx->view_sel.ensure(4 * (size_t)Q));
+        CKS(ctx->flags.ensure(64));
+        CKS(ctx->tables.ensure(tab));
+        // pinned staging: tables, then readback
+        const size_t rb_off = align256(tab);
+        const size_t rb_bytes = 64 + (4 + 4 + 8 + 4) * (size_t)Vtot + (4 + 8) * (size_t)Q;
+        CKS(ctx->pin.ensure(rb_off + rb_bytes));
+        char *pin = (char *)ctx->pin.p;
+        for (auto &sb : sbs) stage_tables(sb, pin, ctx->tables.as<char>());
+        // readback block: doubles first (8-byte aligned), then 32-bit words
+        int *h_overflow = (int *)(pin + rb_off);
+        double *h_scores = (double *)(pin + rb_off + 64);
+        double *h_bscore = h_scores + Vtot;
+        uint32_t *h_nvis = (uint32_t *)(h_bscore + Q);
+        uint32_t *h_ninst = h_nvis + Vtot;
+        int *h_degen = (int *)(h_ninst + Vtot);
+        int *h_best = h_degen + Vtot;
+        if (ctx->prof) {
+            const size_t need = sbs.size() * (RELOC_STAGE_COUNT + 1);
+            while (ctx->ev.size() < need) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->ev.push_back(e);
             }
+        }
+        // ---- enqueue -------------------------------------------------------------
+        cudaStream_t st = ust;
+        if (graph) {
+            CK(cudaEventRecord(ctx->ev_in, ust));
+            CK(cudaStreamWaitEvent(ctx->cap_stream, ctx->ev_in, 0));
+            st = ctx->cap_stream;
+        }
+        CK(cudaMemcpyAsync(ctx->tables.p, pin, tab, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(ctx->flags.p, 0, 64, st));
+        launches = 0;
+        if (graph) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            reloc_status rs = RELOC_OK;
+            for (size_t k = 0; k < sbs.size() && rs == RELOC_OK; ++k)
+                rs = enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, true, launches, final_b);
+            cudaError_t ce_ = cudaStreamEndCapture(st, &g);
+            if (rs != RELOC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rs;
+            }
+            if (ce_ != cudaSuccess) return fail(RELOC_ECUDA, "graph capture: %s", cudaGetErrorString(ce_));
+            ce_ = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (ce_ != cudaSuccess) return fail(RELOC_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce_));
+            ce_ = cudaGraphLaunch(ge, st);
+            cudaGraphExecDestroy(ge);
+            if (ce_ != cudaSuccess) return fail(RELOC_ECUDA, "graph launch: %s", cudaGetErrorString(ce_));
+        } else {
+            for (size_t k = 0; k < sbs.size(); ++k) CKS(enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, false, launches, final_b));
+        }
+        // ---- readback --------------------------------------------------------------
+        CK(cudaMemcpyAsync(h_overflow, ctx->flags.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_nvis, ctx->nvis.p, 4 * (size_t)Vtot, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_ninst, ctx->ninst.p, 4 * (size_t)Vtot, cudaMemcpyDeviceToHost, st));
+        if (o.score) {
+            CK(cudaMemcpyAsync(h_scores, ctx->scores.p, 8 * (size_t)Vtot, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(h_degen, ctx->degen.p, 4 * (size_t)Vtot, cudaMemcpyDeviceToHost, st));
+            if (o.argmax) {
+                CK(cudaMemcpyAsync(h_best, ctx->best.p, 4 * (size_t)Q, cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(h_bscore, ctx->best_score.p, 8 * (size_t)Q, cudaMemcpyDeviceToHost, st));
+            }
+        }
+        if (graph) {
+            CK(cudaEventRecord(ctx->ev_out, st));
+            CK(cudaStreamWaitEvent(ust, ctx->ev_out, 0));
         }
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
-        if (ctx->prof) {
-            for (int s = 0; s < RELOC_STAGE_COUNT; ++s) {
-                float ms = 0;
-                if (cudaEventElapsedTime(&ms, ctx->ev[s], ctx->ev[s + 1]) == cudaSuccess) {
-                    ctx->stage_ms[s] += ms;
-                    ctx->stage_calls[s] += 1;
-                } else {
-                    cudaGetLastError();
+        if (ctx->prof && !graph) {
+            for (size_t k = 0; k < sbs.size(); ++k)
+                for (int s = 0; s < RELOC_STAGE_COUNT; ++s) {
+                    float ms = 0;
+                    const size_t e0 = k * (RELOC_STAGE_COUNT + 1) + s;
+                    if (cudaEventElapsedTime(&ms, ctx->ev[e0], ctx->ev[e0 + 1]) == cudaSuccess) {
+                        ctx->stage_ms[s] += ms;
+                        if (k == 0) ctx->stage_calls[s] += 1;
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
+        }
+        if (!*h_overflow) {
+            // learn the instance ratio for later calls (capacity = ratio * S + slack)
+            int64_t vglob = 0;
+            for (int q = 0; q < Q; ++q)
+                for (int j = 0; j < qs[q].V; ++j, ++vglob)
+                    if (qs[q].S > 0)
+                        ctx->inst_ratio = std::max(ctx->inst_ratio, 1.15 * (double)h_ninst[vglob] / (double)qs[q].S);
+            // results
+            ctx->counts = reloc_counts{};
+            ctx->counts.n_views = Vtot;
+            for (auto &q : qs) ctx->counts.n_gauss += q.S;
+            ctx->last_ninst.assign(h_ninst, h_ninst + (sbs[0].v1 - sbs[0].v0));
+            for (int64_t v = 0; v < Vtot; ++v) {
+                ctx->counts.n_visible += h_nvis[v];
+                ctx->counts.n_instances += h_ninst[v];
+            }
+            ctx->counts.inst_stride = sbs[0].io_off.size() > 1 ? sbs[0].io_off[1] - sbs[0].io_off[0] : 0;
+            ctx->counts.retries = retries;
+            ctx->counts.kernel_launches = launches;
+            if (o.score) {
+                o.scores.assign(h_scores, h_scores + Vtot);
+                o.degen.assign(h_degen, h_degen + Vtot);
+                if (o.argmax) {
+                    o.best.assign(h_best, h_best + Q);
+                    o.best_score.assign(h_bscore, h_bscore + Q);
                 }
             }
+            break;
         }
-        if (!rb->overflow) break;
+        // ---- overflow: grow the capacity of every query that did not fit -------
         if (++retries > 3) return fail(RELOC_EOVERFLOW, "tile-instance workspace still too small after %d grows", retries);
-        int64_t grow = (int64_t)rb->need + rb->need / 4 + 4096;
-        ctx->inst_stride = ceil_div(grow, SORT_CHUNK) * SORT_CHUNK;
-    }
-
-    // ---- results ------------------------------------------------------------
-    ctx->last_V = V;
-    ctx->last_S = S;
-    ctx->last_cam = cp;
-    ctx->last_valid = true;
-    ctx->last_ninst.assign(V, 0);
-    reloc_counts &c = ctx->counts;
-    memset(&c, 0, sizeof c);
-    c.n_views = V;
-    c.n_gauss = S;
-    c.inst_stride = ctx->inst_stride;
-    c.retries = retries;
-    c.kernel_launches = launches;
-    for (int v = 0; v < V; ++v) {
-        c.n_visible += h_nvis[v];
-        c.n_instances += h_ninst[v];
-        ctx->last_ninst[v] = h_ninst[v];
-    }
-    if (o.query) {
-        if (o.scores_host) memcpy(o.scores_host, h_scores, 8 * (size_t)V);
-        if (o.degen_host) memcpy(o.degen_host, h_degen, 4 * (size_t)V);
-        if (o.export_best) {
-            o.best = rb->best;
-            o.best_score = rb->best_score;
+        int64_t vglob = 0;
+        for (int q = 0; q < Q; ++q) {
+            int64_t need = 0;
+            for (int j = 0; j < qs[q].V; ++j, ++vglob) need = std::max<int64_t>(need, h_ninst[vglob]);
+            const int64_t cap = inst_cap(ctx, qs[q].S, caps[q]);
+            if (need > cap) caps[q] = need + need / 8 + 4096;
+            if (qs[q].S > 0) ctx->inst_ratio = std::max(ctx->inst_ratio, 1.15 * (double)need / (double)qs[q].S);
         }
     }
+    // ---- debug export state (first sub-batch) ----------------------------------
+    ctx->last_V = sbs[0].v1 - sbs[0].v0;
+    ctx->last_S = qs[0].S;
+    ctx->last_cam = cp;
+    ctx->last_final_b = final_b;
+    ctx->last_io_off = sbs[0].io_off;
+    ctx->last_vd_off = sbs[0].vd_off;
+    ctx->last_valid = sbs.size() == 1 && sbs[0].q1 - sbs[0].q0 == 1;
     return RELOC_OK;
 }
 
 // ============================================================== entry points ==
+
+static reloc_status one_query(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges, const double *poses, int V,
+                              QuerySpec &q)
+{
+    if (V < 1 || V > 4096) return fail(RELOC_EINVAL, "n_views %d not in 1..4096", V);
+    if (!poses) return fail(RELOC_EINVAL, "poses is NULL");
+    if (n_ranges < 0 || (n_ranges > 0 && !ranges)) return fail(RELOC_EINVAL, "bad ranges");
+    q.runs.assign(ranges, ranges + n_ranges);
+    q.V = V;
+    q.poses.assign(poses, poses + 16 * (size_t)V);
+    return RELOC_OK;
+}
 
 extern "C" reloc_status reloc_render(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges, const double *poses,
                                      int n_views, const reloc_camera *cam, float *rgb_dev, float *depth_dev,
                                      float *alpha_dev, void *stream)
 {
     if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    std::vector<QuerySpec> qs(1);
+    CKS(one_query(ctx, ranges, n_ranges, poses, n_views, qs[0]));
     CallOut o;
     o.rgb = rgb_dev;
     o.depth = depth_dev;
     o.alpha = alpha_dev;
-    return run_views(ctx, ranges, n_ranges, poses, n_views, cam, (cudaStream_t)stream, o);
+    return run_batch(ctx, qs, cam, (cudaStream_t)stream, o, false);
 }
 
 extern "C" reloc_status reloc_score(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges, const double *poses,
@@ -736,23 +979,26 @@ extern "C" reloc_status reloc_score(reloc_ctx *ctx, const reloc_range *ranges, i
 {
     if (!ctx) return fail(RELOC_EINVAL, "NULL context");
     if (!query_dev || !scores_host) return fail(RELOC_EINVAL, "query_dev and scores_host are required");
+    std::vector<QuerySpec> qs(1);
+    CKS(one_query(ctx, ranges, n_ranges, poses, n_views, qs[0]));
+    qs[0].img = query_dev;
     CallOut o;
-    o.query = query_dev;
-    o.scores_host = scores_host;
-    o.degen_host = degenerate_host;
-    return run_views(ctx, ranges, n_ranges, poses, n_views, cam, (cudaStream_t)stream, o);
+    o.score = true;
+    CKS(run_batch(ctx, qs, cam, (cudaStream_t)stream, o, false));
+    memcpy(scores_host, o.scores.data(), sizeof(double) * n_views);
+    if (degenerate_host) memcpy(degenerate_host, o.degen.data(), sizeof(int) * n_views);
+    return RELOC_OK;
 }
 
-static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose, double radius,
-                                  const reloc_grid *grid, const reloc_camera *cam, reloc_result *out,
-                                  double *scores_host, float *brgb, float *bdepth, float *balpha, cudaStream_t st)
+// Block selection + candidate grid of one localization query.
+static reloc_status make_localize_query(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose,
+                                        double radius, const reloc_grid *grid, QuerySpec &q)
 {
-    if (!ctx || !query_dev || !coarse_pose || !grid || !cam || !out) return fail(RELOC_EINVAL, "NULL argument");
-    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    if (!query_dev || !coarse_pose || !grid) return fail(RELOC_EINVAL, "NULL argument");
     if (grid->nx < 1 || grid->ny < 1 || grid->nyaw < 1 || (int64_t)grid->nx * grid->ny * grid->nyaw > 4096)
         return fail(RELOC_EINVAL, "grid %dx%dx%d not in 1..4096 candidates", grid->nx, grid->ny, grid->nyaw);
-    if (!std::isfinite(grid->step_xy) || !std::isfinite(grid->step_yaw_deg))
-        return fail(RELOC_ENUMERIC, "non-finite grid step");
+    if (!std::isfinite(grid->step_xy) || !std::isfinite(grid->step_yaw_deg) || !std::isfinite(radius))
+        return fail(RELOC_ENUMERIC, "non-finite grid step or radius");
     for (int k = 0; k < 16; ++k)
         if (!std::isfinite(coarse_pose[k])) return fail(RELOC_ENUMERIC, "non-finite coarse pose");
     const double *W = coarse_pose;
@@ -760,33 +1006,46 @@ static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const 
     const double Cy = -(W[1] * W[3] + W[5] * W[7] + W[9] * W[11]);
     std::vector<int> ids;
     ctx->blocks.range(Cx, Cy, radius, ids);
-    std::vector<reloc_range> runs;
-    merge_runs(ctx->blocks, ids, runs);
-    std::vector<double> poses;
-    grid_poses(coarse_pose, *grid, poses);
-    const int V = grid->nx * grid->ny * grid->nyaw;
-    std::vector<int> degen(V);
-    std::vector<double> sc(V);
+    merge_runs(ctx->blocks, ids, q.runs);
+    q.n_blocks = (int)ids.size();
+    grid_poses(coarse_pose, *grid, q.poses);
+    q.V = grid->nx * grid->ny * grid->nyaw;
+    q.img = query_dev;
+    return RELOC_OK;
+}
+
+static void fill_result(const QuerySpec &q, const CallOut &o, int qi, int v0, reloc_result *out)
+{
+    memset(out, 0, sizeof *out);
+    const int b = o.best[qi];
+    out->best_index = b;
+    out->n_candidates = q.V;
+    out->best_score = o.best_score[qi];
+    if (b >= 0 && b < q.V) {
+        memcpy(out->best_pose, q.poses.data() + 16 * b, sizeof(double) * 16);
+        out->degenerate = o.degen[v0 + b];
+    }
+    out->n_gauss = q.S;
+    out->n_blocks = q.n_blocks;
+}
+
+static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose, double radius,
+                                  const reloc_grid *grid, const reloc_camera *cam, reloc_result *out,
+                                  double *scores_host, float *brgb, float *bdepth, float *balpha, cudaStream_t st)
+{
+    if (!ctx || !cam || !out) return fail(RELOC_EINVAL, "NULL argument");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    std::vector<QuerySpec> qs(1);
+    CKS(make_localize_query(ctx, query_dev, coarse_pose, radius, grid, qs[0]));
     CallOut o;
-    o.query = query_dev;
-    o.export_best = true;
+    o.score = true;
+    o.argmax = true;
     o.brgb = brgb;
     o.bdepth = bdepth;
     o.balpha = balpha;
-    o.scores_host = sc.data();
-    o.degen_host = degen.data();
-    CKS(run_views(ctx, runs.data(), (int)runs.size(), poses.data(), V, cam, st, o));
-    memset(out, 0, sizeof *out);
-    out->best_index = o.best;
-    out->n_candidates = V;
-    out->best_score = o.best_score;
-    if (o.best >= 0 && o.best < V) {
-        memcpy(out->best_pose, poses.data() + 16 * o.best, sizeof(double) * 16);
-        out->degenerate = degen[o.best];
-    }
-    out->n_gauss = ctx->counts.n_gauss;
-    out->n_blocks = (int)ids.size();
-    if (scores_host) memcpy(scores_host, sc.data(), sizeof(double) * V);
+    CKS(run_batch(ctx, qs, cam, st, o, false));
+    fill_result(qs[0], o, 0, 0, out);
+    if (scores_host) memcpy(scores_host, o.scores.data(), sizeof(double) * qs[0].V);
     return RELOC_OK;
 }
 
@@ -797,6 +1056,41 @@ extern "C" reloc_status reloc_localize(reloc_ctx *ctx, const float *query_dev, c
 {
     return localize_impl(ctx, query_dev, coarse_pose, radius, grid, cam, out, scores_host, best_rgb_dev,
                          best_depth_dev, best_alpha_dev, (cudaStream_t)stream);
+}
+
+extern "C" reloc_status reloc_localize_batch(reloc_ctx *ctx, const reloc_query *queries, int n_queries,
+                                             const reloc_camera *cam, reloc_result *results, double *scores_host,
+                                             float *best_rgb_dev, float *best_depth_dev, void *stream)
+{
+    if (!ctx || !queries || !cam || !results) return fail(RELOC_EINVAL, "NULL argument");
+    if (n_queries < 1) return fail(RELOC_EINVAL, "n_queries %d < 1", n_queries);
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    std::vector<QuerySpec> qs(n_queries);
+    for (int i = 0; i < n_queries; ++i)
+        CKS(make_localize_query(ctx, queries[i].query_dev, queries[i].coarse_pose, queries[i].radius,
+                                &queries[i].grid, qs[i]));
+    CallOut o;
+    o.score = true;
+    o.argmax = true;
+    o.brgb = best_rgb_dev;
+    o.bdepth = best_depth_dev;
+    CKS(run_batch(ctx, qs, cam, (cudaStream_t)stream, o, true));
+    int v0 = 0;
+    for (int i = 0; i < n_queries; ++i) {
+        fill_result(qs[i], o, i, v0, &results[i]);
+        v0 += qs[i].V;
+    }
+    if (scores_host) memcpy(scores_host, o.scores.data(), sizeof(double) * o.scores.size());
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_set_batch_options(reloc_ctx *ctx, const reloc_batch_options *opt)
+{
+    if (!ctx || !opt) return fail(RELOC_EINVAL, "NULL argument");
+    if (opt->mem_budget < ((int64_t)64 << 20)) return fail(RELOC_EINVAL, "mem_budget below 64 MiB");
+    ctx->use_graph = opt->use_graph != 0;
+    ctx->mem_budget = opt->mem_budget;
+    return RELOC_OK;
 }
 
 extern "C" reloc_status reloc_localize_host(reloc_ctx *ctx, const float *query_host, const double *coarse_pose,
@@ -871,21 +1165,21 @@ extern "C" reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, i
                                            int32_t *ranges_dev, void *stream)
 {
     if (!ctx) return fail(RELOC_EINVAL, "NULL context");
-    if (!ctx->last_valid) return fail(RELOC_EINVAL, "no completed call to export");
+    if (!ctx->last_valid) return fail(RELOC_EINVAL, "no completed single-query call to export");
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     const int64_t VS = (int64_t)ctx->last_V * ctx->last_S;
-    const size_t VI = (size_t)ctx->last_V * ctx->inst_stride;
+    const size_t VI = (size_t)ctx->last_io_off.back();
     if (records_dev && VS > 0)
         CK(cudaMemcpyAsync(records_dev, ctx->rec.p, 48 * (size_t)VS, cudaMemcpyDeviceToDevice, st));
     if (rects_dev && VS > 0) {
         k_unpack_rect<<<(unsigned)ceil_div(VS, 256), 256, 0, st>>>(ctx->rect.as<uint2>(), VS, rects_dev);
         CK(cudaGetLastError());
     }
-    if (inst_tiles_dev)
+    if (inst_tiles_dev && VI)
         CK(cudaMemcpyAsync(inst_tiles_dev, ctx->last_final_b ? ctx->ikB.p : ctx->ikA.p, 4 * VI,
                            cudaMemcpyDeviceToDevice, st));
-    if (inst_gauss_dev)
+    if (inst_gauss_dev && VI)
         CK(cudaMemcpyAsync(inst_gauss_dev, ctx->last_final_b ? ctx->ivB.p : ctx->ivA.p, 4 * VI,
                            cudaMemcpyDeviceToDevice, st));
     if (ranges_dev)

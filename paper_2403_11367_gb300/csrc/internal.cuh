@@ -55,68 +55,105 @@ __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { ret
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
+// ---- per-call layout ----------------------------------------------------------
+// A call renders Q queries (each: a Gaussian subset and V_q candidate views)
+// in one pass of every stage.  Views are numbered 0..V-1 across the queries
+// of the call; every per-(view, Gaussian) array places view v at vd_off[v]
+// (length S of its query) and every per-(view, instance) array at io_off[v]
+// (capacity io_off[v+1] - io_off[v]).  The chunk bases map a block index to
+// its view and chunk for the sort, emission and scan kernels.  All tables are
+// built on the host and live in device memory for the call.
+struct Layout {
+    int Q, V;
+    const int32_t *view_q;     // [V]   query of each view
+    const int64_t *vd_off;     // [V+1] dense offsets
+    const int64_t *io_off;     // [V+1] instance offsets
+    const int32_t *c1_base;    // [V+1] depth-sort chunk base (SORT_CHUNK)
+    const int32_t *ce_base;    // [V+1] emission chunk base (EMIT_CHUNK)
+    const int32_t *c2_base;    // [V+1] tile-sort chunk base (SORT_CHUNK)
+    const int64_t *q_gsub;     // [Q+1] subset offsets into the gathered index list
+    const int32_t *q_view;     // [Q+1] first view of each query
+    const int32_t *q_pblk;     // [Q+1] projection block base
+    const float *const *q_img; // [Q]   query images (device pointers) or null
+};
+
+// Largest s in [0, n] with base[s] <= x (base ascending): the segment of x.
+__device__ __forceinline__ int find_segment(const int32_t *base, int n, int x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int PROJ_THREADS = 128;
+
 // ---- launchers (each returns the launch error) -------------------------------
 
 // K1: subset gather.  run_begin/run_off: n_runs block-ordered runs and their
-// exclusive prefix of lengths (device); writes gidx[S] map positions.
+// exclusive prefix of lengths (device); writes gidx[total] map positions.
 cudaError_t launch_gather_subset(const int64_t *run_begin, const int64_t *run_off, int n_runs,
-                                 int64_t S, uint32_t *gidx, cudaStream_t st);
+                                 int64_t total, uint32_t *gidx, cudaStream_t st);
 
-// K2: projection of S Gaussians into V views.
+// K2: projection of every query's subset into that query's views.
+// n_blocks = q_pblk[Q] (host copy).
 cudaError_t launch_project(const float *mx, const float *my, const float *mz, const void *attr,
                            int precision, int sh_degree, int64_t n_map, const uint32_t *gidx,
-                           int64_t S, const ViewParams *views, int V, const CamParams &cam,
-                           float4 *rec, uint2 *rect, uint32_t *ntiles, uint32_t *dkey,
-                           cudaStream_t st);
+                           const Layout &L, int n_blocks, const ViewParams *views, const CamParams &cam,
+                           float4 *rec, uint2 *rect, uint32_t *ntiles, uint32_t *dkey, cudaStream_t st);
 
-// Radix sort pass over V segments of stride `stride`.  filt != null: first
-// pass over dense (view, Gaussian) arrays keeping items with filt != 0 and
-// implicit values (the Gaussian index); len_out receives the kept counts.
-// len == null: every segment is `stride` long.
+// Stable LSD radix sort pass over segments (views).  Segment s holds
+// seg_off[s+1] - seg_off[s] slots at seg_off[s], of which len[s] are valid
+// (len null: all).  filt != null: pass over dense arrays keeping items with
+// filt != 0 and implicit values (the index in the segment); len_out receives
+// the kept counts.  hist: RADIX words per chunk.
 struct RadixPass {
     const uint32_t *keys_in, *vals_in, *filt, *len;
-    uint32_t *keys_out, *vals_out, *len_out;
-    uint32_t *hist;           // [V][RADIX][cps] scratch
-    int64_t stride;
-    int V, cps, shift;
+    uint32_t *keys_out, *vals_out, *len_out, *hist;
+    const int64_t *seg_off;
+    const int32_t *chunk_base;
+    int n_seg, total_chunks, shift;
     uint32_t mask;
 };
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
-int64_t radix_hist_words(int V, int64_t stride);
 
-// K3: scan of tile counts in depth order + instance emission.
-// sorted_g: [V][S] Gaussian indices in depth order (n_vis[v] valid),
-// ntiles/rect: dense [V][S]; writes inst_tile/inst_gauss [V][inst_stride] in
-// (depth, index) order and n_inst[V].  If a view needs more than inst_stride
-// entries nothing is emitted for it, *overflow is set and *need raised.
+// K3: scan of tile counts in depth order + instance emission.  sorted_g holds
+// each view's visible Gaussians in depth order (n_vis[v] at vd_off[v]);
+// writes (tile, Gaussian) entries at io_off[v] in (depth, index) order and
+// n_inst[V].  A view needing more than its capacity emits nothing and sets
+// *overflow.  n_chunks = ce_base[V] (host copy).
 cudaError_t launch_emit(const uint32_t *sorted_g, const uint32_t *n_vis, const uint32_t *ntiles,
-                        const uint2 *rect, int64_t S, int V, int ntx, int64_t inst_stride,
-                        uint32_t *chunk_sums, uint32_t *inst_tile, uint32_t *inst_gauss,
-                        uint32_t *n_inst, unsigned long long *need, int *overflow, cudaStream_t st);
-int64_t emit_chunk_words(int V, int64_t S);
+                        const uint2 *rect, const Layout &L, int n_chunks, int ntx, uint32_t *chunk_sums,
+                        uint32_t *inst_tile, uint32_t *inst_gauss, uint32_t *n_inst, int *overflow,
+                        cudaStream_t st);
 
-// K5: per (view, tile) [begin, end) into the sorted instance list.
-cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, int64_t inst_stride,
-                          int V, int n_tiles, int2 *ranges, const int *overflow, cudaStream_t st);
+// K5: per (view, tile) [begin, end) into the view's sorted instance list.
+cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, const Layout &L, int n_tiles,
+                          int2 *ranges, const int *overflow, cudaStream_t st);
 
-// Query statistics S_q, S_qq over 3*H*W samples -> qstats[2] (double).
-cudaError_t launch_query_stats(const float *query, int64_t n, double *block_scratch, double *qstats,
+// Query statistics S_q, S_qq over n samples of each of the Q query images
+// -> qstats[Q][2] (double).  block_scratch: Q * 2 * 152 doubles.
+cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch, double *qstats,
                                cudaStream_t st);
 
-// K6 (+ K7 partials): blend every (view, tile); optional image export and NCC
-// partials [V][n_tiles][3] = {S_r, S_rr, S_rq}.  view_sel != null: render only
-// the view *view_sel (grid has one view), writing images at view slot 0.
-cudaError_t launch_blend(const float4 *rec, int64_t S, const uint32_t *inst_gauss, int64_t inst_stride,
-                         const int2 *ranges, int V, const CamParams &cam, const float *query,
-                         double *partials, float *rgb, float *depth, float *alpha,
-                         const int *view_sel, const int *overflow, cudaStream_t st);
+// K6 (+ K7 partials): blend every (view, tile) of the layout; optional image
+// export (slot = view) and NCC partials [V][n_tiles][3] = {S_r, S_rr, S_rq}.
+// view_sel != null: blend only the n_sel views view_sel[0..n_sel), image
+// slot k for view_sel[k].
+cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                         const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
+                         const int *view_sel, int n_sel, const int *overflow, cudaStream_t st);
 
-// K7: NCC per view from partials and the query statistics.
-cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, int V, int n_tiles,
+// K7: NCC per view from partials and its query's statistics.
+cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_tiles,
                                 int64_t n_samples, double *scores, int *degenerate, cudaStream_t st);
 
-// K8: argmax (lowest index on ties) -> best[0] = index, best_score[0].
-cudaError_t launch_argmax(const double *scores, int V, int *best, double *best_score, cudaStream_t st);
+// K8: per query, argmax over its views (lowest index on ties):
+// best[q] (index within the query), best_score[q], view_sel[q] (view index).
+cudaError_t launch_argmax(const double *scores, const Layout &L, int *best, double *best_score, int *view_sel,
+                          cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns st.
 int reloc_internal_fail(int st, const char *msg);

@@ -26,11 +26,11 @@ __global__ void k_gather_subset(const int64_t *__restrict__ run_begin, const int
     gidx[i] = (uint32_t)(run_begin[lo] + (i - run_off[lo]));
 }
 
-cudaError_t launch_gather_subset(const int64_t *run_begin, const int64_t *run_off, int n_runs, int64_t S,
+cudaError_t launch_gather_subset(const int64_t *run_begin, const int64_t *run_off, int n_runs, int64_t total,
                                  uint32_t *gidx, cudaStream_t st)
 {
-    if (S <= 0) return cudaSuccess;
-    k_gather_subset<<<(unsigned)ceil_div(S, 256), 256, 0, st>>>(run_begin, run_off, n_runs, S, gidx);
+    if (total <= 0 || n_runs <= 0) return cudaSuccess;
+    k_gather_subset<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(run_begin, run_off, n_runs, total, gidx);
     return cudaGetLastError();
 }
 
@@ -76,28 +76,31 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
     }
 }
 
-constexpr int PROJ_THREADS = 128;
 constexpr int PROJ_VIEW_BATCH = 128;
 
 template <typename T, int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS)
 k_project(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
-          const T *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, int64_t S,
-          const ViewParams *__restrict__ views, int V, CamParams cam, float4 *__restrict__ rec,
+          const T *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, Layout L,
+          const ViewParams *__restrict__ views, CamParams cam, float4 *__restrict__ rec,
           uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles, uint32_t *__restrict__ dkey)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ ViewParams s_view[PROJ_VIEW_BATCH];
 
-    const int64_t i = (int64_t)blockIdx.x * PROJ_THREADS + threadIdx.x;
+    // this block's query and Gaussians
+    const int qi = find_segment(L.q_pblk, L.Q, (int)blockIdx.x);
+    const int64_t S = L.q_gsub[qi + 1] - L.q_gsub[qi];
+    const int64_t i = (int64_t)(blockIdx.x - L.q_pblk[qi]) * PROJ_THREADS + threadIdx.x;
     const bool active = i < S;
+    const int v_begin = L.q_view[qi], V = L.q_view[qi + 1] - v_begin;
 
     // ---- per-Gaussian quantities, loaded and formed once ------------------
     float mu0 = 0, mu1 = 0, mu2 = 0, opac = 0;
     float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
     float sh[3 * K];
     if (active) {
-        const int64_t g = gidx[i];
+        const int64_t g = gidx[L.q_gsub[qi] + i];
         mu0 = __ldg(mx + g); mu1 = __ldg(my + g); mu2 = __ldg(mz + g);
         float s0 = ldattr(attr + (ATTR_SCALE + 0) * n_map + g);
         float s1 = ldattr(attr + (ATTR_SCALE + 1) * n_map + g);
@@ -133,13 +136,13 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
         const int nb = min(PROJ_VIEW_BATCH, V - vb);
         __syncthreads();
         for (int k = threadIdx.x; k < nb * 16; k += PROJ_THREADS)
-            reinterpret_cast<float *>(s_view)[k] = reinterpret_cast<const float *>(views + vb)[k];
+            reinterpret_cast<float *>(s_view)[k] = reinterpret_cast<const float *>(views + v_begin + vb)[k];
         __syncthreads();
         if (!active) continue;
         for (int vv = 0; vv < nb; ++vv) {
             const ViewParams &P = s_view[vv];
-            const int v = vb + vv;
-            const int64_t o = (int64_t)v * S + i;
+            const int v = v_begin + vb + vv;
+            const int64_t o = L.vd_off[v] + i;
             // camera-space position t = R (mu - c)
             float d0 = (mu0 - P.c_hi[0]) - P.c_lo[0];
             float d1 = (mu1 - P.c_hi[1]) - P.c_lo[1];
@@ -238,31 +241,31 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
 
 template <typename T>
 static cudaError_t project_t(const float *mx, const float *my, const float *mz, const T *attr, int sh_degree,
-                             int64_t n_map, const uint32_t *gidx, int64_t S, const ViewParams *views, int V,
-                             const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles, uint32_t *dkey,
-                             cudaStream_t st)
+                             int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
+                             const ViewParams *views, const CamParams &cam, float4 *rec, uint2 *rect,
+                             uint32_t *ntiles, uint32_t *dkey, cudaStream_t st)
 {
-    dim3 grid((unsigned)ceil_div(S, PROJ_THREADS));
+    dim3 grid((unsigned)n_blocks);
     switch (sh_degree) {
-    case 0: k_project<T, 0><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
-    case 1: k_project<T, 1><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
-    case 2: k_project<T, 2><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
-    case 3: k_project<T, 3><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey); break;
+    case 0: k_project<T, 0><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
+    case 1: k_project<T, 1><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
+    case 2: k_project<T, 2><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
+    case 3: k_project<T, 3><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_project(const float *mx, const float *my, const float *mz, const void *attr, int precision,
-                           int sh_degree, int64_t n_map, const uint32_t *gidx, int64_t S, const ViewParams *views,
-                           int V, const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles,
+                           int sh_degree, int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
+                           const ViewParams *views, const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles,
                            uint32_t *dkey, cudaStream_t st)
 {
-    if (S <= 0) return cudaSuccess;
+    if (n_blocks <= 0) return cudaSuccess;
     switch (precision) {
-    case 0: return project_t(mx, my, mz, (const float *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
-    case 1: return project_t(mx, my, mz, (const __half *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
-    case 2: return project_t(mx, my, mz, (const __nv_bfloat16 *)attr, sh_degree, n_map, gidx, S, views, V, cam, rec, rect, ntiles, dkey, st);
+    case 0: return project_t(mx, my, mz, (const float *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
+    case 1: return project_t(mx, my, mz, (const __half *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
+    case 2: return project_t(mx, my, mz, (const __nv_bfloat16 *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -29,9 +29,11 @@ __device__ __forceinline__ float warp_sum_f(float x)
 }
 
 // Fixed grid and fixed reduction order: the sums are deterministic.
-__global__ void __launch_bounds__(QS_THREADS) k_query_stats(const float *__restrict__ q, int64_t n, double *part)
+// grid (QS_BLOCKS, Q): block (b, q) sums its share of query q.
+__global__ void __launch_bounds__(QS_THREADS) k_query_stats(Layout L, int64_t n, double *part)
 {
     __shared__ double s[2][QS_THREADS / 32];
+    const float *q = L.q_img[blockIdx.y];
     double a = 0, b = 0;
     for (int64_t j = (int64_t)blockIdx.x * QS_THREADS + threadIdx.x; j < n; j += (int64_t)QS_BLOCKS * QS_THREADS) {
         double x = q[j];
@@ -45,23 +47,30 @@ __global__ void __launch_bounds__(QS_THREADS) k_query_stats(const float *__restr
     if (threadIdx.x == 0) {
         double A = 0, B = 0;
         for (int w = 0; w < QS_THREADS / 32; ++w) { A += s[0][w]; B += s[1][w]; }
-        part[2 * blockIdx.x] = A;
-        part[2 * blockIdx.x + 1] = B;
+        double *o = part + 2 * ((int64_t)blockIdx.y * QS_BLOCKS + blockIdx.x);
+        o[0] = A;
+        o[1] = B;
     }
 }
 
-__global__ void k_query_stats_final(const double *part, double *qstats)
+__global__ void k_query_stats_final(const double *part, int Q, double *qstats)
 {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
     double A = 0, B = 0;
-    for (int k = 0; k < QS_BLOCKS; ++k) { A += part[2 * k]; B += part[2 * k + 1]; }
-    qstats[0] = A;
-    qstats[1] = B;
+    for (int k = 0; k < QS_BLOCKS; ++k) {
+        A += part[2 * ((int64_t)q * QS_BLOCKS + k)];
+        B += part[2 * ((int64_t)q * QS_BLOCKS + k) + 1];
+    }
+    qstats[2 * q] = A;
+    qstats[2 * q + 1] = B;
 }
 
-cudaError_t launch_query_stats(const float *query, int64_t n, double *block_scratch, double *qstats, cudaStream_t st)
+cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch, double *qstats, cudaStream_t st)
 {
-    k_query_stats<<<QS_BLOCKS, QS_THREADS, 0, st>>>(query, n, block_scratch);
-    k_query_stats_final<<<1, 1, 0, st>>>(block_scratch, qstats);
+    if (L.Q <= 0) return cudaSuccess;
+    k_query_stats<<<dim3(QS_BLOCKS, L.Q), QS_THREADS, 0, st>>>(L, n, block_scratch);
+    k_query_stats_final<<<(L.Q + 127) / 128, 128, 0, st>>>(block_scratch, L.Q, qstats);
     return cudaGetLastError();
 }
 
@@ -133,9 +142,9 @@ __device__ __forceinline__ float quad_min_rect(float a, float b, float c, float 
 
 template <int TW, int TH, int RPL>
 __global__ void __launch_bounds__(TW *TH / 2)
-k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ inst_gauss, int64_t inst_stride,
-        const int2 *__restrict__ ranges, CamParams cam, const float *__restrict__ query, double *__restrict__ partials,
-        float *__restrict__ rgb, float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
+k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
+        const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
+        float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
         const int *__restrict__ overflow)
 {
     constexpr int NT = TW * TH / 2;          // threads
@@ -147,8 +156,8 @@ k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ 
     __shared__ double s_red[3][NW];
 
     const int tile = blockIdx.x;
-    const int v = view_sel ? *view_sel : (int)blockIdx.y;
-    const int out_v = view_sel ? 0 : (int)blockIdx.y;
+    const int v = view_sel ? view_sel[blockIdx.y] : (int)blockIdx.y;
+    const int out_v = blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * TW + (int)(threadIdx.x % TW);
@@ -163,8 +172,8 @@ k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ 
 
     int2 r = make_int2(0, 0);
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
-    const uint32_t *list = inst_gauss + (int64_t)v * inst_stride;
-    const float4 *vrec = rec + (int64_t)v * S * 3;
+    const uint32_t *list = inst_gauss + L.io_off[v];
+    const float4 *vrec = rec + L.vd_off[v] * 3;
     const float lim = -0.5f * cam.cut * cam.cut;
     const float lamin = __logf(cam.alpha_min);
     float4(*const sw)[CH] = s_rec[warp];
@@ -283,6 +292,7 @@ k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ 
         if (in1) alpha[(int64_t)out_v * HW + pix1] = 1.f - T1;
     }
     if (partials) {
+        const float *query = L.q_img[L.view_q[v]];
         // pixels outside the image have zero colour and contribute nothing
         float sr = R0 + G0 + B0 + R1 + G1 + B1;
         float srr = R0 * R0 + G0 * G0 + B0 * B0 + R1 * R1 + G1 * G1 + B1 * B1;
@@ -304,26 +314,25 @@ k_blend(const float4 *__restrict__ rec, int64_t S, const uint32_t *__restrict__ 
 }
 
 template <int TW, int TH, int RPL>
-static cudaError_t blend_t(const float4 *rec, int64_t S, const uint32_t *inst_gauss, int64_t inst_stride,
-                           const int2 *ranges, int V, const CamParams &cam, const float *query, double *partials,
-                           float *rgb, float *depth, float *alpha, const int *view_sel, const int *overflow,
-                           cudaStream_t st)
+static cudaError_t blend_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                           const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
+                           const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
 {
-    dim3 grid(cam.n_tiles, view_sel ? 1 : V);
-    k_blend<TW, TH, RPL><<<grid, TW * TH / 2, 0, st>>>(rec, S, inst_gauss, inst_stride, ranges, cam, query, partials,
-                                                      rgb, depth, alpha, view_sel, overflow);
+    dim3 grid(cam.n_tiles, view_sel ? n_sel : L.V);
+    k_blend<TW, TH, RPL><<<grid, TW * TH / 2, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha,
+                                                      view_sel, overflow);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const float4 *rec, int64_t S, const uint32_t *inst_gauss, int64_t inst_stride,
-                         const int2 *ranges, int V, const CamParams &cam, const float *query, double *partials,
-                         float *rgb, float *depth, float *alpha, const int *view_sel, const int *overflow,
-                         cudaStream_t st)
+cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                         const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
+                         const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
 {
+    if ((view_sel ? n_sel : L.V) <= 0) return cudaSuccess;
 #define RELOC_BLEND_CASE(W_, H_, R_)                                                                             \
     if (cam.tile_w == W_ && cam.tile_h == H_ && cam.blend_rpl == R_)                                            \
-        return blend_t<W_, H_, R_>(rec, S, inst_gauss, inst_stride, ranges, V, cam, query, partials, rgb, depth, \
-                                   alpha, view_sel, overflow, st);
+        return blend_t<W_, H_, R_>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha, view_sel, n_sel, \
+                                   overflow, st);
     RELOC_BLEND_CASE(16, 16, 1)
     RELOC_BLEND_CASE(16, 16, 2)
     RELOC_BLEND_CASE(8, 8, 1)
@@ -347,8 +356,8 @@ cudaError_t launch_blend(const float4 *rec, int64_t S, const uint32_t *inst_gaus
 constexpr int NCC_THREADS = 256;
 
 __global__ void __launch_bounds__(NCC_THREADS)
-k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ qstats, int n_tiles, int64_t n,
-               double *__restrict__ scores, int *__restrict__ degenerate)
+k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ qstats, Layout L, int n_tiles,
+               int64_t n, double *__restrict__ scores, int *__restrict__ degenerate)
 {
     __shared__ double s[3][NCC_THREADS / 32];
     const int v = blockIdx.x;
@@ -368,7 +377,8 @@ k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ q
         double Sr = 0, Srr = 0, Srq = 0;
         for (int w = 0; w < NCC_THREADS / 32; ++w) { Sr += s[0][w]; Srr += s[1][w]; Srq += s[2][w]; }
         const double nn = (double)n;
-        const double Sq = qstats[0], Sqq = qstats[1];
+        const int q = L.view_q[v];
+        const double Sq = qstats[2 * q], Sqq = qstats[2 * q + 1];
         const double cov = Srq - Sr * Sq / nn;
         const double vr = Srr - Sr * Sr / nn;
         const double vq = Sqq - Sq * Sq / nn;
@@ -378,10 +388,11 @@ k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ q
     }
 }
 
-cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, int V, int n_tiles, int64_t n_samples,
-                                double *scores, int *degenerate, cudaStream_t st)
+cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_tiles,
+                                int64_t n_samples, double *scores, int *degenerate, cudaStream_t st)
 {
-    k_ncc_finalize<<<V, NCC_THREADS, 0, st>>>(partials, qstats, n_tiles, n_samples, scores, degenerate);
+    if (L.V <= 0) return cudaSuccess;
+    k_ncc_finalize<<<L.V, NCC_THREADS, 0, st>>>(partials, qstats, L, n_tiles, n_samples, scores, degenerate);
     return cudaGetLastError();
 }
 
@@ -392,14 +403,18 @@ __device__ __forceinline__ bool better(double sa, int ia, double sb, int ib)
     return sa > sb || (sa == sb && ia < ib);
 }
 
-__global__ void __launch_bounds__(256) k_argmax(const double *__restrict__ scores, int V, int *best, double *best_score)
+// one block per query
+__global__ void __launch_bounds__(256)
+k_argmax(const double *__restrict__ scores, Layout L, int *best, double *best_score, int *view_sel)
 {
     __shared__ double s_s[256];
     __shared__ int s_i[256];
+    const int q = blockIdx.x;
+    const int v0 = L.q_view[q], V = L.q_view[q + 1] - v0;
     double bs = -INFINITY;
     int bi = 0x7fffffff;
-    for (int v = threadIdx.x; v < V; v += 256)
-        if (better(scores[v], v, bs, bi)) { bs = scores[v]; bi = v; }
+    for (int k = threadIdx.x; k < V; k += 256)
+        if (better(scores[v0 + k], k, bs, bi)) { bs = scores[v0 + k]; bi = k; }
     s_s[threadIdx.x] = bs;
     s_i[threadIdx.x] = bi;
     __syncthreads();
@@ -411,14 +426,18 @@ __global__ void __launch_bounds__(256) k_argmax(const double *__restrict__ score
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        best[0] = s_i[0] < V ? s_i[0] : 0;
-        best_score[0] = s_s[0];
+        const int b = s_i[0] < V ? s_i[0] : 0;
+        best[q] = b;
+        best_score[q] = s_s[0];
+        view_sel[q] = v0 + b;
     }
 }
 
-cudaError_t launch_argmax(const double *scores, int V, int *best, double *best_score, cudaStream_t st)
+cudaError_t launch_argmax(const double *scores, const Layout &L, int *best, double *best_score, int *view_sel,
+                          cudaStream_t st)
 {
-    k_argmax<<<1, 256, 0, st>>>(scores, V, best, best_score);
+    if (L.Q <= 0) return cudaSuccess;
+    k_argmax<<<L.Q, 256, 0, st>>>(scores, L, best, best_score, view_sel);
     return cudaGetLastError();
 }
 

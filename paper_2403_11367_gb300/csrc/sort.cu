@@ -13,9 +13,9 @@
 // view|tile|depth keys emitted in index order, with far fewer passes over the
 // (much larger) instance list.
 //
-// Every per-view array has a fixed stride, so a block finds its view and
-// chunk from its index alone and valid lengths stay in device memory: no
-// host round trip between stages.
+// Every per-view array sits at a host-planned offset with a host-planned
+// capacity, and chunk tables map a block to its view and chunk, so valid
+// lengths stay in device memory: no host round trip between stages.
 #include "internal.cuh"
 
 namespace reloc {
@@ -59,21 +59,22 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_tmp,
     return r;
 }
 
-int64_t radix_hist_words(int V, int64_t stride) { return (int64_t)V * RADIX * ceil_div(stride, SORT_CHUNK); }
-
 // ------------------------------------------------------------ upsweep ------
 // Per chunk digit counts -> hist[s][d][k] (digit-major inside a segment, so
 // one exclusive scan of the segment's block gives every chunk's offsets).
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
 {
     __shared__ uint32_t s_h[RADIX];
-    const int c = blockIdx.x, s = c / p.cps, k = c % p.cps;
+    const int c = blockIdx.x;
+    const int s = find_segment(p.chunk_base, p.n_seg, c);
+    const int k = c - p.chunk_base[s], cps = p.chunk_base[s + 1] - p.chunk_base[s];
     s_h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t seg_len = p.len ? min64(p.len[s], p.stride) : p.stride;
+    const int64_t cap = p.seg_off[s + 1] - p.seg_off[s];
+    const int64_t seg_len = p.len ? min64(p.len[s], cap) : cap;
     const int64_t begin = (int64_t)k * SORT_CHUNK;
     const int n = (int)max64(0, min64(SORT_CHUNK, seg_len - begin));
-    const int64_t base = (int64_t)s * p.stride + begin;
+    const int64_t base = p.seg_off[s] + begin;
     const unsigned lt = lanemask_lt();
     for (int b = 0; b < n; b += SORT_THREADS) {
         const int idx = b + threadIdx.x;
@@ -87,16 +88,20 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
         if (valid && (peers & lt) == 0) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    p.hist[((int64_t)s * RADIX + threadIdx.x) * p.cps + k] = s_h[threadIdx.x];
+    p.hist[(int64_t)RADIX * p.chunk_base[s] + (int64_t)threadIdx.x * cps + k] = s_h[threadIdx.x];
 }
 
 // --------------------------------------------------- segment scan ----------
 // In-place exclusive scan of `count` words per segment; total_out[s] = sum.
+// In-place exclusive scan of segment s = data[mult*base[s], mult*base[s+1]);
+// total_out[s] = its sum.  One block per segment.
 constexpr int SCAN_THREADS = 1024;
-__global__ void __launch_bounds__(SCAN_THREADS) k_seg_scan(uint32_t *data, int64_t count, uint32_t *total_out)
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_seg_scan(uint32_t *data, const int32_t *__restrict__ base, int mult, uint32_t *total_out)
 {
     __shared__ uint32_t s_tmp[33];
-    uint32_t *a = data + (int64_t)blockIdx.x * count;
+    uint32_t *a = data + (int64_t)mult * base[blockIdx.x];
+    const int64_t count = (int64_t)mult * (base[blockIdx.x + 1] - base[blockIdx.x]);
     const int64_t per = ceil_div(count, SCAN_THREADS);
     const int64_t lo = min64(count, threadIdx.x * per), hi = min64(count, lo + per);
     uint32_t sum = 0;
@@ -127,8 +132,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
     __shared__ uint32_t s_val[SORT_CHUNK];
     __shared__ uint32_t s_tmp[33];
 
-    const int c = blockIdx.x, s = c / p.cps, k = c % p.cps;
-    const int64_t seg_len = p.len ? min64(p.len[s], p.stride) : p.stride;
+    const int c = blockIdx.x;
+    const int s = find_segment(p.chunk_base, p.n_seg, c);
+    const int k = c - p.chunk_base[s], cps = p.chunk_base[s + 1] - p.chunk_base[s];
+    const int64_t cap = p.seg_off[s + 1] - p.seg_off[s];
+    const int64_t seg_len = p.len ? min64(p.len[s], cap) : cap;
     const int64_t begin = (int64_t)k * SORT_CHUNK;
     if (begin >= seg_len) return;                       // uniform for the block
     const int n = (int)min64(SORT_CHUNK, seg_len - begin);
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
     for (int w = 0; w < NW; ++w) s_wcnt[w][threadIdx.x] = 0;
     __syncthreads();
 
-    const int64_t base = (int64_t)s * p.stride + begin;
+    const int64_t base = p.seg_off[s] + begin;
     const unsigned lt = lanemask_lt();
     uint32_t key[SORT_IPT], val[SORT_IPT], rank[SORT_IPT];
 #pragma unroll
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
     uint32_t nvalid;
     const uint32_t excl = block_excl_scan(tot, s_tmp, &nvalid);
     s_boff[threadIdx.x] = excl;
-    s_goff[threadIdx.x] = p.hist[((int64_t)s * RADIX + threadIdx.x) * p.cps + k];
+    s_goff[threadIdx.x] = p.hist[(int64_t)RADIX * p.chunk_base[s] + (int64_t)threadIdx.x * cps + k];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < SORT_IPT; ++r) {
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
         }
     }
     __syncthreads();
-    const int64_t obase = (int64_t)s * p.stride;
+    const int64_t obase = p.seg_off[s];
     for (int j = threadIdx.x; j < (int)nvalid; j += SORT_THREADS) {
         const uint32_t kk = s_key[j];
         const uint32_t d = (kk >> p.shift) & p.mask;
@@ -197,29 +205,29 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
 
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st)
 {
-    if (p.V <= 0 || p.stride <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((int64_t)p.V * p.cps);
-    k_radix_upsweep<<<blocks, SORT_THREADS, 0, st>>>(p);
-    k_seg_scan<<<p.V, SCAN_THREADS, 0, st>>>(p.hist, (int64_t)RADIX * p.cps, p.len_out);
-    k_radix_scatter<<<blocks, SORT_THREADS, 0, st>>>(p);
+    if (p.n_seg <= 0 || p.total_chunks <= 0) return cudaSuccess;
+    k_radix_upsweep<<<p.total_chunks, SORT_THREADS, 0, st>>>(p);
+    k_seg_scan<<<p.n_seg, SCAN_THREADS, 0, st>>>(p.hist, p.chunk_base, RADIX, p.len_out);
+    k_radix_scatter<<<p.total_chunks, SORT_THREADS, 0, st>>>(p);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- K3 emit -----
 
-int64_t emit_chunk_words(int V, int64_t S) { return (int64_t)V * ceil_div(S, EMIT_CHUNK); }
-
 __global__ void __launch_bounds__(EMIT_THREADS)
 k_emit_sums(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis,
-            const uint32_t *__restrict__ ntiles, int64_t S, int cpe, uint32_t *__restrict__ chunk_sums)
+            const uint32_t *__restrict__ ntiles, Layout L, uint32_t *__restrict__ chunk_sums)
 {
     __shared__ uint32_t s_tmp[33];
-    const int c = blockIdx.x, v = c / cpe, k = c % cpe;
+    const int c = blockIdx.x;
+    const int v = find_segment(L.ce_base, L.V, c);
+    const int k = c - L.ce_base[v];
+    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
     const int64_t nv = min64(n_vis[v], S);
     const int64_t begin = (int64_t)k * EMIT_CHUNK;
     const int n = (int)max64(0, min64(EMIT_CHUNK, nv - begin));
-    const uint32_t *g = sorted_g + (int64_t)v * S + begin;
-    const uint32_t *nt = ntiles + (int64_t)v * S;
+    const uint32_t *g = sorted_g + L.vd_off[v] + begin;
+    const uint32_t *nt = ntiles + L.vd_off[v];
     uint32_t sum = 0;
     for (int j = threadIdx.x; j < n; j += EMIT_THREADS) sum += nt[g[j]];
     uint32_t tot;
@@ -229,33 +237,33 @@ k_emit_sums(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ 
 
 __global__ void __launch_bounds__(EMIT_THREADS)
 k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis,
-       const uint32_t *__restrict__ ntiles, const uint2 *__restrict__ rect, int64_t S, int cpe, int ntx,
-       int64_t inst_stride, const uint32_t *__restrict__ chunk_off, const uint32_t *__restrict__ n_inst,
-       uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_gauss, unsigned long long *need,
-       int *overflow)
+       const uint32_t *__restrict__ ntiles, const uint2 *__restrict__ rect, Layout L, int ntx,
+       const uint32_t *__restrict__ chunk_off, const uint32_t *__restrict__ n_inst,
+       uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_gauss, int *overflow)
 {
     __shared__ uint32_t s_g[EMIT_CHUNK];
     __shared__ uint32_t s_off[EMIT_CHUNK];
     __shared__ uint2 s_rect[EMIT_CHUNK];
     __shared__ uint32_t s_tmp[33];
-    const int c = blockIdx.x, v = c / cpe, k = c % cpe;
-    if (n_inst[v] > inst_stride) {                      // this view does not fit
-        if (k == 0 && threadIdx.x == 0) {
-            atomicMax(need, (unsigned long long)n_inst[v]);
-            atomicExch(overflow, 1);
-        }
+    const int c = blockIdx.x;
+    const int v = find_segment(L.ce_base, L.V, c);
+    const int k = c - L.ce_base[v];
+    const int64_t cap = L.io_off[v + 1] - L.io_off[v];
+    if ((int64_t)n_inst[v] > cap) {                     // this view does not fit
+        if (k == 0 && threadIdx.x == 0) atomicExch(overflow, 1);
         return;
     }
+    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
     const int64_t nv = min64(n_vis[v], S);
     const int64_t begin = (int64_t)k * EMIT_CHUNK;
     if (begin >= nv) return;
     const int n = (int)min64(EMIT_CHUNK, nv - begin);
-    const uint32_t *g = sorted_g + (int64_t)v * S + begin;
+    const uint32_t *g = sorted_g + L.vd_off[v] + begin;
     for (int j = threadIdx.x; j < n; j += EMIT_THREADS) {
         const uint32_t gi = g[j];
         s_g[j] = gi;
-        s_off[j] = ntiles[(int64_t)v * S + gi];
-        s_rect[j] = rect[(int64_t)v * S + gi];
+        s_off[j] = ntiles[L.vd_off[v] + gi];
+        s_rect[j] = rect[L.vd_off[v] + gi];
     }
     __syncthreads();
     // blocked exclusive scan of the counts (item order = depth order)
@@ -278,7 +286,7 @@ k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis
     }
     __syncthreads();
     // one thread per emitted entry: find its item by binary search
-    const int64_t obase = (int64_t)v * inst_stride + chunk_off[c];
+    const int64_t obase = L.io_off[v] + chunk_off[c];
     for (uint32_t m = threadIdx.x; m < total; m += EMIT_THREADS) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
@@ -296,29 +304,26 @@ k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis
 }
 
 cudaError_t launch_emit(const uint32_t *sorted_g, const uint32_t *n_vis, const uint32_t *ntiles, const uint2 *rect,
-                        int64_t S, int V, int ntx, int64_t inst_stride, uint32_t *chunk_sums, uint32_t *inst_tile,
-                        uint32_t *inst_gauss, uint32_t *n_inst, unsigned long long *need, int *overflow,
-                        cudaStream_t st)
+                        const Layout &L, int n_chunks, int ntx, uint32_t *chunk_sums, uint32_t *inst_tile,
+                        uint32_t *inst_gauss, uint32_t *n_inst, int *overflow, cudaStream_t st)
 {
-    if (S <= 0 || V <= 0) return cudaSuccess;
-    const int cpe = (int)ceil_div(S, EMIT_CHUNK);
-    const unsigned blocks = (unsigned)((int64_t)V * cpe);
-    k_emit_sums<<<blocks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, S, cpe, chunk_sums);
-    k_seg_scan<<<V, SCAN_THREADS, 0, st>>>(chunk_sums, cpe, n_inst);
-    k_emit<<<blocks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, rect, S, cpe, ntx, inst_stride, chunk_sums,
-                                            n_inst, inst_tile, inst_gauss, need, overflow);
+    if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
+    k_emit_sums<<<n_chunks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, L, chunk_sums);
+    k_seg_scan<<<L.V, SCAN_THREADS, 0, st>>>(chunk_sums, L.ce_base, 1, n_inst);
+    k_emit<<<n_chunks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, rect, L, ntx, chunk_sums, n_inst, inst_tile,
+                                              inst_gauss, overflow);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ K5 ranges ----
 
-__global__ void k_ranges(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ n_inst, int64_t stride,
+__global__ void k_ranges(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ n_inst, Layout L,
                          int n_tiles, int2 *__restrict__ ranges, const int *__restrict__ overflow)
 {
     if (*overflow) return;
     const int v = blockIdx.y;
-    const int64_t n = min64(n_inst[v], stride);
-    const uint32_t *t = tiles + (int64_t)v * stride;
+    const int64_t n = min64(n_inst[v], L.io_off[v + 1] - L.io_off[v]);
+    const uint32_t *t = tiles + L.io_off[v];
     int2 *R = ranges + (int64_t)v * n_tiles;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t tj = t[j];
@@ -327,14 +332,14 @@ __global__ void k_ranges(const uint32_t *__restrict__ tiles, const uint32_t *__r
     }
 }
 
-cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, int64_t inst_stride, int V, int n_tiles,
+cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, const Layout &L, int n_tiles,
                           int2 *ranges, const int *overflow, cudaStream_t st)
 {
-    if (V <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)V * n_tiles, st);
+    if (L.V <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.V * n_tiles, st);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)min64(64, ceil_div(inst_stride, 256)), V);
-    k_ranges<<<grid, 256, 0, st>>>(inst_tile, n_inst, inst_stride, n_tiles, ranges, overflow);
+    dim3 grid(64, L.V);
+    k_ranges<<<grid, 256, 0, st>>>(inst_tile, n_inst, L, n_tiles, ranges, overflow);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,16 @@ class Grid(C.Structure):
                 ("step_yaw_deg", C.c_double)]
 
 
+class Query(C.Structure):
+    _fields_ = [("query_dev", C.c_void_p), ("coarse_pose", C.c_double * 16), ("radius", C.c_double),
+                ("grid", Grid)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("use_graph", C.c_int32), ("reserved0", C.c_int32), ("mem_budget", C.c_int64),
+                ("reserved", C.c_int32 * 8)]
+
+
 class Result(C.Structure):
     _fields_ = [("best_index", C.c_int32), ("n_candidates", C.c_int32), ("best_score", C.c_double),
                 ("best_pose", C.c_double * 16), ("n_gauss", C.c_int64), ("n_blocks", C.c_int32),
@@ -88,6 +98,9 @@ SIGNATURES = {
                                  _dp, _vp, _vp, _vp, _vp]),
     "reloc_localize_host": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera),
                                       C.POINTER(Result), _vp, _vp, _vp]),
+    "reloc_localize_batch": (C.c_int, [_vp, C.POINTER(Query), C.c_int, C.POINTER(Camera), C.POINTER(Result), _dp,
+                                       _vp, _vp, _vp]),
+    "reloc_set_batch_options": (C.c_int, [_vp, C.POINTER(BatchOptions)]),
     "reloc_last_counts": (C.c_int, [_vp, C.POINTER(Counts)]),
     "reloc_set_profiling": (C.c_int, [_vp, C.c_int]),
     "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
@@ -242,6 +255,35 @@ class Context:
                                   C.byref(res), sc.ctypes.data_as(_dp) if sc is not None else None,
                                   _ptr(best_rgb), _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
         return res, sc
+
+    def localize_batch(self, queries, cam, best_rgb=None, best_depth=None, stream=None, want_scores=True):
+        """queries: list of (query tensor [3,H,W] on the device, coarse_pose 4x4, radius, grid tuple).
+        Returns (list of Result, scores per query as numpy arrays or None)."""
+        n = len(queries)
+        arr = (Query * n)()
+        counts = []
+        for i, (img, pose, radius, grid) in enumerate(queries):
+            arr[i].query_dev = _ptr(img).value
+            arr[i].coarse_pose = (C.c_double * 16)(*np.asarray(pose, np.float64).reshape(16))
+            arr[i].radius = float(radius)
+            arr[i].grid = Grid(*grid) if not isinstance(grid, Grid) else grid
+            counts.append(arr[i].grid.nx * arr[i].grid.ny * arr[i].grid.nyaw)
+        res = (Result * n)()
+        sc = np.zeros(sum(counts)) if want_scores else None
+        c = camera(cam)
+        _check(lib.reloc_localize_batch(self._h, arr, n, C.byref(c), res,
+                                        sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
+                                        _ptr(best_depth), _stream(stream)))
+        split = None
+        if sc is not None:
+            split = np.split(sc, np.cumsum(counts)[:-1])
+        return list(res), split
+
+    def set_batch_options(self, use_graph=True, mem_budget=16 << 30):
+        o = BatchOptions()
+        o.use_graph = 1 if use_graph else 0
+        o.mem_budget = int(mem_budget)
+        _check(lib.reloc_set_batch_options(self._h, C.byref(o)))
 
     def localize_host(self, query_host, coarse_pose, radius, grid, cam, best_rgb_host=None, best_depth_host=None,
                       stream=None):
