@@ -104,6 +104,53 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def batch_queries(ctx, cam, n, seed, dev):
+    """Batching workload: n queries along the street, candidate grids with 8..128
+    candidates (nx, ny in 2..4, nyaw in 2..8) and block radii 15..95 m (subsets of
+    about 50k..800k Gaussians); query images rendered at the hidden poses."""
+    import torch
+    import scenegen as sg
+    r = sg.Rng(seed)
+    hidden, seeds = sg.street_queries(n, seed=seed)
+    out = []
+    for i in range(n):
+        nx = int(r.uniform(1, 2, 5)[0]); ny = int(r.uniform(1, 2, 5)[0]); nyaw = int(r.uniform(1, 2, 9)[0])
+        radius = float(r.uniform(1, 15.0, 95.0)[0])
+        runs, _, _ = ctx.select_block(hidden[i][0], hidden[i][1], radius)
+        img = torch.empty((1, 3, cam.height, cam.width), device=dev)
+        ctx.render(runs, sg.pose_from_xyz_yaw(*hidden[i])[None], cam, rgb=img)
+        img = (img[0] + torch.tensor(sg.image_noise(1000 + i, cam.height, cam.width), device=dev)).contiguous()
+        out.append((img, sg.pose_from_xyz_yaw(*seeds[i]), radius, (nx, ny, nyaw, 0.5, 2.0)))
+    return out
+
+
+def run_batch_leg(ctx, cam, dev, stream, n_queries=256):
+    """One graph-captured reloc_localize_batch over n_queries queries (autotuned)."""
+    import tempfile
+    import torch
+    qs = batch_queries(ctx, cam, n_queries, 21, dev)
+    table = os.path.join(tempfile.gettempdir(), "reloc_tune_table.txt")
+    tune = ctx.autotune(qs[:4], cam, table, force=True, stream=stream)
+    ctx.set_batch_options(use_graph=True, mem_budget=24 << 30)
+    ctx.localize_batch(qs, cam, stream=stream, want_scores=False)       # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res, _ = ctx.localize_batch(qs, cam, stream=stream, want_scores=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c = ctx.last_counts()
+    n_cand = sum(q[3][0] * q[3][1] * q[3][2] for q in qs)
+    subs = [r.n_gauss for r in res]
+    ctx.set_batch_options(use_graph=False, mem_budget=16 << 30)
+    return {"queries": n_queries, "candidates": int(n_cand), "ms": ms,
+            "candidates_per_s": n_cand / (ms / 1e3), "queries_per_s": n_queries / (ms / 1e3),
+            "subset_min": int(min(subs)), "subset_max": int(max(subs)), "kernel_launches": c.kernel_launches,
+            "cuda_graph": True, "tuned": {"tile": [tune.tile_w, tune.tile_h], "rpl": tune.blend_rpl,
+                                          "configs_timed": tune.n_tried}}
+
+
 def make_workload(rank: int = 0):
     import scenegen as sg
     g = sg.street_gaussians(N_GAUSS, seed=11, sh_degree=3)
@@ -263,6 +310,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    batch = run_batch_leg(ctx, cam, dev, stream) if not args.no_batch else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -300,6 +349,7 @@ def run_ours(args):
                      "launch_ms": blend_ms},
         "stage_ms": {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()},
         "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
+        "batch": batch,
         "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},
         "clocks": clocks,
@@ -316,6 +366,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-query batching leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

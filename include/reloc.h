@@ -243,6 +243,27 @@ typedef struct reloc_batch_options {
 /* Set the batch options of the context.  Errors: EINVAL. */
 reloc_status reloc_set_batch_options(reloc_ctx *ctx, const reloc_batch_options *opt);
 
+typedef struct reloc_tune_result {
+    int32_t tile_w, tile_h;    /* chosen blend tile                                     */
+    int32_t blend_rpl;         /* chosen records per lane per warp step                 */
+    int32_t from_table;        /* 1: taken from the table without timing                */
+    double ms_per_query;       /* measured (or tabled) time per sample query            */
+    int32_t n_tried;           /* configurations timed                                  */
+    int32_t reserved[5];
+} reloc_tune_result;
+
+/* Autotuner (no counterpart in the paper: a scheduling choice of this build).
+ * Times reloc_localize_batch on the sample queries with every supported
+ * (tile_w, tile_h, blend_rpl) -- 16x16, 8x8, 32x8, 16x8, 8x16, 32x16 tiles,
+ * 1 or 2 records per lane -- and keeps the fastest in the context's config.
+ * table_path (may be NULL): a text table keyed by image size, SH degree,
+ * precision and the log2 buckets of the sample's mean candidate count and
+ * subset size; a matching line is used without timing unless force != 0, and
+ * a timed result is appended.  Runs on `stream`, synchronises it.
+ * Errors: EINVAL, ENOMAP, ECUDA (no configuration ran). */
+reloc_status reloc_autotune(reloc_ctx *ctx, const reloc_query *sample, int n_sample, const reloc_camera *cam,
+                            const char *table_path, int force, reloc_tune_result *out, void *stream);
+
 /* Work counts of the last render/score/localize call. */
 reloc_status reloc_last_counts(reloc_ctx *ctx, reloc_counts *out);
 

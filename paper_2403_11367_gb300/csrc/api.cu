@@ -1093,6 +1093,111 @@ extern "C" reloc_status reloc_set_batch_options(reloc_ctx *ctx, const reloc_batc
     return RELOC_OK;
 }
 
+// ================================================================ autotuner ==
+// Tile shape and records-per-step of the blend are chosen by timing a sample
+// batch with every supported configuration; the winner is kept in a text
+// table (one line per workload key) so later processes reuse it.
+
+static const int kTuneConfigs[][3] = {{16, 16, 1}, {16, 16, 2}, {8, 8, 1}, {8, 8, 2},  {32, 8, 1}, {32, 8, 2},
+                                      {16, 8, 1},  {16, 8, 2},  {8, 16, 1}, {8, 16, 2}, {32, 16, 1}, {32, 16, 2}};
+
+static std::string tune_key(const reloc_ctx *ctx, const reloc_camera *cam, double avg_v, double avg_s)
+{
+    char buf[160];
+    snprintf(buf, sizeof buf, "%d %d %d %d %d %d", cam->width, cam->height, ctx->sh_degree, ctx->precision,
+             (int)std::lround(std::log2(std::max(1.0, avg_v))), (int)std::lround(std::log2(std::max(1.0, avg_s))));
+    return buf;
+}
+
+extern "C" reloc_status reloc_autotune(reloc_ctx *ctx, const reloc_query *sample, int n_sample,
+                                       const reloc_camera *cam, const char *table_path, int force,
+                                       reloc_tune_result *out, void *stream)
+{
+    if (!ctx || !sample || !cam || !out || n_sample < 1) return fail(RELOC_EINVAL, "NULL argument or empty sample");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    memset(out, 0, sizeof *out);
+    double sv = 0, ss = 0;
+    for (int i = 0; i < n_sample; ++i) {
+        QuerySpec q;
+        CKS(make_localize_query(ctx, sample[i].query_dev, sample[i].coarse_pose, sample[i].radius, &sample[i].grid, q));
+        for (auto &r : q.runs) ss += (double)(r.end - r.begin);
+        sv += q.V;
+    }
+    const std::string key = tune_key(ctx, cam, sv / n_sample, ss / n_sample);
+    if (table_path && !force) {
+        FILE *f = fopen(table_path, "r");
+        if (f) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {
+                int w, h, deg, prec, vb, sb, tw, th, rpl;
+                double ms;
+                if (sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &w, &h, &deg, &prec, &vb, &sb, &tw, &th, &rpl, &ms) == 10) {
+                    char k2[160];
+                    snprintf(k2, sizeof k2, "%d %d %d %d %d %d", w, h, deg, prec, vb, sb);
+                    if (key == k2 && tile_ok(tw, th) && (rpl == 1 || rpl == 2)) {
+                        ctx->cfg.tile_w = tw;
+                        ctx->cfg.tile_h = th;
+                        ctx->cfg.blend_rpl = rpl;
+                        out->tile_w = tw;
+                        out->tile_h = th;
+                        out->blend_rpl = rpl;
+                        out->ms_per_query = ms;
+                        out->from_table = 1;
+                    }
+                }
+            }
+            fclose(f);
+            if (out->from_table) return RELOC_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<reloc_result> res(n_sample);
+    const reloc_config saved = ctx->cfg;
+    double best_ms = 1e300;
+    int best = -1;
+    for (int c = 0; c < (int)(sizeof kTuneConfigs / sizeof kTuneConfigs[0]); ++c) {
+        ctx->cfg.tile_w = kTuneConfigs[c][0];
+        ctx->cfg.tile_h = kTuneConfigs[c][1];
+        ctx->cfg.blend_rpl = kTuneConfigs[c][2];
+        reloc_status s = reloc_localize_batch(ctx, sample, n_sample, cam, res.data(), nullptr, nullptr, nullptr, stream);
+        if (s != RELOC_OK) continue;          // e.g. a shape this camera cannot tile: skip it
+        cudaEventRecord(e0, st);
+        s = reloc_localize_batch(ctx, sample, n_sample, cam, res.data(), nullptr, nullptr, nullptr, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        if (s == RELOC_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            out->n_tried++;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaGetLastError();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->cfg = saved;
+    if (best < 0) return fail(RELOC_ECUDA, "autotune: no configuration ran");
+    ctx->cfg.tile_w = kTuneConfigs[best][0];
+    ctx->cfg.tile_h = kTuneConfigs[best][1];
+    ctx->cfg.blend_rpl = kTuneConfigs[best][2];
+    out->tile_w = ctx->cfg.tile_w;
+    out->tile_h = ctx->cfg.tile_h;
+    out->blend_rpl = ctx->cfg.blend_rpl;
+    out->ms_per_query = best_ms / n_sample;
+    if (table_path) {
+        FILE *f = fopen(table_path, "a");
+        if (!f) return fail(RELOC_EINVAL, "autotune: cannot append to %s", table_path);
+        fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), out->tile_w, out->tile_h, out->blend_rpl, out->ms_per_query);
+        fclose(f);
+    }
+    return RELOC_OK;
+}
+
 extern "C" reloc_status reloc_localize_host(reloc_ctx *ctx, const float *query_host, const double *coarse_pose,
                                             double radius, const reloc_grid *grid, const reloc_camera *cam,
                                             reloc_result *out, float *best_rgb_host, float *best_depth_host,

@@ -64,6 +64,11 @@ class BatchOptions(C.Structure):
                 ("reserved", C.c_int32 * 8)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("blend_rpl", C.c_int32), ("from_table", C.c_int32),
+                ("ms_per_query", C.c_double), ("n_tried", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
 class Result(C.Structure):
     _fields_ = [("best_index", C.c_int32), ("n_candidates", C.c_int32), ("best_score", C.c_double),
                 ("best_pose", C.c_double * 16), ("n_gauss", C.c_int64), ("n_blocks", C.c_int32),
@@ -101,6 +106,8 @@ SIGNATURES = {
     "reloc_localize_batch": (C.c_int, [_vp, C.POINTER(Query), C.c_int, C.POINTER(Camera), C.POINTER(Result), _dp,
                                        _vp, _vp, _vp]),
     "reloc_set_batch_options": (C.c_int, [_vp, C.POINTER(BatchOptions)]),
+    "reloc_autotune": (C.c_int, [_vp, C.POINTER(Query), C.c_int, C.POINTER(Camera), C.c_char_p, C.c_int,
+                                 C.POINTER(TuneResult), _vp]),
     "reloc_last_counts": (C.c_int, [_vp, C.POINTER(Counts)]),
     "reloc_set_profiling": (C.c_int, [_vp, C.c_int]),
     "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
@@ -278,6 +285,24 @@ class Context:
         if sc is not None:
             split = np.split(sc, np.cumsum(counts)[:-1])
         return list(res), split
+
+    @staticmethod
+    def _queries(queries):
+        arr = (Query * len(queries))()
+        for i, (img, pose, radius, grid) in enumerate(queries):
+            arr[i].query_dev = _ptr(img).value
+            arr[i].coarse_pose = (C.c_double * 16)(*np.asarray(pose, np.float64).reshape(16))
+            arr[i].radius = float(radius)
+            arr[i].grid = Grid(*grid) if not isinstance(grid, Grid) else grid
+        return arr
+
+    def autotune(self, sample, cam, table_path=None, force=False, stream=None) -> TuneResult:
+        out = TuneResult()
+        c = camera(cam)
+        _check(lib.reloc_autotune(self._h, self._queries(sample), len(sample), C.byref(c),
+                                  table_path.encode() if table_path else None, 1 if force else 0, C.byref(out),
+                                  _stream(stream)))
+        return out
 
     def set_batch_options(self, use_graph=True, mem_budget=16 << 30):
         o = BatchOptions()

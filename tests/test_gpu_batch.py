@@ -154,3 +154,20 @@ def test_batch_rejects_bad_queries(R, street):
     assert e.value.status == R.ENUMERIC
     # the context still works
     batched(ctx, qs, cam)
+
+
+def test_autotune_picks_and_persists(R, street, tmp_path):
+    g, cam = street
+    ctx = R.Context()
+    ctx.load_map(g)
+    qs = make_queries(ctx, g, cam, 3, seed=27)
+    table = str(tmp_path / "tune.txt")
+    t1 = ctx.autotune(qs, cam, table)
+    assert t1.from_table == 0 and t1.n_tried >= 10 and t1.ms_per_query > 0
+    ctx2 = R.Context()
+    ctx2.load_map(g)
+    t2 = ctx2.autotune(qs, cam, table)
+    assert t2.from_table == 1
+    assert (t2.tile_w, t2.tile_h, t2.blend_rpl) == (t1.tile_w, t1.tile_h, t1.blend_rpl)
+    # the tuned configuration still gives the separate-call results
+    assert_same(separate(ctx, qs, cam), batched(ctx, qs, cam))
