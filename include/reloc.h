@@ -99,6 +99,9 @@ typedef struct reloc_result {
     int64_t n_gauss;           /* Gaussians in the selected block subset               */
     int32_t n_blocks;          /* blocks selected                                      */
     int32_t degenerate;        /* 1 if the best render or the query has zero variance  */
+    int32_t n_scored;          /* candidates rendered and scored (all, unless the
+                                  learned proposal picked a top-k)                     */
+    int32_t reserved;
 } reloc_result;
 
 /* Work counts of the last render/score/localize call (sums over views). */
@@ -263,6 +266,69 @@ typedef struct reloc_tune_result {
  * Errors: EINVAL, ENOMAP, ECUDA (no configuration ran). */
 reloc_status reloc_autotune(reloc_ctx *ctx, const reloc_query *sample, int n_sample, const reloc_camera *cam,
                             const char *table_path, int force, reloc_tune_result *out, void *stream);
+
+/* ---- learned candidate proposal ------------------------------------------
+ * No counterpart in the paper (its Sec. II points at learned relocalization
+ * as related work): a CNN ranks the 64 cells of a 4 x 4 x 4 candidate grid
+ * from gray 176 x 47 views (box average over f x f pixels, f = H / 47 =
+ * W / 176) of the query and of the render at the coarse pose; only the top-k
+ * cells are rendered and scored, and the full 64-candidate sweep runs
+ * whenever the softmax margin p1 - p2 is below the threshold.  Architecture:
+ * five 3x3 stride-2 convolutions 2-32-64-64-128-128 with ReLU, FC 1536-1024
+ * ReLU, FC 1024-64; BF16 weights and activations, FP32 accumulation on the
+ * tensor cores; softmax cross-entropy; Adam.  Flat parameter layout (FP32,
+ * RELOC_PROPOSAL_PARAMS values): per conv layer W[Cout][3][3][Cin], b[Cout];
+ * FC1 W[1024][1536], b[1024]; FC2 W[64][1024], b[64].  Network input: NHWC
+ * BF16 [batch][47][176][2] (channel 0 query, 1 coarse render), passed as
+ * uint16_t bit patterns. */
+#define RELOC_PROPOSAL_H 47
+#define RELOC_PROPOSAL_W 176
+#define RELOC_PROPOSAL_CLASSES 64
+#define RELOC_PROPOSAL_PARAMS 1916960
+
+/* Create (or re-create) the network with He-normal weights from `seed`.
+ * Errors: ENOMEM, ECUDA. */
+reloc_status reloc_proposal_init(reloc_ctx *ctx, uint64_t seed);
+
+/* Copy the parameters (which = 0) or the gradients of the last train step
+ * (which = 1) to flat_host [RELOC_PROPOSAL_PARAMS], or load parameters from
+ * it (reloc_proposal_set_params, which also resets the Adam state).
+ * Errors: EINVAL (no network), ECUDA. */
+reloc_status reloc_proposal_get(reloc_ctx *ctx, int which, float *flat_host);
+reloc_status reloc_proposal_set_params(reloc_ctx *ctx, const float *flat_host);
+
+/* Network input of one sample from a query image and the render at its coarse
+ * pose (both [3][H][W] device, H = 47 f, W = 176 f) into input_dev
+ * [47][176][2].  Errors: EINVAL. */
+reloc_status reloc_proposal_make_input(reloc_ctx *ctx, const float *query_dev, const float *coarse_rgb_dev,
+                                       const reloc_camera *cam, uint16_t *input_dev, void *stream);
+
+/* Logits [batch][64] (FP32, device) of inputs_dev [batch][47][176][2]. */
+reloc_status reloc_proposal_forward(reloc_ctx *ctx, const uint16_t *inputs_dev, int batch, float *logits_dev,
+                                    void *stream);
+
+/* One training step on a batch (batch a multiple of 64): forward, mean
+ * softmax cross-entropy against labels_dev [batch] (int32 grid cell), backward;
+ * Adam update with learning rate lr if update != 0.  *loss_host = mean loss.
+ * Synchronises `stream`.  Errors: EINVAL, ECUDA, ETIMEOUT (a tensor-core wait
+ * gave up). */
+reloc_status reloc_proposal_train_step(reloc_ctx *ctx, const uint16_t *inputs_dev, const int32_t *labels_dev,
+                                       int batch, float lr, int update, float *loss_host, void *stream);
+
+/* The proposal's dense contraction, exposed for callers and checks:
+ * C[m][n] = sum_k A[m][k] B[n][k] (+ bias[n], ReLU if relu != 0), A [M][K] and
+ * B [N][K] row-major BF16 (uint16_t bit patterns, 16-byte aligned), C [M][N]
+ * FP32, all device; FP32 accumulation on the tensor cores (tcgen05).  K a
+ * multiple of 64; split_k > 1 splits K into that many parts (K / split_k a
+ * multiple of 64) summed in a fixed order.  Synchronises `stream`.
+ * Errors: EINVAL, ECUDA, ETIMEOUT (a tensor-core wait gave up). */
+reloc_status reloc_gemm_bf16(reloc_ctx *ctx, const uint16_t *A_dev, const uint16_t *B_dev, const float *bias_dev,
+                             float *C_dev, int M, int N, int K, int relu, int split_k, void *stream);
+
+/* Use the proposal in reloc_localize / reloc_localize_batch for queries with a
+ * 4 x 4 x 4 grid: render and score the top_k (2..32) cells, or all 64 when
+ * p1 - p2 < margin.  enabled = 0 restores the full sweep.  Errors: EINVAL. */
+reloc_status reloc_set_proposal(reloc_ctx *ctx, int enabled, int top_k, float margin);
 
 /* Work counts of the last render/score/localize call. */
 reloc_status reloc_last_counts(reloc_ctx *ctx, reloc_counts *out);

@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "reloc_oracle.c")
+_SRC_CNN = os.path.join(_HERE, "cnn_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -37,10 +38,11 @@ FLAG_POWER, FLAG_ALPHA, FLAG_T, FLAG_DEPTH = 1, 2, 4, 8
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math) into oracle/_build/."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CNN))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                               "-Wall", "-Wno-misleading-indentation", "-o", tmp, _SRC, "-lm"])
+                               "-Wall", "-Wno-misleading-indentation", "-o", tmp, _SRC, _SRC_CNN, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -77,6 +79,14 @@ def lib():
             L.or_insertion_sort_u64.argtypes = [u64p, u32p, C.c_int64]
             L.or_render_views.argtypes = [fp, fp, fp, fp, fp, C.c_int, C.c_int64, dp, C.c_int, dp, dp,
                                           dp, dp, C.POINTER(C.c_int), dp, dp, dp, u8p, dp, i64p]
+            L.orc_param_count.restype = C.c_int64
+            L.orc_forward.argtypes = [dp, dp, C.c_int, dp]
+            L.orc_loss_grad.argtypes = [dp, dp, i32p, C.c_int, dp, dp]
+            L.orc_loss_grad.restype = C.c_double
+            L.orc_adam.argtypes = [dp, dp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_int]
+            L.orc_downsample_gray.argtypes = [fp, C.c_int, C.c_int, C.c_int, dp]
+            L.orc_conv3x3s2.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -265,3 +275,76 @@ def tile_ranges(keys, n_views, n_tiles):
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+# ---------------------------------------------------------------------------
+# learned candidate proposal (cnn_oracle.c)
+# ---------------------------------------------------------------------------
+
+CNN_IN = (47, 176, 2)
+
+
+def cnn_param_count() -> int:
+    return int(lib().orc_param_count())
+
+
+def cnn_forward(params, inputs) -> np.ndarray:
+    """logits [B][64] of inputs [B][47][176][2] (FP64)."""
+    p = _c(params, np.float64)
+    x = _c(inputs, np.float64)
+    B = x.shape[0]
+    out = np.zeros((B, 64))
+    lib().orc_forward(_p(p, C.c_double), _p(x, C.c_double), B, _p(out, C.c_double))
+    return out
+
+
+def cnn_loss_grad(params, inputs, labels, want_input_grad=False):
+    """(mean softmax cross-entropy, gradient w.r.t. params [, w.r.t. inputs])."""
+    p = _c(params, np.float64)
+    x = _c(inputs, np.float64)
+    y = _c(labels, np.int32)
+    g = np.zeros(p.size)
+    gi = np.zeros(x.shape) if want_input_grad else None
+    loss = lib().orc_loss_grad(_p(p, C.c_double), _p(x, C.c_double), _p(y, C.c_int32), x.shape[0],
+                               _p(g, C.c_double), _p(gi, C.c_double))
+    return (float(loss), g, gi) if want_input_grad else (float(loss), g)
+
+
+def adam(w, m, v, g, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    w = _c(w, np.float64).copy(); m = _c(m, np.float64).copy(); v = _c(v, np.float64).copy()
+    gg = _c(g, np.float64)
+    lib().orc_adam(_p(w, C.c_double), _p(m, C.c_double), _p(v, C.c_double), _p(gg, C.c_double), w.size, lr, b1, b2,
+                   eps, t)
+    return w, m, v
+
+
+def downsample_gray(img, f) -> np.ndarray:
+    a = _c(img, np.float32)
+    _, H, W = a.shape
+    out = np.zeros((H // f, W // f))
+    lib().orc_downsample_gray(_p(a, C.c_float), H, W, f, _p(out, C.c_double))
+    return out
+
+
+def conv3x3s2(x, w, b):
+    """One conv layer of the proposal (+ bias, ReLU): x [H][W][Ci], w [Co][3][3][Ci]."""
+    xx = _c(x, np.float64); ww = _c(w, np.float64); bb = _c(b, np.float64)
+    H, W, Ci = xx.shape
+    Co = ww.shape[0]
+    y = np.zeros(((H - 1) // 2 + 1, (W - 1) // 2 + 1, Co))
+    lib().orc_conv3x3s2(_p(xx, C.c_double), H, W, Ci, _p(ww, C.c_double), _p(bb, C.c_double), Co, _p(y, C.c_double))
+    return y
+
+
+def cnn_offsets():
+    """(w_offset, b_offset, w_shape) of the 7 parameter tensors in the flat layout."""
+    cin, cout = [2, 32, 64, 64, 128], [32, 64, 64, 128, 128]
+    out, o = [], 0
+    for l in range(5):
+        shape = (cout[l], 3, 3, cin[l])
+        n = int(np.prod(shape))
+        out.append((o, o + n, shape)); o += n + cout[l]
+    for shape in [(1024, 1536), (64, 1024)]:
+        n = shape[0] * shape[1]
+        out.append((o, o + n, shape)); o += n + shape[0]
+    return out

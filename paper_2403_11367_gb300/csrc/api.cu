@@ -136,6 +136,11 @@ struct reloc_ctx {
     bool last_final_b = false;      // final instance lists live in ikB/ivB
     std::vector<int64_t> last_ninst, last_io_off, last_vd_off;
     reloc_counts counts{};
+    // learned candidate proposal
+    ProposalNet *prop = nullptr;
+    int prop_enabled = 0, prop_k = 8;
+    float prop_margin = 0.f;
+    DevBuf prop_in, prop_seed, prop_logits, prop_idx, prop_mrg, prop_loss;
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev;    // (RELOC_STAGE_COUNT + 1) per sub-batch
@@ -222,8 +227,10 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
                       &ctx->ikA, &ctx->ivA, &ctx->ikB, &ctx->ivB, &ctx->hist2, &ctx->ranges, &ctx->partials,
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
                       &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
-                      &ctx->hdepth};
+                      &ctx->hdepth, &ctx->prop_in, &ctx->prop_seed, &ctx->prop_logits, &ctx->prop_idx,
+                      &ctx->prop_mrg, &ctx->prop_loss};
     for (DevBuf *b : bufs) b->release();
+    if (ctx->prop) proposal_destroy(ctx->prop);
     ctx->pin.release();
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -437,6 +444,9 @@ struct QuerySpec {
     std::vector<double> poses;      // V x 16, world-to-camera
     const float *img = nullptr;     // device query image ([3][H][W]) or null
     int n_blocks = 0;
+    int gx = 0, gy = 0, gyaw = 0;    // candidate grid shape (localize calls)
+    std::vector<double> coarse;      // coarse pose (localize calls)
+    std::vector<int> grid_index;     // view -> grid cell when a subset is rendered
 };
 
 // What a call produces.  Per-view device outputs use the call's global view
@@ -1011,6 +1021,10 @@ static reloc_status make_localize_query(reloc_ctx *ctx, const float *query_dev, 
     grid_poses(coarse_pose, *grid, q.poses);
     q.V = grid->nx * grid->ny * grid->nyaw;
     q.img = query_dev;
+    q.gx = grid->nx;
+    q.gy = grid->ny;
+    q.gyaw = grid->nyaw;
+    q.coarse.assign(coarse_pose, coarse_pose + 16);
     return RELOC_OK;
 }
 
@@ -1018,8 +1032,9 @@ static void fill_result(const QuerySpec &q, const CallOut &o, int qi, int v0, re
 {
     memset(out, 0, sizeof *out);
     const int b = o.best[qi];
-    out->best_index = b;
-    out->n_candidates = q.V;
+    out->best_index = q.grid_index.empty() ? b : q.grid_index[b];
+    out->n_candidates = q.grid_index.empty() ? q.V : q.gx * q.gy * q.gyaw;
+    out->n_scored = q.V;
     out->best_score = o.best_score[qi];
     if (b >= 0 && b < q.V) {
         memcpy(out->best_pose, q.poses.data() + 16 * b, sizeof(double) * 16);
@@ -1027,6 +1042,79 @@ static void fill_result(const QuerySpec &q, const CallOut &o, int qi, int v0, re
     }
     out->n_gauss = q.S;
     out->n_blocks = q.n_blocks;
+}
+
+// Learned proposal: for every query with a 4 x 4 x 4 grid, render the coarse
+// view, rank the cells with the CNN and keep the top-k (ascending cell order,
+// so ties still resolve to the lowest cell), or all cells when p1 - p2 < margin.
+static reloc_status apply_proposal(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const reloc_camera *cam,
+                                   cudaStream_t st)
+{
+    std::vector<int> sel;
+    for (int i = 0; i < (int)qs.size(); ++i)
+        if (qs[i].gx == 4 && qs[i].gy == 4 && qs[i].gyaw == 4) sel.push_back(i);
+    if (sel.empty()) return RELOC_OK;
+    const int H = cam->height, W = cam->width;
+    if (H % PROPOSAL_H || W % PROPOSAL_W || H / PROPOSAL_H != W / PROPOSAL_W)
+        return fail(RELOC_EINVAL, "the proposal needs H = 47 f and W = 176 f (got %dx%d)", W, H);
+    const int Ql = (int)sel.size();
+    const int64_t HW = (int64_t)H * W;
+    CKS(ctx->prop_seed.ensure(12 * (size_t)HW * Ql));
+    CKS(ctx->prop_in.ensure(2 * (size_t)PROPOSAL_H * PROPOSAL_W * 2 * Ql));
+    CKS(ctx->prop_logits.ensure(4 * (size_t)PROPOSAL_CLASSES * Ql));
+    CKS(ctx->prop_idx.ensure(4 * (size_t)32 * Ql));
+    CKS(ctx->prop_mrg.ensure(4 * (size_t)Ql));
+    // (a) coarse-pose renders
+    std::vector<QuerySpec> seeds(Ql);
+    for (int j = 0; j < Ql; ++j) {
+        seeds[j].runs = qs[sel[j]].runs;
+        seeds[j].V = 1;
+        seeds[j].poses = qs[sel[j]].coarse;
+    }
+    CallOut ro;
+    ro.rgb = ctx->prop_seed.as<float>();
+    CKS(run_batch(ctx, seeds, cam, st, ro, false));
+    // (b) inputs, (c) logits and top-k
+    __nv_bfloat16 *in = ctx->prop_in.as<__nv_bfloat16>();
+    for (int j = 0; j < Ql; ++j)
+        CK(proposal_make_input(qs[sel[j]].img, ctx->prop_seed.as<float>() + (int64_t)j * 3 * HW, H, W,
+                               in + (int64_t)j * PROPOSAL_H * PROPOSAL_W * 2, st));
+    CK(proposal_forward(ctx->prop, in, Ql, ctx->prop_logits.as<float>(), st));
+    CK(launch_topk(ctx->prop_logits.as<float>(), Ql, PROPOSAL_CLASSES, ctx->prop_k, ctx->prop_idx.as<int32_t>(),
+                   ctx->prop_mrg.as<float>(), st));
+    std::vector<int32_t> idx((size_t)Ql * ctx->prop_k);
+    std::vector<float> mrg(Ql);
+    int status = 0;
+    CK(cudaMemcpyAsync(idx.data(), ctx->prop_idx.p, 4 * idx.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(mrg.data(), ctx->prop_mrg.p, 4 * (size_t)Ql, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, proposal_status(ctx->prop), 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status) return fail(RELOC_ETIMEOUT, "proposal: a tensor-core wait gave up");
+    // (d) the candidate subsets
+    for (int j = 0; j < Ql; ++j) {
+        QuerySpec &q = qs[sel[j]];
+        if (mrg[j] < ctx->prop_margin) continue;       // low confidence: full sweep
+        std::vector<int> cells(idx.begin() + (size_t)j * ctx->prop_k, idx.begin() + (size_t)(j + 1) * ctx->prop_k);
+        std::sort(cells.begin(), cells.end());
+        std::vector<double> poses;
+        for (int c : cells) poses.insert(poses.end(), q.poses.begin() + 16 * c, q.poses.begin() + 16 * (c + 1));
+        q.poses.swap(poses);
+        q.V = (int)cells.size();
+        q.grid_index = cells;
+    }
+    return RELOC_OK;
+}
+
+// scores of a query in grid order (NaN for cells the proposal did not render)
+static void grid_scores(const QuerySpec &q, const double *sc, double *out)
+{
+    if (q.grid_index.empty()) {
+        memcpy(out, sc, sizeof(double) * q.V);
+        return;
+    }
+    const int n = q.gx * q.gy * q.gyaw;
+    for (int c = 0; c < n; ++c) out[c] = std::nan("");
+    for (int j = 0; j < q.V; ++j) out[q.grid_index[j]] = sc[j];
 }
 
 static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose, double radius,
@@ -1037,6 +1125,7 @@ static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const 
     if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
     std::vector<QuerySpec> qs(1);
     CKS(make_localize_query(ctx, query_dev, coarse_pose, radius, grid, qs[0]));
+    if (ctx->prop_enabled && ctx->prop) CKS(apply_proposal(ctx, qs, cam, st));
     CallOut o;
     o.score = true;
     o.argmax = true;
@@ -1045,7 +1134,7 @@ static reloc_status localize_impl(reloc_ctx *ctx, const float *query_dev, const 
     o.balpha = balpha;
     CKS(run_batch(ctx, qs, cam, st, o, false));
     fill_result(qs[0], o, 0, 0, out);
-    if (scores_host) memcpy(scores_host, o.scores.data(), sizeof(double) * qs[0].V);
+    if (scores_host) grid_scores(qs[0], o.scores.data(), scores_host);
     return RELOC_OK;
 }
 
@@ -1069,6 +1158,7 @@ extern "C" reloc_status reloc_localize_batch(reloc_ctx *ctx, const reloc_query *
     for (int i = 0; i < n_queries; ++i)
         CKS(make_localize_query(ctx, queries[i].query_dev, queries[i].coarse_pose, queries[i].radius,
                                 &queries[i].grid, qs[i]));
+    if (ctx->prop_enabled && ctx->prop) CKS(apply_proposal(ctx, qs, cam, (cudaStream_t)stream));
     CallOut o;
     o.score = true;
     o.argmax = true;
@@ -1076,11 +1166,13 @@ extern "C" reloc_status reloc_localize_batch(reloc_ctx *ctx, const reloc_query *
     o.bdepth = best_depth_dev;
     CKS(run_batch(ctx, qs, cam, (cudaStream_t)stream, o, true));
     int v0 = 0;
+    int64_t g0 = 0;
     for (int i = 0; i < n_queries; ++i) {
         fill_result(qs[i], o, i, v0, &results[i]);
+        if (scores_host) grid_scores(qs[i], o.scores.data() + v0, scores_host + g0);
         v0 += qs[i].V;
+        g0 += qs[i].grid_index.empty() ? qs[i].V : qs[i].gx * qs[i].gy * qs[i].gyaw;
     }
-    if (scores_host) memcpy(scores_host, o.scores.data(), sizeof(double) * o.scores.size());
     return RELOC_OK;
 }
 
@@ -1090,6 +1182,119 @@ extern "C" reloc_status reloc_set_batch_options(reloc_ctx *ctx, const reloc_batc
     if (opt->mem_budget < ((int64_t)64 << 20)) return fail(RELOC_EINVAL, "mem_budget below 64 MiB");
     ctx->use_graph = opt->use_graph != 0;
     ctx->mem_budget = opt->mem_budget;
+    return RELOC_OK;
+}
+
+// ================================================================= proposal ==
+
+extern "C" reloc_status reloc_proposal_init(reloc_ctx *ctx, uint64_t seed)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->prop) proposal_destroy(ctx->prop);
+    ctx->prop = nullptr;
+    cudaError_t e = cudaSuccess;
+    ctx->prop = proposal_create(seed, &e);
+    if (!ctx->prop) return fail(e == cudaErrorMemoryAllocation ? RELOC_ENOMEM : RELOC_ECUDA, "proposal init: %s",
+                                cudaGetErrorString(e));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_proposal_get(reloc_ctx *ctx, int which, float *flat_host)
+{
+    if (!ctx || !flat_host || (which != 0 && which != 1)) return fail(RELOC_EINVAL, "bad argument");
+    if (!ctx->prop) return fail(RELOC_EINVAL, "no proposal network (reloc_proposal_init)");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    CK(proposal_get(ctx->prop, which, flat_host));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_proposal_set_params(reloc_ctx *ctx, const float *flat_host)
+{
+    if (!ctx || !flat_host) return fail(RELOC_EINVAL, "bad argument");
+    if (!ctx->prop) return fail(RELOC_EINVAL, "no proposal network (reloc_proposal_init)");
+    CK(cudaSetDevice(ctx->device));
+    CK(proposal_set(ctx->prop, flat_host));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_proposal_make_input(reloc_ctx *ctx, const float *query_dev, const float *coarse_rgb_dev,
+                                                  const reloc_camera *cam, uint16_t *input_dev, void *stream)
+{
+    if (!ctx || !query_dev || !coarse_rgb_dev || !cam || !input_dev) return fail(RELOC_EINVAL, "NULL argument");
+    if (cam->height % PROPOSAL_H || cam->width % PROPOSAL_W || cam->height / PROPOSAL_H != cam->width / PROPOSAL_W)
+        return fail(RELOC_EINVAL, "the proposal needs H = 47 f and W = 176 f");
+    CK(cudaSetDevice(ctx->device));
+    CK(proposal_make_input(query_dev, coarse_rgb_dev, cam->height, cam->width, (__nv_bfloat16 *)input_dev,
+                           (cudaStream_t)stream));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_proposal_forward(reloc_ctx *ctx, const uint16_t *inputs_dev, int batch,
+                                               float *logits_dev, void *stream)
+{
+    if (!ctx || !inputs_dev || !logits_dev || batch < 1) return fail(RELOC_EINVAL, "bad argument");
+    if (!ctx->prop) return fail(RELOC_EINVAL, "no proposal network (reloc_proposal_init)");
+    CK(cudaSetDevice(ctx->device));
+    CK(proposal_forward(ctx->prop, (const __nv_bfloat16 *)inputs_dev, batch, logits_dev, (cudaStream_t)stream));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_proposal_train_step(reloc_ctx *ctx, const uint16_t *inputs_dev, const int32_t *labels_dev,
+                                                  int batch, float lr, int update, float *loss_host, void *stream)
+{
+    if (!ctx || !inputs_dev || !labels_dev || batch < 64 || batch % 64) return fail(RELOC_EINVAL, "bad argument");
+    if (!ctx->prop) return fail(RELOC_EINVAL, "no proposal network (reloc_proposal_init)");
+    if (!(lr >= 0) || !std::isfinite(lr)) return fail(RELOC_ENUMERIC, "bad learning rate");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CKS(ctx->prop_loss.ensure(4 * (size_t)batch));
+    CK(proposal_train_step(ctx->prop, (const __nv_bfloat16 *)inputs_dev, labels_dev, batch, lr, update != 0,
+                           ctx->prop_loss.as<float>(), st));
+    std::vector<float> rows(batch);
+    int status = 0;
+    CK(cudaMemcpyAsync(rows.data(), ctx->prop_loss.p, 4 * (size_t)batch, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, proposal_status(ctx->prop), 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status) return fail(RELOC_ETIMEOUT, "proposal: a tensor-core wait gave up");
+    double sum = 0;
+    for (float r : rows) sum += r;
+    if (loss_host) *loss_host = (float)(sum / batch);
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_gemm_bf16(reloc_ctx *ctx, const uint16_t *A_dev, const uint16_t *B_dev,
+                                        const float *bias_dev, float *C_dev, int M, int N, int K, int relu, int split_k,
+                                        void *stream)
+{
+    if (!ctx || !A_dev || !B_dev || !C_dev) return fail(RELOC_EINVAL, "NULL argument");
+    if (M < 1 || N < 1 || K < 64 || K % 64 || split_k < 1 || (K / split_k) % 64 || K % split_k)
+        return fail(RELOC_EINVAL, "gemm: K must be a multiple of 64 and of 64 * split_k");
+    if (((uintptr_t)A_dev & 15) || ((uintptr_t)B_dev & 15)) return fail(RELOC_EINVAL, "gemm: A, B need 16-byte alignment");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CKS(ctx->flags.ensure(64));
+    DevBuf &part = ctx->chunk_sums;     // scratch for split-K partials
+    if (split_k > 1) CKS(part.ensure(4 * (size_t)split_k * M * N));
+    CK(cudaMemsetAsync(ctx->flags.p, 0, 4, st));
+    CK(launch_gemm_bf16((const __nv_bfloat16 *)A_dev, (const __nv_bfloat16 *)B_dev, bias_dev, C_dev, nullptr, M, N, K,
+                        K, K, N, relu, split_k, part.as<float>(), ctx->flags.as<int>(), st));
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, ctx->flags.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status) return fail(RELOC_ETIMEOUT, "gemm: a tensor-core wait gave up");
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_set_proposal(reloc_ctx *ctx, int enabled, int top_k, float margin)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    if (enabled && !ctx->prop) return fail(RELOC_EINVAL, "no proposal network (reloc_proposal_init)");
+    if (top_k < 2 || top_k > 32 || !std::isfinite(margin)) return fail(RELOC_EINVAL, "top_k in 2..32, finite margin");
+    ctx->prop_enabled = enabled != 0;
+    ctx->prop_k = top_k;
+    ctx->prop_margin = margin;
     return RELOC_OK;
 }
 

@@ -155,6 +155,28 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 cudaError_t launch_argmax(const double *scores, const Layout &L, int *best, double *best_score, int *view_sel,
                           cudaStream_t st);
 
+// ---- learned candidate proposal (proposal.cu, cnn.cu, gemm.cu) ----------------
+constexpr int PROPOSAL_H = 47;
+constexpr int PROPOSAL_W = 176;
+constexpr int PROPOSAL_CLASSES = 64;
+struct ProposalNet;
+int64_t proposal_param_count();
+ProposalNet *proposal_create(uint64_t seed, cudaError_t *err);
+void proposal_destroy(ProposalNet *P);
+cudaError_t proposal_get(const ProposalNet *P, int which, float *flat);   // 0 params, 1 grads
+cudaError_t proposal_set(ProposalNet *P, const float *flat);
+cudaError_t proposal_forward(ProposalNet *P, const __nv_bfloat16 *in, int B, float *out, cudaStream_t st);
+cudaError_t proposal_train_step(ProposalNet *P, const __nv_bfloat16 *in, const int32_t *labels, int B, float lr,
+                                bool update, float *loss_rows_dev, cudaStream_t st);
+const float *proposal_logits(const ProposalNet *P);
+int *proposal_status(const ProposalNet *P);
+cudaError_t proposal_make_input(const float *query, const float *seed_rgb, int H, int W, __nv_bfloat16 *out,
+                                cudaStream_t st);
+cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias, float *Cf,
+                             __nv_bfloat16 *Cb, int M, int N, int K, int lda, int ldb, int ldc, int relu, int split_k,
+                             float *partials, int *status, cudaStream_t st);
+cudaError_t launch_topk(const float *logits, int B, int C, int k, int32_t *idx, float *margin, cudaStream_t st);
+
 // Record msg as the calling thread's last error; returns st.
 int reloc_internal_fail(int st, const char *msg);
 

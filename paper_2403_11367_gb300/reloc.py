@@ -72,7 +72,7 @@ class TuneResult(C.Structure):
 class Result(C.Structure):
     _fields_ = [("best_index", C.c_int32), ("n_candidates", C.c_int32), ("best_score", C.c_double),
                 ("best_pose", C.c_double * 16), ("n_gauss", C.c_int64), ("n_blocks", C.c_int32),
-                ("degenerate", C.c_int32)]
+                ("degenerate", C.c_int32), ("n_scored", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Counts(C.Structure):
@@ -108,6 +108,14 @@ SIGNATURES = {
     "reloc_set_batch_options": (C.c_int, [_vp, C.POINTER(BatchOptions)]),
     "reloc_autotune": (C.c_int, [_vp, C.POINTER(Query), C.c_int, C.POINTER(Camera), C.c_char_p, C.c_int,
                                  C.POINTER(TuneResult), _vp]),
+    "reloc_proposal_init": (C.c_int, [_vp, C.c_uint64]),
+    "reloc_proposal_get": (C.c_int, [_vp, C.c_int, _fp]),
+    "reloc_proposal_set_params": (C.c_int, [_vp, _fp]),
+    "reloc_proposal_make_input": (C.c_int, [_vp, _vp, _vp, C.POINTER(Camera), _vp, _vp]),
+    "reloc_proposal_forward": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp]),
+    "reloc_proposal_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_float, C.c_int, _fp, _vp]),
+    "reloc_set_proposal": (C.c_int, [_vp, C.c_int, C.c_int, C.c_float]),
+    "reloc_gemm_bf16": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp]),
     "reloc_last_counts": (C.c_int, [_vp, C.POINTER(Counts)]),
     "reloc_set_profiling": (C.c_int, [_vp, C.c_int]),
     "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
@@ -115,6 +123,7 @@ SIGNATURES = {
     "reloc_ncc_images_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
 }
 NOALLOC_MAX_VIEWS = 512
+PROPOSAL_H, PROPOSAL_W, PROPOSAL_CLASSES, PROPOSAL_PARAMS = 47, 176, 64, 1916960
 
 
 def _load():
@@ -332,6 +341,44 @@ class Context:
                                        C.byref(c), C.byref(res), hp(best_rgb_host), hp(best_depth_host),
                                        _stream(stream)))
         return res
+
+    # -- learned proposal ------------------------------------------------------------
+    def proposal_init(self, seed=0):
+        _check(lib.reloc_proposal_init(self._h, seed))
+
+    def proposal_get(self, which=0) -> np.ndarray:
+        out = np.zeros(PROPOSAL_PARAMS, np.float32)
+        _check(lib.reloc_proposal_get(self._h, which, out.ctypes.data_as(_fp)))
+        return out
+
+    def proposal_set_params(self, flat):
+        f = np.ascontiguousarray(flat, np.float32)
+        assert f.size == PROPOSAL_PARAMS
+        _check(lib.reloc_proposal_set_params(self._h, f.ctypes.data_as(_fp)))
+
+    def proposal_make_input(self, query, coarse_rgb, cam, out, stream=None):
+        c = camera(cam)
+        _check(lib.reloc_proposal_make_input(self._h, _ptr(query), _ptr(coarse_rgb), C.byref(c), _ptr(out),
+                                             _stream(stream)))
+
+    def proposal_forward(self, inputs, logits, stream=None):
+        _check(lib.reloc_proposal_forward(self._h, _ptr(inputs), inputs.shape[0], _ptr(logits), _stream(stream)))
+
+    def proposal_train_step(self, inputs, labels, lr, update=True, stream=None) -> float:
+        loss = C.c_float(0)
+        _check(lib.reloc_proposal_train_step(self._h, _ptr(inputs), _ptr(labels), inputs.shape[0], lr,
+                                             1 if update else 0, C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+    def gemm_bf16(self, A, B, C, bias=None, relu=False, split_k=1, stream=None):
+        """C[M,N] (float32) = A[M,K] @ B[N,K]^T for bfloat16 CUDA tensors."""
+        M, K = A.shape
+        N = B.shape[0]
+        _check(lib.reloc_gemm_bf16(self._h, _ptr(A), _ptr(B), _ptr(bias), _ptr(C), M, N, K, 1 if relu else 0,
+                                   split_k, _stream(stream)))
+
+    def set_proposal(self, enabled=True, top_k=8, margin=0.0):
+        _check(lib.reloc_set_proposal(self._h, 1 if enabled else 0, top_k, margin))
 
     # -- introspection ------------------------------------------------------------
     def last_counts(self) -> Counts:
