@@ -151,6 +151,84 @@ def run_batch_leg(ctx, cam, dev, stream, n_queries=256):
                                           "configs_timed": tune.n_tried}}
 
 
+WEIGHTS = os.path.join(ROOT, "paper_2403_11367_gb300", "weights", "proposal_street.bin")
+
+
+def run_learned_leg(ctx, cam, dev, stream, n_queries=256):
+    """Learned proposal (top-k + margin fallback) vs the plain 64-candidate
+    sweep on the same queries: queries/s of both, recall of the plain winner."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    if not os.path.exists(WEIGHTS):
+        return {"available": False, "reason": "no trained weights (run paper_2403_11367_gb300.train_proposal)"}
+    with open(os.path.splitext(WEIGHTS)[0] + ".json") as f:
+        meta = json.load(f)
+    ctx.proposal_init(0)
+    ctx.proposal_set_params(np.fromfile(WEIGHTS, dtype="<f4"))
+    hidden, seeds = sg.street_queries(n_queries, seed=33)
+    qs = []
+    for i in range(n_queries):
+        runs, _, _ = ctx.select_block(hidden[i][0], hidden[i][1], RADIUS)
+        img = torch.empty((1, 3, cam.height, cam.width), device=dev)
+        ctx.render(runs, sg.pose_from_xyz_yaw(*hidden[i])[None], cam, rgb=img)
+        img = (img[0] + torch.tensor(sg.image_noise(2000 + i, cam.height, cam.width), device=dev)).contiguous()
+        qs.append((img, sg.pose_from_xyz_yaw(*seeds[i]), RADIUS, GRID))
+    out = {"available": True, "queries": n_queries, "top_k": meta["top_k"], "tau": meta["tau"],
+           "trained_on": meta["samples"], "recall_heldout_4096": meta.get("recall_heldout")}
+    ctx.set_batch_options(use_graph=True, mem_budget=24 << 30)
+    best = {}
+    for mode in ("plain", "learned"):
+        ctx.set_proposal(mode == "learned", meta["top_k"], meta["tau"])
+        ctx.localize_batch(qs, cam, stream=stream, want_scores=False)       # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, _ = ctx.localize_batch(qs, cam, stream=stream, want_scores=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best[mode] = [r.best_index for r in res]
+        out[f"queries_per_s_{mode}"] = n_queries / (ms / 1e3)
+        out[f"candidates_scored_per_query_{mode}"] = float(np.mean([r.n_scored for r in res]))
+    ctx.set_proposal(False, meta["top_k"], meta["tau"])
+    ctx.set_batch_options(use_graph=False, mem_budget=16 << 30)
+    out["recall_vs_full_sweep"] = float(np.mean(np.array(best["plain"]) == np.array(best["learned"])))
+    out["speedup"] = out["queries_per_s_learned"] / out["queries_per_s_plain"]
+    return out
+
+
+def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best):
+    """FP16 / BF16 attribute storage on the driving workload: candidates/s and
+    deviation of every NCC score and winner from the FP32 path."""
+    import numpy as np
+    import torch
+    from paper_2403_11367_gb300 import reloc as R
+    out = {}
+    V = GRID[0] * GRID[1] * GRID[2]
+    for name, prec in (("fp16", R.FP16), ("bf16", R.BF16)):
+        ctx = R.Context(R.reloc_default_config())
+        ctx.load_map(g, prec)
+        dev_sc, agree = 0.0, 0
+        for k in range(len(queries)):
+            res, sc = ctx.localize(queries[k], seed_poses[k], RADIUS, GRID, cam, stream=stream)
+            dev_sc = max(dev_sc, float(np.abs(sc - ref_scores[k]).max()))
+            agree += int(res.best_index == ref_best[k])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(8):
+            ctx.localize(queries[k % len(queries)], seed_poses[k % len(queries)], RADIUS, GRID, cam, stream=stream,
+                         want_scores=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"candidates_per_s": 8 * V / (e0.elapsed_time(e1) / 1e3), "max_ncc_dev_vs_fp32": dev_sc,
+                     "winner_agreement_vs_fp32": agree / len(queries),
+                     "map_bytes_per_gaussian": 12 + 2 * (8 + 3 * 16)}
+        ctx.close()
+    return out
+
+
 def make_workload(rank: int = 0):
     import scenegen as sg
     g = sg.street_gaussians(N_GAUSS, seed=11, sh_degree=3)
@@ -310,7 +388,16 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    # FP32 reference scores of the bench queries for the precision leg
+    ref_scores, ref_best = [], []
+    for k in range(N_QUERIES):
+        res, sc = ctx.localize(queries[k], seed_poses[k], RADIUS, GRID, cam, stream=stream)
+        ref_scores.append(sc)
+        ref_best.append(res.best_index)
+    precision = run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best) \
+        if not args.no_batch else None
     batch = run_batch_leg(ctx, cam, dev, stream) if not args.no_batch else None
+    learned = run_learned_leg(ctx, cam, dev, stream) if not args.no_batch else None
 
     if rank != 0:
         if dist is not None:
@@ -350,6 +437,8 @@ def run_ours(args):
         "stage_ms": {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()},
         "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
         "batch": batch,
+        "learned": learned,
+        "precision": precision,
         "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},
         "clocks": clocks,
@@ -366,7 +455,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-batch", action="store_true", help="skip the 256-query batching leg")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batching, learned-proposal and precision legs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
