@@ -229,13 +229,38 @@ def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_
     return out
 
 
+def rank_queries(rank: int = 0):
+    """This replica's queries: the rank-th run of N_QUERIES draws of one seeded
+    query stream, so the ranks' queries are disjoint and rank 0's are the
+    single-GPU workload's."""
+    import scenegen as sg
+    hidden, seeds = sg.street_queries(N_QUERIES * (rank + 1), seed=12)
+    return hidden[N_QUERIES * rank:], seeds[N_QUERIES * rank:]
+
+
 def make_workload(rank: int = 0):
     import scenegen as sg
     g = sg.street_gaussians(N_GAUSS, seed=11, sh_degree=3)
     cam = sg.street_camera()
-    hidden, seeds = sg.street_queries(N_QUERIES * (rank + 1), seed=12)
-    hidden, seeds = hidden[N_QUERIES * rank:], seeds[N_QUERIES * rank:]
+    hidden, seeds = rank_queries(rank)
     return g, cam, hidden, seeds
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, slowest_s: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's time."""
+    return world * units_per_rank / slowest_s
 
 
 # ---------------------------------------------------------------- oracle ----
@@ -360,11 +385,8 @@ def run_ours(args):
     stage_ms, stage_calls = ctx.stage_times()
     counts = ctx.last_counts()
     ctx.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * V * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, total_ms, dev)
+    value = job_throughput(world, V * args.steps, total_ms / 1e3)
 
     # e2e: the host-buffer entry point, pinned host query and winner buffers
     qh = [q.cpu().pin_memory() for q in queries]
@@ -383,10 +405,7 @@ def run_ours(args):
         ctx.localize_host(qh[k % N_QUERIES], seed_poses[k % N_QUERIES], RADIUS, GRID, cam, rgb_h, dep_h,
                           stream=stream)
         e2e_s += time.perf_counter() - a
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, e2e_s, dev)
 
     # FP32 reference scores of the bench queries for the precision leg
     ref_scores, ref_best = [], []
@@ -421,8 +440,8 @@ def run_ours(args):
         "data": "synthetic (seeded street scene standing in for KITTI-360)",
         "config": {"workload": WORKLOAD, "queries": N_QUERIES, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas{world}"},
-        "queries_per_s": world * args.steps / (total_ms / 1e3),
-        "e2e": {"value": world * V * args.steps / e2e_s, "unit": UNIT,
+        "queries_per_s": job_throughput(world, args.steps, total_ms / 1e3),
+        "e2e": {"value": job_throughput(world, V * args.steps, e2e_s), "unit": UNIT,
                 # query image + candidate view parameters + block runs in; winner RGB + depth
                 # + per-view counts/scores + flags out
                 "h2d_bytes_per_step": 3 * H * W * 4 + 64 * V + 16 * (n_runs + 1),

@@ -44,12 +44,14 @@ struct CamParams {
 
 // Stable LSD radix sort over view-strided segments (sort.cu).
 constexpr int SORT_THREADS = 256;
-constexpr int SORT_IPT = 16;
-constexpr int SORT_CHUNK = SORT_THREADS * SORT_IPT;   // 4096 items per block
+constexpr int SORT_IPT = 8;
+constexpr int SORT_CHUNK = SORT_THREADS * SORT_IPT;   // 2048 items per block
 constexpr int RADIX = 256;
 constexpr int EMIT_THREADS = 256;
-constexpr int EMIT_IPT = 8;
-constexpr int EMIT_CHUNK = EMIT_THREADS * EMIT_IPT;   // 2048 items per block
+constexpr int EMIT_IPT = 4;
+constexpr int EMIT_CHUNK = EMIT_THREADS * EMIT_IPT;   // 1024 items per block
+constexpr int EMIT_RUN = 8;                           // consecutive entries per thread
+constexpr int EMIT_WINDOW = EMIT_THREADS * EMIT_RUN;  // entries staged per window
 
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }

@@ -94,26 +94,36 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
 // --------------------------------------------------- segment scan ----------
 // In-place exclusive scan of `count` words per segment; total_out[s] = sum.
 // In-place exclusive scan of segment s = data[mult*base[s], mult*base[s+1]);
-// total_out[s] = its sum.  One block per segment.
-constexpr int SCAN_THREADS = 1024;
+// total_out[s] = its sum.  One block per segment walks it in tiles of
+// SCAN_THREADS * 4 words (each thread 4 consecutive words, coalesced),
+// carrying the running total from tile to tile.
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_IPT = 4;
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_seg_scan(uint32_t *data, const int32_t *__restrict__ base, int mult, uint32_t *total_out)
 {
     __shared__ uint32_t s_tmp[33];
     uint32_t *a = data + (int64_t)mult * base[blockIdx.x];
     const int64_t count = (int64_t)mult * (base[blockIdx.x + 1] - base[blockIdx.x]);
-    const int64_t per = ceil_div(count, SCAN_THREADS);
-    const int64_t lo = min64(count, threadIdx.x * per), hi = min64(count, lo + per);
-    uint32_t sum = 0;
-    for (int64_t j = lo; j < hi; ++j) sum += a[j];
-    uint32_t tot;
-    uint32_t run = block_excl_scan(sum, s_tmp, &tot);
-    for (int64_t j = lo; j < hi; ++j) {
-        uint32_t t = a[j];
-        a[j] = run;
-        run += t;
+    uint32_t carry = 0;
+    for (int64_t t0 = 0; t0 < count; t0 += SCAN_THREADS * SCAN_IPT) {
+        const int64_t i0 = t0 + (int64_t)threadIdx.x * SCAN_IPT;
+        uint32_t v[SCAN_IPT], sum = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_IPT; ++j) {
+            v[j] = i0 + j < count ? a[i0 + j] : 0u;
+            sum += v[j];
+        }
+        uint32_t tot;
+        uint32_t run = carry + block_excl_scan(sum, s_tmp, &tot);
+#pragma unroll
+        for (int j = 0; j < SCAN_IPT; ++j) {
+            if (i0 + j < count) a[i0 + j] = run;
+            run += v[j];
+        }
+        carry += tot;
     }
-    if (total_out && threadIdx.x == 0) total_out[blockIdx.x] = tot;
+    if (total_out && threadIdx.x == 0) total_out[blockIdx.x] = carry;
 }
 
 // ------------------------------------------------------------ scatter ------
@@ -244,6 +254,7 @@ k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis
     __shared__ uint32_t s_g[EMIT_CHUNK];
     __shared__ uint32_t s_off[EMIT_CHUNK];
     __shared__ uint2 s_rect[EMIT_CHUNK];
+    __shared__ uint2 s_win[EMIT_WINDOW];
     __shared__ uint32_t s_tmp[33];
     const int c = blockIdx.x;
     const int v = find_segment(L.ce_base, L.V, c);
@@ -285,21 +296,48 @@ k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis
         run += loc[r];
     }
     __syncthreads();
-    // one thread per emitted entry: find its item by binary search
+    // Windows of EMIT_THREADS * EMIT_RUN entries: each thread fills EMIT_RUN
+    // consecutive entries of the window in shared memory (one binary search,
+    // then a walk along the items' tile rectangles, row-major), and the block
+    // copies the window out with coalesced stores.
     const int64_t obase = L.io_off[v] + chunk_off[c];
-    for (uint32_t m = threadIdx.x; m < total; m += EMIT_THREADS) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= m) lo = mid; else hi = mid - 1;
+    for (uint32_t w0 = 0; w0 < total; w0 += EMIT_WINDOW) {
+        const uint32_t m0 = w0 + threadIdx.x * EMIT_RUN;
+        if (m0 < total) {
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= m0) lo = mid; else hi = mid - 1;
+            }
+            uint2 rc = s_rect[lo];
+            uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.x >> 16, y0 = rc.y & 0xFFFFu;
+            const uint32_t local = m0 - s_off[lo], w = x1 - x0 + 1;
+            uint32_t ty = y0 + local / w, tx = x0 + local % w;
+            uint32_t end = lo + 1 < n ? s_off[lo + 1] : total;
+            uint32_t gi = s_g[lo];
+            const uint32_t m1 = min(total, m0 + EMIT_RUN);
+            for (uint32_t m = m0; m < m1; ++m) {
+                while (m == end) {                   // next item with tiles
+                    ++lo;
+                    rc = s_rect[lo];
+                    x0 = rc.x & 0xFFFFu; x1 = rc.x >> 16; y0 = rc.y & 0xFFFFu;
+                    tx = x0;
+                    ty = y0;
+                    gi = s_g[lo];
+                    end = lo + 1 < n ? s_off[lo + 1] : total;
+                }
+                s_win[m - w0] = make_uint2(ty * (uint32_t)ntx + tx, gi);
+                if (++tx > x1) { tx = x0; ++ty; }
+            }
         }
-        const uint2 rc = s_rect[lo];
-        const uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.x >> 16, y0 = rc.y & 0xFFFFu;
-        const uint32_t w = x1 - x0 + 1;
-        const uint32_t local = m - s_off[lo];
-        const uint32_t ty = y0 + local / w, tx = x0 + local % w;
-        inst_tile[obase + m] = ty * (uint32_t)ntx + tx;
-        inst_gauss[obase + m] = s_g[lo];
+        __syncthreads();
+        const uint32_t wn = min((uint32_t)EMIT_WINDOW, total - w0);
+        for (uint32_t j = threadIdx.x; j < wn; j += EMIT_THREADS) {
+            const uint2 e = s_win[j];
+            inst_tile[obase + w0 + j] = e.x;
+            inst_gauss[obase + w0 + j] = e.y;
+        }
+        __syncthreads();
     }
 }
 
