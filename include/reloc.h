@@ -120,9 +120,8 @@ enum {
     RELOC_STAGE_CULL = 0,      /* block subset gather (K1)                              */
     RELOC_STAGE_PROJECT,       /* EWA projection + SH (K2)                              */
     RELOC_STAGE_DEPTH_SORT,    /* visibility compaction + depth radix sort             */
-    RELOC_STAGE_EMIT,          /* scan of tile counts + tile|depth instance emission (K3) */
-    RELOC_STAGE_TILE_SORT,     /* stable tile radix sort (K4)                          */
-    RELOC_STAGE_RANGES,        /* tile ranges (K5)                                      */
+    RELOC_STAGE_TILE_COUNT,    /* per-chunk tile counts, scan into tile ranges (K3)     */
+    RELOC_STAGE_TILE_EMIT,     /* instances into depth-ordered tile lists (K4)          */
     RELOC_STAGE_BLEND,         /* blend + fused NCC partials (K6, K7 partials)          */
     RELOC_STAGE_SCORE,         /* NCC finalise + argmax + winner export (K7, K8)        */
     RELOC_STAGE_COUNT

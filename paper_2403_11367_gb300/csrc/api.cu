@@ -1,13 +1,13 @@
 // api.cu -- the C ABI of reloc.h: context, map load, block selection,
 // candidate grid, and the per-call orchestration of the kernels
-// (K1 gather -> K2 project -> depth sort -> K3 emit -> K4 tile sort ->
-//  K5 ranges -> K6 blend + NCC partials -> K7 NCC -> K8 argmax -> export).
+// (K1 gather -> K2 project -> depth sort -> K3 tile counts + ranges ->
+//  K4 tile emission -> K6 blend + NCC partials -> K7 NCC -> K8 argmax -> export).
 //
 // All stages run on the caller's stream with device-resident counts, so a
 // call needs one host synchronisation at its end (to return scores and to
 // check workspace capacity).  If a view produced more tile instances than
 // the workspace holds, the call grows the workspace to the size the device
-// reported and re-runs from the emission stage.
+// reported and re-runs the call.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -117,7 +117,7 @@ struct reloc_ctx {
     BlockIndex blocks;
     // workspace (sized for the largest sub-batch of a call)
     DevBuf gidx, tables, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums;
-    DevBuf ikA, ivA, ikB, ivB, hist2, ranges, partials, qpart, qstats;
+    DevBuf srect, bhist, inst, ranges, partials, qpart, qstats;
     // per-call results (all views / queries of the call)
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
     DevBuf hq, hrgb, hdepth;
@@ -133,7 +133,6 @@ struct reloc_ctx {
     int64_t last_S = 0;
     CamParams last_cam{};
     bool last_valid = false;
-    bool last_final_b = false;      // final instance lists live in ikB/ivB
     std::vector<int64_t> last_ninst, last_io_off, last_vd_off;
     reloc_counts counts{};
     // learned candidate proposal
@@ -214,6 +213,11 @@ extern "C" reloc_status reloc_create(const reloc_config *cfg, int device, reloc_
         reloc_destroy(ctx);
         return fail(RELOC_ECUDA, "stream/event creation failed");
     }
+    if (configure_tile_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        reloc_destroy(ctx);
+        return fail(RELOC_ECUDA, "kernel attribute setup failed");
+    }
     *out = ctx;
     return RELOC_OK;
 }
@@ -224,7 +228,7 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
     cudaSetDevice(ctx->device);
     DevBuf *bufs[] = {&ctx->mean, &ctx->attr, &ctx->gidx, &ctx->tables, &ctx->rec, &ctx->rect, &ctx->ntiles,
                       &ctx->dkey, &ctx->k1a, &ctx->v1a, &ctx->k1b, &ctx->v1b, &ctx->hist1, &ctx->chunk_sums,
-                      &ctx->ikA, &ctx->ivA, &ctx->ikB, &ctx->ivB, &ctx->hist2, &ctx->ranges, &ctx->partials,
+                      &ctx->srect, &ctx->bhist, &ctx->inst, &ctx->ranges, &ctx->partials,
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
                       &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
                       &ctx->hdepth, &ctx->prop_in, &ctx->prop_seed, &ctx->prop_logits, &ctx->prop_idx,
@@ -404,6 +408,7 @@ static reloc_status make_cam(const reloc_ctx *ctx, const reloc_camera *cam, CamP
     int tb = 0;
     while ((1 << tb) < cp.n_tiles) ++tb;
     cp.tile_bits = tb;
+    cp.bin_chunk = BIN_CHUNK_MIN * (int)std::max<int64_t>(1, ceil_div(cp.n_tiles, BIN_TILES_PER_CHUNK_STEP));
     cp.fx = (float)cam->fx;
     cp.fy = (float)cam->fy;
     cp.cx = (float)cam->cx;
@@ -465,8 +470,8 @@ struct CallOut {
 struct SubBatch {
     int q0 = 0, q1 = 0, v0 = 0, v1 = 0;
     int64_t S_tot = 0, VS = 0, VI = 0;
-    int c1 = 0, ce = 0, c2 = 0, pblk = 0, n_runs = 0;
-    std::vector<int32_t> view_q, c1_base, ce_base, c2_base, q_view, q_pblk;
+    int c1 = 0, cb = 0, pblk = 0, n_runs = 0;
+    std::vector<int32_t> view_q, c1_base, cb_base, q_view, q_pblk;
     std::vector<int64_t> vd_off, io_off, q_gsub, run_begin, run_off;
     std::vector<ViewParams> views;
     std::vector<const float *> q_img;
@@ -486,9 +491,15 @@ static int64_t inst_cap(const reloc_ctx *ctx, int64_t S, int64_t override_cap)
     return ceil_div(c, SORT_CHUNK) * SORT_CHUNK;
 }
 
-static int64_t query_bytes(int64_t S, int V, int64_t cap, int n_tiles)
+// Workspace bytes of one query: per view, the per-Gaussian arrays (records,
+// rectangle, tile count, depth key, two key/value radix buffers, depth-ordered
+// rectangle, radix histograms), the instance list, ranges + NCC partials and
+// the per-chunk tile counts; plus the gathered subset.
+static int64_t query_bytes(int64_t S, int V, int64_t cap, const CamParams &cp)
 {
-    return (int64_t)V * (S * 80 + cap * 16 + (int64_t)n_tiles * 32 + 1024) + S * 4 + 4096;
+    const int64_t per_view = S * 89 + cap * 4 + (int64_t)cp.n_tiles * 32 +
+                             4 * (int64_t)cp.n_tiles * ceil_div(S, cp.bin_chunk) + 1024;
+    return (int64_t)V * per_view + S * 4 + 4096;
 }
 
 // Split the call into sub-batches and build each one's host tables.
@@ -504,7 +515,7 @@ static void plan_batches(const reloc_ctx *ctx, const std::vector<QuerySpec> &qs,
         sb.v0 = vglob;
         int64_t bytes = 0;
         while (q < Q) {
-            const int64_t b = query_bytes(qs[q].S, qs[q].V, caps[q], cp.n_tiles);
+            const int64_t b = query_bytes(qs[q].S, qs[q].V, caps[q], cp);
             if (q > sb.q0 && bytes + b > ctx->mem_budget) break;
             bytes += b;
             vglob += qs[q].V;
@@ -516,8 +527,7 @@ static void plan_batches(const reloc_ctx *ctx, const std::vector<QuerySpec> &qs,
         sb.vd_off.assign(nv + 1, 0);
         sb.io_off.assign(nv + 1, 0);
         sb.c1_base.assign(nv + 1, 0);
-        sb.ce_base.assign(nv + 1, 0);
-        sb.c2_base.assign(nv + 1, 0);
+        sb.cb_base.assign(nv + 1, 0);
         sb.view_q.assign(nv, 0);
         sb.q_gsub.assign(nq + 1, 0);
         sb.q_view.assign(nq + 1, 0);
@@ -543,22 +553,20 @@ static void plan_batches(const reloc_ctx *ctx, const std::vector<QuerySpec> &qs,
                 sb.vd_off[v + 1] = sb.vd_off[v] + Qs.S;
                 sb.io_off[v + 1] = sb.io_off[v] + cap;
                 sb.c1_base[v + 1] = sb.c1_base[v] + (int32_t)ceil_div(Qs.S, SORT_CHUNK);
-                sb.ce_base[v + 1] = sb.ce_base[v] + (int32_t)ceil_div(Qs.S, EMIT_CHUNK);
-                sb.c2_base[v + 1] = sb.c2_base[v] + (int32_t)ceil_div(cap, SORT_CHUNK);
+                sb.cb_base[v + 1] = sb.cb_base[v] + (int32_t)ceil_div(Qs.S, cp.bin_chunk);
             }
         }
         sb.S_tot = sb.q_gsub[nq];
         sb.VS = sb.vd_off[nv];
         sb.VI = sb.io_off[nv];
         sb.c1 = sb.c1_base[nv];
-        sb.ce = sb.ce_base[nv];
-        sb.c2 = sb.c2_base[nv];
+        sb.cb = sb.cb_base[nv];
         sb.pblk = sb.q_pblk[nq];
         sb.n_runs = (int)sb.run_begin.size();
         if (sb.run_begin.empty()) sb.run_begin.push_back(0);
         // table bytes (each array 256-aligned)
         size_t t = 0;
-        t += align256(4 * (size_t)nv) + 2 * align256(8 * (size_t)(nv + 1)) + 3 * align256(4 * (size_t)(nv + 1));
+        t += align256(4 * (size_t)nv) + 2 * align256(8 * (size_t)(nv + 1)) + 2 * align256(4 * (size_t)(nv + 1));
         t += align256(8 * (size_t)(nq + 1)) + 2 * align256(4 * (size_t)(nq + 1)) + align256(8 * (size_t)nq);
         t += align256(8 * sb.run_begin.size()) + align256(8 * sb.run_off.size()) + align256(sizeof(ViewParams) * nv);
         sb.tab_bytes = t;
@@ -584,8 +592,7 @@ static void stage_tables(SubBatch &sb, char *host, char *dev)
     sb.L.vd_off = (const int64_t *)put(sb.vd_off.data(), 8 * (size_t)(nv + 1));
     sb.L.io_off = (const int64_t *)put(sb.io_off.data(), 8 * (size_t)(nv + 1));
     sb.L.c1_base = (const int32_t *)put(sb.c1_base.data(), 4 * (size_t)(nv + 1));
-    sb.L.ce_base = (const int32_t *)put(sb.ce_base.data(), 4 * (size_t)(nv + 1));
-    sb.L.c2_base = (const int32_t *)put(sb.c2_base.data(), 4 * (size_t)(nv + 1));
+    sb.L.cb_base = (const int32_t *)put(sb.cb_base.data(), 4 * (size_t)(nv + 1));
     sb.L.q_gsub = (const int64_t *)put(sb.q_gsub.data(), 8 * (size_t)(nq + 1));
     sb.L.q_view = (const int32_t *)put(sb.q_view.data(), 4 * (size_t)(nq + 1));
     sb.L.q_pblk = (const int32_t *)put(sb.q_pblk.data(), 4 * (size_t)(nq + 1));
@@ -602,7 +609,7 @@ static void stage_mark(reloc_ctx *ctx, int sbi, int s, cudaStream_t st, bool cap
 
 // Enqueue every kernel of one sub-batch on st.  Returns the launch count.
 static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, const CamParams &cp, const CallOut &o,
-                                     cudaStream_t st, bool capturing, int &launches, bool &final_b)
+                                     cudaStream_t st, bool capturing, int &launches)
 {
     const int64_t HW = (int64_t)cp.width * cp.height;
     const Layout &L = sb.L;
@@ -660,51 +667,17 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
             launches += 3;
         }
     }
-    stage_mark(ctx, sbi, RELOC_STAGE_EMIT, st, capturing);
-    if (sb.ce > 0) {
-        CK(launch_emit(ctx->v1b.as<uint32_t>(), nvis, ctx->ntiles.as<uint32_t>(), ctx->rect.as<uint2>(), L, sb.ce,
-                       cp.ntx, ctx->chunk_sums.as<uint32_t>(), ctx->ikA.as<uint32_t>(), ctx->ivA.as<uint32_t>(), ninst,
-                       d_overflow, st));
-        launches += 3;
+    stage_mark(ctx, sbi, RELOC_STAGE_TILE_COUNT, st, capturing);
+    CK(launch_tile_count(ctx->v1b.as<uint32_t>(), nvis, ctx->rect.as<uint2>(), L, cp, sb.cb, ctx->srect.as<uint2>(),
+                         ctx->bhist.as<uint32_t>(), ctx->ranges.as<int2>(), ninst, d_overflow, st));
+    launches += sb.cb > 0 ? 3 : 2;
+    stage_mark(ctx, sbi, RELOC_STAGE_TILE_EMIT, st, capturing);
+    if (sb.cb > 0) {
+        CK(launch_tile_emit(ctx->v1b.as<uint32_t>(), ctx->srect.as<uint2>(), nvis, ninst, ctx->bhist.as<uint32_t>(),
+                            ctx->ranges.as<int2>(), L, cp, sb.cb, ctx->inst.as<uint32_t>(), st));
+        launches += 1;
     }
-    stage_mark(ctx, sbi, RELOC_STAGE_TILE_SORT, st, capturing);
-    final_b = false;
-    if (sb.c2 > 0 && sb.ce > 0 && cp.tile_bits > 0) {
-        RadixPass p{};
-        p.seg_off = L.io_off;
-        p.chunk_base = L.c2_base;
-        p.n_seg = L.V;
-        p.total_chunks = sb.c2;
-        p.hist = ctx->hist2.as<uint32_t>();
-        p.len = ninst;
-        const int b1 = cp.tile_bits <= 8 ? cp.tile_bits : (cp.tile_bits + 1) / 2;
-        const int b2 = cp.tile_bits - b1;
-        p.keys_in = ctx->ikA.as<uint32_t>();
-        p.vals_in = ctx->ivA.as<uint32_t>();
-        p.keys_out = ctx->ikB.as<uint32_t>();
-        p.vals_out = ctx->ivB.as<uint32_t>();
-        p.shift = 0;
-        p.mask = (1u << b1) - 1;
-        CK(launch_radix_pass(p, st));
-        launches += 3;
-        final_b = true;
-        if (b2 > 0) {
-            p.keys_in = ctx->ikB.as<uint32_t>();
-            p.vals_in = ctx->ivB.as<uint32_t>();
-            p.keys_out = ctx->ikA.as<uint32_t>();
-            p.vals_out = ctx->ivA.as<uint32_t>();
-            p.shift = b1;
-            p.mask = (1u << b2) - 1;
-            CK(launch_radix_pass(p, st));
-            launches += 3;
-            final_b = false;
-        }
-    }
-    const uint32_t *ftile = final_b ? ctx->ikB.as<uint32_t>() : ctx->ikA.as<uint32_t>();
-    const uint32_t *fgauss = final_b ? ctx->ivB.as<uint32_t>() : ctx->ivA.as<uint32_t>();
-    stage_mark(ctx, sbi, RELOC_STAGE_RANGES, st, capturing);
-    CK(launch_ranges(ftile, ninst, L, cp.n_tiles, ctx->ranges.as<int2>(), d_overflow, st));
-    launches += 1;
+    const uint32_t *fgauss = ctx->inst.as<uint32_t>();
     stage_mark(ctx, sbi, RELOC_STAGE_BLEND, st, capturing);
     if (o.score) {
         CK(launch_query_stats(L, 3 * HW, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
@@ -772,19 +745,17 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
     std::vector<int64_t> caps(Q, 0);
     std::vector<SubBatch> sbs;
     int retries = 0, launches = 0;
-    bool final_b = false;
     for (;;) {
         plan_batches(ctx, qs, caps, cp, sbs);
         // ---- workspace: the largest sub-batch --------------------------------
-        int64_t S_tot = 1, VS = 1, VI = 1, c1 = 1, ce = 1, c2 = 1, V = 1, Qm = 1;
+        int64_t S_tot = 1, VS = 1, VI = 1, c1 = 1, cb = 1, V = 1, Qm = 1;
         size_t tab = 0;
         for (auto &sb : sbs) {
             S_tot = std::max(S_tot, sb.S_tot);
             VS = std::max(VS, sb.VS);
             VI = std::max(VI, sb.VI);
             c1 = std::max<int64_t>(c1, sb.c1);
-            ce = std::max<int64_t>(ce, sb.ce);
-            c2 = std::max<int64_t>(c2, sb.c2);
+            cb = std::max<int64_t>(cb, sb.cb);
             V = std::max<int64_t>(V, sb.v1 - sb.v0);
             Qm = std::max<int64_t>(Qm, sb.q1 - sb.q0);
             sb.tab_off = tab;
@@ -800,12 +771,9 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->k1b.ensure(4 * (size_t)VS));
         CKS(ctx->v1b.ensure(4 * (size_t)VS));
         CKS(ctx->hist1.ensure(4 * (size_t)RADIX * c1));
-        CKS(ctx->chunk_sums.ensure(4 * (size_t)ce));
-        CKS(ctx->ikA.ensure(4 * (size_t)VI));
-        CKS(ctx->ivA.ensure(4 * (size_t)VI));
-        CKS(ctx->ikB.ensure(4 * (size_t)VI));
-        CKS(ctx->ivB.ensure(4 * (size_t)VI));
-        CKS(ctx->hist2.ensure(4 * (size_t)RADIX * c2));
+        CKS(ctx->srect.ensure(8 * (size_t)VS));
+        CKS(ctx->bhist.ensure(4 * (size_t)cp.n_tiles * cb));
+        CKS(ctx->inst.ensure(4 * (size_t)VI));
         CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
         CKS(ctx->partials.ensure(24 * (size_t)V * cp.n_tiles));
         CKS(ctx->qpart.ensure(16 * 152 * (size_t)Qm));
@@ -857,7 +825,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             reloc_status rs = RELOC_OK;
             for (size_t k = 0; k < sbs.size() && rs == RELOC_OK; ++k)
-                rs = enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, true, launches, final_b);
+                rs = enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, true, launches);
             cudaError_t ce_ = cudaStreamEndCapture(st, &g);
             if (rs != RELOC_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -871,7 +839,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
             cudaGraphExecDestroy(ge);
             if (ce_ != cudaSuccess) return fail(RELOC_ECUDA, "graph launch: %s", cudaGetErrorString(ce_));
         } else {
-            for (size_t k = 0; k < sbs.size(); ++k) CKS(enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, false, launches, final_b));
+            for (size_t k = 0; k < sbs.size(); ++k) CKS(enqueue_subbatch(ctx, sbs[k], (int)k, cp, o, st, false, launches));
         }
         // ---- readback --------------------------------------------------------------
         CK(cudaMemcpyAsync(h_overflow, ctx->flags.p, 4, cudaMemcpyDeviceToHost, st));
@@ -948,7 +916,6 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
     ctx->last_V = sbs[0].v1 - sbs[0].v0;
     ctx->last_S = qs[0].S;
     ctx->last_cam = cp;
-    ctx->last_final_b = final_b;
     ctx->last_io_off = sbs[0].io_off;
     ctx->last_vd_off = sbs[0].vd_off;
     ctx->last_valid = sbs.size() == 1 && sbs[0].q1 - sbs[0].q0 == 1;
@@ -1487,11 +1454,11 @@ extern "C" reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, i
         CK(cudaGetLastError());
     }
     if (inst_tiles_dev && VI)
-        CK(cudaMemcpyAsync(inst_tiles_dev, ctx->last_final_b ? ctx->ikB.p : ctx->ikA.p, 4 * VI,
-                           cudaMemcpyDeviceToDevice, st));
+        for (int v = 0; v < ctx->last_V; ++v)
+            CK(launch_fill_tiles(ctx->ranges.as<int2>() + (int64_t)v * ctx->last_cam.n_tiles, ctx->last_cam.n_tiles,
+                                 inst_tiles_dev + ctx->last_io_off[v], st));
     if (inst_gauss_dev && VI)
-        CK(cudaMemcpyAsync(inst_gauss_dev, ctx->last_final_b ? ctx->ivB.p : ctx->ivA.p, 4 * VI,
-                           cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(inst_gauss_dev, ctx->inst.p, 4 * VI, cudaMemcpyDeviceToDevice, st));
     if (ranges_dev)
         CK(cudaMemcpyAsync(ranges_dev, ctx->ranges.p, sizeof(int2) * (size_t)ctx->last_V * ctx->last_cam.n_tiles,
                            cudaMemcpyDeviceToDevice, st));

@@ -40,6 +40,7 @@ struct CamParams {
     float near_plane, eps2d, cut, det_fp64;
     float alpha_min, alpha_max, t_min;
     int blend_rpl;     // records per lane per warp step in K6 (1 or 2)
+    int bin_chunk;     // depth-ordered Gaussians per tile-binning chunk (K3, K4)
 };
 
 // Stable LSD radix sort over view-strided segments (sort.cu).
@@ -47,11 +48,12 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_IPT = 8;
 constexpr int SORT_CHUNK = SORT_THREADS * SORT_IPT;   // 2048 items per block
 constexpr int RADIX = 256;
-constexpr int EMIT_THREADS = 256;
-constexpr int EMIT_IPT = 4;
-constexpr int EMIT_CHUNK = EMIT_THREADS * EMIT_IPT;   // 1024 items per block
-constexpr int EMIT_RUN = 8;                           // consecutive entries per thread
-constexpr int EMIT_WINDOW = EMIT_THREADS * EMIT_RUN;  // entries staged per window
+// Tile binning (sort.cu): chunks of bin_chunk depth-ordered Gaussians.
+constexpr int BIN_CHUNK_MIN = 2048;
+constexpr int BIN_TILES_PER_CHUNK_STEP = 8192;        // bin_chunk grows by 2048 per 8192 tiles
+constexpr int TILE_COUNT_SMEM = 48 * 1024;            // difference-array band
+constexpr int TILE_EMIT_WARPS = 8;                    // tile rows per K4 block
+constexpr int TILE_EMIT_SMEM_MAX = 64 * 1024;         // slot counters: 8 rows x ntx <= 2048
 
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -63,7 +65,7 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 // of the call; every per-(view, Gaussian) array places view v at vd_off[v]
 // (length S of its query) and every per-(view, instance) array at io_off[v]
 // (capacity io_off[v+1] - io_off[v]).  The chunk bases map a block index to
-// its view and chunk for the sort, emission and scan kernels.  All tables are
+// its view and chunk for the sort, binning and scan kernels.  All tables are
 // built on the host and live in device memory for the call.
 struct Layout {
     int Q, V;
@@ -71,8 +73,7 @@ struct Layout {
     const int64_t *vd_off;     // [V+1] dense offsets
     const int64_t *io_off;     // [V+1] instance offsets
     const int32_t *c1_base;    // [V+1] depth-sort chunk base (SORT_CHUNK)
-    const int32_t *ce_base;    // [V+1] emission chunk base (EMIT_CHUNK)
-    const int32_t *c2_base;    // [V+1] tile-sort chunk base (SORT_CHUNK)
+    const int32_t *cb_base;    // [V+1] tile-binning chunk base (bin_chunk)
     const int64_t *q_gsub;     // [Q+1] subset offsets into the gathered index list
     const int32_t *q_view;     // [Q+1] first view of each query
     const int32_t *q_pblk;     // [Q+1] projection block base
@@ -121,19 +122,27 @@ struct RadixPass {
 };
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
 
-// K3: scan of tile counts in depth order + instance emission.  sorted_g holds
-// each view's visible Gaussians in depth order (n_vis[v] at vd_off[v]);
-// writes (tile, Gaussian) entries at io_off[v] in (depth, index) order and
-// n_inst[V].  A view needing more than its capacity emits nothing and sets
-// *overflow.  n_chunks = ce_base[V] (host copy).
-cudaError_t launch_emit(const uint32_t *sorted_g, const uint32_t *n_vis, const uint32_t *ntiles,
-                        const uint2 *rect, const Layout &L, int n_chunks, int ntx, uint32_t *chunk_sums,
-                        uint32_t *inst_tile, uint32_t *inst_gauss, uint32_t *n_inst, int *overflow,
-                        cudaStream_t st);
+// K3: per chunk of each view's depth-ordered visible Gaussians (sorted_g,
+// n_vis[v] at vd_off[v]) the number covering each tile -> bhist[chunk][tile]
+// (n_chunks = cb_base[V], host copy); rectangles in depth order -> srect;
+// then per view the chunk prefix per tile (in place), ranges[v][tile] =
+// [begin, end) of the tile's list relative to io_off[v] (empty [0, 0)) and
+// n_inst[v].  A view over its capacity sets *overflow.
+cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, const uint2 *rect, const Layout &L,
+                              const CamParams &cp, int n_chunks, uint2 *srect, uint32_t *bhist, int2 *ranges,
+                              uint32_t *n_inst, int *overflow, cudaStream_t st);
 
-// K5: per (view, tile) [begin, end) into the view's sorted instance list.
-cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, const Layout &L, int n_tiles,
-                          int2 *ranges, const int *overflow, cudaStream_t st);
+// K4: every (tile, Gaussian) instance into inst_gauss at io_off[v] + its slot,
+// each tile's list in (depth, index) order.  Views over capacity emit nothing.
+cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
+                             const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
+                             const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st);
+
+// Allow K4 its largest shared-memory footprint (once per device, before any capture).
+cudaError_t configure_tile_kernels();
+
+// Tile id of each instance of one view from its ranges (debug export).
+cudaError_t launch_fill_tiles(const int2 *ranges_view, int n_tiles, uint32_t *tiles_view, cudaStream_t st);
 
 // Query statistics S_q, S_qq over n samples of each of the Q query images
 // -> qstats[Q][2] (double).  block_scratch: Q * 2 * 152 doubles.

@@ -2,16 +2,18 @@
 //
 // Sec. III-A of 3DGS-ReLoc composites each pixel's Gaussians "sorted by
 // depth".  Per view the required order of a tile's list is (depth, Gaussian
-// index).  It is produced in two stable stages instead of one wide-key sort:
+// index).  It is produced without any sort over the (much larger) instance
+// list:
 //   1. a stable LSD radix sort of the visible (view, Gaussian) pairs by the
 //      float32 depth bit pattern (4 passes of 8 bits; the first pass also
 //      drops invisible pairs, so compaction costs nothing extra);
-//   2. emission of one (tile, Gaussian) entry per covered tile in that depth
-//      order (K3), then a stable LSD radix sort by tile id (K4, 1-2 passes).
-// Stability of both stages makes every tile's list ordered by depth and, for
-// equal depth bits, by Gaussian index -- the same order as one stable sort of
-// view|tile|depth keys emitted in index order, with far fewer passes over the
-// (much larger) instance list.
+//   2. per chunk of that depth order, tile coverage counts (K3: 2D difference
+//      arrays), scanned into each tile's list start and each chunk's slot in it;
+//   3. emission of every (tile, Gaussian) instance straight into its slot, a
+//      warp per (chunk, tile row) walking the chunk in depth order (K4).
+// Stability of the depth sort makes every tile's list ordered by depth and,
+// for equal depth bits, by Gaussian index -- the same order as one stable sort
+// of view|tile|depth keys emitted in index order.
 //
 // Every per-view array sits at a host-planned offset with a host-planned
 // capacity, and chunk tables map a block to its view and chunk, so valid
@@ -222,162 +224,338 @@ cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------- K3 emit -----
+// ------------------------------------------------------ K3 tile counts -----
+// Each view's visible Gaussians, in depth order, are cut into chunks of
+// cp.bin_chunk.  Per chunk, k_tile_count counts how many of them cover each
+// tile: every rectangle adds +1/-1 at its four corners of a 2D difference
+// array in shared memory, and two prefix sums (along x, then y) turn it into
+// counts.  The tile grid is processed in row bands that fit shared memory.
+// It also writes the rectangles in depth order (srect) for K4.
+constexpr int BIN_THREADS = 256;
 
-__global__ void __launch_bounds__(EMIT_THREADS)
-k_emit_sums(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis,
-            const uint32_t *__restrict__ ntiles, Layout L, uint32_t *__restrict__ chunk_sums)
+__global__ void __launch_bounds__(BIN_THREADS)
+k_tile_count(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis,
+             const uint2 *__restrict__ rect, Layout L, CamParams cp, int band_rows, uint2 *__restrict__ srect,
+             uint32_t *__restrict__ bhist)
 {
-    __shared__ uint32_t s_tmp[33];
+    extern __shared__ uint32_t s_d[];   // (band_rows + 1) x (ntx + 1)
     const int c = blockIdx.x;
-    const int v = find_segment(L.ce_base, L.V, c);
-    const int k = c - L.ce_base[v];
+    const int v = find_segment(L.cb_base, L.V, c);
+    const int k = c - L.cb_base[v];
     const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
     const int64_t nv = min64(n_vis[v], S);
-    const int64_t begin = (int64_t)k * EMIT_CHUNK;
-    const int n = (int)max64(0, min64(EMIT_CHUNK, nv - begin));
-    const uint32_t *g = sorted_g + L.vd_off[v] + begin;
-    const uint32_t *nt = ntiles + L.vd_off[v];
-    uint32_t sum = 0;
-    for (int j = threadIdx.x; j < n; j += EMIT_THREADS) sum += nt[g[j]];
-    uint32_t tot;
-    block_excl_scan(sum, s_tmp, &tot);
-    if (threadIdx.x == 0) chunk_sums[c] = tot;
-}
-
-__global__ void __launch_bounds__(EMIT_THREADS)
-k_emit(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__ n_vis,
-       const uint32_t *__restrict__ ntiles, const uint2 *__restrict__ rect, Layout L, int ntx,
-       const uint32_t *__restrict__ chunk_off, const uint32_t *__restrict__ n_inst,
-       uint32_t *__restrict__ inst_tile, uint32_t *__restrict__ inst_gauss, int *overflow)
-{
-    __shared__ uint32_t s_g[EMIT_CHUNK];
-    __shared__ uint32_t s_off[EMIT_CHUNK];
-    __shared__ uint2 s_rect[EMIT_CHUNK];
-    __shared__ uint2 s_win[EMIT_WINDOW];
-    __shared__ uint32_t s_tmp[33];
-    const int c = blockIdx.x;
-    const int v = find_segment(L.ce_base, L.V, c);
-    const int k = c - L.ce_base[v];
-    const int64_t cap = L.io_off[v + 1] - L.io_off[v];
-    if ((int64_t)n_inst[v] > cap) {                     // this view does not fit
-        if (k == 0 && threadIdx.x == 0) atomicExch(overflow, 1);
-        return;
-    }
-    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
-    const int64_t nv = min64(n_vis[v], S);
-    const int64_t begin = (int64_t)k * EMIT_CHUNK;
+    const int64_t begin = (int64_t)k * cp.bin_chunk;
     if (begin >= nv) return;
-    const int n = (int)min64(EMIT_CHUNK, nv - begin);
+    const int n = (int)min64(cp.bin_chunk, nv - begin);
+    const int ntx = cp.ntx, W = ntx + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *g = sorted_g + L.vd_off[v] + begin;
-    for (int j = threadIdx.x; j < n; j += EMIT_THREADS) {
-        const uint32_t gi = g[j];
-        s_g[j] = gi;
-        s_off[j] = ntiles[L.vd_off[v] + gi];
-        s_rect[j] = rect[L.vd_off[v] + gi];
-    }
-    __syncthreads();
-    // blocked exclusive scan of the counts (item order = depth order)
-    const int j0 = threadIdx.x * EMIT_IPT;
-    uint32_t loc[EMIT_IPT];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int r = 0; r < EMIT_IPT; ++r) {
-        const int j = j0 + r;
-        loc[r] = j < n ? s_off[j] : 0u;
-        sum += loc[r];
-    }
-    uint32_t total;
-    uint32_t run = block_excl_scan(sum, s_tmp, &total);
-#pragma unroll
-    for (int r = 0; r < EMIT_IPT; ++r) {
-        const int j = j0 + r;
-        if (j < n) s_off[j] = run;
-        run += loc[r];
-    }
-    __syncthreads();
-    // Windows of EMIT_THREADS * EMIT_RUN entries: each thread fills EMIT_RUN
-    // consecutive entries of the window in shared memory (one binary search,
-    // then a walk along the items' tile rectangles, row-major), and the block
-    // copies the window out with coalesced stores.
-    const int64_t obase = L.io_off[v] + chunk_off[c];
-    for (uint32_t w0 = 0; w0 < total; w0 += EMIT_WINDOW) {
-        const uint32_t m0 = w0 + threadIdx.x * EMIT_RUN;
-        if (m0 < total) {
-            int lo = 0, hi = n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= m0) lo = mid; else hi = mid - 1;
+    const uint2 *rv = rect + L.vd_off[v];
+    uint2 *sr = srect + L.vd_off[v] + begin;
+    uint32_t *h = bhist + (int64_t)cp.n_tiles * c;
+    for (int r0 = 0; r0 < cp.nty; r0 += band_rows) {
+        const int r1 = min(cp.nty, r0 + band_rows), H = r1 - r0;
+        for (int i = threadIdx.x; i < (H + 1) * W; i += BIN_THREADS) s_d[i] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += BIN_THREADS) {
+            uint2 rc;
+            if (r0 == 0) {               // first band: gather in depth order
+                rc = rv[g[j]];
+                sr[j] = rc;
+            } else {
+                rc = sr[j];              // written by this thread in band 0
             }
-            uint2 rc = s_rect[lo];
-            uint32_t x0 = rc.x & 0xFFFFu, x1 = rc.x >> 16, y0 = rc.y & 0xFFFFu;
-            const uint32_t local = m0 - s_off[lo], w = x1 - x0 + 1;
-            uint32_t ty = y0 + local / w, tx = x0 + local % w;
-            uint32_t end = lo + 1 < n ? s_off[lo + 1] : total;
-            uint32_t gi = s_g[lo];
-            const uint32_t m1 = min(total, m0 + EMIT_RUN);
-            for (uint32_t m = m0; m < m1; ++m) {
-                while (m == end) {                   // next item with tiles
-                    ++lo;
-                    rc = s_rect[lo];
-                    x0 = rc.x & 0xFFFFu; x1 = rc.x >> 16; y0 = rc.y & 0xFFFFu;
-                    tx = x0;
-                    ty = y0;
-                    gi = s_g[lo];
-                    end = lo + 1 < n ? s_off[lo + 1] : total;
+            const int y0 = (int)(rc.y & 0xFFFFu), y1 = (int)(rc.y >> 16);
+            if (y1 < r0 || y0 >= r1) continue;
+            const int x0 = (int)(rc.x & 0xFFFFu), x1 = (int)(rc.x >> 16);
+            const int ya = max(y0, r0) - r0, yb = min(y1, r1 - 1) - r0 + 1;
+            atomicAdd(&s_d[ya * W + x0], 1u);
+            atomicAdd(&s_d[ya * W + x1 + 1], 0xFFFFFFFFu);
+            atomicAdd(&s_d[yb * W + x0], 0xFFFFFFFFu);
+            atomicAdd(&s_d[yb * W + x1 + 1], 1u);
+        }
+        __syncthreads();
+        for (int y = warp; y < H; y += BIN_THREADS / 32) {      // prefix along x: a warp per row
+            uint32_t carry = 0;
+            for (int x0 = 0; x0 < ntx; x0 += 32) {
+                const int x = x0 + lane;
+                uint32_t inc = x < ntx ? s_d[y * W + x] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t;
                 }
-                s_win[m - w0] = make_uint2(ty * (uint32_t)ntx + tx, gi);
-                if (++tx > x1) { tx = x0; ++ty; }
+                if (x < ntx) s_d[y * W + x] = carry + inc;
+                carry += __shfl_sync(0xffffffffu, inc, 31);
             }
         }
         __syncthreads();
-        const uint32_t wn = min((uint32_t)EMIT_WINDOW, total - w0);
-        for (uint32_t j = threadIdx.x; j < wn; j += EMIT_THREADS) {
-            const uint2 e = s_win[j];
-            inst_tile[obase + w0 + j] = e.x;
-            inst_gauss[obase + w0 + j] = e.y;
+        for (int x = threadIdx.x; x < ntx; x += BIN_THREADS) {  // prefix along y: a thread per column
+            uint32_t run = 0;
+            for (int y = 0; y < H; ++y) {
+                run += s_d[y * W + x];
+                s_d[y * W + x] = run;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < H * ntx; t += BIN_THREADS) {
+            const int y = t / ntx, x = t - y * ntx;
+            h[(int64_t)r0 * ntx + t] = s_d[y * W + x];
         }
         __syncthreads();
     }
 }
 
-cudaError_t launch_emit(const uint32_t *sorted_g, const uint32_t *n_vis, const uint32_t *ntiles, const uint2 *rect,
-                        const Layout &L, int n_chunks, int ntx, uint32_t *chunk_sums, uint32_t *inst_tile,
-                        uint32_t *inst_gauss, uint32_t *n_inst, int *overflow, cudaStream_t st)
+// Per view: bhist[chunk][tile] becomes the exclusive prefix over the view's
+// chunks (each chunk's first slot inside a tile's list, relative to the
+// tile's start), a thread per (view, tile), totals -> ranges[v][tile].y; then
+// a block per view scans the totals in tile order into ranges[v][tile] =
+// [begin, end) (empty tiles [0, 0)) and n_inst[v].
+constexpr int TCOL_THREADS = 128;
+constexpr int TSCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(TCOL_THREADS)
+k_tile_chunk_scan(const uint32_t *__restrict__ n_vis, Layout L, CamParams cp, uint32_t *__restrict__ bhist,
+                  int2 *__restrict__ ranges)
 {
-    if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
-    k_emit_sums<<<n_chunks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, L, chunk_sums);
-    k_seg_scan<<<L.V, SCAN_THREADS, 0, st>>>(chunk_sums, L.ce_base, 1, n_inst);
-    k_emit<<<n_chunks, EMIT_THREADS, 0, st>>>(sorted_g, n_vis, ntiles, rect, L, ntx, chunk_sums, n_inst, inst_tile,
-                                              inst_gauss, overflow);
+    const int v = blockIdx.y;
+    const int t = blockIdx.x * TCOL_THREADS + threadIdx.x;
+    const int nt = cp.n_tiles;
+    if (t >= nt) return;
+    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
+    const int64_t nv = min64(n_vis[v], S);
+    const int nch = (int)ceil_div(nv, cp.bin_chunk);
+    uint32_t *h = bhist + (int64_t)nt * L.cb_base[v] + t;
+    uint32_t run = 0;
+    int c = 0;
+    for (; c + 8 <= nch; c += 8) {                      // eight independent loads in flight
+        uint32_t x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = h[(int64_t)(c + j) * nt];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            h[(int64_t)(c + j) * nt] = run;
+            run += x[j];
+        }
+    }
+    for (; c < nch; ++c) {
+        const uint32_t x = h[(int64_t)c * nt];
+        h[(int64_t)c * nt] = run;
+        run += x;
+    }
+    ranges[(int64_t)v * nt + t].y = (int)run;
+}
+
+__global__ void __launch_bounds__(TSCAN_THREADS)
+k_tile_scan(Layout L, CamParams cp, int2 *__restrict__ ranges, uint32_t *__restrict__ n_inst, int *overflow)
+{
+    __shared__ uint32_t s_tmp[33];
+    const int v = blockIdx.x;
+    const int nt = cp.n_tiles;
+    int2 *R = ranges + (int64_t)v * nt;
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < nt; t0 += TSCAN_THREADS) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t x = t < nt ? (uint32_t)R[t].y : 0u;
+        uint32_t tot;
+        const uint32_t start = carry + block_excl_scan(x, s_tmp, &tot);
+        if (t < nt) R[t] = x ? make_int2((int)start, (int)(start + x)) : make_int2(0, 0);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        n_inst[v] = carry;
+        if ((int64_t)carry > L.io_off[v + 1] - L.io_off[v]) atomicExch(overflow, 1);
+    }
+}
+
+cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, const uint2 *rect, const Layout &L,
+                              const CamParams &cp, int n_chunks, uint2 *srect, uint32_t *bhist, int2 *ranges,
+                              uint32_t *n_inst, int *overflow, cudaStream_t st)
+{
+    if (L.V <= 0) return cudaSuccess;
+    if (n_chunks > 0) {
+        const int W = cp.ntx + 1;
+        const int band_rows = max(1, min(cp.nty, TILE_COUNT_SMEM / (4 * W) - 1));
+        const size_t smem = 4 * (size_t)(band_rows + 1) * W;
+        k_tile_count<<<n_chunks, BIN_THREADS, smem, st>>>(sorted_g, n_vis, rect, L, cp, band_rows, srect, bhist);
+    }
+    k_tile_chunk_scan<<<dim3((unsigned)ceil_div(cp.n_tiles, TCOL_THREADS), L.V), TCOL_THREADS, 0, st>>>(
+        n_vis, L, cp, bhist, ranges);
+    k_tile_scan<<<L.V, TSCAN_THREADS, 0, st>>>(L, cp, ranges, n_inst, overflow);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------ K5 ranges ----
+// ------------------------------------------------------ K4 tile emission ----
+// A warp per (chunk, tile row).  The block stages the chunk's depth-ordered
+// (rectangle, Gaussian) pairs in shared memory; each warp picks, in order,
+// the pairs whose rectangle covers its row (ballot + popc into a per-warp
+// queue) and, per queued pair, writes the Gaussian into each covered tile's
+// list at that tile's running slot.  Lane l owns the tiles x = l (mod 32) of
+// the row, so a tile's slot counter is only ever touched by one thread, and
+// the pairs are handled in depth order: every list comes out ordered by
+// (depth, index) without a sort over the instances.
+//
+// KT > 0: rows of at most 32*KT tiles; lane l keeps the slots of its KT tiles
+// in registers and tests coverage with predicates (no divergence, no
+// dependent shared-memory round trip per pair -- the row through the horizon
+// can take most pairs of every chunk).  KT == 0: any row width, slots in
+// shared memory.
+constexpr int EMIT_STAGE = 2048;
 
-__global__ void k_ranges(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ n_inst, Layout L,
-                         int n_tiles, int2 *__restrict__ ranges, const int *__restrict__ overflow)
+template <int KT>
+__global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
+k_tile_emit(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
+            const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
+            const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
+            uint32_t *__restrict__ inst_gauss)
 {
-    if (*overflow) return;
-    const int v = blockIdx.y;
-    const int64_t n = min64(n_inst[v], L.io_off[v + 1] - L.io_off[v]);
-    const uint32_t *t = tiles + L.io_off[v];
-    int2 *R = ranges + (int64_t)v * n_tiles;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t tj = t[j];
-        if (j == 0 || t[j - 1] != tj) R[tj].x = (int)j;
-        if (j == n - 1 || t[j + 1] != tj) R[tj].y = (int)(j + 1);
+    __shared__ uint2 s_rc[EMIT_STAGE];
+    __shared__ uint32_t s_g[EMIT_STAGE];
+    __shared__ uint2 s_q[TILE_EMIT_WARPS][64];
+    extern __shared__ uint32_t s_cnt[];                 // KT == 0: [TILE_EMIT_WARPS][ntx]
+    const int c = blockIdx.x;
+    const int v = find_segment(L.cb_base, L.V, c);
+    const int k = c - L.cb_base[v];
+    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
+    const int64_t nv = min64(n_vis[v], S);
+    const int64_t begin = (int64_t)k * cp.bin_chunk;
+    if (begin >= nv) return;
+    if ((int64_t)n_inst[v] > L.io_off[v + 1] - L.io_off[v]) return;   // overflow: nothing is emitted
+    const int n = (int)min64(cp.bin_chunk, nv - begin);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
+    const bool active = row < cp.nty;
+    const int ntx = cp.ntx;
+    uint2 *q = s_q[warp];
+    uint32_t *out = inst_gauss + L.io_off[v];
+    uint32_t slot[KT > 0 ? KT : 1];
+    uint32_t *cnt = s_cnt + warp * ntx;
+    if (active) {
+        const uint32_t *h = bhist + (int64_t)cp.n_tiles * c + (int64_t)row * ntx;
+        const int2 *R = ranges + (int64_t)v * cp.n_tiles + (int64_t)row * ntx;
+        if (KT > 0) {
+#pragma unroll
+            for (int j = 0; j < (KT > 0 ? KT : 1); ++j) {
+                const int x = lane + 32 * j;
+                slot[j] = x < ntx ? (uint32_t)R[x].x + h[x] : 0u;
+            }
+        } else {
+            for (int x = lane; x < ntx; x += 32) cnt[x] = (uint32_t)R[x].x + h[x];
+        }
+    }
+    const uint32_t *g = sorted_g + L.vd_off[v] + begin;
+    const uint2 *sr = srect + L.vd_off[v] + begin;
+    const unsigned lt = lanemask_lt();
+    int qn = 0;
+    auto drain = [&](int cnt_q) {
+        if (KT > 0) {
+#pragma unroll 4
+            for (int j = 0; j < cnt_q; ++j) {
+                const uint2 e = q[j];
+                const uint32_t x0 = e.y & 0xFFFFu, w = (e.y >> 16) - x0;
+#pragma unroll
+                for (int t = 0; t < (KT > 0 ? KT : 1); ++t) {
+                    if ((uint32_t)(lane + 32 * t) - x0 <= w) {      // x0 <= x <= x1
+                        out[slot[t]] = e.x;
+                        ++slot[t];
+                    }
+                }
+            }
+        } else {
+            for (int j = 0; j < cnt_q; ++j) {
+                const uint2 e = q[j];
+                const uint32_t x0 = e.y & 0xFFFFu, x1 = e.y >> 16;
+                for (uint32_t x = x0 + (((uint32_t)lane - x0) & 31u); x <= x1; x += 32) {
+                    const uint32_t p = cnt[x];
+                    out[p] = e.x;
+                    cnt[x] = p + 1;
+                }
+            }
+        }
+    };
+    for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
+        const int m = min(EMIT_STAGE, n - s0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += TILE_EMIT_WARPS * 32) {
+            s_rc[j] = sr[s0 + j];
+            s_g[j] = g[s0 + j];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int i0 = 0; i0 < m; i0 += 32) {
+            const int i = i0 + lane;
+            bool p = false;
+            uint2 e = make_uint2(0u, 0u);
+            if (i < m) {
+                const uint2 rc = s_rc[i];
+                p = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
+                e = make_uint2(s_g[i], rc.x);
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, p);
+            if (p) q[qn + __popc(mask & lt)] = e;
+            qn += __popc(mask);
+            if (qn >= 32) {
+                __syncwarp();
+                drain(qn);
+                qn = 0;
+                __syncwarp();
+            }
+        }
+    }
+    if (active && qn > 0) {
+        __syncwarp();
+        drain(qn);
     }
 }
 
-cudaError_t launch_ranges(const uint32_t *inst_tile, const uint32_t *n_inst, const Layout &L, int n_tiles,
-                          int2 *ranges, const int *overflow, cudaStream_t st)
+template <int KT>
+static cudaError_t tile_emit_t(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
+                               const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
+                               const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
 {
-    if (L.V <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.V * n_tiles, st);
-    if (e != cudaSuccess) return e;
-    dim3 grid(64, L.V);
-    k_ranges<<<grid, 256, 0, st>>>(inst_tile, n_inst, L, n_tiles, ranges, overflow);
+    const size_t smem = KT > 0 ? 0 : 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
+    dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
+    k_tile_emit<KT><<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp,
+                                                             inst_gauss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
+                             const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
+                             const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
+{
+    if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
+    const int kt = (int)ceil_div(cp.ntx, 32);
+#define TILE_EMIT_CASE(K) \
+    if (kt <= K) return tile_emit_t<K>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, n_chunks, inst_gauss, st)
+    TILE_EMIT_CASE(1);
+    TILE_EMIT_CASE(2);
+    TILE_EMIT_CASE(3);
+    TILE_EMIT_CASE(4);
+    TILE_EMIT_CASE(6);
+    TILE_EMIT_CASE(8);
+#undef TILE_EMIT_CASE
+    return tile_emit_t<0>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, n_chunks, inst_gauss, st);
+}
+
+cudaError_t configure_tile_kernels()
+{
+    return cudaFuncSetAttribute(k_tile_emit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_EMIT_SMEM_MAX);
+}
+
+// Tile id of every instance of one view, from its ranges (debug export).
+__global__ void k_fill_tiles(const int2 *__restrict__ R, int n_tiles, uint32_t *__restrict__ tiles)
+{
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const int2 r = R[t];
+    for (int j = r.x + threadIdx.x; j < r.y; j += blockDim.x) tiles[j] = (uint32_t)t;
+}
+
+cudaError_t launch_fill_tiles(const int2 *ranges_view, int n_tiles, uint32_t *tiles_view, cudaStream_t st)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    k_fill_tiles<<<n_tiles, 128, 0, st>>>(ranges_view, n_tiles, tiles_view);
     return cudaGetLastError();
 }
 

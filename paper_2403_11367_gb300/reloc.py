@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libreloc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOMAP, ENUMERIC, EOVERFLOW = range(8)
 FP32, FP16, BF16 = 0, 1, 2
-STAGES = ["cull", "project", "depth_sort", "emit", "tile_sort", "ranges", "blend", "score"]
+STAGES = ["cull", "project", "depth_sort", "tile_count", "tile_emit", "blend", "score"]
 
 
 class RelocError(RuntimeError):
