@@ -96,6 +96,13 @@ cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch
 // (low = pixel row y, high = pixel row y + 1); fma/mul/add.rn.f32x2 operate on
 // both halves with IEEE round-to-nearest, like two scalar instructions.
 typedef unsigned long long f32x2;
+__device__ __forceinline__ unsigned lanemask_lt_u()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
 __device__ __forceinline__ f32x2 pk(float lo, float hi)
 {
     f32x2 r;
@@ -140,6 +147,22 @@ __device__ __forceinline__ float quad_min_rect(float a, float b, float c, float 
     return fminf(fminf(edge_x(x0), edge_x(x1)), fminf(edge_y(y0), edge_y(y1)));
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Pixel arithmetic in base 2: with A' = -a/2 log2(e), B' = -b log2(e),
+// C' = -c/2 log2(e) and dx, dy the pixel's offset from the mean,
+//   p' = A' dx^2 + B' dx dy + C' dy^2 + log2(o) = power * log2(e) + log2(o),
+// so alpha = min(alpha_max, 2^p') = min(alpha_max, o exp(power)).  The 3-sigma
+// rule (power >= -cut^2/2) and alpha >= alpha_min become one threshold on p':
+// p' >= max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)).  A pixel that stops
+// (T (1 - alpha) < t_min, the stopping Gaussian not added) gets T = 0, so
+// later weights vanish without a flag; its alpha output is the sum of its
+// weights, which telescopes to 1 - T before the stop.
 template <int TW, int TH, int RPL>
 __global__ void __launch_bounds__(TW *TH / 2)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
@@ -152,7 +175,10 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     constexpr int WROWS = 64 / TW;           // pixel rows per warp
     constexpr int CH = 32 * RPL;             // records per warp step
     static_assert(NT % 32 == 0 && TH % 2 == 0, "tile shape");
-    __shared__ float4 s_rec[NW][3][CH];      // per warp: u v o z | conic a b c thr | rgb
+    // per warp, kept records compacted: (-u,-u,A',A') (B',B',log2 o,log2 o)
+    // (-v,-v,C',C') (r,r,g,g) (b,b,z,z) and the p' threshold
+    __shared__ float4 s_rec[NW][5][CH];
+    __shared__ float s_thr[NW][CH];
     __shared__ double s_red[3][NW];
 
     const int tile = blockIdx.x;
@@ -174,15 +200,20 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
+    constexpr float L2E = 1.4426950408889634f;
     const float lim = -0.5f * cam.cut * cam.cut;
     const float lamin = __logf(cam.alpha_min);
+    const float limL = lim * L2E;
+    const float l2amin = log2f(cam.alpha_min);
     float4(*const sw)[CH] = s_rec[warp];
+    float *const sthr = s_thr[warp];
+    const unsigned lt = lanemask_lt_u();
 
-    // pixel pair state: transmittance, colour, depth (low = row y, high = y + 1)
-    float T0 = 1.f, T1 = 1.f;
-    f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, D2 = 0ull;
-    bool done0 = !in0, done1 = !in1;
-    const f32x2 FY2 = pk(fy0, fy1);
+    // pixel pair state (low = row y, high = row y + 1): transmittance, colour,
+    // depth and weight sums
+    f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
+    f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
+    const f32x2 FX2 = pk(fxp, fxp), FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
 
     // software pipeline: list indices two steps ahead, records one step ahead
     uint32_t gnext[RPL];
@@ -197,8 +228,12 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         gnext[q] = j1 < r.y ? __ldg(list + j1) : 0u;
     }
     for (int b = r.x; b < r.y; b += CH) {
-        if (__all_sync(0xffffffffu, done0 && done1)) break;
-        unsigned keep[RPL];
+        {
+            float t0, t1;
+            upk(T2, t0, t1);
+            if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+        }
+        int nk = 0;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             const int j = b + q * 32 + lane;
@@ -219,63 +254,58 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                     const float qmin = quad_min_rect(pb.x, pb.y, pb.z, wx0 - pa.x, wx1 - pa.x, wy0 - pa.y, wy1 - pa.y);
                     hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
                 }
-                if (hit) {
-                    // power(dx, dy) = dx (A dx + B dy) + C dy^2
-                    sw[0][q * 32 + lane] = make_float4(pa.x, pa.y, pa.w, pa.z);
-                    sw[1][q * 32 + lane] = make_float4(-0.5f * pb.x, -pb.y, -0.5f * pb.z, thr);
-                    sw[2][q * 32 + lane] = pc;
-                }
             }
-            keep[q] = __ballot_sync(0xffffffffu, hit);
+            const unsigned keep = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int k = nk + __popc(keep & lt);
+                const float l2o = __log2f(pa.w);
+                const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
+                sw[0][k] = make_float4(-pa.x, -pa.x, Ap, Ap);
+                sw[1][k] = make_float4(Bp, Bp, l2o, l2o);
+                sw[2][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
+                sw[3][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
+                sw[4][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
+                sthr[k] = fmaxf(limL + l2o, l2amin);
+            }
+            nk += __popc(keep);
         }
         __syncwarp();
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            unsigned m = keep[q];
-            while (m) {
-                const int k = q * 32 + __ffs(m) - 1;
-                m &= m - 1;
-                const float4 a = sw[0][k];       // u, v, opacity, depth
-                const float4 cb = sw[1][k];      // A = -a/2, B = -b, C = -c/2, threshold
-                // power(dx, dy) = dx (A dx + B dy) + C dy^2 for both rows
-                const float dx = fxp - a.x;
-                const f32x2 dy2 = add2(FY2, pk(-a.y, -a.y));
-                const f32x2 Cdy2 = mul2(pk(cb.z, cb.z), dy2);
-                const f32x2 t2 = fma2(pk(cb.y, cb.y), dy2, pk(cb.x * dx, cb.x * dx));
-                const f32x2 p2 = fma2(Cdy2, dy2, mul2(pk(dx, dx), t2));
-                float p0, p1;
-                upk(p2, p0, p1);
-                const bool t0 = !done0 && p0 >= cb.w;
-                const bool t1 = !done1 && p1 >= cb.w;
-                if (!(t0 || t1)) continue;
-                // both pixels without branches: alpha, stop test, weights
-                const float al0 = fminf(cam.alpha_max, a.z * __expf(p0));
-                const float al1 = fminf(cam.alpha_max, a.z * __expf(p1));
-                const bool ok0 = t0 && al0 >= cam.alpha_min;
-                const bool ok1 = t1 && al1 >= cam.alpha_min;
-                const float tn0 = T0 * (1.f - al0), tn1 = T1 * (1.f - al1);
-                const bool st0 = ok0 && tn0 < cam.t_min, st1 = ok1 && tn1 < cam.t_min;
-                const bool ad0 = ok0 && !st0, ad1 = ok1 && !st1;
-                const f32x2 w2 = pk(ad0 ? al0 * T0 : 0.f, ad1 ? al1 * T1 : 0.f);
-                const float4 c = sw[2][k];
-                R2 = fma2(pk(c.x, c.x), w2, R2);
-                G2 = fma2(pk(c.y, c.y), w2, G2);
-                B2 = fma2(pk(c.z, c.z), w2, B2);
-                D2 = fma2(pk(a.w, a.w), w2, D2);
-                T0 = ad0 ? tn0 : T0;
-                T1 = ad1 ? tn1 : T1;
-                done0 = done0 || st0;
-                done1 = done1 || st1;
-            }
+        for (int k = 0; k < nk; ++k) {
+            const float4 s0 = sw[0][k], s1 = sw[1][k], s2 = sw[2][k];
+            const float thl = sthr[k];
+            const f32x2 DX2 = add2(FX2, pk(s0.x, s0.y));
+            const f32x2 K1 = mul2(pk(s1.x, s1.y), DX2);
+            const f32x2 K0 = fma2(mul2(pk(s0.z, s0.w), DX2), DX2, pk(s1.z, s1.w));
+            const f32x2 DY2 = add2(FY2, pk(s2.x, s2.y));
+            const f32x2 P2 = fma2(DY2, fma2(pk(s2.z, s2.w), DY2, K1), K0);
+            float p0, p1;
+            upk(P2, p0, p1);
+            const float a0 = fminf(cam.alpha_max, ex2_approx(p0 >= thl ? p0 : -INFINITY));
+            const float a1 = fminf(cam.alpha_max, ex2_approx(p1 >= thl ? p1 : -INFINITY));
+            const f32x2 W2 = mul2(T2, pk(a0, a1));
+            const f32x2 TN2 = fma2(W2, NEG1, T2);
+            float w0, w1, n0, n1;
+            upk(W2, w0, w1);
+            upk(TN2, n0, n1);
+            const bool st0 = n0 < cam.t_min, st1 = n1 < cam.t_min;
+            const f32x2 WF = pk(st0 ? 0.f : w0, st1 ? 0.f : w1);
+            T2 = pk(st0 ? 0.f : n0, st1 ? 0.f : n1);
+            const float4 c0 = sw[3][k], c1 = sw[4][k];
+            R2 = fma2(pk(c0.x, c0.y), WF, R2);
+            G2 = fma2(pk(c0.z, c0.w), WF, G2);
+            B2 = fma2(pk(c1.x, c1.y), WF, B2);
+            Z2 = fma2(pk(c1.z, c1.w), WF, Z2);
+            S2 = add2(S2, WF);
         }
         __syncwarp();
     }
 
-    float R0, R1, G0, G1, B0, B1, D0, D1;
+    float R0, R1, G0, G1, B0, B1, D0, D1, A0, A1;
     upk(R2, R0, R1);
     upk(G2, G0, G1);
     upk(B2, B0, B1);
-    upk(D2, D0, D1);
+    upk(Z2, D0, D1);
+    upk(S2, A0, A1);
     const int64_t HW = (int64_t)cam.width * cam.height;
     const int64_t pix0 = (int64_t)py0 * cam.width + px, pix1 = pix0 + cam.width;
     if (rgb) {
@@ -288,8 +318,8 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         if (in1) depth[(int64_t)out_v * HW + pix1] = D1;
     }
     if (alpha) {
-        if (in0) alpha[(int64_t)out_v * HW + pix0] = 1.f - T0;
-        if (in1) alpha[(int64_t)out_v * HW + pix1] = 1.f - T1;
+        if (in0) alpha[(int64_t)out_v * HW + pix0] = A0;
+        if (in1) alpha[(int64_t)out_v * HW + pix1] = A1;
     }
     if (partials) {
         const float *query = L.q_img[L.view_q[v]];

@@ -388,91 +388,180 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
 // ------------------------------------------------------ K4 tile emission ----
 // A warp per (chunk, tile row).  The block stages the chunk's depth-ordered
 // (rectangle, Gaussian) pairs in shared memory; each warp picks, in order,
-// the pairs whose rectangle covers its row (ballot + popc into a per-warp
-// queue) and, per queued pair, writes the Gaussian into each covered tile's
+// the pairs whose rectangle covers its row (ballot + popc into per-warp
+// queues) and, per queued pair, writes the Gaussian into each covered tile's
 // list at that tile's running slot.  Lane l owns the tiles x = l (mod 32) of
 // the row, so a tile's slot counter is only ever touched by one thread, and
 // the pairs are handled in depth order: every list comes out ordered by
 // (depth, index) without a sort over the instances.
 //
-// KT > 0: rows of at most 32*KT tiles; lane l keeps the slots of its KT tiles
-// in registers and tests coverage with predicates (no divergence, no
-// dependent shared-memory round trip per pair -- the row through the horizon
-// can take most pairs of every chunk).  KT == 0: any row width, slots in
-// shared memory.
-constexpr int EMIT_STAGE = 2048;
+// k_tile_emit_reg<KT>: rows of at most 32*KT tiles.  The row is cut into KT
+// bands of 32 tiles with one queue each (a pair straddling a band edge goes
+// to both); lane l keeps the slot of its tile in band b in register slot[b],
+// so draining band b's queue costs one predicated store per pair, with no
+// divergence and no dependent shared-memory round trip (the row through the
+// horizon takes most pairs of every chunk).
+// k_tile_emit_smem: any row width, one queue, slots in shared memory.
+constexpr int EMIT_STAGE = 1024;
+
+struct EmitChunk {
+    int v, n;
+    int64_t begin;
+    bool skip;
+};
+
+__device__ __forceinline__ EmitChunk emit_chunk(const uint32_t *n_vis, const uint32_t *n_inst, const Layout &L,
+                                                const CamParams &cp)
+{
+    EmitChunk ch;
+    const int c = blockIdx.x;
+    ch.v = find_segment(L.cb_base, L.V, c);
+    const int k = c - L.cb_base[ch.v];
+    const int64_t S = L.vd_off[ch.v + 1] - L.vd_off[ch.v];
+    const int64_t nv = min64(n_vis[ch.v], S);
+    ch.begin = (int64_t)k * cp.bin_chunk;
+    ch.skip = ch.begin >= nv ||                                             // past the visible list
+              (int64_t)n_inst[ch.v] > L.io_off[ch.v + 1] - L.io_off[ch.v];   // overflow: nothing emitted
+    ch.n = ch.skip ? 0 : (int)min64(cp.bin_chunk, nv - ch.begin);
+    return ch;
+}
 
 template <int KT>
 __global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
-k_tile_emit(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
-            const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
-            const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
-            uint32_t *__restrict__ inst_gauss)
+k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
+                const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
+                const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
+                uint32_t *__restrict__ inst_gauss)
+{
+    __shared__ uint2 s_rc[EMIT_STAGE];
+    __shared__ uint32_t s_g[EMIT_STAGE];
+    extern __shared__ uint2 s_qb[];                     // [TILE_EMIT_WARPS][KT][64]
+    const EmitChunk ch = emit_chunk(n_vis, n_inst, L, cp);
+    if (ch.skip) return;
+    const int v = ch.v, n = ch.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
+    const bool active = row < cp.nty;
+    const int ntx = cp.ntx;
+    uint2 *q = s_qb + warp * KT * 64;
+    uint32_t *out = inst_gauss + L.io_off[v];
+    uint32_t slot[KT];
+    int qn[KT];
+#pragma unroll
+    for (int b = 0; b < KT; ++b) {
+        qn[b] = 0;
+        slot[b] = 0;
+    }
+    if (active) {
+        const uint32_t *h = bhist + (int64_t)cp.n_tiles * blockIdx.x + (int64_t)row * ntx;
+        const int2 *R = ranges + (int64_t)v * cp.n_tiles + (int64_t)row * ntx;
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {
+            const int x = lane + 32 * b;
+            if (x < ntx) slot[b] = (uint32_t)R[x].x + h[x];
+        }
+    }
+    // band b's queue: pairs covering tile lane + 32 b go to out[slot[b]++]
+    auto drain = [&](const uint2 *qb, int cnt_q, int b, uint32_t &sl) {
+        const uint32_t xl = (uint32_t)(lane + 32 * b);
+#pragma unroll 4
+        for (int j = 0; j < cnt_q; ++j) {
+            const uint2 e = qb[j];
+            const uint32_t x0 = e.y & 0xFFFFu;
+            if (xl - x0 <= (e.y >> 16) - x0) {         // x0 <= x <= x1
+                out[sl] = e.x;
+                ++sl;
+            }
+        }
+    };
+    const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
+    const uint2 *sr = srect + L.vd_off[v] + ch.begin;
+    const unsigned lt = lanemask_lt();
+    for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
+        const int m = min(EMIT_STAGE, n - s0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += TILE_EMIT_WARPS * 32) {
+            s_rc[j] = sr[s0 + j];
+            s_g[j] = g[s0 + j];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int i0 = 0; i0 < m; i0 += 32) {
+            const int i = i0 + lane;
+            bool in_row = false;
+            uint2 rc = make_uint2(0u, 0u);
+            if (i < m) {
+                rc = s_rc[i];
+                in_row = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
+            }
+            if (__ballot_sync(0xffffffffu, in_row) == 0) continue;
+            const uint32_t gi = in_row ? s_g[i] : 0u;
+            const int b0 = (int)((rc.x & 0xFFFFu) >> 5), b1 = (int)(rc.x >> 21);
+#pragma unroll
+            for (int b = 0; b < KT; ++b) {
+                const bool p = in_row && b0 <= b && b <= b1;
+                const unsigned mask = __ballot_sync(0xffffffffu, p);
+                if (mask == 0) continue;
+                uint2 *qb = q + b * 64;
+                if (p) qb[qn[b] + __popc(mask & lt)] = make_uint2(gi, rc.x);
+                qn[b] += __popc(mask);
+                if (qn[b] >= 32) {
+                    __syncwarp();
+                    drain(qb, qn[b], b, slot[b]);
+                    qn[b] = 0;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (active) {
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < KT; ++b)
+            if (qn[b] > 0) drain(q + b * 64, qn[b], b, slot[b]);
+    }
+}
+
+__global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
+k_tile_emit_smem(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
+                 const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
+                 const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
+                 uint32_t *__restrict__ inst_gauss)
 {
     __shared__ uint2 s_rc[EMIT_STAGE];
     __shared__ uint32_t s_g[EMIT_STAGE];
     __shared__ uint2 s_q[TILE_EMIT_WARPS][64];
-    extern __shared__ uint32_t s_cnt[];                 // KT == 0: [TILE_EMIT_WARPS][ntx]
-    const int c = blockIdx.x;
-    const int v = find_segment(L.cb_base, L.V, c);
-    const int k = c - L.cb_base[v];
-    const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
-    const int64_t nv = min64(n_vis[v], S);
-    const int64_t begin = (int64_t)k * cp.bin_chunk;
-    if (begin >= nv) return;
-    if ((int64_t)n_inst[v] > L.io_off[v + 1] - L.io_off[v]) return;   // overflow: nothing is emitted
-    const int n = (int)min64(cp.bin_chunk, nv - begin);
+    extern __shared__ uint32_t s_cnt[];                 // [TILE_EMIT_WARPS][ntx]
+    const EmitChunk ch = emit_chunk(n_vis, n_inst, L, cp);
+    if (ch.skip) return;
+    const int v = ch.v, n = ch.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
     const bool active = row < cp.nty;
     const int ntx = cp.ntx;
     uint2 *q = s_q[warp];
     uint32_t *out = inst_gauss + L.io_off[v];
-    uint32_t slot[KT > 0 ? KT : 1];
     uint32_t *cnt = s_cnt + warp * ntx;
     if (active) {
-        const uint32_t *h = bhist + (int64_t)cp.n_tiles * c + (int64_t)row * ntx;
+        const uint32_t *h = bhist + (int64_t)cp.n_tiles * blockIdx.x + (int64_t)row * ntx;
         const int2 *R = ranges + (int64_t)v * cp.n_tiles + (int64_t)row * ntx;
-        if (KT > 0) {
-#pragma unroll
-            for (int j = 0; j < (KT > 0 ? KT : 1); ++j) {
-                const int x = lane + 32 * j;
-                slot[j] = x < ntx ? (uint32_t)R[x].x + h[x] : 0u;
-            }
-        } else {
-            for (int x = lane; x < ntx; x += 32) cnt[x] = (uint32_t)R[x].x + h[x];
-        }
+        for (int x = lane; x < ntx; x += 32) cnt[x] = (uint32_t)R[x].x + h[x];
     }
-    const uint32_t *g = sorted_g + L.vd_off[v] + begin;
-    const uint2 *sr = srect + L.vd_off[v] + begin;
-    const unsigned lt = lanemask_lt();
-    int qn = 0;
     auto drain = [&](int cnt_q) {
-        if (KT > 0) {
-#pragma unroll 4
-            for (int j = 0; j < cnt_q; ++j) {
-                const uint2 e = q[j];
-                const uint32_t x0 = e.y & 0xFFFFu, w = (e.y >> 16) - x0;
-#pragma unroll
-                for (int t = 0; t < (KT > 0 ? KT : 1); ++t) {
-                    if ((uint32_t)(lane + 32 * t) - x0 <= w) {      // x0 <= x <= x1
-                        out[slot[t]] = e.x;
-                        ++slot[t];
-                    }
-                }
-            }
-        } else {
-            for (int j = 0; j < cnt_q; ++j) {
-                const uint2 e = q[j];
-                const uint32_t x0 = e.y & 0xFFFFu, x1 = e.y >> 16;
-                for (uint32_t x = x0 + (((uint32_t)lane - x0) & 31u); x <= x1; x += 32) {
-                    const uint32_t p = cnt[x];
-                    out[p] = e.x;
-                    cnt[x] = p + 1;
-                }
+        for (int j = 0; j < cnt_q; ++j) {
+            const uint2 e = q[j];
+            const uint32_t x0 = e.y & 0xFFFFu, x1 = e.y >> 16;
+            for (uint32_t x = x0 + (((uint32_t)lane - x0) & 31u); x <= x1; x += 32) {
+                const uint32_t p = cnt[x];
+                out[p] = e.x;
+                cnt[x] = p + 1;
             }
         }
     };
+    const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
+    const uint2 *sr = srect + L.vd_off[v] + ch.begin;
+    const unsigned lt = lanemask_lt();
+    int qn = 0;
     for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
         const int m = min(EMIT_STAGE, n - s0);
         __syncthreads();
@@ -489,7 +578,7 @@ k_tile_emit(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ sre
             if (i < m) {
                 const uint2 rc = s_rc[i];
                 p = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
-                e = make_uint2(s_g[i], rc.x);
+                e = make_uint2(p ? s_g[i] : 0u, rc.x);
             }
             const unsigned mask = __ballot_sync(0xffffffffu, p);
             if (p) q[qn + __popc(mask & lt)] = e;
@@ -513,10 +602,16 @@ static cudaError_t tile_emit_t(const uint32_t *sorted_g, const uint2 *srect, con
                                const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
                                const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
 {
-    const size_t smem = KT > 0 ? 0 : 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
     dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
-    k_tile_emit<KT><<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp,
-                                                             inst_gauss);
+    if (KT > 0) {
+        const size_t smem = sizeof(uint2) * TILE_EMIT_WARPS * (KT > 0 ? KT : 1) * 64;
+        k_tile_emit_reg<(KT > 0 ? KT : 1)><<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(
+            sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, inst_gauss);
+    } else {
+        const size_t smem = 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
+        k_tile_emit_smem<<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
+                                                                  L, cp, inst_gauss);
+    }
     return cudaGetLastError();
 }
 
@@ -540,7 +635,7 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 
 cudaError_t configure_tile_kernels()
 {
-    return cudaFuncSetAttribute(k_tile_emit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_EMIT_SMEM_MAX);
+    return cudaFuncSetAttribute(k_tile_emit_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_EMIT_SMEM_MAX);
 }
 
 // Tile id of every instance of one view, from its ranges (debug export).
