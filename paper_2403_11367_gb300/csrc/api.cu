@@ -493,11 +493,11 @@ static int64_t inst_cap(const reloc_ctx *ctx, int64_t S, int64_t override_cap)
 
 // Workspace bytes of one query: per view, the per-Gaussian arrays (records,
 // rectangle, tile count, depth key, two key/value radix buffers, depth-ordered
-// rectangle, radix histograms), the instance list, ranges + NCC partials and
-// the per-chunk tile counts; plus the gathered subset.
+// rectangle, radix histograms), the instance list, ranges, NCC partials per
+// warp block and the per-chunk tile counts; plus the gathered subset.
 static int64_t query_bytes(int64_t S, int V, int64_t cap, const CamParams &cp)
 {
-    const int64_t per_view = S * 89 + cap * 4 + (int64_t)cp.n_tiles * 32 +
+    const int64_t per_view = S * 89 + cap * 4 + (int64_t)cp.n_tiles * 8 + (int64_t)blend_units(cp) * 24 +
                              4 * (int64_t)cp.n_tiles * ceil_div(S, cp.bin_chunk) + 1024;
     return (int64_t)V * per_view + S * 4 + 4096;
 }
@@ -690,7 +690,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     launches += 1;
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
     if (o.score) {
-        CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, cp.n_tiles, 3 * HW,
+        CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, blend_units(cp), 3 * HW,
                                ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0, st));
         launches += 1;
         if (o.argmax) {
@@ -775,7 +775,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->bhist.ensure(4 * (size_t)cp.n_tiles * cb));
         CKS(ctx->inst.ensure(4 * (size_t)VI));
         CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
-        CKS(ctx->partials.ensure(24 * (size_t)V * cp.n_tiles));
+        CKS(ctx->partials.ensure(24 * (size_t)V * blend_units(cp)));
         CKS(ctx->qpart.ensure(16 * 152 * (size_t)Qm));
         CKS(ctx->qstats.ensure(16 * (size_t)Qm));
         CKS(ctx->nvis.ensure(4 * (size_t)Vtot));

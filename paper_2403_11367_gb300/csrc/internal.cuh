@@ -149,16 +149,20 @@ cudaError_t launch_fill_tiles(const int2 *ranges_view, int n_tiles, uint32_t *ti
 cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch, double *qstats,
                                cudaStream_t st);
 
-// K6 (+ K7 partials): blend every (view, tile) of the layout; optional image
-// export (slot = view) and NCC partials [V][n_tiles][3] = {S_r, S_rr, S_rq}.
+// K6 (+ K7 partials): blend every (view, tile) of the layout, a warp per
+// 64-pixel block; optional image export (slot = view) and NCC partials
+// [V][blend_units(cam)][3] = {S_r, S_rr, S_rq} per warp block.
 // view_sel != null: blend only the n_sel views view_sel[0..n_sel), image
 // slot k for view_sel[k].
 cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                          const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
                          const int *view_sel, int n_sel, const int *overflow, cudaStream_t st);
 
-// K7: NCC per view from partials and its query's statistics.
-cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_tiles,
+// 64-pixel warp blocks of one view: the blend's unit of work and of NCC partials.
+inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w * cam.tile_h / 64); }
+
+// K7: NCC per view from its n_units partials and its query's statistics.
+cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_units,
                                 int64_t n_samples, double *scores, int *degenerate, cudaStream_t st);
 
 // K8: per query, argmax over its views (lowest index on ties):

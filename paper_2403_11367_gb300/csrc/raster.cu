@@ -162,32 +162,37 @@ __device__ __forceinline__ float ex2_approx(float x)
 // p' >= max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)).  A pixel that stops
 // (T (1 - alpha) < t_min, the stopping Gaussian not added) gets T = 0, so
 // later weights vanish without a flag; its alpha output is the sum of its
-// weights, which telescopes to 1 - T before the stop.
+// weights, which telescopes to 1 - T before the stop.  Both tests are step
+// functions sat((x - t) 2^60), one saturating fused multiply-add per pixel:
+// any positive float difference times 2^60 saturates to 1, a negative one to
+// 0 (only x == t exactly falls on the other side of a >= test).
+constexpr float STEP_SCALE = 1152921504606846976.f;   // 2^60
 template <int TW, int TH, int RPL>
-__global__ void __launch_bounds__(TW *TH / 2)
+__global__ void __launch_bounds__(32, RPL == 1 ? 32 : 24)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
         const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
         float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
         const int *__restrict__ overflow)
 {
-    constexpr int NT = TW * TH / 2;          // threads
-    constexpr int NW = NT / 32;
+    constexpr int WPT = TW * TH / 64;        // warps (64-pixel blocks) per tile
     constexpr int WROWS = 64 / TW;           // pixel rows per warp
     constexpr int CH = 32 * RPL;             // records per warp step
-    static_assert(NT % 32 == 0 && TH % 2 == 0, "tile shape");
-    // per warp, kept records compacted: (-u,-u,A',A') (B',B',log2 o,log2 o)
-    // (-v,-v,C',C') (r,r,g,g) (b,b,z,z) and the p' threshold
-    __shared__ float4 s_rec[NW][5][CH];
-    __shared__ float s_thr[NW][CH];
-    __shared__ double s_red[3][NW];
+    static_assert(WPT >= 1 && TH % WROWS == 0, "tile shape");
+    // kept records compacted: (-u,-u,A',A') (B',B',log2 o,log2 o)
+    // (-v,-v,C',C') (r,r,g,g) (b,b,z,z) and -2^60 times the p' threshold
+    __shared__ float4 s_rec[5][CH];
+    __shared__ float s_thr[CH];
 
-    const int tile = blockIdx.x;
+    // one warp per block: (tile, warp block) units, so a warp that finishes
+    // early frees its slot instead of waiting for the tile's slowest warp
+    const int unit = blockIdx.x;
+    const int tile = unit / WPT, warp = unit - tile * WPT;
     const int v = view_sel ? view_sel[blockIdx.y] : (int)blockIdx.y;
     const int out_v = blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * TW + (int)(threadIdx.x % TW);
-    const int py0 = ty * TH + 2 * (int)(threadIdx.x / TW);
+    const int lane = threadIdx.x;
+    const int px = tx * TW + lane % TW;
+    const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
     const int py1 = py0 + 1;
     const bool in0 = px < cam.width && py0 < cam.height;
     const bool in1 = px < cam.width && py1 < cam.height;
@@ -205,8 +210,8 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     const float lamin = __logf(cam.alpha_min);
     const float limL = lim * L2E;
     const float l2amin = log2f(cam.alpha_min);
-    float4(*const sw)[CH] = s_rec[warp];
-    float *const sthr = s_thr[warp];
+    float4(*const sw)[CH] = s_rec;
+    float *const sthr = s_thr;
     const unsigned lt = lanemask_lt_u();
 
     // pixel pair state (low = row y, high = row y + 1): transmittance, colour,
@@ -214,6 +219,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
     const f32x2 FX2 = pk(fxp, fxp), FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
+    const float ntmin = -cam.t_min * STEP_SCALE;
 
     // software pipeline: list indices two steps ahead, records one step ahead
     uint32_t gnext[RPL];
@@ -265,14 +271,14 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 sw[2][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
                 sw[3][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
                 sw[4][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
-                sthr[k] = fmaxf(limL + l2o, l2amin);
+                sthr[k] = -STEP_SCALE * fmaxf(limL + l2o, l2amin);
             }
             nk += __popc(keep);
         }
         __syncwarp();
         for (int k = 0; k < nk; ++k) {
             const float4 s0 = sw[0][k], s1 = sw[1][k], s2 = sw[2][k];
-            const float thl = sthr[k];
+            const float nth = sthr[k];
             const f32x2 DX2 = add2(FX2, pk(s0.x, s0.y));
             const f32x2 K1 = mul2(pk(s1.x, s1.y), DX2);
             const f32x2 K0 = fma2(mul2(pk(s0.z, s0.w), DX2), DX2, pk(s1.z, s1.w));
@@ -280,16 +286,18 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             const f32x2 P2 = fma2(DY2, fma2(pk(s2.z, s2.w), DY2, K1), K0);
             float p0, p1;
             upk(P2, p0, p1);
-            const float a0 = fminf(cam.alpha_max, ex2_approx(p0 >= thl ? p0 : -INFINITY));
-            const float a1 = fminf(cam.alpha_max, ex2_approx(p1 >= thl ? p1 : -INFINITY));
-            const f32x2 W2 = mul2(T2, pk(a0, a1));
+            // p' >= threshold
+            const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
+            const float a0 = fminf(cam.alpha_max, ex2_approx(p0));
+            const float a1 = fminf(cam.alpha_max, ex2_approx(p1));
+            const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), IN2));
             const f32x2 TN2 = fma2(W2, NEG1, T2);
-            float w0, w1, n0, n1;
-            upk(W2, w0, w1);
+            float n0, n1;
             upk(TN2, n0, n1);
-            const bool st0 = n0 < cam.t_min, st1 = n1 < cam.t_min;
-            const f32x2 WF = pk(st0 ? 0.f : w0, st1 ? 0.f : w1);
-            T2 = pk(st0 ? 0.f : n0, st1 ? 0.f : n1);
+            // T (1 - alpha) >= t_min
+            const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
+            const f32x2 WF = mul2(W2, GO2);
+            T2 = mul2(TN2, GO2);
             const float4 c0 = sw[3][k], c1 = sw[4][k];
             R2 = fma2(pk(c0.x, c0.y), WF, R2);
             G2 = fma2(pk(c0.z, c0.w), WF, G2);
@@ -332,13 +340,11 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         sr = warp_sum_f(sr);
         srr = warp_sum_f(srr);
         srq = warp_sum_f(srq);
-        if (lane == 0) { s_red[0][warp] = sr; s_red[1][warp] = srr; s_red[2][warp] = srq; }
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            double acc = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) acc += s_red[threadIdx.x][k];
-            partials[((int64_t)blockIdx.y * cam.n_tiles + tile) * 3 + threadIdx.x] = acc;
+        if (lane == 0) {
+            double *o = partials + ((int64_t)blockIdx.y * cam.n_tiles * WPT + unit) * 3;
+            o[0] = sr;
+            o[1] = srr;
+            o[2] = srq;
         }
     }
 }
@@ -348,8 +354,8 @@ static cudaError_t blend_t(const float4 *rec, const Layout &L, const uint32_t *i
                            const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
                            const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
 {
-    dim3 grid(cam.n_tiles, view_sel ? n_sel : L.V);
-    k_blend<TW, TH, RPL><<<grid, TW * TH / 2, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha,
+    dim3 grid(cam.n_tiles * (TW * TH / 64), view_sel ? n_sel : L.V);
+    k_blend<TW, TH, RPL><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha,
                                                       view_sel, overflow);
     return cudaGetLastError();
 }
@@ -386,14 +392,14 @@ cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *ins
 constexpr int NCC_THREADS = 256;
 
 __global__ void __launch_bounds__(NCC_THREADS)
-k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ qstats, Layout L, int n_tiles,
+k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ qstats, Layout L, int n_units,
                int64_t n, double *__restrict__ scores, int *__restrict__ degenerate)
 {
     __shared__ double s[3][NCC_THREADS / 32];
     const int v = blockIdx.x;
-    const double *p = partials + (int64_t)v * n_tiles * 3;
+    const double *p = partials + (int64_t)v * n_units * 3;
     double a = 0, b = 0, c = 0;
-    for (int t = threadIdx.x; t < n_tiles; t += NCC_THREADS) {
+    for (int t = threadIdx.x; t < n_units; t += NCC_THREADS) {
         a += p[3 * t];
         b += p[3 * t + 1];
         c += p[3 * t + 2];
@@ -418,11 +424,11 @@ k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ q
     }
 }
 
-cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_tiles,
+cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_units,
                                 int64_t n_samples, double *scores, int *degenerate, cudaStream_t st)
 {
     if (L.V <= 0) return cudaSuccess;
-    k_ncc_finalize<<<L.V, NCC_THREADS, 0, st>>>(partials, qstats, L, n_tiles, n_samples, scores, degenerate);
+    k_ncc_finalize<<<L.V, NCC_THREADS, 0, st>>>(partials, qstats, L, n_units, n_samples, scores, degenerate);
     return cudaGetLastError();
 }
 
