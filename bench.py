@@ -49,9 +49,41 @@ def _peaks():
         return {}
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def stage_rooflines(stage_ms, S, V, n_vis, n_inst, n_eval_per_view, fp32_peak, ex2_peak_gops, hbm_gbs):
+    """Per-stage achieved fractions from algorithmic work (not from what the
+    kernels happen to move).  S subset Gaussians, V views, n_vis visible
+    (view, Gaussian) pairs, n_inst tile instances.
+      project     HBM: attributes read once per Gaussian (236 B, SH3 FP32) +
+                  16 B per (view, Gaussian) (rectangle, tile count, depth key)
+                  + a 48-byte record per visible pair
+      depth_sort  HBM: first pass reads key + tile count of every pair twice
+                  (16 B) and writes the visible pairs (8 B); three more passes
+                  read the key for counting and key + value for scattering
+                  and write key + value (20 B per visible pair each)
+      tile_count  HBM: depth-ordered index (4 B) and rectangle (8 B) read,
+      + tile_emit rectangle written (8 B), read back with the index (12 B),
+                  each instance written once (4 B)
+      blend       FP32: 24 flop per included (pixel, Gaussian) pair (oracle
+                  count), against the measured FP32 FMA peak; plus one
+                  exponential per pair against the measured ex2 rate"""
+    gb = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9
+    out = {}
+    b = S * 236 + S * V * 16 + n_vis * 48
+    out["project"] = {"bound": "hbm", "bytes": b, "achieved_gbs": gb(b, stage_ms["project"])}
+    b = S * V * 16 + n_vis * 8 + 3 * 20 * n_vis
+    out["depth_sort"] = {"bound": "hbm", "bytes": b, "achieved_gbs": gb(b, stage_ms["depth_sort"])}
+    b = n_vis * (4 + 8 + 8 + 12) + n_inst * 4
+    ms = stage_ms["tile_count"] + stage_ms["tile_emit"]
+    out["tile_binning"] = {"bound": "hbm", "bytes": b, "achieved_gbs": gb(b, ms)}
+    for k in ("project", "depth_sort", "tile_binning"):
+        out[k]["peak_gbs"] = hbm_gbs
+        out[k]["frac"] = out[k]["achieved_gbs"] / hbm_gbs if hbm_gbs else None
+    flops = n_eval_per_view * V * FLOPS_PER_EVAL
+    t = stage_ms["blend"] * 1e-3
+    out["blend"] = {"bound": "alu", "flop": flops, "achieved_tflops": flops / t / 1e12, "peak_tflops": fp32_peak,
+                    "frac": flops / t / 1e12 / fp32_peak,
+                    "ex2_frac": n_eval_per_view * V / t / 1e9 / ex2_peak_gops}
+    return out
 
 
 class ClockSampler:
@@ -360,6 +392,7 @@ def run_ours(args):
                               stream=stream, want_scores=False)
         return res
 
+    peaks = R.reloc_measure_peaks(local)          # roofline denominators, this GPU, before the timed region
     for k in range(args.warmup):
         step(k)
     ctx.set_profiling(True)
@@ -384,6 +417,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     stage_ms, stage_calls = ctx.stage_times()
     counts = ctx.last_counts()
+    S_sub = counts.n_gauss
     ctx.set_profiling(False)
     total_ms = max_over_ranks(dist, total_ms, dev)
     value = job_throughput(world, V * args.steps, total_ms / 1e3)
@@ -430,9 +464,9 @@ def run_ours(args):
     cpu_s, cores, ocounts, _, _ = oracle_sample(g, cam, hidden, seeds, 16, 0)
     n_eval_per_view = float(ocounts[:, 2].mean())
     flops = n_eval_per_view * V * FLOPS_PER_EVAL
-    sm_clock = clocks.get("sm_mhz") or 2070.0
-    peak = fp32_peak_tflops(2070.0)
+    peak = max(peaks["fp32_scalar_tflops"], peaks["fp32_packed_tflops"])
     achieved = flops / (blend_ms / 1e3) / 1e12
+    per_stage = {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -449,11 +483,16 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_blend", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                     "peak_source": "measured on this GPU before the timed region: register-resident "
+                                    "FP32 FMA microbenchmark (reloc_measure_peaks), the larger of scalar "
+                                    f"{peaks['fp32_scalar_tflops']:.1f} and packed f32x2 "
+                                    f"{peaks['fp32_packed_tflops']:.1f} TFLOP/s",
                      "work": f"{n_eval_per_view:.4g} included pixel-Gaussian pairs/view x {V} views x "
                              f"{FLOPS_PER_EVAL} flop (oracle count)",
                      "launch_ms": blend_ms},
-        "stage_ms": {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()},
+        "stage_ms": per_stage,
+        "stage_roofline": stage_rooflines(per_stage, S_sub, V, counts.n_visible, counts.n_instances,
+                                          n_eval_per_view, peak, peaks["ex2_gops"], _peaks().get("hbm_gbs")),
         "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
         "batch": batch,
         "learned": learned,
@@ -461,7 +500,7 @@ def run_ours(args):
         "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},
         "clocks": clocks,
-        "peaks": {"hbm_gbs": _peaks().get("hbm_gbs"), "bf16_tflops": _peaks().get("bf16_tflops")},
+        "peaks": {"hbm_gbs": _peaks().get("hbm_gbs"), "bf16_tflops": _peaks().get("bf16_tflops"), **peaks},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -471,7 +510,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true",

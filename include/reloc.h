@@ -378,6 +378,19 @@ reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rec
  * race and must be ordered by the caller.  Errors: EINVAL (NULL pointer,
  * n_views outside 1..RELOC_NOALLOC_MAX_VIEWS, image size outside 1..16383),
  * ECUDA. */
+/* Measured arithmetic throughput of `device`, the denominators of the
+ * projection's and the blend's rooflines.  The paper has no counterpart: it
+ * is a measurement utility.  Register-resident microbenchmarks (independent
+ * dependency chains per thread, four waves of the SM count) give
+ *   fp32_scalar_tflops  FP32 fused multiply-add, 2 flop each (TFLOP/s)
+ *   fp32_packed_tflops  the same with packed two-lane f32x2 FMAs (TFLOP/s)
+ *   ex2_gops            base-2 exponentials, ex2.approx (10^9 per second)
+ * Any output pointer may be NULL.  Takes some milliseconds, allocates 1 KB
+ * of device memory for the duration of the call and synchronises the
+ * device.  Errors: ECUDA (no such device or a launch failure). */
+reloc_status reloc_measure_peaks(int device, double *fp32_scalar_tflops, double *fp32_packed_tflops,
+                                 double *ex2_gops);
+
 #define RELOC_NOALLOC_MAX_VIEWS 512
 reloc_status reloc_ncc_images_noalloc(const float *images_dev, int n_views, int height, int width,
                                       const float *query_dev, double *scores_dev, int *degenerate_dev,

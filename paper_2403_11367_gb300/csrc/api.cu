@@ -1467,3 +1467,14 @@ extern "C" reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, i
     CK(cudaStreamSynchronize(st));
     return RELOC_OK;
 }
+
+extern "C" reloc_status reloc_measure_peaks(int device, double *fp32_scalar_tflops, double *fp32_packed_tflops,
+                                            double *ex2_gops)
+{
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(RELOC_ECUDA, "device %d not present (%d devices)", device, ndev);
+    CK(cudaSetDevice(device));
+    CK(measure_peaks(fp32_scalar_tflops, fp32_packed_tflops, ex2_gops));
+    return RELOC_OK;
+}

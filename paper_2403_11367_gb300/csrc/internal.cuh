@@ -141,6 +141,9 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 // Allow K4 its largest shared-memory footprint (once per device, before any capture).
 cudaError_t configure_tile_kernels();
 
+// FP32 (scalar and packed) FMA and ex2 throughput of the current device (peaks.cu).
+cudaError_t measure_peaks(double *fp32_scalar_tflops, double *fp32_packed_tflops, double *ex2_gops);
+
 // Tile id of each instance of one view from its ranges (debug export).
 cudaError_t launch_fill_tiles(const int2 *ranges_view, int n_tiles, uint32_t *tiles_view, cudaStream_t st);
 

@@ -276,6 +276,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             nk += __popc(keep);
         }
         __syncwarp();
+#pragma unroll 4
         for (int k = 0; k < nk; ++k) {
             const float4 s0 = sw[0][k], s1 = sw[1][k], s2 = sw[2][k];
             const float nth = sthr[k];

@@ -121,6 +121,7 @@ SIGNATURES = {
     "reloc_stage_times": (C.c_int, [_vp, _dp, _i64p]),
     "reloc_export_debug": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64p, _vp, _vp]),
     "reloc_ncc_images_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
+    "reloc_measure_peaks": (C.c_int, [C.c_int, _dp, _dp, _dp]),
 }
 NOALLOC_MAX_VIEWS = 512
 PROPOSAL_H, PROPOSAL_W, PROPOSAL_CLASSES, PROPOSAL_PARAMS = 47, 176, 64, 1916960
@@ -186,6 +187,13 @@ def reloc_ncc_images_noalloc(images, query, scores_out, degenerate_out=None, str
     V, _, H, W = images.shape
     _check(lib.reloc_ncc_images_noalloc(_ptr(images), V, H, W, _ptr(query), _ptr(scores_out),
                                         _ptr(degenerate_out), _stream(stream)))
+
+
+def reloc_measure_peaks(device: int = 0) -> dict:
+    """Measured FP32 FMA (scalar, packed f32x2) TFLOP/s and ex2 G/s of a device."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.reloc_measure_peaks(device, C.byref(a), C.byref(b), C.byref(c)))
+    return {"fp32_scalar_tflops": a.value, "fp32_packed_tflops": b.value, "ex2_gops": c.value}
 
 
 def reloc_default_config(**over) -> Config:
