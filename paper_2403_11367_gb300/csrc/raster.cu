@@ -166,8 +166,11 @@ __device__ __forceinline__ float ex2_approx(float x)
 // functions sat((x - t) 2^60), one saturating fused multiply-add per pixel:
 // any positive float difference times 2^60 saturates to 1, a negative one to
 // 0 (only x == t exactly falls on the other side of a >= test).
+// The column terms dx, A' dx^2 + log2(o) and B' dx are shared by the pixel
+// pair and computed once (scalar); the row terms run packed.  DA: accumulate
+// depth and alpha too (image export); the scoring launches need colour only.
 constexpr float STEP_SCALE = 1152921504606846976.f;   // 2^60
-template <int TW, int TH, int RPL>
+template <int TW, int TH, int RPL, bool DA>
 __global__ void __launch_bounds__(32, RPL == 1 ? 32 : 24)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
         const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
@@ -178,9 +181,9 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     constexpr int WROWS = 64 / TW;           // pixel rows per warp
     constexpr int CH = 32 * RPL;             // records per warp step
     static_assert(WPT >= 1 && TH % WROWS == 0, "tile shape");
-    // kept records compacted: (-u,-u,A',A') (B',B',log2 o,log2 o)
-    // (-v,-v,C',C') (r,r,g,g) (b,b,z,z) and -2^60 times the p' threshold
-    __shared__ float4 s_rec[5][CH];
+    // kept records compacted: (-u,A',B',log2 o) (-v,-v,C',C') (r,r,g,g)
+    // (b,b,z,z) and -2^60 times the p' threshold
+    __shared__ float4 s_rec[4][CH];
     __shared__ float s_thr[CH];
 
     // one warp per block: (tile, warp block) units, so a warp that finishes
@@ -218,7 +221,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     // depth and weight sums
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
-    const f32x2 FX2 = pk(fxp, fxp), FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
+    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
     const float ntmin = -cam.t_min * STEP_SCALE;
 
     // software pipeline: list indices two steps ahead, records one step ahead
@@ -266,11 +269,10 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 const int k = nk + __popc(keep & lt);
                 const float l2o = __log2f(pa.w);
                 const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
-                sw[0][k] = make_float4(-pa.x, -pa.x, Ap, Ap);
-                sw[1][k] = make_float4(Bp, Bp, l2o, l2o);
-                sw[2][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
-                sw[3][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
-                sw[4][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
+                sw[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
+                sw[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
+                sw[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
+                sw[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
                 sthr[k] = -STEP_SCALE * fmaxf(limL + l2o, l2amin);
             }
             nk += __popc(keep);
@@ -278,13 +280,12 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         __syncwarp();
 #pragma unroll 4
         for (int k = 0; k < nk; ++k) {
-            const float4 s0 = sw[0][k], s1 = sw[1][k], s2 = sw[2][k];
+            const float4 s0 = sw[0][k], s1 = sw[1][k];
             const float nth = sthr[k];
-            const f32x2 DX2 = add2(FX2, pk(s0.x, s0.y));
-            const f32x2 K1 = mul2(pk(s1.x, s1.y), DX2);
-            const f32x2 K0 = fma2(mul2(pk(s0.z, s0.w), DX2), DX2, pk(s1.z, s1.w));
-            const f32x2 DY2 = add2(FY2, pk(s2.x, s2.y));
-            const f32x2 P2 = fma2(DY2, fma2(pk(s2.z, s2.w), DY2, K1), K0);
+            const float dx = fxp + s0.x;
+            const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
+            const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
+            const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
             float p0, p1;
             upk(P2, p0, p1);
             // p' >= threshold
@@ -299,12 +300,18 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
             const f32x2 WF = mul2(W2, GO2);
             T2 = mul2(TN2, GO2);
-            const float4 c0 = sw[3][k], c1 = sw[4][k];
+            const float4 c0 = sw[2][k];
             R2 = fma2(pk(c0.x, c0.y), WF, R2);
             G2 = fma2(pk(c0.z, c0.w), WF, G2);
-            B2 = fma2(pk(c1.x, c1.y), WF, B2);
-            Z2 = fma2(pk(c1.z, c1.w), WF, Z2);
-            S2 = add2(S2, WF);
+            if (DA) {
+                const float4 c1 = sw[3][k];
+                B2 = fma2(pk(c1.x, c1.y), WF, B2);
+                Z2 = fma2(pk(c1.z, c1.w), WF, Z2);
+                S2 = add2(S2, WF);
+            } else {
+                const float2 c1 = *reinterpret_cast<const float2 *>(&sw[3][k]);
+                B2 = fma2(pk(c1.x, c1.y), WF, B2);
+            }
         }
         __syncwarp();
     }
@@ -356,8 +363,12 @@ static cudaError_t blend_t(const float4 *rec, const Layout &L, const uint32_t *i
                            const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
 {
     dim3 grid(cam.n_tiles * (TW * TH / 64), view_sel ? n_sel : L.V);
-    k_blend<TW, TH, RPL><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha,
-                                                      view_sel, overflow);
+    if (depth || alpha)
+        k_blend<TW, TH, RPL, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth,
+                                                        alpha, view_sel, overflow);
+    else
+        k_blend<TW, TH, RPL, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth,
+                                                         alpha, view_sel, overflow);
     return cudaGetLastError();
 }
 

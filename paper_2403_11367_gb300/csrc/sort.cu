@@ -402,7 +402,7 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
 // divergence and no dependent shared-memory round trip (the row through the
 // horizon takes most pairs of every chunk).
 // k_tile_emit_smem: any row width, one queue, slots in shared memory.
-constexpr int EMIT_STAGE = 1024;
+constexpr int EMIT_STAGE = BIN_CHUNK_MIN;             // a whole chunk of the usual size: one barrier
 
 struct EmitChunk {
     int v, n;
@@ -635,7 +635,12 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 
 cudaError_t configure_tile_kernels()
 {
-    return cudaFuncSetAttribute(k_tile_emit_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_EMIT_SMEM_MAX);
+    cudaError_t e = cudaFuncSetAttribute(k_tile_emit_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TILE_EMIT_SMEM_MAX);
+    if (e == cudaSuccess)   // band queues of the widest register variant: 8 x 8 warps x 64 pairs x 8 B
+        e = cudaFuncSetAttribute(k_tile_emit_reg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(uint2) * TILE_EMIT_WARPS * 8 * 64);
+    return e;
 }
 
 // Tile id of every instance of one view, from its ranges (debug export).
