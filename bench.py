@@ -230,6 +230,58 @@ def run_learned_leg(ctx, cam, dev, stream, n_queries=256):
     return out
 
 
+PAPER_GRID = (15, 15, 36, 2.0, 10.0)   # 2 m x 10 deg over (-15, 15) m and a full turn: 8100 cells
+SEARCH_FRACTION, SEARCH_BATCH, SEARCH_STOP = 0.2, 64, 0.8
+
+
+def run_random_leg(ctx, cam, dev, stream, n_queries=8):
+    """Random search with early stop (Sec. IV-A) on the paper's grid: coarse
+    poses off the hidden pose by x, y ~ U(-10, 10) m and yaw ~ U(-90, 90) deg;
+    20% of the 8100 cells visited in batches of 64, stop at NCC >= 0.8.
+    Reports candidates/s, queries/s, cells scored per query, early stops and
+    how often the best cell is the hidden pose's nearest cell or a neighbour
+    (within one grid step in x, y and yaw)."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    hidden, _ = sg.street_queries(n_queries, seed=51)
+    r = sg.Rng(52)
+    off = np.stack([r.uniform(n_queries, -10, 10), r.uniform(n_queries, -10, 10),
+                    r.uniform(n_queries, -np.pi / 2, np.pi / 2)], 1)
+    nx, ny, nyaw, sxy, syaw = PAPER_GRID
+    jobs = []
+    for i in range(n_queries):
+        h = hidden[i]
+        runs, _, _ = ctx.select_block(h[0], h[1], RADIUS)
+        img = torch.empty((1, 3, cam.height, cam.width), device=dev)
+        ctx.render(runs, sg.pose_from_xyz_yaw(*h)[None], cam, rgb=img)
+        img = (img[0] + torch.tensor(sg.image_noise(3000 + i, cam.height, cam.width), device=dev)).contiguous()
+        jobs.append((img, sg.pose_from_xyz_yaw(h[0] + off[i, 0], h[1] + off[i, 1], h[2], h[3] + off[i, 2])))
+    ctx.localize_random(jobs[0][0], jobs[0][1], RADIUS, PAPER_GRID, cam, fraction=0.02, batch=SEARCH_BATCH,
+                        stream=stream, want_scores=False)                 # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = [ctx.localize_random(img, pose, RADIUS, PAPER_GRID, cam, fraction=SEARCH_FRACTION, ncc_stop=SEARCH_STOP,
+                               batch=SEARCH_BATCH, seed=100 + i, stream=stream, want_scores=False)[0]
+           for i, (img, pose) in enumerate(jobs)]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    near = 0
+    for i, rr in enumerate(res):
+        ix, iy, iyaw = rr.best_index % nx, (rr.best_index // nx) % ny, rr.best_index // (nx * ny)
+        # the hidden pose's offset from the coarse pose, in grid steps
+        fx = -off[i, 0] / sxy + 0.5 * (nx - 1)
+        fy = -off[i, 1] / sxy + 0.5 * (ny - 1)
+        fyaw = -np.degrees(off[i, 2]) / syaw + 0.5 * (nyaw - 1)
+        near += int(abs(ix - fx) <= 1 and abs(iy - fy) <= 1 and abs(iyaw - fyaw) <= 1)
+    scored = sum(rr.n_scored for rr in res)
+    return {"grid": "15 x 15 x 36 cells, 2 m / 10 deg (8100)", "fraction": SEARCH_FRACTION,
+            "ncc_stop": SEARCH_STOP, "batch": SEARCH_BATCH, "queries": n_queries, "candidates_scored": scored,
+            "candidates_per_s": scored / dt, "queries_per_s": n_queries / dt,
+            "mean_scored_per_query": scored / n_queries, "stopped_early": sum(rr.stopped_early for rr in res),
+            "best_within_one_cell_of_hidden": near, "best_ncc": [round(rr.best_score, 4) for rr in res]}
+
+
 def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best):
     """FP16 / BF16 attribute storage on the driving workload: candidates/s and
     deviation of every NCC score and winner from the FP32 path."""
@@ -451,6 +503,7 @@ def run_ours(args):
         if not args.no_batch else None
     batch = run_batch_leg(ctx, cam, dev, stream) if not args.no_batch else None
     learned = run_learned_leg(ctx, cam, dev, stream) if not args.no_batch else None
+    random_search = run_random_leg(ctx, cam, dev, stream) if not args.no_batch else None
 
     if rank != 0:
         if dist is not None:
@@ -496,6 +549,7 @@ def run_ours(args):
         "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
         "batch": batch,
         "learned": learned,
+        "random_search": random_search,
         "precision": precision,
         "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},

@@ -100,8 +100,9 @@ typedef struct reloc_result {
     int32_t n_blocks;          /* blocks selected                                      */
     int32_t degenerate;        /* 1 if the best render or the query has zero variance  */
     int32_t n_scored;          /* candidates rendered and scored (all, unless the
-                                  learned proposal picked a top-k)                     */
-    int32_t reserved;
+                                  learned proposal picked a top-k or a random search
+                                  visited a part)                                      */
+    int32_t stopped_early;     /* random search: 1 if the NCC threshold ended it      */
 } reloc_result;
 
 /* Work counts of the last render/score/localize call (sums over views). */
@@ -202,6 +203,51 @@ reloc_status reloc_localize(reloc_ctx *ctx, const float *query_dev, const double
                             double radius, const reloc_grid *grid, const reloc_camera *cam,
                             reloc_result *out, double *scores_host, float *best_rgb_dev,
                             float *best_depth_dev, float *best_alpha_dev, void *stream);
+
+/* Random search with early stop (Sec. IV-A, initial relocalization): instead
+ * of the whole grid, visit a share of its cells in random order, a batch at
+ * a time, and stop after the first batch whose best NCC reaches a threshold.
+ * The paper visits 20% of a 2 m x 10 deg grid over (-15, 15) m and a full
+ * turn; it gives no threshold value, and its second stop test (enough
+ * feature matches for the refinement) needs a learned matcher and is not
+ * part of this call.
+ *   fraction   share of the grid's cells visited, in (0, 1]; the visit is
+ *              the first ceil(fraction * n_cells) cells of the order
+ *   ncc_stop   stop after the batch in which the best NCC so far is >= this
+ *              (+inf: never stop early)
+ *   batch      cells rendered and scored together, 1..4096
+ *   seed       the visiting order when `order` is NULL: the cells 0..n-1
+ *              shuffled by Fisher-Yates (for i = n-1 down to 1, swap cell i
+ *              with cell j = x mod (i + 1), x the next SplitMix64 output of
+ *              a generator started at `seed`)
+ *   order      explicit visiting order (cell indices, each in 0..n-1, no
+ *              repeats), n_order entries, visited in full (fraction
+ *              ignored); the caller keeps ownership
+ */
+typedef struct reloc_search {
+    double fraction;
+    double ncc_stop;
+    int32_t batch;
+    int32_t n_order;
+    uint64_t seed;
+    const int32_t *order;
+    int32_t reserved[4];
+} reloc_search;
+
+/* Cells are numbered as in reloc_localize (index = ix + nx (iy + ny iyaw),
+ * offsets centred on the coarse pose) but the grid may hold up to 2^20 cells.
+ * out: best_index = best visited cell (highest NCC, lowest cell on ties),
+ * n_candidates = cells in the grid, n_scored = cells visited, stopped_early.
+ * scores_host[n_cells] (may be NULL) gets each visited cell's NCC and NaN for
+ * the others.  The winner's images go to the *_dev buffers as in
+ * reloc_localize.  The host reads the batch's scores after each batch (one
+ * synchronisation per batch).  Errors: EINVAL (bad options, grid or order),
+ * ENOMAP, ENUMERIC, ECUDA, EOVERFLOW. */
+reloc_status reloc_localize_random(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose,
+                                   double radius, const reloc_grid *grid, const reloc_camera *cam,
+                                   const reloc_search *search, reloc_result *out, double *scores_host,
+                                   float *best_rgb_dev, float *best_depth_dev, float *best_alpha_dev,
+                                   void *stream);
 
 /* reloc_localize for callers holding HOST buffers: copies query_host
  * ([3][H][W]) to the device and the winner's RGB/depth back to best_rgb_host

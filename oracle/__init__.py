@@ -12,6 +12,7 @@ follows in the C source.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -67,6 +68,8 @@ def lib():
             L.or_argmax.argtypes = [dp, C.c_int]
             L.or_argmax.restype = C.c_int
             L.or_grid_poses.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp]
+            L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
+            L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
             L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
                                           C.c_double, i64p, i64p]
             L.or_block_select.restype = C.c_int64
@@ -228,6 +231,50 @@ def grid_poses(seed_pose, nx, ny, nyaw, step_xy, step_yaw_deg) -> np.ndarray:
     lib().or_grid_poses(_p(_c(seed_pose, np.float64).reshape(16), C.c_double), nx, ny, nyaw,
                         step_xy, step_yaw_deg, _p(out, C.c_double))
     return out.reshape(-1, 4, 4)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """The first ``count`` outputs of SplitMix64 started at ``seed``."""
+    out = np.zeros(count, np.uint64)
+    lib().or_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, count, _p(out, C.c_uint64))
+    return out
+
+
+def search_order(seed: int, n: int) -> np.ndarray:
+    """Visiting order of the random search (Sec. IV-A): cells 0..n-1 shuffled
+    by Fisher-Yates driven by SplitMix64(seed)."""
+    out = np.zeros(n, np.int32)
+    lib().or_search_order(seed & 0xFFFFFFFFFFFFFFFF, n, _p(out, C.c_int32))
+    return out
+
+
+def visit_count(fraction: float, n_cells: int) -> int:
+    """Cells a random search visits: ceil(fraction * n_cells) in double precision."""
+    return min(n_cells, int(math.ceil(fraction * n_cells)))
+
+
+def random_search(g, cell_poses, cam, query, order, batch, ncc_stop, prm=None):
+    """Random search with early stop (Sec. IV-A), FP64: render and score the
+    cells of ``order`` in consecutive batches of ``batch``; after each batch,
+    stop if the best NCC so far is >= ncc_stop.  The best cell is the visited
+    cell with the highest NCC, the lowest cell index on ties.
+    Returns dict(best_index, best_score, n_scored, stopped_early, scores) with
+    NaN scores for cells not visited."""
+    order = np.asarray(order, np.int64)
+    scores = np.full(len(cell_poses), np.nan)
+    best, best_sc, visited, stopped = -1, -np.inf, 0, False
+    for b0 in range(0, len(order), batch):
+        cells = order[b0:b0 + batch]
+        out = render_views(g, np.asarray(cell_poses)[cells], cam, prm, query=query, images=False, flags=False)
+        for c, sc in zip(cells, out["scores"]):
+            scores[c] = sc
+            if sc > best_sc or (sc == best_sc and c < best):
+                best, best_sc = int(c), float(sc)
+        visited += len(cells)
+        if best_sc >= ncc_stop:
+            stopped = visited < len(order)
+            break
+    return dict(best_index=best, best_score=best_sc, n_scored=visited, stopped_early=stopped, scores=scores)
 
 
 def block_select(means, block_size, cx, cy, radius):

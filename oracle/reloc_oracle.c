@@ -499,6 +499,39 @@ void or_grid_poses(const double *seed, int nx, int ny, int nyaw, double step_xy,
 }
 
 /* ========================================================================= */
+/* Random search of Sec. IV-A: the order in which grid cells are visited.     */
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the state advances by     */
+/* the odd constant 0x9E3779B97F4A7C15 and each output is the new state mixed */
+/* by xor-shift 30, multiply, xor-shift 27, multiply, xor-shift 31.  The      */
+/* cells 0..n-1 are shuffled by Fisher-Yates: for i = n-1 down to 1, draw the */
+/* next output x and swap cells i and x mod (i + 1).                          */
+/* ========================================================================= */
+static uint64_t or_sm64_next(uint64_t *state)
+{
+    uint64_t x = *state + 0x9E3779B97F4A7C15ULL;
+    *state = x;
+    x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ULL;
+    x ^= x >> 27; x *= 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+void or_splitmix64(uint64_t seed, int64_t count, uint64_t *out)
+{
+    uint64_t st = seed;
+    for (int64_t k = 0; k < count; ++k) out[k] = or_sm64_next(&st);
+}
+
+void or_search_order(uint64_t seed, int64_t n, int32_t *cells)
+{
+    uint64_t st = seed;
+    for (int64_t i = 0; i < n; ++i) cells[i] = (int32_t)i;
+    for (int64_t i = n - 1; i >= 1; --i) {
+        const int64_t j = (int64_t)(or_sm64_next(&st) % (uint64_t)(i + 1));
+        const int32_t t = cells[i]; cells[i] = cells[j]; cells[j] = t;
+    }
+}
+
+/* ========================================================================= */
 /* 2D voxel blocks (Sec. III-B.2): block (floor(x/B), floor(y/B)); the map is */
 /* ordered by block key (bx, by) ascending, Gaussians of a block in index     */
 /* order.  Selection (Sec. III-C.1): every block whose centre lies within     */

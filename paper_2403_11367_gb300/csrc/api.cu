@@ -1114,6 +1114,136 @@ extern "C" reloc_status reloc_localize(reloc_ctx *ctx, const float *query_dev, c
                          best_depth_dev, best_alpha_dev, (cudaStream_t)stream);
 }
 
+// ================================================ random search (Sec. IV-A) ==
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): a Weyl sequence with step 0x9E3779B97F4A7C15
+// passed through the variant-13 64-bit finaliser.
+static uint64_t splitmix64_next(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" reloc_status reloc_localize_random(reloc_ctx *ctx, const float *query_dev, const double *coarse_pose,
+                                              double radius, const reloc_grid *grid, const reloc_camera *cam,
+                                              const reloc_search *search, reloc_result *out, double *scores_host,
+                                              float *best_rgb_dev, float *best_depth_dev, float *best_alpha_dev,
+                                              void *stream)
+{
+    if (!ctx || !cam || !out || !search || !grid || !query_dev || !coarse_pose) return fail(RELOC_EINVAL, "NULL argument");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    const int64_t n_cells = (int64_t)grid->nx * grid->ny * grid->nyaw;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nyaw < 1 || n_cells > (1 << 20))
+        return fail(RELOC_EINVAL, "grid %dx%dx%d not in 1..2^20 cells", grid->nx, grid->ny, grid->nyaw);
+    if (search->batch < 1 || search->batch > 4096) return fail(RELOC_EINVAL, "batch %d not in 1..4096", search->batch);
+    if (!std::isfinite(grid->step_xy) || !std::isfinite(grid->step_yaw_deg) || !std::isfinite(radius))
+        return fail(RELOC_ENUMERIC, "non-finite grid step or radius");
+    if (std::isnan(search->ncc_stop)) return fail(RELOC_ENUMERIC, "ncc_stop is NaN");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(coarse_pose[k])) return fail(RELOC_ENUMERIC, "non-finite coarse pose");
+    // the visit: an explicit order, or the first ceil(fraction n) cells of a seeded shuffle
+    std::vector<int> order;
+    if (search->order) {
+        if (search->n_order < 1 || search->n_order > n_cells)
+            return fail(RELOC_EINVAL, "n_order %d not in 1..%lld", search->n_order, (long long)n_cells);
+        std::vector<char> seen((size_t)n_cells, 0);
+        for (int i = 0; i < search->n_order; ++i) {
+            const int c = search->order[i];
+            if (c < 0 || c >= n_cells || seen[c]) return fail(RELOC_EINVAL, "order[%d] = %d invalid or repeated", i, c);
+            seen[c] = 1;
+            order.push_back(c);
+        }
+    } else {
+        if (!(search->fraction > 0.0 && search->fraction <= 1.0))
+            return fail(RELOC_EINVAL, "fraction %g not in (0, 1]", search->fraction);
+        std::vector<int> perm((size_t)n_cells);
+        for (int64_t i = 0; i < n_cells; ++i) perm[i] = (int)i;
+        uint64_t state = search->seed;
+        for (int64_t i = n_cells - 1; i > 0; --i) {
+            const uint64_t j = splitmix64_next(state) % (uint64_t)(i + 1);
+            std::swap(perm[i], perm[j]);
+        }
+        const int64_t m = std::min<int64_t>(n_cells, (int64_t)std::ceil(search->fraction * (double)n_cells));
+        order.assign(perm.begin(), perm.begin() + m);
+    }
+    // blocks around the coarse pose, every cell's pose
+    QuerySpec base;
+    {
+        const double *W = coarse_pose;
+        const double Cx = -(W[0] * W[3] + W[4] * W[7] + W[8] * W[11]);
+        const double Cy = -(W[1] * W[3] + W[5] * W[7] + W[9] * W[11]);
+        std::vector<int> ids;
+        ctx->blocks.range(Cx, Cy, radius, ids);
+        merge_runs(ctx->blocks, ids, base.runs);
+        base.n_blocks = (int)ids.size();
+    }
+    std::vector<double> cell_pose;
+    grid_poses(coarse_pose, *grid, cell_pose);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> sc_all;
+    if (scores_host) sc_all.assign((size_t)n_cells, std::nan(""));
+    int best = -1, best_degen = 0;
+    double best_sc = -INFINITY;
+    int64_t visited = 0, S = 0;
+    for (const reloc_range &r : base.runs) S += r.end - r.begin;
+    bool stopped = false;
+    for (size_t b0 = 0; b0 < order.size(); b0 += (size_t)search->batch) {
+        const int nb = (int)std::min<size_t>((size_t)search->batch, order.size() - b0);
+        std::vector<QuerySpec> qs(1);
+        qs[0].runs = base.runs;
+        qs[0].n_blocks = base.n_blocks;
+        qs[0].V = nb;
+        qs[0].img = query_dev;
+        for (int j = 0; j < nb; ++j) {
+            const double *p = cell_pose.data() + 16 * (size_t)order[b0 + j];
+            qs[0].poses.insert(qs[0].poses.end(), p, p + 16);
+        }
+        CallOut o;
+        o.score = true;
+        CKS(run_batch(ctx, qs, cam, st, o, false));
+        for (int j = 0; j < nb; ++j) {
+            const int c = order[b0 + j];
+            const double s_c = o.scores[j];
+            if (scores_host) sc_all[c] = s_c;
+            if (s_c > best_sc || (s_c == best_sc && c < best)) {
+                best = c;
+                best_sc = s_c;
+                best_degen = o.degen[j];
+            }
+        }
+        visited += nb;
+        if (best_sc >= search->ncc_stop) {
+            stopped = visited < (int64_t)order.size();
+            break;
+        }
+    }
+    if (best >= 0 && (best_rgb_dev || best_depth_dev || best_alpha_dev)) {
+        std::vector<QuerySpec> wq(1);
+        wq[0].runs = base.runs;
+        wq[0].V = 1;
+        wq[0].poses.assign(cell_pose.begin() + 16 * (size_t)best, cell_pose.begin() + 16 * (size_t)(best + 1));
+        CallOut o;
+        o.rgb = best_rgb_dev;
+        o.depth = best_depth_dev;
+        o.alpha = best_alpha_dev;
+        CKS(run_batch(ctx, wq, cam, st, o, false));
+    }
+    memset(out, 0, sizeof *out);
+    out->best_index = best;
+    out->n_candidates = (int32_t)n_cells;
+    out->best_score = best >= 0 ? best_sc : 0.0;
+    if (best >= 0) memcpy(out->best_pose, cell_pose.data() + 16 * (size_t)best, sizeof(double) * 16);
+    out->n_gauss = S;
+    out->n_blocks = base.n_blocks;
+    out->degenerate = best_degen;
+    out->n_scored = (int32_t)visited;
+    out->stopped_early = stopped ? 1 : 0;
+    if (scores_host) memcpy(scores_host, sc_all.data(), sizeof(double) * (size_t)n_cells);
+    return RELOC_OK;
+}
+
 extern "C" reloc_status reloc_localize_batch(reloc_ctx *ctx, const reloc_query *queries, int n_queries,
                                              const reloc_camera *cam, reloc_result *results, double *scores_host,
                                              float *best_rgb_dev, float *best_depth_dev, void *stream)

@@ -72,7 +72,12 @@ class TuneResult(C.Structure):
 class Result(C.Structure):
     _fields_ = [("best_index", C.c_int32), ("n_candidates", C.c_int32), ("best_score", C.c_double),
                 ("best_pose", C.c_double * 16), ("n_gauss", C.c_int64), ("n_blocks", C.c_int32),
-                ("degenerate", C.c_int32), ("n_scored", C.c_int32), ("reserved", C.c_int32)]
+                ("degenerate", C.c_int32), ("n_scored", C.c_int32), ("stopped_early", C.c_int32)]
+
+
+class Search(C.Structure):
+    _fields_ = [("fraction", C.c_double), ("ncc_stop", C.c_double), ("batch", C.c_int32), ("n_order", C.c_int32),
+                ("seed", C.c_uint64), ("order", C.c_void_p), ("reserved", C.c_int32 * 4)]
 
 
 class Counts(C.Structure):
@@ -101,6 +106,8 @@ SIGNATURES = {
                               _vp]),
     "reloc_localize": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera), C.POINTER(Result),
                                  _dp, _vp, _vp, _vp, _vp]),
+    "reloc_localize_random": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera),
+                                        C.POINTER(Search), C.POINTER(Result), _dp, _vp, _vp, _vp, _vp]),
     "reloc_localize_host": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera),
                                       C.POINTER(Result), _vp, _vp, _vp]),
     "reloc_localize_batch": (C.c_int, [_vp, C.POINTER(Query), C.c_int, C.POINTER(Camera), C.POINTER(Result), _dp,
@@ -278,6 +285,30 @@ class Context:
         _check(lib.reloc_localize(self._h, _ptr(query), cp.ctypes.data_as(_dp), radius, C.byref(g), C.byref(c),
                                   C.byref(res), sc.ctypes.data_as(_dp) if sc is not None else None,
                                   _ptr(best_rgb), _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
+        return res, sc
+
+    def localize_random(self, query, coarse_pose, radius, grid, cam, fraction=0.2, ncc_stop=float("inf"), batch=64,
+                        seed=0, order=None, best_rgb=None, best_depth=None, best_alpha=None, stream=None,
+                        want_scores=True):
+        """Random search with early stop over the grid's cells (include/reloc.h).
+        order: optional explicit visiting order (cell indices).  Returns
+        (Result, scores per cell with NaN for unvisited cells, or None)."""
+        cp = np.ascontiguousarray(coarse_pose, np.float64).reshape(16)
+        g = Grid(*grid) if not isinstance(grid, Grid) else grid
+        c = camera(cam)
+        opt = Search()
+        opt.fraction, opt.ncc_stop, opt.batch, opt.seed = float(fraction), float(ncc_stop), int(batch), int(seed)
+        ordr = None
+        if order is not None:
+            ordr = np.ascontiguousarray(order, np.int32)
+            opt.order, opt.n_order = ordr.ctypes.data, len(ordr)
+        res = Result()
+        n = g.nx * g.ny * g.nyaw
+        sc = np.zeros(n) if want_scores else None
+        _check(lib.reloc_localize_random(self._h, _ptr(query), cp.ctypes.data_as(_dp), radius, C.byref(g),
+                                         C.byref(c), C.byref(opt), C.byref(res),
+                                         sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
+                                         _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
         return res, sc
 
     def localize_batch(self, queries, cam, best_rgb=None, best_depth=None, stream=None, want_scores=True):
