@@ -37,6 +37,10 @@ GRID = (4, 4, 4, 0.5, 2.0)
 RADIUS = 40.0
 N_QUERIES = 4
 FLOPS_PER_EVAL = 24          # FP32 ops per included (pixel, Gaussian) pair (plus one exp)
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this
+# workload's 64-view k_blend<16,16,1,false> launch (query 0: 628.4 MB + 15.6 MB);
+# to be re-taken whenever that kernel changes
+BLEND_DRAM_BYTES_PER_LAUNCH = 643_998_208
 WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
             "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
 
@@ -535,7 +539,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": 4 * H * W * 4 + 20 * V + 24},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_blend", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": BLEND_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_gbs": BLEND_DRAM_BYTES_PER_LAUNCH / (blend_ms / 1e3) / 1e9,
                      "peak_source": "measured on this GPU before the timed region: register-resident "
                                     "FP32 FMA microbenchmark (reloc_measure_peaks), the larger of scalar "
                                     f"{peaks['fp32_scalar_tflops']:.1f} and packed f32x2 "
