@@ -259,6 +259,55 @@ reloc_status reloc_localize_host(reloc_ctx *ctx, const float *query_host, const 
                                  reloc_result *out, float *best_rgb_host, float *best_depth_host,
                                  void *stream);
 
+/* Pose refinement step of Sec. III-C.2 without its learned matcher: the
+ * caller supplies matched pixel pairs between a view rendered at
+ * pose_render (its depth and alpha from reloc_render / reloc_localize) and
+ * the query image; each render pixel is back-projected with the rendered
+ * depth, and the query's world-to-camera pose is estimated from the
+ * resulting 2D-3D pairs by Perspective-n-Point.  Iterating render -> match
+ * -> refine is the paper's refinement loop.
+ *   depth_dev, alpha_dev  [H][W] float32, device: Eq. (depth) D and
+ *                         1 - T of the view (caller-owned)
+ *   pairs_dev             [n_pairs][4] float32, device: (u_r, v_r, u_q, v_q)
+ *                         pixel coordinates, pixel (x, y) centred at
+ *                         (x + 0.5, y + 0.5)
+ *   pose_init             world-to-camera start (typically pose_render)
+ * Back-projection: D and A are sampled bilinearly at (u_r - 0.5, v_r - 0.5)
+ * in pixel-index space (the 2 x 2 neighbourhood must lie in the image); a
+ * pair is used when A >= alpha_min, with depth z = D / A and camera point
+ * z ((u_r - cx) / fx, (v_r - cy) / fy, 1), mapped to the world by
+ * pose_render.  PnP: minimise sum_i huber(|pi(W X_i) - (u_q, v_q)|) over W
+ * (Huber threshold huber_px; points with camera z <= 1e-6 are ignored) by
+ * iteratively reweighted Gauss-Newton in FP64: the update delta = (rho, phi)
+ * solves (H + 1e-9 tr(H)/6 I) delta = -g, W <- [Exp(phi) R | Exp(phi) t +
+ * rho]; a step that does not lower the cost is halved up to 10 times, then
+ * the solve stops; it also stops when max |delta| < tol or after max_iters.
+ * Errors: EINVAL (NULL pointer, n_pairs < 1, bad options), ENUMERIC
+ * (non-finite pose or fewer than 3 usable pairs), ECUDA. */
+typedef struct reloc_pnp_options {
+    int32_t max_iters;         /* default 30                                          */
+    int32_t reserved0;
+    double huber_px;           /* default 2 px                                        */
+    double alpha_min;          /* default 0.5                                         */
+    double tol;                /* default 1e-12                                       */
+    int32_t reserved[4];
+} reloc_pnp_options;
+
+typedef struct reloc_pnp_result {
+    double pose[16];           /* refined world-to-camera pose                        */
+    double rms_px;             /* RMS reprojection error of the used pairs (px)       */
+    double cost;               /* final Huber cost                                    */
+    int32_t n_used;            /* pairs with a usable depth                           */
+    int32_t iters;             /* Gauss-Newton iterations run                         */
+    int32_t reserved[2];
+} reloc_pnp_result;
+
+void reloc_default_pnp_options(reloc_pnp_options *opt);
+reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_render, const double *pose_init,
+                              const reloc_camera *cam, const float *depth_dev, const float *alpha_dev,
+                              const float *pairs_dev, int n_pairs, const reloc_pnp_options *opt,
+                              reloc_pnp_result *out, void *stream);
+
 /* One query of a batch (Sec. III-C.1 applied to many queries at once). */
 typedef struct reloc_query {
     const float *query_dev;    /* [3][H][W] device image of the query (caller-owned)   */

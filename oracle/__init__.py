@@ -68,6 +68,13 @@ def lib():
             L.or_argmax.argtypes = [dp, C.c_int]
             L.or_argmax.restype = C.c_int
             L.or_grid_poses.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp]
+            L.or_pnp_apply.argtypes = [dp, dp, C.c_double, dp]
+            L.or_pnp_residual.argtypes = [dp, dp, dp, dp, dp, dp]
+            L.or_pnp_residual.restype = C.c_int
+            L.or_refine_pnp.argtypes = [dp, dp, dp, fp, fp, fp, C.c_int64, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, dp]
+            L.or_pnp_backproject.argtypes = [dp, dp, fp, fp, dp, C.c_int64, C.c_double, dp, u8p]
+            L.or_pnp_backproject.restype = C.c_int64
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
             L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
             L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
@@ -275,6 +282,50 @@ def random_search(g, cell_poses, cam, query, order, batch, ncc_stop, prm=None):
             stopped = visited < len(order)
             break
     return dict(best_index=best, best_score=best_sc, n_scored=visited, stopped_early=stopped, scores=scores)
+
+
+def pnp_apply(pose, delta, s=1.0):
+    """pose updated on the left by s * delta, delta = (rho, phi)."""
+    out = np.zeros(16)
+    lib().or_pnp_apply(_p(_c(pose, np.float64).reshape(16), C.c_double), _p(_c(delta, np.float64), C.c_double),
+                       s, _p(out, C.c_double))
+    return out.reshape(4, 4)
+
+
+def pnp_residual(pose, X, cam, q):
+    """Reprojection residual (2) and its Jacobian (2 x 6) w.r.t. the left update
+    at zero; None if the point is not in front of the camera."""
+    r, J = np.zeros(2), np.zeros(12)
+    ok = lib().or_pnp_residual(_p(_c(pose, np.float64).reshape(16), C.c_double),
+                               _p(_c(X, np.float64), C.c_double), _p(camvec(cam), C.c_double),
+                               _p(_c(q, np.float64), C.c_double), _p(r, C.c_double), _p(J, C.c_double))
+    return (r, J.reshape(2, 6)) if ok else None
+
+
+def pnp_backproject(pose_render, cam, depth, alpha, uv, alpha_min=0.5):
+    """World points of render pixels uv [n, 2] from the view's depth D / A
+    (bilinear); returns (X [n, 3], used [n] bool)."""
+    uv = _c(uv, np.float64).reshape(-1, 2)
+    X = np.zeros((uv.shape[0], 3))
+    use = np.zeros(uv.shape[0], np.uint8)
+    lib().or_pnp_backproject(_p(_c(pose_render, np.float64).reshape(16), C.c_double), _p(camvec(cam), C.c_double),
+                             _p(_c(depth, np.float32), C.c_float), _p(_c(alpha, np.float32), C.c_float),
+                             _p(uv, C.c_double), uv.shape[0], alpha_min, _p(X, C.c_double), _p(use, C.c_uint8))
+    return X, use.astype(bool)
+
+
+def refine_pnp(pose_render, cam, depth, alpha, pairs, pose_init=None, max_iters=30, huber_px=2.0,
+               alpha_min=0.5, tol=1e-12):
+    """PnP refinement (Sec. III-C.2) in FP64: depth, alpha [H, W] and pairs [n, 4]
+    (u_r, v_r, u_q, v_q) float32.  Returns dict(pose, rms_px, cost, n_used, iters)."""
+    pr = _c(pose_render, np.float64).reshape(16)
+    pi = pr if pose_init is None else _c(pose_init, np.float64).reshape(16)
+    d, a, p = _c(depth, np.float32), _c(alpha, np.float32), _c(pairs, np.float32)
+    out = np.zeros(20)
+    lib().or_refine_pnp(_p(pr, C.c_double), _p(pi, C.c_double), _p(camvec(cam), C.c_double), _p(d, C.c_float),
+                        _p(a, C.c_float), _p(p, C.c_float), p.shape[0], max_iters, huber_px, alpha_min, tol,
+                        _p(out, C.c_double))
+    return dict(pose=out[:16].reshape(4, 4), rms_px=out[16], cost=out[17], n_used=int(out[18]), iters=int(out[19]))
 
 
 def block_select(means, block_size, cx, cy, radius):

@@ -668,3 +668,213 @@ void or_render_views(const float *means, const float *scales, const float *quats
         free(recs);
     }
 }
+
+/* ========================================================================= */
+/* Pose refinement of Sec. III-C.2 (the PnP step; the matcher is an input):   */
+/* back-project render pixels with the view's depth D / A (bilinear at        */
+/* (u - 0.5, v - 0.5)), then minimise sum_i huber(|pi(W X_i) - q_i|) over the */
+/* world-to-camera pose W by reweighted Gauss-Newton: the update (rho, phi)   */
+/* acts on the left, P' = Exp(phi) P + rho for camera points P = R X + t.    */
+/* ========================================================================= */
+static double or_bilinear(const float *img, int W, double sx, double sy)
+{
+    const int x0 = (int)floor(sx), y0 = (int)floor(sy);
+    const double ax = sx - x0, ay = sy - y0;
+    const double a = img[(int64_t)y0 * W + x0], b = img[(int64_t)y0 * W + x0 + 1];
+    const double c = img[(int64_t)(y0 + 1) * W + x0], d = img[(int64_t)(y0 + 1) * W + x0 + 1];
+    return (1.0 - ay) * ((1.0 - ax) * a + ax * b) + ay * ((1.0 - ax) * c + ax * d);
+}
+
+/* Rodrigues: Exp(phi) = I + sin(th)/th K + (1 - cos(th))/th^2 K^2. */
+static void or_so3_exp(const double phi[3], double E[9])
+{
+    const double th = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+    double K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            K2[3 * i + j] = 0;
+            for (int m = 0; m < 3; ++m) K2[3 * i + j] += K[3 * i + m] * K[3 * m + j];
+        }
+    double s1, s2;
+    if (th < 1e-8) { s1 = 1.0 - th * th / 6.0; s2 = 0.5 - th * th / 24.0; }
+    else { s1 = sin(th) / th; s2 = (1.0 - cos(th)) / (th * th); }
+    for (int i = 0; i < 9; ++i) E[i] = (i % 4 == 0 ? 1.0 : 0.0) + s1 * K[i] + s2 * K2[i];
+}
+
+/* pose (4x4 row-major) updated by s * delta on the left. */
+void or_pnp_apply(const double *pose, const double *delta, double s, double *out)
+{
+    const double phi[3] = {s * delta[3], s * delta[4], s * delta[5]};
+    double E[9];
+    or_so3_exp(phi, E);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double v = 0;
+            for (int m = 0; m < 3; ++m) v += E[3 * i + m] * pose[4 * m + j];
+            out[4 * i + j] = v;
+        }
+        out[4 * i + 3] += s * delta[i];
+    }
+    out[12] = out[13] = out[14] = 0; out[15] = 1;
+}
+
+/* residual (2) and its Jacobian (2 x 6, row-major) w.r.t. (rho, phi) at 0. */
+int or_pnp_residual(const double *pose, const double *X, const double *cam, const double *q, double *r, double *J)
+{
+    double P[3];
+    for (int i = 0; i < 3; ++i) P[i] = pose[4 * i] * X[0] + pose[4 * i + 1] * X[1] + pose[4 * i + 2] * X[2] + pose[4 * i + 3];
+    if (P[2] <= 1e-6) return 0;
+    const double fx = cam[C_FX], fy = cam[C_FY];
+    r[0] = fx * P[0] / P[2] + cam[C_CX] - q[0];
+    r[1] = fy * P[1] / P[2] + cam[C_CY] - q[1];
+    if (J) {
+        /* d pixel / d P */
+        const double Jp[6] = {fx / P[2], 0, -fx * P[0] / (P[2] * P[2]), 0, fy / P[2], -fy * P[1] / (P[2] * P[2])};
+        /* d P / d (rho, phi) = [I | -[P]x] */
+        const double M[18] = {1, 0, 0, 0, P[2], -P[1],
+                              0, 1, 0, -P[2], 0, P[0],
+                              0, 0, 1, P[1], -P[0], 0};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 6; ++b) {
+                J[6 * a + b] = 0;
+                for (int m = 0; m < 3; ++m) J[6 * a + b] += Jp[3 * a + m] * M[6 * m + b];
+            }
+    }
+    return 1;
+}
+
+static double or_huber(double e, double k) { return e <= k ? 0.5 * e * e : k * (e - 0.5 * k); }
+
+static double or_pnp_cost(const double *pose, const double *X, const uint8_t *use, const double *q, int64_t n,
+                          const double *cam, double k, double *sq, int64_t *cnt)
+{
+    double c = 0, s2 = 0; int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!use[i]) continue;
+        double r[2];
+        if (!or_pnp_residual(pose, X + 3 * i, cam, q + 2 * i, r, NULL)) continue;
+        const double e = sqrt(r[0] * r[0] + r[1] * r[1]);
+        c += or_huber(e, k); s2 += e * e; ++m;
+    }
+    if (sq) *sq = s2;
+    if (cnt) *cnt = m;
+    return c;
+}
+
+/* Solve A x = b for a symmetric positive definite 6 x 6 A (Gaussian
+ * elimination with partial pivoting; returns 0 if singular). */
+static int or_solve6(double A[36], double b[6], double x[6])
+{
+    for (int c = 0; c < 6; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 6; ++r) if (fabs(A[6 * r + c]) > fabs(A[6 * p + c])) p = r;
+        if (fabs(A[6 * p + c]) < 1e-300) return 0;
+        if (p != c) {
+            for (int j = 0; j < 6; ++j) { double t = A[6 * c + j]; A[6 * c + j] = A[6 * p + j]; A[6 * p + j] = t; }
+            double t = b[c]; b[c] = b[p]; b[p] = t;
+        }
+        for (int r = c + 1; r < 6; ++r) {
+            const double f = A[6 * r + c] / A[6 * c + c];
+            for (int j = c; j < 6; ++j) A[6 * r + j] -= f * A[6 * c + j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 5; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < 6; ++j) s -= A[6 * r + j] * x[j];
+        x[r] = s / A[6 * r + r];
+    }
+    return 1;
+}
+
+/* World point of render pixel (u, v): use[i] = 0 when its 2 x 2 neighbourhood
+ * leaves the image or the alpha there is below alpha_min.  Returns the count used. */
+int64_t or_pnp_backproject(const double *pose_render, const double *cam, const float *depth, const float *alpha,
+                           const double *uv, int64_t n, double alpha_min, double *X, uint8_t *use)
+{
+    const int W = (int)cam[C_W], H = (int)cam[C_H];
+    int64_t n_used = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double u = uv[2 * i], v = uv[2 * i + 1];
+        const double sx = u - 0.5, sy = v - 0.5;
+        use[i] = 0;
+        X[3 * i] = X[3 * i + 1] = X[3 * i + 2] = 0;
+        if (!isfinite(sx) || !isfinite(sy)) continue;
+        if (floor(sx) < 0 || floor(sy) < 0 || floor(sx) + 1 >= W || floor(sy) + 1 >= H) continue;
+        const double A = or_bilinear(alpha, W, sx, sy);
+        if (A < alpha_min) continue;
+        const double z = or_bilinear(depth, W, sx, sy) / A;
+        const double Pc[3] = {z * (u - cam[C_CX]) / cam[C_FX], z * (v - cam[C_CY]) / cam[C_FY], z};
+        /* X = R^T (P - t) */
+        for (int k = 0; k < 3; ++k) {
+            double s = 0;
+            for (int m = 0; m < 3; ++m) s += pose_render[4 * m + k] * (Pc[m] - pose_render[4 * m + 3]);
+            X[3 * i + k] = s;
+        }
+        use[i] = 1; ++n_used;
+    }
+    return n_used;
+}
+
+/* out[20]: pose[16], rms, cost, n_used, iterations. */
+void or_refine_pnp(const double *pose_render, const double *pose_init, const double *cam, const float *depth,
+                   const float *alpha, const float *pairs, int64_t n, int max_iters, double huber,
+                   double alpha_min, double tol, double *out)
+{
+    double *X = (double *)calloc((size_t)(3 * n + 1), sizeof(double));
+    double *q = (double *)calloc((size_t)(2 * n + 1), sizeof(double));
+    double *uv = (double *)calloc((size_t)(2 * n + 1), sizeof(double));
+    uint8_t *use = (uint8_t *)calloc((size_t)(n + 1), 1);
+    for (int64_t i = 0; i < n; ++i) {
+        uv[2 * i] = pairs[4 * i]; uv[2 * i + 1] = pairs[4 * i + 1];
+        q[2 * i] = pairs[4 * i + 2]; q[2 * i + 1] = pairs[4 * i + 3];
+    }
+    int64_t n_used = or_pnp_backproject(pose_render, cam, depth, alpha, uv, n, alpha_min, X, use);
+    for (int64_t i = 0; i < n; ++i)
+        if (use[i] && !(isfinite(q[2 * i]) && isfinite(q[2 * i + 1]))) { use[i] = 0; --n_used; }
+    double pose[16], trial[16];
+    memcpy(pose, pose_init, sizeof pose);
+    int it = 0;
+    if (n_used >= 3) {
+        for (; it < max_iters; ++it) {
+            double Hm[36] = {0}, g[6] = {0};
+            const double c0 = or_pnp_cost(pose, X, use, q, n, cam, huber, NULL, NULL);
+            for (int64_t i = 0; i < n; ++i) {
+                if (!use[i]) continue;
+                double r[2], J[12];
+                if (!or_pnp_residual(pose, X + 3 * i, cam, q + 2 * i, r, J)) continue;
+                const double e = sqrt(r[0] * r[0] + r[1] * r[1]);
+                const double w = e <= huber ? 1.0 : huber / e;
+                for (int a = 0; a < 6; ++a) {
+                    g[a] += w * (J[a] * r[0] + J[6 + a] * r[1]);
+                    for (int b = 0; b < 6; ++b) Hm[6 * a + b] += w * (J[a] * J[b] + J[6 + a] * J[6 + b]);
+                }
+            }
+            const double tr = Hm[0] + Hm[7] + Hm[14] + Hm[21] + Hm[28] + Hm[35];
+            for (int a = 0; a < 6; ++a) { Hm[7 * a] += 1e-9 * tr / 6.0; g[a] = -g[a]; }
+            double delta[6];
+            if (!or_solve6(Hm, g, delta)) break;
+            double s = 1.0;
+            int ok = 0;
+            for (int bt = 0; bt <= 10; ++bt) {
+                or_pnp_apply(pose, delta, s, trial);
+                if (or_pnp_cost(trial, X, use, q, n, cam, huber, NULL, NULL) < c0) { ok = 1; break; }
+                s *= 0.5;
+            }
+            if (!ok) break;
+            memcpy(pose, trial, sizeof pose);
+            double dmax = 0;
+            for (int a = 0; a < 6; ++a) dmax = fmax(dmax, fabs(s * delta[a]));
+            if (dmax < tol) { ++it; break; }
+        }
+    }
+    double sq = 0; int64_t cnt = 0;
+    const double cost = or_pnp_cost(pose, X, use, q, n, cam, huber, &sq, &cnt);
+    memcpy(out, pose, sizeof pose);
+    out[16] = cnt ? sqrt(sq / (double)cnt) : 0.0;
+    out[17] = cost;
+    out[18] = (double)n_used;
+    out[19] = (double)it;
+    free(X); free(q); free(uv); free(use);
+}

@@ -121,6 +121,7 @@ struct reloc_ctx {
     // per-call results (all views / queries of the call)
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
     DevBuf hq, hrgb, hdepth;
+    DevBuf pnp_X, pnp_out;
     PinBuf pin;
     double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
     // batch options
@@ -232,7 +233,7 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
                       &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
                       &ctx->hdepth, &ctx->prop_in, &ctx->prop_seed, &ctx->prop_logits, &ctx->prop_idx,
-                      &ctx->prop_mrg, &ctx->prop_loss};
+                      &ctx->prop_mrg, &ctx->prop_loss, &ctx->pnp_X, &ctx->pnp_out};
     for (DevBuf *b : bufs) b->release();
     if (ctx->prop) proposal_destroy(ctx->prop);
     ctx->pin.release();
@@ -1606,5 +1607,55 @@ extern "C" reloc_status reloc_measure_peaks(int device, double *fp32_scalar_tflo
     if (device < 0 || device >= ndev) return fail(RELOC_ECUDA, "device %d not present (%d devices)", device, ndev);
     CK(cudaSetDevice(device));
     CK(measure_peaks(fp32_scalar_tflops, fp32_packed_tflops, ex2_gops));
+    return RELOC_OK;
+}
+
+// ========================================== PnP refinement (Sec. III-C.2) ==
+extern "C" void reloc_default_pnp_options(reloc_pnp_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof *opt);
+    opt->max_iters = 30;
+    opt->huber_px = 2.0;
+    opt->alpha_min = 0.5;
+    opt->tol = 1e-12;
+}
+
+extern "C" reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_render, const double *pose_init,
+                                         const reloc_camera *cam, const float *depth_dev, const float *alpha_dev,
+                                         const float *pairs_dev, int n_pairs, const reloc_pnp_options *opt,
+                                         reloc_pnp_result *out, void *stream)
+{
+    if (!ctx || !pose_render || !pose_init || !cam || !depth_dev || !alpha_dev || !pairs_dev || !out)
+        return fail(RELOC_EINVAL, "NULL argument");
+    if (n_pairs < 1) return fail(RELOC_EINVAL, "n_pairs %d < 1", n_pairs);
+    if (cam->width < 2 || cam->height < 2 || cam->width > 16383 || cam->height > 16383)
+        return fail(RELOC_EINVAL, "image size %dx%d out of range", cam->width, cam->height);
+    if (!(cam->fx > 0) || !(cam->fy > 0) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return fail(RELOC_ENUMERIC, "invalid intrinsics");
+    reloc_pnp_options o;
+    if (opt) o = *opt; else reloc_default_pnp_options(&o);
+    if (o.max_iters < 0 || o.max_iters > 1000 || !(o.huber_px > 0) || !(o.tol >= 0) || !std::isfinite(o.alpha_min))
+        return fail(RELOC_EINVAL, "bad PnP options");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(pose_render[k]) || !std::isfinite(pose_init[k]))
+            return fail(RELOC_ENUMERIC, "non-finite pose");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CKS(ctx->pnp_X.ensure(32 * (size_t)n_pairs));
+    CKS(ctx->pnp_out.ensure(sizeof(double) * 20));
+    CK(launch_refine_pnp(pose_render, pose_init, cam->fx, cam->fy, cam->cx, cam->cy, cam->width, cam->height,
+                         depth_dev, alpha_dev, pairs_dev, n_pairs, o.max_iters, o.huber_px, o.alpha_min, o.tol,
+                         ctx->pnp_X.as<double>(), ctx->pnp_out.as<double>(), st));
+    double h[20];
+    CK(cudaMemcpyAsync(h, ctx->pnp_out.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memset(out, 0, sizeof *out);
+    memcpy(out->pose, h, sizeof(double) * 16);
+    out->rms_px = h[16];
+    out->cost = h[17];
+    out->n_used = (int32_t)h[18];
+    out->iters = (int32_t)h[19];
+    if (out->n_used < 3) return fail(RELOC_ENUMERIC, "%d usable pairs (3 needed)", out->n_used);
     return RELOC_OK;
 }

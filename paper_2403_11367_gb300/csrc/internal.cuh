@@ -141,6 +141,13 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 // Allow K4 its largest shared-memory footprint (once per device, before any capture).
 cudaError_t configure_tile_kernels();
 
+// Pose refinement by PnP on one view's depth (pnp.cu): out_dev[20] = pose[16],
+// rms, cost, n_used, iterations; X_scratch: 4 doubles per pair.
+cudaError_t launch_refine_pnp(const double *pose_render, const double *pose_init, double fx, double fy, double cx,
+                              double cy, int width, int height, const float *depth, const float *alpha,
+                              const float *pairs, int n, int max_iters, double huber, double alpha_min, double tol,
+                              double *X_scratch, double *out_dev, cudaStream_t st);
+
 // FP32 (scalar and packed) FMA and ex2 throughput of the current device (peaks.cu).
 cudaError_t measure_peaks(double *fp32_scalar_tflops, double *fp32_packed_tflops, double *ex2_gops);
 

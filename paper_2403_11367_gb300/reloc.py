@@ -80,6 +80,16 @@ class Search(C.Structure):
                 ("seed", C.c_uint64), ("order", C.c_void_p), ("reserved", C.c_int32 * 4)]
 
 
+class PnpOptions(C.Structure):
+    _fields_ = [("max_iters", C.c_int32), ("reserved0", C.c_int32), ("huber_px", C.c_double),
+                ("alpha_min", C.c_double), ("tol", C.c_double), ("reserved", C.c_int32 * 4)]
+
+
+class PnpResult(C.Structure):
+    _fields_ = [("pose", C.c_double * 16), ("rms_px", C.c_double), ("cost", C.c_double), ("n_used", C.c_int32),
+                ("iters", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
 class Counts(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_gauss", C.c_int64), ("n_visible", C.c_int64),
                 ("n_instances", C.c_int64), ("inst_stride", C.c_int64), ("retries", C.c_int32),
@@ -129,6 +139,9 @@ SIGNATURES = {
     "reloc_export_debug": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64p, _vp, _vp]),
     "reloc_ncc_images_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
     "reloc_measure_peaks": (C.c_int, [C.c_int, _dp, _dp, _dp]),
+    "reloc_default_pnp_options": (None, [C.POINTER(PnpOptions)]),
+    "reloc_refine_pnp": (C.c_int, [_vp, _dp, _dp, C.POINTER(Camera), _vp, _vp, _vp, C.c_int, C.POINTER(PnpOptions),
+                                   C.POINTER(PnpResult), _vp]),
 }
 NOALLOC_MAX_VIEWS = 512
 PROPOSAL_H, PROPOSAL_W, PROPOSAL_CLASSES, PROPOSAL_PARAMS = 47, 176, 64, 1916960
@@ -310,6 +323,22 @@ class Context:
                                          sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
                                          _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
         return res, sc
+
+    def refine_pnp(self, pose_render, cam, depth, alpha, pairs, pose_init=None, stream=None, **opts):
+        """PnP refinement (include/reloc.h): depth/alpha [H,W] and pairs [n,4]
+        (u_r, v_r, u_q, v_q) are CUDA float32 tensors.  Returns PnpResult."""
+        o = PnpOptions()
+        lib.reloc_default_pnp_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        pr = np.ascontiguousarray(pose_render, np.float64).reshape(16)
+        pi = pr if pose_init is None else np.ascontiguousarray(pose_init, np.float64).reshape(16)
+        c = camera(cam)
+        res = PnpResult()
+        _check(lib.reloc_refine_pnp(self._h, pr.ctypes.data_as(_dp), pi.ctypes.data_as(_dp), C.byref(c),
+                                    _ptr(depth), _ptr(alpha), _ptr(pairs), int(pairs.shape[0]), C.byref(o),
+                                    C.byref(res), _stream(stream)))
+        return res
 
     def localize_batch(self, queries, cam, best_rgb=None, best_depth=None, stream=None, want_scores=True):
         """queries: list of (query tensor [3,H,W] on the device, coarse_pose 4x4, radius, grid tuple).
