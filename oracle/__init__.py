@@ -75,6 +75,7 @@ def lib():
                                         C.c_double, dp]
             L.or_pnp_backproject.argtypes = [dp, dp, fp, fp, dp, C.c_int64, C.c_double, dp, u8p]
             L.or_pnp_backproject.restype = C.c_int64
+            L.or_ncc_pose_grad.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, dp, dp, dp]
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
             L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
             L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
@@ -282,6 +283,22 @@ def random_search(g, cell_poses, cam, query, order, batch, ncc_stop, prm=None):
             stopped = visited < len(order)
             break
     return dict(best_index=best, best_score=best_sc, n_scored=visited, stopped_early=stopped, scores=scores)
+
+
+def ncc_pose_grad(g, pose, cam, query, prm=None):
+    """NCC of the view at ``pose`` against ``query`` and its gradient with
+    respect to the left pose update (rho, phi), by forward-mode
+    differentiation in FP64 (SH degree 0 maps).  Returns (ncc, grad[6])."""
+    if g.sh_degree != 0:
+        raise ValueError("pose gradients need view-independent colour (SH degree 0)")
+    prm = params() if prm is None else prm
+    m, s, q, o, sh = _gauss_ptrs(g)
+    out = np.zeros(7)
+    lib().or_ncc_pose_grad(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
+                           _p(sh, C.c_float), g.n, _p(_c(pose, np.float64).reshape(16), C.c_double),
+                           _p(camvec(cam), C.c_double), _p(_c(prm, np.float64), C.c_double),
+                           _p(_c(query, np.float64).reshape(-1), C.c_double), _p(out, C.c_double))
+    return out[0], out[1:]
 
 
 def pnp_apply(pose, delta, s=1.0):

@@ -878,3 +878,176 @@ void or_refine_pnp(const double *pose_render, const double *pose_init, const dou
     out[19] = (double)it;
     free(X); free(q); free(uv); free(use);
 }
+
+/* ========================================================================= */
+/* NCC pose gradient (the paper's future direction: direct pose descent on   */
+/* NCC), by forward-mode differentiation: every quantity of the projection,   */
+/* compositing and NCC above is carried as a value plus its six derivatives  */
+/* with respect to the pose update delta = (rho, phi), W(delta) =             */
+/* [Exp(phi) R | Exp(phi) t + rho], at delta = 0.  Inclusion, alpha-skip,     */
+/* clamp and stop decisions are taken on the values (the derivative of the    */
+/* function with those decisions fixed).  Colour must be view-independent     */
+/* (SH degree 0).                                                             */
+/* ========================================================================= */
+typedef struct { double v, d[6]; } dual;
+
+static dual dk(double v) { dual r; r.v = v; for (int k = 0; k < 6; ++k) r.d[k] = 0; return r; }
+static dual dadd(dual a, dual b) { for (int k = 0; k < 6; ++k) a.d[k] += b.d[k]; a.v += b.v; return a; }
+static dual dsub(dual a, dual b) { for (int k = 0; k < 6; ++k) a.d[k] -= b.d[k]; a.v -= b.v; return a; }
+static dual dmul(dual a, dual b)
+{
+    dual r; r.v = a.v * b.v;
+    for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+static dual ddiv(dual a, dual b)
+{
+    dual r; r.v = a.v / b.v;
+    for (int k = 0; k < 6; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dual dscale(dual a, double s) { a.v *= s; for (int k = 0; k < 6; ++k) a.d[k] *= s; return a; }
+static dual dexp(dual a) { dual r; r.v = exp(a.v); for (int k = 0; k < 6; ++k) r.d[k] = r.v * a.d[k]; return r; }
+static dual dsqrt(dual a) { dual r; r.v = sqrt(a.v); for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] / (2 * r.v); return r; }
+
+typedef struct { dual u, v, A, B, C; double z, o, col[3], rx, ry; int vis; } drec;
+
+/* Project one Gaussian (SH degree 0) as in project_one, in duals. */
+static void dproject(const float *mu, const float *scale, const float *quat, float opac, const float *rgb,
+                     const double *W, const double *cam, const double *p, drec *out)
+{
+    out->vis = 0;
+    double Rw[9] = {W[0], W[1], W[2], W[4], W[5], W[6], W[8], W[9], W[10]};
+    double tv[3];
+    for (int i = 0; i < 3; ++i) tv[i] = Rw[3 * i] * mu[0] + Rw[3 * i + 1] * mu[1] + Rw[3 * i + 2] * mu[2] + W[4 * i + 3];
+    if (!(tv[2] > p[P_NEAR])) return;
+    /* t(delta) = Exp(phi) t + rho: d t / d rho_k = e_k, d t / d phi_k = e_k x t */
+    dual t[3];
+    for (int i = 0; i < 3; ++i) t[i] = dk(tv[i]);
+    for (int k = 0; k < 3; ++k) t[k].d[k] = 1.0;
+    t[1].d[3] = -tv[2]; t[2].d[3] = tv[1];        /* e_0 x t = (0, -t2, t1) */
+    t[0].d[4] = tv[2];  t[2].d[4] = -tv[0];       /* e_1 x t = (t2, 0, -t0) */
+    t[0].d[5] = -tv[1]; t[1].d[5] = tv[0];        /* e_2 x t = (-t1, t0, 0) */
+    /* R(delta) = Exp(phi) R: d R / d phi_k = [e_k]x R */
+    dual R[9];
+    for (int i = 0; i < 9; ++i) R[i] = dk(Rw[i]);
+    for (int k = 0; k < 3; ++k) {
+        double E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};       /* [e_k]x */
+        if (k == 0) { E[5] = -1; E[7] = 1; }
+        if (k == 1) { E[2] = 1; E[6] = -1; }
+        if (k == 2) { E[1] = -1; E[3] = 1; }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                R[3 * i + j].d[3 + k] = E[3 * i] * Rw[j] + E[3 * i + 1] * Rw[3 + j] + E[3 * i + 2] * Rw[6 + j];
+    }
+    double q[4] = {quat[0], quat[1], quat[2], quat[3]}, Rq[9], M[9], S3[9];
+    or_quat_to_rot(q, Rq);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * (double)scale[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S3[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+    const double fx = cam[C_FX], fy = cam[C_FY];
+    const double limx = p[P_FOV_CLAMP] * (0.5 * cam[C_W]) / fx, limy = p[P_FOV_CLAMP] * (0.5 * cam[C_H]) / fy;
+    dual xz = ddiv(t[0], t[2]), yz = ddiv(t[1], t[2]);
+    if (xz.v < -limx) xz = dk(-limx); if (xz.v > limx) xz = dk(limx);
+    if (yz.v < -limy) yz = dk(-limy); if (yz.v > limy) yz = dk(limy);
+    dual J[6] = {ddiv(dk(fx), t[2]), dk(0), dscale(ddiv(xz, t[2]), -fx),
+                 dk(0), ddiv(dk(fy), t[2]), dscale(ddiv(yz, t[2]), -fy)};
+    dual T[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = dadd(dadd(dmul(J[3 * i], R[j]), dmul(J[3 * i + 1], R[3 + j])), dmul(J[3 * i + 2], R[6 + j]));
+    dual TS[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            TS[3 * i + j] = dadd(dadd(dscale(T[3 * i], S3[j]), dscale(T[3 * i + 1], S3[3 + j])),
+                                 dscale(T[3 * i + 2], S3[6 + j]));
+    dual c00 = dadd(dadd(dmul(TS[0], T[0]), dmul(TS[1], T[1])), dmul(TS[2], T[2]));
+    dual c01 = dadd(dadd(dmul(TS[0], T[3]), dmul(TS[1], T[4])), dmul(TS[2], T[5]));
+    dual c11 = dadd(dadd(dmul(TS[3], T[3]), dmul(TS[4], T[4])), dmul(TS[5], T[5]));
+    dual a = dadd(c00, dk(p[P_EPS2D])), b = c01, c = dadd(c11, dk(p[P_EPS2D]));
+    dual det = dsub(dmul(a, c), dmul(b, b));
+    if (!(det.v > 0)) return;
+    out->A = ddiv(c, det); out->B = dscale(ddiv(b, det), -1.0); out->C = ddiv(a, det);
+    out->u = dadd(dscale(ddiv(t[0], t[2]), fx), dk(cam[C_CX]));
+    out->v = dadd(dscale(ddiv(t[1], t[2]), fy), dk(cam[C_CY]));
+    out->rx = p[P_CUT] * sqrt(a.v); out->ry = p[P_CUT] * sqrt(c.v);
+    const double W_ = cam[C_W], H_ = cam[C_H];
+    if (out->u.v + out->rx < 0 || out->u.v - out->rx >= W_ || out->v.v + out->ry < 0 || out->v.v - out->ry >= H_) return;
+    out->z = tv[2]; out->o = opac;
+    out->col[0] = rgb[0]; out->col[1] = rgb[1]; out->col[2] = rgb[2];
+    out->vis = 1;
+}
+
+typedef struct { dual T, c[3]; int done; } dpix;
+
+/* out[7]: NCC and its six derivatives (rho_x, rho_y, rho_z, phi_x, phi_y, phi_z). */
+void or_ncc_pose_grad(const float *means, const float *scales, const float *quats, const float *opac,
+                      const float *rgb, int64_t n, const double *W, const double *cam, const double *p,
+                      const double *query, double *out)
+{
+    const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
+    const int64_t npx = (int64_t)Wd * Hd;
+    drec *r = (drec *)malloc(sizeof(drec) * (n + 1));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    double *zkey = (double *)malloc(sizeof(double) * (n + 1));
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        dproject(means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], rgb + 3 * i, W, cam, p, &r[i]);
+        zkey[i] = r[i].vis ? r[i].z : 0;
+        if (r[i].vis) order[nv++] = i;
+    }
+    msort_by_double(order, tmp, nv, zkey);
+    dpix *px = (dpix *)malloc(sizeof(dpix) * npx);
+    for (int64_t k = 0; k < npx; ++k) { px[k].T = dk(1.0); px[k].c[0] = px[k].c[1] = px[k].c[2] = dk(0); px[k].done = 0; }
+    const double lim = -0.5 * p[P_CUT] * p[P_CUT];
+    for (int64_t j = 0; j < nv; ++j) {
+        const drec *g = &r[order[j]];
+        int x0 = (int)floor(g->u.v - g->rx - 1), x1 = (int)ceil(g->u.v + g->rx);
+        int y0 = (int)floor(g->v.v - g->ry - 1), y1 = (int)ceil(g->v.v + g->ry);
+        if (x0 < 0) x0 = 0; if (y0 < 0) y0 = 0;
+        if (x1 > Wd - 1) x1 = Wd - 1; if (y1 > Hd - 1) y1 = Hd - 1;
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) {
+                dpix *s = &px[(int64_t)y * Wd + x];
+                if (s->done) continue;
+                dual dx = dsub(dk(x + 0.5), g->u), dy = dsub(dk(y + 0.5), g->v);
+                dual pw = dsub(dscale(dadd(dmul(g->A, dmul(dx, dx)), dmul(g->C, dmul(dy, dy))), -0.5),
+                               dmul(g->B, dmul(dx, dy)));
+                if (pw.v < lim) continue;
+                dual raw = dscale(dexp(pw), g->o);
+                dual al = raw.v < p[P_ALPHA_MAX] ? raw : dk(p[P_ALPHA_MAX]);
+                if (al.v < p[P_ALPHA_MIN]) continue;
+                dual tn = dmul(s->T, dsub(dk(1.0), al));
+                if (tn.v < p[P_T_MIN]) { s->done = 1; continue; }
+                dual w = dmul(al, s->T);
+                for (int ch = 0; ch < 3; ++ch) s->c[ch] = dadd(s->c[ch], dscale(w, g->col[ch]));
+                s->T = tn;
+            }
+    }
+    /* NCC over all 3 H W samples, two-pass, in duals (query constant) */
+    const int64_t ns = 3 * npx;
+    dual mr = dk(0); double mq = 0;
+    for (int ch = 0; ch < 3; ++ch)
+        for (int64_t k = 0; k < npx; ++k) { mr = dadd(mr, px[k].c[ch]); mq += query[ch * npx + k]; }
+    mr = dscale(mr, 1.0 / ns); mq /= ns;
+    dual sab = dk(0), saa = dk(0); double sbb = 0;
+    for (int ch = 0; ch < 3; ++ch)
+        for (int64_t k = 0; k < npx; ++k) {
+            dual da = dsub(px[k].c[ch], mr);
+            const double db = query[ch * npx + k] - mq;
+            sab = dadd(sab, dscale(da, db));
+            saa = dadd(saa, dmul(da, da));
+            sbb += db * db;
+        }
+    out[0] = 0;
+    for (int k = 0; k < 6; ++k) out[1 + k] = 0;
+    if (saa.v > 1e-12 * ns && sbb > 1e-12 * ns) {
+        dual ncc = ddiv(sab, dscale(dsqrt(saa), sqrt(sbb)));
+        out[0] = ncc.v;
+        for (int k = 0; k < 6; ++k) out[1 + k] = ncc.d[k];
+    }
+    free(r); free(order); free(tmp); free(zkey); free(px);
+}
