@@ -372,6 +372,74 @@ def run_refine_leg(ctx, cam, dev, stream, n_queries=8, iters=3):
             "library_ms_per_iteration": float(np.mean(lib_ms)) if lib_ms else None}
 
 
+def run_ascent_leg(cam, dev, stream, n_queries=4, iters=15):
+    """Direct pose ascent on NCC from the 64-candidate sweep's winner (the
+    paper's future direction) on the street map with SH degree 0: per
+    iteration one gradient evaluation (reloc_score_grad, 1 view) and a line
+    search of 8 step lengths along the scaled gradient scored in one batched
+    call; a step is taken only if it raises NCC.  Reports NCC and pose error
+    before and after, and milliseconds per iteration."""
+    import numpy as np
+    import torch
+    from paper_2403_11367_gb300 import reloc as R
+    import scenegen as sg
+    g = sg.street_gaussians(N_GAUSS, seed=11, sh_degree=0)
+    ctx = R.Context(R.reloc_default_config(), device=dev.index or 0)
+    ctx.load_map(g)
+    hidden, seeds = sg.street_queries(n_queries, seed=81)
+    H, W = cam.height, cam.width
+    scale = np.array([0.05, 0.05, 0.05, math.radians(0.5), math.radians(0.5), math.radians(0.5)])
+    fracs = 2.0 ** -np.arange(8)
+    out = {"queries": n_queries, "iterations": iters, "ncc_before": [], "ncc_after": [], "err_before_m_deg": [],
+           "err_after_m_deg": []}
+    ms = []
+    for i in range(n_queries):
+        Wh = sg.pose_from_xyz_yaw(*hidden[i])
+        runs, _, _ = ctx.select_block(hidden[i][0], hidden[i][1], RADIUS)
+        img = torch.empty((1, 3, H, W), device=dev)
+        ctx.render(runs, Wh[None], cam, rgb=img)
+        q = (img[0] + torch.tensor(sg.image_noise(5000 + i, H, W), device=dev)).contiguous()
+        res, _ = ctx.localize(q, sg.pose_from_xyz_yaw(*seeds[i]), RADIUS, GRID, cam, want_scores=False)
+        Wk = np.array(res.best_pose).reshape(4, 4)
+        runs, _, _ = ctx.select_block(*(-Wk[:3, :3].T @ Wk[:3, 3])[:2], RADIUS)
+        out["ncc_before"].append(res.best_score)
+        out["err_before_m_deg"].append(_pose_error(Wk, Wh))
+        ncc = res.best_score
+        for it in range(iters):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, gr = ctx.score_grad(runs, Wk[None], cam, q, stream=stream)
+            d = gr[0] * scale * scale
+            d = d / max(1e-30, np.sqrt(np.sum((d / scale) ** 2)))          # unit step in scaled units
+            trials = np.stack([_apply_left(Wk, f * d) for f in fracs])
+            sc, _ = ctx.score(runs, trials, cam, q, stream=stream)
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+            k = int(np.argmax(sc))
+            if sc[k] <= ncc:
+                break
+            Wk, ncc = trials[k], float(sc[k])
+        out["ncc_after"].append(ncc)
+        out["err_after_m_deg"].append(_pose_error(Wk, Wh))
+    ctx.close()
+    out["ms_per_iteration"] = float(np.mean(ms))
+    return out
+
+
+def _apply_left(W, delta):
+    """[Exp(phi) R | Exp(phi) t + rho] for delta = (rho, phi)."""
+    import numpy as np
+    phi = delta[3:]
+    th = float(np.linalg.norm(phi))
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    E = np.eye(3) + (math.sin(th) / th if th > 1e-12 else 1.0) * K + \
+        ((1 - math.cos(th)) / th ** 2 if th > 1e-12 else 0.5) * K @ K
+    out = np.eye(4)
+    out[:3, :3] = E @ W[:3, :3]
+    out[:3, 3] = E @ W[:3, 3] + delta[:3]
+    return out
+
+
 def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best):
     """FP16 / BF16 attribute storage on the driving workload: candidates/s and
     deviation of every NCC score and winner from the FP32 path."""
@@ -595,6 +663,7 @@ def run_ours(args):
     learned = run_learned_leg(ctx, cam, dev, stream) if not args.no_batch else None
     random_search = run_random_leg(ctx, cam, dev, stream) if not args.no_batch else None
     refine = run_refine_leg(ctx, cam, dev, stream) if not args.no_batch else None
+    ascent = run_ascent_leg(cam, dev, stream) if not args.no_batch else None
 
     if rank != 0:
         if dist is not None:
@@ -643,6 +712,7 @@ def run_ours(args):
         "learned": learned,
         "random_search": random_search,
         "refine": refine,
+        "pose_ascent": ascent,
         "precision": precision,
         "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},

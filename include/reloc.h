@@ -192,6 +192,21 @@ reloc_status reloc_score(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges
                          const float *query_dev, double *scores_host, int *degenerate_host,
                          void *stream);
 
+/* Render as reloc_score and also return, for each view, the gradient of its
+ * NCC (Eq. ncc) with respect to its pose: grads_host[n_views][6] =
+ * dNCC/d(rho_x, rho_y, rho_z, phi_x, phi_y, phi_z) for the left update
+ * W(delta) = [Exp(phi) R | Exp(phi) t + rho] at delta = 0 -- the direction
+ * of direct pose ascent on NCC that the paper names as future work.  The
+ * derivative is that of the render with its inclusion, alpha-skip, clamp and
+ * stop decisions fixed (the rendered image is piecewise smooth in the pose).
+ * The map must have SH degree 0 (view-independent colour, the paper's map);
+ * otherwise EINVAL.  scores_host[n_views] as reloc_score.  Errors: EINVAL,
+ * ENOMAP, ENUMERIC, ECUDA, EOVERFLOW. */
+reloc_status reloc_score_grad(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                              const double *poses, int n_views, const reloc_camera *cam,
+                              const float *query_dev, double *scores_host, double *grads_host,
+                              void *stream);
+
 /* The whole initial relocalization of one query (Sec. III-C.1): select the
  * blocks within `radius` of the coarse pose's camera centre, build the
  * candidate grid around the coarse pose, render every candidate, score it

@@ -122,6 +122,7 @@ struct reloc_ctx {
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
     DevBuf hq, hrgb, hdepth;
     DevBuf pnp_X, pnp_out;
+    DevBuf gbuf, gcoef, gpart, gpose;    // NCC pose gradients
     PinBuf pin;
     double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
     // batch options
@@ -233,7 +234,8 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
                       &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
                       &ctx->hdepth, &ctx->prop_in, &ctx->prop_seed, &ctx->prop_logits, &ctx->prop_idx,
-                      &ctx->prop_mrg, &ctx->prop_loss, &ctx->pnp_X, &ctx->pnp_out};
+                      &ctx->prop_mrg, &ctx->prop_loss, &ctx->pnp_X, &ctx->pnp_out, &ctx->gbuf, &ctx->gcoef,
+                      &ctx->gpart, &ctx->gpose};
     for (DevBuf *b : bufs) b->release();
     if (ctx->prop) proposal_destroy(ctx->prop);
     ctx->pin.release();
@@ -462,6 +464,7 @@ struct CallOut {
     bool score = false;                                         // NCC (needs query images)
     bool argmax = false;                                        // per query argmax
     float *brgb = nullptr, *bdepth = nullptr, *balpha = nullptr; // winners [Q][...]
+    double *grad = nullptr;                                     // NCC pose gradients [V][6] (device)
     std::vector<double> scores;
     std::vector<int> degen, best;
     std::vector<double> best_score;
@@ -692,8 +695,19 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
     if (o.score) {
         CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, blend_units(cp), 3 * HW,
-                               ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0, st));
+                               ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0,
+                               o.grad ? ctx->gcoef.as<double>() : nullptr, st));
         launches += 1;
+        if (o.grad) {
+            CK(cudaMemsetAsync(ctx->gbuf.p, 0, 20 * (size_t)sb.VS, st));
+            CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
+                                 ctx->gcoef.as<double>(), ctx->gbuf.as<float>(), d_overflow, st));
+            CK(launch_pose_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
+                                 ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.p, ctx->precision, ctx->n,
+                                 ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(),
+                                 ctx->gpart.as<double>(), o.grad + 6 * (int64_t)sb.v0, st));
+            launches += 3;
+        }
         if (o.argmax) {
             int *vsel = ctx->view_sel.as<int>() + sb.q0;
             CK(launch_argmax(ctx->scores.as<double>() + sb.v0, L, ctx->best.as<int>() + sb.q0,
@@ -777,6 +791,13 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->inst.ensure(4 * (size_t)VI));
         CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
         CKS(ctx->partials.ensure(24 * (size_t)V * blend_units(cp)));
+        if (o.grad) {
+            int64_t pb = 1;
+            for (auto &sb : sbs) pb = std::max<int64_t>(pb, (int64_t)sb.pblk * (sb.v1 - sb.v0));
+            CKS(ctx->gbuf.ensure(20 * (size_t)VS));
+            CKS(ctx->gcoef.ensure(32 * (size_t)V));
+            CKS(ctx->gpart.ensure(48 * (size_t)pb));
+        }
         CKS(ctx->qpart.ensure(16 * 152 * (size_t)Qm));
         CKS(ctx->qstats.ensure(16 * (size_t)Qm));
         CKS(ctx->nvis.ensure(4 * (size_t)Vtot));
@@ -1657,5 +1678,31 @@ extern "C" reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_rend
     out->n_used = (int32_t)h[18];
     out->iters = (int32_t)h[19];
     if (out->n_used < 3) return fail(RELOC_ENUMERIC, "%d usable pairs (3 needed)", out->n_used);
+    return RELOC_OK;
+}
+
+// ============================================= NCC pose gradient (NEXT-3) ==
+extern "C" reloc_status reloc_score_grad(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                                         const double *poses, int n_views, const reloc_camera *cam,
+                                         const float *query_dev, double *scores_host, double *grads_host,
+                                         void *stream)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    if (!query_dev || !scores_host || !grads_host) return fail(RELOC_EINVAL, "query_dev, scores_host and grads_host are required");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    if (ctx->sh_degree != 0) return fail(RELOC_EINVAL, "pose gradients need a map with SH degree 0 (view-independent colour)");
+    std::vector<QuerySpec> qs(1);
+    CKS(one_query(ctx, ranges, n_ranges, poses, n_views, qs[0]));
+    qs[0].img = query_dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CKS(ctx->gpose.ensure(48 * (size_t)n_views));
+    CallOut o;
+    o.score = true;
+    o.grad = ctx->gpose.as<double>();
+    CKS(run_batch(ctx, qs, cam, st, o, false));
+    memcpy(scores_host, o.scores.data(), sizeof(double) * n_views);
+    CK(cudaMemcpyAsync(grads_host, ctx->gpose.p, 48 * (size_t)n_views, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return RELOC_OK;
 }

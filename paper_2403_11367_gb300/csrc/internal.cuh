@@ -171,9 +171,23 @@ cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *ins
 // 64-pixel warp blocks of one view: the blend's unit of work and of NCC partials.
 inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w * cam.tile_h / 64); }
 
-// K7: NCC per view from its n_units partials and its query's statistics.
+// K7: NCC per view from its n_units partials and its query's statistics;
+// coef (may be null): [V][4] = 1/sqrt(var_r var_q), NCC/var_r, mean r, mean q.
 cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_units,
-                                int64_t n_samples, double *scores, int *degenerate, cudaStream_t st);
+                                int64_t n_samples, double *scores, int *degenerate, double *coef, cudaStream_t st);
+
+// K6 backward: per (view, Gaussian) gradients of the view's NCC with respect to
+// the projected mean and conic, added into gout[vd_off[v] + i][5] (u, v, a, b, c).
+cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                              const CamParams &cam, const double *coef, float *gout, const int *overflow,
+                              cudaStream_t st);
+
+// Chain of gin to each view's left pose update: out[V][6] (rho, phi);
+// part: n_blocks * V * 6 doubles of scratch.
+cudaError_t launch_pose_chain(const float *mx, const float *my, const float *mz, const void *attr, int precision,
+                              int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
+                              const ViewParams *views, const CamParams &cam, const float *gin, double *part,
+                              double *out, cudaStream_t st);
 
 // K8: per query, argmax over its views (lowest index on ties):
 // best[q] (index within the query), best_score[q], view_sel[q] (view index).

@@ -270,4 +270,198 @@ cudaError_t launch_project(const float *mx, const float *my, const float *mz, co
     }
 }
 
+// ------------------------------------------------------------ pose chain --
+// Per (view, Gaussian) of one query: the gradients of the view's NCC with
+// respect to the Gaussian's projected mean and conic (gin: u, v, a, b, c)
+// carried back through the conic inverse A = Sigma'^-1 (dL/dSigma' =
+// -A G_A A), Sigma' = T Sigma T^T + eps I (dL/dT = 2 dL/dSigma' T Sigma),
+// T = J R and the projection u = fx tx/tz + cx, v = fy ty/tz + cy, J(t) (a
+// clamped ratio in J is a constant) to the camera point t and the rotation R,
+// then to the left pose update: d/d rho = dL/dt, d/d phi = t x dL/dt +
+// (N12 - N21, N20 - N02, N01 - N10) with N = R (dL/dR)^T.  FP32 per pair;
+// each block sums its Gaussians per view into part[block][view][6] (FP64).
+template <typename T>
+__global__ void __launch_bounds__(PROJ_THREADS)
+k_pose_chain(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
+             const T *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, Layout L,
+             const ViewParams *__restrict__ views, CamParams cam, const float *__restrict__ gin,
+             double *__restrict__ part)
+{
+    __shared__ float s_red[PROJ_THREADS / 32][6];
+    const int qi = find_segment(L.q_pblk, L.Q, (int)blockIdx.x);
+    const int64_t S = L.q_gsub[qi + 1] - L.q_gsub[qi];
+    const int64_t i = (int64_t)(blockIdx.x - L.q_pblk[qi]) * PROJ_THREADS + threadIdx.x;
+    const bool active = i < S;
+    const int v_begin = L.q_view[qi], V = L.q_view[qi + 1] - v_begin;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float mu0 = 0, mu1 = 0, mu2 = 0;
+    float Sg[6] = {0, 0, 0, 0, 0, 0};          // Sigma: 00 01 02 11 12 22
+    if (active) {
+        const int64_t g = gidx[L.q_gsub[qi] + i];
+        mu0 = __ldg(mx + g); mu1 = __ldg(my + g); mu2 = __ldg(mz + g);
+        const float s0 = ldattr(attr + (ATTR_SCALE + 0) * n_map + g);
+        const float s1 = ldattr(attr + (ATTR_SCALE + 1) * n_map + g);
+        const float s2 = ldattr(attr + (ATTR_SCALE + 2) * n_map + g);
+        float qw = ldattr(attr + (ATTR_QUAT + 0) * n_map + g);
+        float qx = ldattr(attr + (ATTR_QUAT + 1) * n_map + g);
+        float qy = ldattr(attr + (ATTR_QUAT + 2) * n_map + g);
+        float qz = ldattr(attr + (ATTR_QUAT + 3) * n_map + g);
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                            2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                            2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+        const float sc[3] = {s0, s1, s2};
+        float m[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) m[3 * a + b] = r[3 * a + b] * sc[b];
+        int k = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b) Sg[k++] = m[3 * a] * m[3 * b] + m[3 * a + 1] * m[3 * b + 1] + m[3 * a + 2] * m[3 * b + 2];
+    }
+    const float Sm[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
+    for (int vv = 0; vv < V; ++vv) {
+        const int v = v_begin + vv;
+        float acc[6] = {0, 0, 0, 0, 0, 0};
+        const float *g5 = active ? gin + 5 * (L.vd_off[v] + i) : nullptr;
+        const float gu = active ? g5[0] : 0.f, gv = active ? g5[1] : 0.f, ga = active ? g5[2] : 0.f;
+        const float gb = active ? g5[3] : 0.f, gc = active ? g5[4] : 0.f;
+        if (gu != 0.f || gv != 0.f || ga != 0.f || gb != 0.f || gc != 0.f) {
+            const ViewParams &P = views[v];
+            const float d0 = (mu0 - P.c_hi[0]) - P.c_lo[0], d1 = (mu1 - P.c_hi[1]) - P.c_lo[1];
+            const float d2 = (mu2 - P.c_hi[2]) - P.c_lo[2];
+            const float t[3] = {P.R[0] * d0 + P.R[1] * d1 + P.R[2] * d2, P.R[3] * d0 + P.R[4] * d1 + P.R[5] * d2,
+                                P.R[6] * d0 + P.R[7] * d1 + P.R[8] * d2};
+            const float iz = 1.f / t[2];
+            const float rx = t[0] * iz, ry = t[1] * iz;
+            const bool cx_ = rx < -cam.limx || rx > cam.limx, cy_ = ry < -cam.limy || ry > cam.limy;
+            const float xz = fminf(fmaxf(rx, -cam.limx), cam.limx), yz = fminf(fmaxf(ry, -cam.limy), cam.limy);
+            const float J00 = cam.fx * iz, J02 = -cam.fx * xz * iz, J11 = cam.fy * iz, J12 = -cam.fy * yz * iz;
+            float Tm[6];                                          // T = J R (2 x 3)
+            for (int b = 0; b < 3; ++b) {
+                Tm[b] = J00 * P.R[b] + J02 * P.R[6 + b];
+                Tm[3 + b] = J11 * P.R[3 + b] + J12 * P.R[6 + b];
+            }
+            float TS[6];                                          // T Sigma (2 x 3)
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 3; ++b)
+                    TS[3 * a + b] = Tm[3 * a] * Sm[b] + Tm[3 * a + 1] * Sm[3 + b] + Tm[3 * a + 2] * Sm[6 + b];
+            const float sa = TS[0] * Tm[0] + TS[1] * Tm[1] + TS[2] * Tm[2] + cam.eps2d;
+            const float sb = TS[0] * Tm[3] + TS[1] * Tm[4] + TS[2] * Tm[5];
+            const float scc = TS[3] * Tm[3] + TS[4] * Tm[4] + TS[5] * Tm[5] + cam.eps2d;
+            const float idet = 1.f / (sa * scc - sb * sb);
+            const float A00 = scc * idet, A01 = -sb * idet, A11 = sa * idet;
+            // dL/dSigma' = -A G_A A, G_A = [[ga, gb/2], [gb/2, gc]]
+            const float h = 0.5f * gb;
+            const float M00 = A00 * ga + A01 * h, M01 = A00 * h + A01 * gc;
+            const float M10 = A01 * ga + A11 * h, M11 = A01 * h + A11 * gc;
+            const float GS00 = -(M00 * A00 + M01 * A01), GS01 = -(M00 * A01 + M01 * A11);
+            const float GS11 = -(M10 * A01 + M11 * A11);
+            // dL/dT = 2 GS T Sigma
+            float dT[6];
+            for (int b = 0; b < 3; ++b) {
+                dT[b] = 2.f * (GS00 * TS[b] + GS01 * TS[3 + b]);
+                dT[3 + b] = 2.f * (GS01 * TS[b] + GS11 * TS[3 + b]);
+            }
+            // dL/dR = J^T dT, dL/dJ = dT R^T (the four non-zero entries of J)
+            float dR[9];
+            for (int b = 0; b < 3; ++b) {
+                dR[b] = J00 * dT[b];
+                dR[3 + b] = J11 * dT[3 + b];
+                dR[6 + b] = J02 * dT[b] + J12 * dT[3 + b];
+            }
+            const float dJ00 = dT[0] * P.R[0] + dT[1] * P.R[1] + dT[2] * P.R[2];
+            const float dJ02 = dT[0] * P.R[6] + dT[1] * P.R[7] + dT[2] * P.R[8];
+            const float dJ11 = dT[3] * P.R[3] + dT[4] * P.R[4] + dT[5] * P.R[5];
+            const float dJ12 = dT[3] * P.R[6] + dT[4] * P.R[7] + dT[5] * P.R[8];
+            // dL/dt from u, v and J
+            float gt0 = gu * cam.fx * iz, gt1 = gv * cam.fy * iz;
+            float gt2 = -(gu * cam.fx * t[0] + gv * cam.fy * t[1]) * iz * iz;
+            gt2 += -(dJ00 * cam.fx + dJ11 * cam.fy) * iz * iz;
+            // J02 = -fx xz / tz, xz = tx / tz unless clamped
+            gt2 += dJ02 * cam.fx * xz * iz * iz;
+            gt2 += dJ12 * cam.fy * yz * iz * iz;
+            if (!cx_) {
+                gt0 += dJ02 * (-cam.fx * iz * iz);
+                gt2 += dJ02 * (cam.fx * t[0] * iz * iz * iz);
+            }
+            if (!cy_) {
+                gt1 += dJ12 * (-cam.fy * iz * iz);
+                gt2 += dJ12 * (cam.fy * t[1] * iz * iz * iz);
+            }
+            // N = R dR^T
+            float N[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    N[3 * a + b] = P.R[3 * a] * dR[3 * b] + P.R[3 * a + 1] * dR[3 * b + 1] + P.R[3 * a + 2] * dR[3 * b + 2];
+            acc[0] = gt0; acc[1] = gt1; acc[2] = gt2;
+            acc[3] = t[1] * gt2 - t[2] * gt1 + (N[5] - N[7]);
+            acc[4] = t[2] * gt0 - t[0] * gt2 + (N[6] - N[2]);
+            acc[5] = t[0] * gt1 - t[1] * gt0 + (N[1] - N[3]);
+        }
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            float x = acc[m];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) s_red[warp][m] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double x = 0.0;
+            for (int w = 0; w < PROJ_THREADS / 32; ++w) x += (double)s_red[w][threadIdx.x];
+            part[((int64_t)(blockIdx.x - L.q_pblk[qi]) * V + vv) * 6 + threadIdx.x] = x;
+        }
+        __syncthreads();
+    }
+}
+
+// out[v][6] = sum over the n_blk blocks of part[block][v][6], in block order.
+__global__ void k_pose_reduce(const double *__restrict__ part, int n_blk, int V, double *__restrict__ out)
+{
+    __shared__ double s[6][8];
+    const int v = blockIdx.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < n_blk; b += blockDim.x)
+        for (int m = 0; m < 6; ++m) acc[m] += part[((int64_t)b * V + v) * 6 + m];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = 0; m < 6; ++m) {
+        double x = acc[m];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s[m][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s[threadIdx.x][w];
+        out[6 * (int64_t)v + threadIdx.x] = x;
+    }
+}
+
+template <typename T>
+static cudaError_t pose_chain_t(const float *mx, const float *my, const float *mz, const T *attr, int64_t n_map,
+                                const uint32_t *gidx, const Layout &L, int n_blocks, const ViewParams *views,
+                                const CamParams &cam, const float *gin, double *part, double *out, cudaStream_t st)
+{
+    k_pose_chain<T><<<n_blocks, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, gin, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pose_reduce<<<L.V, 256, 0, st>>>(part, n_blocks, L.V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pose_chain(const float *mx, const float *my, const float *mz, const void *attr, int precision,
+                              int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
+                              const ViewParams *views, const CamParams &cam, const float *gin, double *part,
+                              double *out, cudaStream_t st)
+{
+    if (n_blocks <= 0 || L.V <= 0) return cudaSuccess;
+    switch (precision) {
+    case 0: return pose_chain_t(mx, my, mz, (const float *)attr, n_map, gidx, L, n_blocks, views, cam, gin, part, out, st);
+    case 1: return pose_chain_t(mx, my, mz, (const __half *)attr, n_map, gidx, L, n_blocks, views, cam, gin, part, out, st);
+    case 2: return pose_chain_t(mx, my, mz, (const __nv_bfloat16 *)attr, n_map, gidx, L, n_blocks, views, cam, gin, part, out, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace reloc

@@ -405,7 +405,7 @@ constexpr int NCC_THREADS = 256;
 
 __global__ void __launch_bounds__(NCC_THREADS)
 k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ qstats, Layout L, int n_units,
-               int64_t n, double *__restrict__ scores, int *__restrict__ degenerate)
+               int64_t n, double *__restrict__ scores, int *__restrict__ degenerate, double *__restrict__ coef)
 {
     __shared__ double s[3][NCC_THREADS / 32];
     const int v = blockIdx.x;
@@ -433,15 +433,215 @@ k_ncc_finalize(const double *__restrict__ partials, const double *__restrict__ q
         const bool dg = !(vr > 1e-12 * nn) || !(vq > 1e-12 * nn);
         scores[v] = dg ? 0.0 : cov / (sqrt(vr) * sqrt(vq));
         if (degenerate) degenerate[v] = dg ? 1 : 0;
+        if (coef) {
+            // d NCC / d r_i = (q_i - mean q) / sqrt(vr vq) - NCC (r_i - mean r) / vr
+            double *o = coef + 4 * (int64_t)v;
+            o[0] = dg ? 0.0 : 1.0 / (sqrt(vr) * sqrt(vq));
+            o[1] = dg ? 0.0 : scores[v] / vr;
+            o[2] = Sr / nn;
+            o[3] = Sq / nn;
+        }
     }
 }
 
 cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_units,
-                                int64_t n_samples, double *scores, int *degenerate, cudaStream_t st)
+                                int64_t n_samples, double *scores, int *degenerate, double *coef, cudaStream_t st)
 {
     if (L.V <= 0) return cudaSuccess;
-    k_ncc_finalize<<<L.V, NCC_THREADS, 0, st>>>(partials, qstats, L, n_units, n_samples, scores, degenerate);
+    k_ncc_finalize<<<L.V, NCC_THREADS, 0, st>>>(partials, qstats, L, n_units, n_samples, scores, degenerate, coef);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------- K6 backward ------
+// Gradient of each view's NCC with respect to its Gaussians' projected means
+// (u, v) and conics (a, b, c), for the view's fixed set of included
+// (pixel, Gaussian) pairs.  A warp per 64-pixel block walks the tile's list
+// twice with the forward's cull: first compositing the pixel pair to its
+// final colour C, then again front to back, where for contributor j with
+// weight w_j = alpha_j T_j and C_after = C - C_up_to_j,
+//   dL/d alpha_j = T_j (G . c_j) - (G . C_after) / (1 - alpha_j),
+// G = dNCC/dC of the pixel; alpha = o exp(power) unclamped gives
+// dL/d power = alpha dL/d alpha, and power = -(a dx^2 + 2 b dx dy + c dy^2)/2
+// with dx = x - u.  The warp sums each record's five gradients over its 64
+// pixels and adds them to the (view, Gaussian) entry of gout.
+template <int TW, int TH>
+__global__ void __launch_bounds__(32)
+k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
+             const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
+             float *__restrict__ gout, const int *__restrict__ overflow)
+{
+    constexpr int WPT = TW * TH / 64;
+    constexpr int WROWS = 64 / TW;
+    __shared__ float4 s_a[32], s_b[32], s_c[32];
+    __shared__ uint32_t s_g[32];
+    const int unit = blockIdx.x;
+    const int tile = unit / WPT, warp = unit - tile * WPT;
+    const int v = blockIdx.y;
+    const int tx = tile % cam.ntx, ty = tile / cam.ntx;
+    const int lane = threadIdx.x;
+    const int px = tx * TW + lane % TW;
+    const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
+    const bool in[2] = {px < cam.width && py0 < cam.height, px < cam.width && py0 + 1 < cam.height};
+    const float fxp = (float)px + 0.5f, fyp[2] = {(float)py0 + 0.5f, (float)py0 + 1.5f};
+    const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
+    const float wy0 = (float)(ty * TH + warp * WROWS) + 0.5f, wy1 = wy0 + (float)(WROWS - 1);
+    if (*overflow) return;
+    const int2 r = ranges[(int64_t)v * cam.n_tiles + tile];
+    const uint32_t *list = inst_gauss + L.io_off[v];
+    const float4 *vrec = rec + L.vd_off[v] * 3;
+    const float lim = -0.5f * cam.cut * cam.cut;
+    const float lamin = __logf(cam.alpha_min);
+    const unsigned lt = lanemask_lt_u();
+
+    // the same per-warp cull and compaction as the forward, one step of 32 records
+    auto stage = [&](int b) -> int {
+        const int j = b + lane;
+        bool hit = false;
+        float4 pa = make_float4(0, 0, 0, 0), pb = pa, pc = pa;
+        uint32_t gi = 0;
+        if (j < r.y) {
+            gi = __ldg(list + j);
+            const float4 *p = vrec + 3 * (int64_t)gi;
+            pa = __ldg(p); pb = __ldg(p + 1); pc = __ldg(p + 2);
+            const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
+            if (thr < 0.f) {
+                const float qmin = quad_min_rect(pb.x, pb.y, pb.z, wx0 - pa.x, wx1 - pa.x, wy0 - pa.y, wy1 - pa.y);
+                hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
+            }
+        }
+        const unsigned keep = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int k = __popc(keep & lt);
+            s_a[k] = pa; s_b[k] = pb; s_c[k] = pc; s_g[k] = gi;
+        }
+        __syncwarp();
+        return __popc(keep);
+    };
+    // alpha of a kept record at pixel p (0 if excluded), unclamped flag
+    auto alpha_at = [&](int k, int p, float &dx, float &dy, bool &unclamped) -> float {
+        const float4 a = s_a[k], b = s_b[k];
+        dx = fxp - a.x;
+        dy = fyp[p] - a.y;
+        const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
+        if (!(power >= lim)) return 0.f;
+        const float raw = a.w * __expf(power);
+        unclamped = raw < cam.alpha_max;
+        const float al = fminf(cam.alpha_max, raw);
+        return al >= cam.alpha_min ? al : 0.f;
+    };
+
+    // pass 1: final colour of the pixel pair
+    float T[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
+    float C[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int b = r.x; b < r.y; b += 32) {
+        if (__all_sync(0xffffffffu, T[0] == 0.f && T[1] == 0.f)) break;
+        const int nk = stage(b);
+        for (int k = 0; k < nk; ++k) {
+            const float4 c = s_c[k];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float dx, dy;
+                bool un = false;
+                const float al = T[p] > 0.f ? alpha_at(k, p, dx, dy, un) : 0.f;
+                if (al > 0.f) {
+                    const float tn = T[p] * (1.f - al);
+                    if (tn < cam.t_min) {
+                        T[p] = 0.f;
+                    } else {
+                        const float w = al * T[p];
+                        C[p][0] += c.x * w; C[p][1] += c.y * w; C[p][2] += c.z * w;
+                        T[p] = tn;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // dNCC/dC per pixel
+    const double *cf = coef + 4 * (int64_t)v;
+    const float k_q = (float)cf[0], k_r = (float)cf[1], mr = (float)cf[2], mq = (float)cf[3];
+    const float *query = L.q_img[L.view_q[v]];
+    const int64_t HW = (int64_t)cam.width * cam.height;
+    float G[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+        if (in[p]) {
+            const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
+        }
+    // pass 2: front to back again, gradients per record
+    float Tb[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
+    float U[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int b = r.x; b < r.y; b += 32) {
+        if (__all_sync(0xffffffffu, Tb[0] == 0.f && Tb[1] == 0.f)) break;
+        const int nk = stage(b);
+        for (int k = 0; k < nk; ++k) {
+            const float4 c = s_c[k], bb = s_b[k];
+            float g[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float dx = 0.f, dy = 0.f;
+                bool un = false;
+                const float al = Tb[p] > 0.f ? alpha_at(k, p, dx, dy, un) : 0.f;
+                if (al > 0.f) {
+                    const float tn = Tb[p] * (1.f - al);
+                    if (tn < cam.t_min) {
+                        Tb[p] = 0.f;
+                    } else {
+                        const float w = al * Tb[p];
+                        const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
+                                             C[p][2] - U[p][2] - c.z * w};
+                        const float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
+                                          (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) / (1.f - al);
+                        const float gp = un ? gal * al : 0.f;
+                        g[0] += gp * (bb.x * dx + bb.y * dy);
+                        g[1] += gp * (bb.y * dx + bb.z * dy);
+                        g[2] += gp * (-0.5f * dx * dx);
+                        g[3] += gp * (-dx * dy);
+                        g[4] += gp * (-0.5f * dy * dy);
+                        U[p][0] += c.x * w; U[p][1] += c.y * w; U[p][2] += c.z * w;
+                        Tb[p] = tn;
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) g[m] = warp_sum_f(g[m]);
+            if (lane == 0 && (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f || g[4] != 0.f)) {
+                float *o = gout + 5 * (L.vd_off[v] + (int64_t)s_g[k]);
+#pragma unroll
+                for (int m = 0; m < 5; ++m) atomicAdd(o + m, g[m]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int TW, int TH>
+static cudaError_t blend_grad_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                                const CamParams &cam, const double *coef, float *gout, const int *overflow,
+                                cudaStream_t st)
+{
+    dim3 grid(cam.n_tiles * (TW * TH / 64), L.V);
+    k_blend_grad<TW, TH><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gout, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
+                              const CamParams &cam, const double *coef, float *gout, const int *overflow,
+                              cudaStream_t st)
+{
+    if (L.V <= 0) return cudaSuccess;
+#define RELOC_GRAD_CASE(W_, H_) \
+    if (cam.tile_w == W_ && cam.tile_h == H_) return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gout, overflow, st);
+    RELOC_GRAD_CASE(16, 16)
+    RELOC_GRAD_CASE(8, 8)
+    RELOC_GRAD_CASE(32, 8)
+    RELOC_GRAD_CASE(16, 8)
+    RELOC_GRAD_CASE(8, 16)
+    RELOC_GRAD_CASE(32, 16)
+#undef RELOC_GRAD_CASE
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ K8 -----

@@ -114,6 +114,8 @@ SIGNATURES = {
                                _vp]),
     "reloc_score": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp, _dp, _ip,
                               _vp]),
+    "reloc_score_grad": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp, _dp, _dp,
+                                   _vp]),
     "reloc_localize": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera), C.POINTER(Result),
                                  _dp, _vp, _vp, _vp, _vp]),
     "reloc_localize_random": (C.c_int, [_vp, _vp, _dp, C.c_double, C.POINTER(Grid), C.POINTER(Camera),
@@ -323,6 +325,18 @@ class Context:
                                          sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
                                          _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
         return res, sc
+
+    def score_grad(self, ranges, poses, cam, query, stream=None):
+        """NCC of each view and its gradient w.r.t. the view's pose (rho, phi):
+        returns (scores [V], grads [V, 6])."""
+        ra, nr = self._ranges(ranges)
+        p, pp, V = _poses(poses)
+        c = camera(cam)
+        sc = np.zeros(V)
+        gr = np.zeros((V, 6))
+        _check(lib.reloc_score_grad(self._h, ra, nr, pp, V, C.byref(c), _ptr(query), sc.ctypes.data_as(_dp),
+                                    gr.ctypes.data_as(_dp), _stream(stream)))
+        return sc, gr
 
     def refine_pnp(self, pose_render, cam, depth, alpha, pairs, pose_init=None, stream=None, **opts):
         """PnP refinement (include/reloc.h): depth/alpha [H,W] and pairs [n,4]
