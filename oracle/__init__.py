@@ -76,6 +76,7 @@ def lib():
             L.or_pnp_backproject.argtypes = [dp, dp, fp, fp, dp, C.c_int64, C.c_double, dp, u8p]
             L.or_pnp_backproject.restype = C.c_int64
             L.or_ncc_pose_grad.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, dp, dp, dp]
+            L.or_photo_loss_jvp.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, C.c_int, dp, dp, dp, dp]
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
             L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
             L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
@@ -298,6 +299,29 @@ def ncc_pose_grad(g, pose, cam, query, prm=None):
                            _p(sh, C.c_float), g.n, _p(_c(pose, np.float64).reshape(16), C.c_double),
                            _p(camvec(cam), C.c_double), _p(_c(prm, np.float64), C.c_double),
                            _p(_c(query, np.float64).reshape(-1), C.c_double), _p(out, C.c_double))
+    return out[0], out[1:]
+
+
+PARAM_ORDER = ["mean_x", "mean_y", "mean_z", "scale_x", "scale_y", "scale_z", "quat_w", "quat_x", "quat_y",
+               "quat_z", "opacity", "red", "green", "blue"]
+
+
+def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None):
+    """Map-training loss (Sec. III-B.3, L1 part of L_rgb: mean |render - gt|
+    over all samples of all views) and its derivatives along six directions
+    dirs [n, 14, 6] in the Gaussians' parameters (PARAM_ORDER), forward mode
+    in FP64 (SH degree 0).  Returns (loss, jvp[6])."""
+    if g.sh_degree != 0:
+        raise ValueError("map training needs SH degree 0")
+    prm = params() if prm is None else prm
+    m, s, q, o, sh = _gauss_ptrs(g)
+    poses = _c(poses, np.float64).reshape(-1, 16)
+    out = np.zeros(7)
+    lib().or_photo_loss_jvp(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
+                            _p(sh, C.c_float), g.n, _p(_c(dirs, np.float64), C.c_double),
+                            _p(poses, C.c_double), poses.shape[0], _p(camvec(cam), C.c_double),
+                            _p(_c(prm, np.float64), C.c_double), _p(_c(gt, np.float64), C.c_double),
+                            _p(out, C.c_double))
     return out[0], out[1:]
 
 

@@ -1051,3 +1051,158 @@ void or_ncc_pose_grad(const float *means, const float *scales, const float *quat
     }
     free(r); free(order); free(tmp); free(zkey); free(px);
 }
+
+/* ========================================================================= */
+/* Map training loss (Sec. III-B.3): L_photo = L_rgb(R(G), I) with           */
+/* L_rgb(I1, I2) = (1 - lambda) L1(I1, I2) + lambda L_D-SSIM(I1, I2), here   */
+/* with its L1 part, the mean absolute difference over all 3 H W samples of   */
+/* every view.  Directional derivatives of the loss along six directions in  */
+/* the space of all Gaussian parameters -- mean (3), scale (3), quaternion    */
+/* (4), opacity (1), RGB (3): 14 per Gaussian, SH degree 0 -- by forward-mode */
+/* duals through the same projection and compositing as above.               */
+/* dirs: [n][14][6] tangents.  out: [7] = loss and its six derivatives.       */
+/* ========================================================================= */
+enum { NPAR = 14 };
+typedef struct { dual u, v, A, B, C, o, col[3]; double z, rx, ry; int vis; } dprec;
+
+static void dproject_params(const float *mu, const float *scale, const float *quat, float opac, const float *rgb,
+                            const double *dir, const double *W, const double *cam, const double *p, dprec *out)
+{
+    out->vis = 0;
+    dual m[3], sc[3], q[4];
+    for (int i = 0; i < 3; ++i) { m[i] = dk(mu[i]); sc[i] = dk(scale[i]); }
+    for (int i = 0; i < 4; ++i) q[i] = dk(quat[i]);
+    dual o = dk(opac), col[3];
+    for (int i = 0; i < 3; ++i) col[i] = dk(rgb[i]);
+    for (int k = 0; k < 6; ++k) {
+        for (int i = 0; i < 3; ++i) { m[i].d[k] = dir[6 * i + k]; sc[i].d[k] = dir[6 * (3 + i) + k]; }
+        for (int i = 0; i < 4; ++i) q[i].d[k] = dir[6 * (6 + i) + k];
+        o.d[k] = dir[6 * 10 + k];
+        for (int i = 0; i < 3; ++i) col[i].d[k] = dir[6 * (11 + i) + k];
+    }
+    dual t[3];
+    for (int i = 0; i < 3; ++i)
+        t[i] = dadd(dadd(dadd(dscale(m[0], W[4 * i]), dscale(m[1], W[4 * i + 1])), dscale(m[2], W[4 * i + 2])),
+                    dk(W[4 * i + 3]));
+    if (!(t[2].v > p[P_NEAR])) return;
+    /* rotation of the normalised quaternion, Sigma = (R S)(R S)^T */
+    dual nq = dsqrt(dadd(dadd(dmul(q[0], q[0]), dmul(q[1], q[1])), dadd(dmul(q[2], q[2]), dmul(q[3], q[3]))));
+    dual w = ddiv(q[0], nq), x = ddiv(q[1], nq), y = ddiv(q[2], nq), z = ddiv(q[3], nq);
+    dual one = dk(1.0);
+    dual R[9] = {dsub(one, dscale(dadd(dmul(y, y), dmul(z, z)), 2)), dscale(dsub(dmul(x, y), dmul(w, z)), 2),
+                 dscale(dadd(dmul(x, z), dmul(w, y)), 2),
+                 dscale(dadd(dmul(x, y), dmul(w, z)), 2), dsub(one, dscale(dadd(dmul(x, x), dmul(z, z)), 2)),
+                 dscale(dsub(dmul(y, z), dmul(w, x)), 2),
+                 dscale(dsub(dmul(x, z), dmul(w, y)), 2), dscale(dadd(dmul(y, z), dmul(w, x)), 2),
+                 dsub(one, dscale(dadd(dmul(x, x), dmul(y, y)), 2))};
+    dual M[9], S3[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = dmul(R[3 * i + j], sc[j]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S3[3 * i + j] = dadd(dadd(dmul(M[3 * i], M[3 * j]), dmul(M[3 * i + 1], M[3 * j + 1])),
+                                 dmul(M[3 * i + 2], M[3 * j + 2]));
+    const double fx = cam[C_FX], fy = cam[C_FY];
+    const double limx = p[P_FOV_CLAMP] * (0.5 * cam[C_W]) / fx, limy = p[P_FOV_CLAMP] * (0.5 * cam[C_H]) / fy;
+    dual xz = ddiv(t[0], t[2]), yz = ddiv(t[1], t[2]);
+    if (xz.v < -limx) xz = dk(-limx); if (xz.v > limx) xz = dk(limx);
+    if (yz.v < -limy) yz = dk(-limy); if (yz.v > limy) yz = dk(limy);
+    dual J[6] = {ddiv(dk(fx), t[2]), dk(0), dscale(ddiv(xz, t[2]), -fx),
+                 dk(0), ddiv(dk(fy), t[2]), dscale(ddiv(yz, t[2]), -fy)};
+    const double Rw[9] = {W[0], W[1], W[2], W[4], W[5], W[6], W[8], W[9], W[10]};
+    dual T[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = dadd(dadd(dscale(J[3 * i], Rw[j]), dscale(J[3 * i + 1], Rw[3 + j])),
+                                dscale(J[3 * i + 2], Rw[6 + j]));
+    dual TS[6];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            TS[3 * i + j] = dadd(dadd(dmul(T[3 * i], S3[j]), dmul(T[3 * i + 1], S3[3 + j])),
+                                 dmul(T[3 * i + 2], S3[6 + j]));
+    dual c00 = dadd(dadd(dmul(TS[0], T[0]), dmul(TS[1], T[1])), dmul(TS[2], T[2]));
+    dual c01 = dadd(dadd(dmul(TS[0], T[3]), dmul(TS[1], T[4])), dmul(TS[2], T[5]));
+    dual c11 = dadd(dadd(dmul(TS[3], T[3]), dmul(TS[4], T[4])), dmul(TS[5], T[5]));
+    dual a = dadd(c00, dk(p[P_EPS2D])), b = c01, c = dadd(c11, dk(p[P_EPS2D]));
+    dual det = dsub(dmul(a, c), dmul(b, b));
+    if (!(det.v > 0)) return;
+    out->A = ddiv(c, det); out->B = dscale(ddiv(b, det), -1.0); out->C = ddiv(a, det);
+    out->u = dadd(dscale(ddiv(t[0], t[2]), fx), dk(cam[C_CX]));
+    out->v = dadd(dscale(ddiv(t[1], t[2]), fy), dk(cam[C_CY]));
+    out->rx = p[P_CUT] * sqrt(a.v); out->ry = p[P_CUT] * sqrt(c.v);
+    if (out->u.v + out->rx < 0 || out->u.v - out->rx >= cam[C_W] || out->v.v + out->ry < 0 || out->v.v - out->ry >= cam[C_H])
+        return;
+    out->z = t[2].v; out->o = o;
+    for (int i = 0; i < 3; ++i) out->col[i] = col[i];
+    out->vis = 1;
+}
+
+/* Composite one view in duals: img[3][H][W] duals (caller-allocated). */
+static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const double *p, dual *img)
+{
+    const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
+    const int64_t npx = (int64_t)Wd * Hd;
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    double *zkey = (double *)malloc(sizeof(double) * (n + 1));
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        zkey[i] = r[i].vis ? r[i].z : 0;
+        if (r[i].vis) order[nv++] = i;
+    }
+    msort_by_double(order, tmp, nv, zkey);
+    dual *T = (dual *)malloc(sizeof(dual) * npx);
+    uint8_t *done = (uint8_t *)calloc(npx, 1);
+    for (int64_t k = 0; k < npx; ++k) { T[k] = dk(1.0); img[k] = img[npx + k] = img[2 * npx + k] = dk(0); }
+    const double lim = -0.5 * p[P_CUT] * p[P_CUT];
+    for (int64_t j = 0; j < nv; ++j) {
+        const dprec *g = &r[order[j]];
+        int x0 = (int)floor(g->u.v - g->rx - 1), x1 = (int)ceil(g->u.v + g->rx);
+        int y0 = (int)floor(g->v.v - g->ry - 1), y1 = (int)ceil(g->v.v + g->ry);
+        if (x0 < 0) x0 = 0; if (y0 < 0) y0 = 0;
+        if (x1 > Wd - 1) x1 = Wd - 1; if (y1 > Hd - 1) y1 = Hd - 1;
+        for (int y = y0; y <= y1; ++y)
+            for (int xx = x0; xx <= x1; ++xx) {
+                const int64_t k = (int64_t)y * Wd + xx;
+                if (done[k]) continue;
+                dual dx = dsub(dk(xx + 0.5), g->u), dy = dsub(dk(y + 0.5), g->v);
+                dual pw = dsub(dscale(dadd(dmul(g->A, dmul(dx, dx)), dmul(g->C, dmul(dy, dy))), -0.5),
+                               dmul(g->B, dmul(dx, dy)));
+                if (pw.v < lim) continue;
+                dual raw = dmul(dexp(pw), g->o);
+                dual al = raw.v < p[P_ALPHA_MAX] ? raw : dk(p[P_ALPHA_MAX]);
+                if (al.v < p[P_ALPHA_MIN]) continue;
+                dual tn = dmul(T[k], dsub(dk(1.0), al));
+                if (tn.v < p[P_T_MIN]) { done[k] = 1; continue; }
+                dual wgt = dmul(al, T[k]);
+                for (int ch = 0; ch < 3; ++ch) img[ch * npx + k] = dadd(img[ch * npx + k], dmul(wgt, g->col[ch]));
+                T[k] = tn;
+            }
+    }
+    free(order); free(tmp); free(zkey); free(T); free(done);
+}
+
+void or_photo_loss_jvp(const float *means, const float *scales, const float *quats, const float *opac,
+                       const float *rgb, int64_t n, const double *dirs, const double *poses, int n_views,
+                       const double *cam, const double *p, const double *gt, double *out)
+{
+    const int64_t npx = (int64_t)cam[C_W] * (int64_t)cam[C_H];
+    dprec *r = (dprec *)malloc(sizeof(dprec) * (n + 1));
+    dual *img = (dual *)malloc(sizeof(dual) * 3 * npx);
+    dual loss = dk(0);
+    const double inv = 1.0 / ((double)n_views * 3.0 * (double)npx);
+    for (int v = 0; v < n_views; ++v) {
+        for (int64_t i = 0; i < n; ++i)
+            dproject_params(means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], rgb + 3 * i,
+                            dirs + (int64_t)NPAR * 6 * i, poses + 16 * v, cam, p, &r[i]);
+        dcomposite_view(r, n, cam, p, img);
+        const double *I = gt + (int64_t)v * 3 * npx;
+        for (int64_t k = 0; k < 3 * npx; ++k) {
+            dual d = dsub(img[k], dk(I[k]));
+            loss = dadd(loss, dscale(d, (d.v >= 0 ? 1.0 : -1.0) * inv));
+        }
+    }
+    out[0] = loss.v;
+    for (int k = 0; k < 6; ++k) out[1 + k] = loss.d[k];
+    free(r); free(img);
+}
