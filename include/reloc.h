@@ -323,6 +323,72 @@ reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_render, const d
                               const float *pairs_dev, int n_pairs, const reloc_pnp_options *opt,
                               reloc_pnp_result *out, void *stream);
 
+/* ---- map training (Sec. III-B.3) ------------------------------------------
+ * The loss of Eq. 6, L = w_photo L_photo + w_reproj L_reproj, with L_photo =
+ * L_rgb(R(G, W_t), I_t) (Eq. 4) averaged over the training views and L_rgb =
+ * (1 - lambda) L1 + lambda D-SSIM (Eq. 3); L1 is the mean absolute difference
+ * over the 3 H W samples of a view.  The paper gives no values for lambda,
+ * w_photo and w_reproj; the defaults are 3D Gaussian Splatting's lambda = 0.2
+ * and w_photo = w_reproj = 1.  The derivative is that of the render with its
+ * inclusion, alpha-skip, clamp and stop decisions fixed, and the right
+ * derivative of |x| at 0.  Only lambda = 0 and w_reproj = 0 are accepted
+ * (EINVAL otherwise) until the D-SSIM and reprojection terms are added.
+ * Adam (Kingma and Ba 2015) updates 3D Gaussian Splatting's latent
+ * parameters: mean, log scale, quaternion (as stored; normalised on use),
+ * logit opacity, colour, each group with its own learning rate; the scale
+ * and opacity stored in the map are the activated values. */
+typedef struct reloc_train_options {
+    double lambda_dssim;       /* lambda of Eq. 3: 0.2                                */
+    double w_photo, w_reproj;  /* omega_1, omega_2 of Eq. 6: 1, 1                     */
+    double lr_mean;            /* metres per step: 1.6e-4                             */
+    double lr_scale;           /* log-scale per step: 5e-3                            */
+    double lr_quat;            /* 1e-3                                                */
+    double lr_opacity;         /* logit per step: 5e-2                                */
+    double lr_color;           /* 2.5e-3                                              */
+    double beta1, beta2, eps;  /* Adam: 0.9, 0.999, 1e-15                             */
+    int32_t views_per_group;   /* views rendered per group (one gathered copy of the
+                                  subset each; bounds the workspace): 16              */
+    int32_t reserved[7];
+} reloc_train_options;
+
+void reloc_default_train_options(reloc_train_options *opt);
+
+/* The loss over n_views training views at poses[n_views][16] (world-to-camera,
+ * row-major, host) of the Gaussians in `ranges` (the block-ordered map;
+ * reloc_select_block or [0, n)), against targets_dev[n_views][3][H][W]
+ * (device, FP32, channel-planar), written to *loss_host, and its gradient
+ * with respect to every Gaussian's parameters written to grad_dev[14][n]
+ * (device, FP32, zeroed by the call first; rows: mean x, y, z, scale x, y,
+ * z, quaternion w, x, y, z, opacity, red, green, blue; columns in block
+ * order; Gaussians outside `ranges` get 0).  The map must have SH degree 0
+ * and FP32 attributes.  Per-Gaussian sums are FP32 atomics (their order
+ * varies from call to call).  Synchronous on `stream`.  Errors: EINVAL,
+ * ENOMAP, ENUMERIC, ECUDA, EOVERFLOW. */
+reloc_status reloc_train_grad(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                              const double *poses, int n_views, const reloc_camera *cam,
+                              const float *targets_dev, const reloc_train_options *opt,
+                              double *loss_host, float *grad_dev, void *stream);
+
+/* One training step: the loss and gradient as reloc_train_grad (into a
+ * context-owned buffer), then one Adam step on the device map.  *loss_host is
+ * the loss before the step.  The Adam moments and step count live in the
+ * context; reloc_load_map and reloc_train_reset start them afresh.  The map's
+ * block partition is not rebuilt: reload the map read back with
+ * reloc_read_map to re-partition moved Gaussians.  opt NULL: defaults.
+ * Synchronous on `stream`.  Errors: as reloc_train_grad. */
+reloc_status reloc_train_step(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                              const double *poses, int n_views, const reloc_camera *cam,
+                              const float *targets_dev, const reloc_train_options *opt,
+                              double *loss_host, void *stream);
+reloc_status reloc_train_reset(reloc_ctx *ctx);
+
+/* Copy the device map back to host arrays in block order (reloc_map_order
+ * gives each row's original index), in the layout of reloc_gaussians_host:
+ * mean[n][3], scale[n][3], quat[n][4], opacity[n], sh[n][K][3]; any pointer
+ * may be NULL.  FP32 maps only.  Errors: EINVAL, ENOMAP, ECUDA. */
+reloc_status reloc_read_map(reloc_ctx *ctx, float *mean, float *scale, float *quat, float *opacity,
+                            float *sh);
+
 /* One query of a batch (Sec. III-C.1 applied to many queries at once). */
 typedef struct reloc_query {
     const float *query_dev;    /* [3][H][W] device image of the query (caller-owned)   */

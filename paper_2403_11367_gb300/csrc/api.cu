@@ -123,6 +123,9 @@ struct reloc_ctx {
     DevBuf hq, hrgb, hdepth;
     DevBuf pnp_X, pnp_out;
     DevBuf gbuf, gcoef, gpart, gpose;    // NCC pose gradients
+    // map training: render and dL/dC scratch, loss, parameter gradients, Adam moments
+    DevBuf trgb, tgimg, tloss, tgrad, adam_m, adam_v;
+    int64_t adam_t = 0;
     PinBuf pin;
     double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
     // batch options
@@ -313,6 +316,7 @@ extern "C" reloc_status reloc_load_map(reloc_ctx *ctx, const reloc_gaussians_hos
     ctx->n = n;
     ctx->sh_degree = sh_degree;
     ctx->precision = precision;
+    ctx->adam_t = 0;
     return RELOC_OK;
 }
 
@@ -465,6 +469,9 @@ struct CallOut {
     bool argmax = false;                                        // per query argmax
     float *brgb = nullptr, *bdepth = nullptr, *balpha = nullptr; // winners [Q][...]
     double *grad = nullptr;                                     // NCC pose gradients [V][6] (device)
+    const float *target = nullptr;  // training: target images [V][3][H][W] (device)
+    double l1_scale = 0.0;          // training: weight of sum |C - I| in the loss
+    float *tgrad = nullptr;         // training: dL/dparameters [14][n] (device, accumulated)
     std::vector<double> scores;
     std::vector<int> degen, best;
     std::vector<double> best_score;
@@ -687,12 +694,26 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         CK(launch_query_stats(L, 3 * HW, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
         launches += 2;
     }
+    float *rgb_out = o.target ? ctx->trgb.as<float>() : (o.rgb ? o.rgb + (int64_t)sb.v0 * 3 * HW : nullptr);
     CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
-                    o.score ? ctx->partials.as<double>() : nullptr, o.rgb ? o.rgb + (int64_t)sb.v0 * 3 * HW : nullptr,
+                    o.score ? ctx->partials.as<double>() : nullptr, rgb_out,
                     o.depth ? o.depth + (int64_t)sb.v0 * HW : nullptr, o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr,
                     nullptr, 0, d_overflow, st));
     launches += 1;
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
+    if (o.target) {
+        // map training: the image loss and dL/dC, then back through the blend and the projection
+        CK(launch_photo_l1(ctx->trgb.as<float>(), o.target + (int64_t)sb.v0 * 3 * HW, (int64_t)L.V * 3 * HW,
+                           o.l1_scale, ctx->tgimg.as<float>(), false, ctx->tloss.as<double>(), st));
+        CK(cudaMemsetAsync(ctx->gbuf.p, 0, 36 * (size_t)sb.VS, st));
+        CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
+                             ctx->tgimg.as<float>(), ctx->gbuf.as<float>(), d_overflow, st));
+        CK(launch_param_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
+                              ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.as<float>(), ctx->n,
+                              ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(), o.tgrad,
+                              st));
+        launches += 3;
+    }
     if (o.score) {
         CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, blend_units(cp), 3 * HW,
                                ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0,
@@ -701,7 +722,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         if (o.grad) {
             CK(cudaMemsetAsync(ctx->gbuf.p, 0, 20 * (size_t)sb.VS, st));
             CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
-                                 ctx->gcoef.as<double>(), ctx->gbuf.as<float>(), d_overflow, st));
+                                 ctx->gcoef.as<double>(), nullptr, ctx->gbuf.as<float>(), d_overflow, st));
             CK(launch_pose_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
                                  ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.p, ctx->precision, ctx->n,
                                  ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(),
@@ -791,6 +812,11 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->inst.ensure(4 * (size_t)VI));
         CKS(ctx->ranges.ensure(sizeof(int2) * (size_t)V * cp.n_tiles));
         CKS(ctx->partials.ensure(24 * (size_t)V * blend_units(cp)));
+        if (o.target) {
+            CKS(ctx->trgb.ensure(12 * (size_t)V * HW));
+            CKS(ctx->tgimg.ensure(12 * (size_t)V * HW));
+            CKS(ctx->gbuf.ensure(36 * (size_t)VS));
+        }
         if (o.grad) {
             int64_t pb = 1;
             for (auto &sb : sbs) pb = std::max<int64_t>(pb, (int64_t)sb.pblk * (sb.v1 - sb.v0));
@@ -840,6 +866,10 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         }
         CK(cudaMemcpyAsync(ctx->tables.p, pin, tab, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(ctx->flags.p, 0, 64, st));
+        if (o.target) {     // every attempt starts from zero (an overflow retry re-runs the call)
+            CK(cudaMemsetAsync(ctx->tloss.p, 0, 8, st));
+            CK(cudaMemsetAsync(o.tgrad, 0, sizeof(float) * 14 * (size_t)ctx->n, st));
+        }
         launches = 0;
         if (graph) {
             cudaGraph_t g = nullptr;
@@ -1704,5 +1734,148 @@ extern "C" reloc_status reloc_score_grad(reloc_ctx *ctx, const reloc_range *rang
     memcpy(scores_host, o.scores.data(), sizeof(double) * n_views);
     CK(cudaMemcpyAsync(grads_host, ctx->gpose.p, 48 * (size_t)n_views, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return RELOC_OK;
+}
+
+// ============================================== map training (NEXT-4) ========
+extern "C" void reloc_default_train_options(reloc_train_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof *opt);
+    opt->lambda_dssim = 0.2;
+    opt->w_photo = 1.0;
+    opt->w_reproj = 1.0;
+    opt->lr_mean = 1.6e-4;
+    opt->lr_scale = 5e-3;
+    opt->lr_quat = 1e-3;
+    opt->lr_opacity = 5e-2;
+    opt->lr_color = 2.5e-3;
+    opt->beta1 = 0.9;
+    opt->beta2 = 0.999;
+    opt->eps = 1e-15;
+    opt->views_per_group = 16;
+}
+
+// The loss of the call and its gradient, added into grad (device [14][n]).
+static reloc_status train_loss_grad(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges, const double *poses,
+                                    int n_views, const reloc_camera *cam, const float *targets_dev,
+                                    const reloc_train_options &o, float *grad, double *loss_host, cudaStream_t st)
+{
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    if (ctx->sh_degree != 0) return fail(RELOC_EINVAL, "map training needs SH degree 0 (plain RGB colours)");
+    if (ctx->precision != RELOC_FP32) return fail(RELOC_EINVAL, "map training needs FP32 attributes");
+    if (!targets_dev || !poses || !cam || !loss_host) return fail(RELOC_EINVAL, "NULL argument");
+    if (n_views < 1) return fail(RELOC_EINVAL, "n_views %d < 1", n_views);
+    if (!(o.lambda_dssim >= 0 && o.lambda_dssim <= 1) || !(o.w_photo >= 0) || !(o.w_reproj >= 0) ||
+        !std::isfinite(o.w_photo) || !std::isfinite(o.w_reproj) || o.views_per_group < 1 || o.views_per_group > 4096)
+        return fail(RELOC_EINVAL, "bad training options");
+    if (o.lambda_dssim != 0) return fail(RELOC_EINVAL, "D-SSIM not available yet (lambda_dssim must be 0)");
+    if (o.w_reproj != 0) return fail(RELOC_EINVAL, "reprojection loss not available yet (w_reproj must be 0)");
+    if (n_ranges < 0 || (n_ranges > 0 && !ranges)) return fail(RELOC_EINVAL, "bad ranges");
+    if (cam->width < 1 || cam->height < 1) return fail(RELOC_EINVAL, "bad camera");
+    const int64_t HW = (int64_t)cam->width * cam->height;
+    std::vector<QuerySpec> qs;
+    for (int v0 = 0; v0 < n_views; v0 += o.views_per_group) {
+        QuerySpec q;
+        CKS(one_query(ctx, ranges, n_ranges, poses + 16 * (size_t)v0, std::min(o.views_per_group, n_views - v0), q));
+        qs.push_back(std::move(q));
+    }
+    CK(cudaSetDevice(ctx->device));
+    CKS(ctx->tloss.ensure(8));
+    CallOut co;
+    co.target = targets_dev;
+    co.l1_scale = o.w_photo * (1.0 - o.lambda_dssim) / ((double)n_views * 3.0 * (double)HW);
+    co.tgrad = grad;
+    CKS(run_batch(ctx, qs, cam, st, co, false));
+    CK(cudaMemcpyAsync(loss_host, ctx->tloss.p, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_train_grad(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                                         const double *poses, int n_views, const reloc_camera *cam,
+                                         const float *targets_dev, const reloc_train_options *opt,
+                                         double *loss_host, float *grad_dev, void *stream)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    if (!grad_dev) return fail(RELOC_EINVAL, "grad_dev is NULL");
+    reloc_train_options o;
+    if (opt) o = *opt; else reloc_default_train_options(&o);
+    return train_loss_grad(ctx, ranges, n_ranges, poses, n_views, cam, targets_dev, o, grad_dev, loss_host,
+                           (cudaStream_t)stream);
+}
+
+extern "C" reloc_status reloc_train_step(reloc_ctx *ctx, const reloc_range *ranges, int n_ranges,
+                                         const double *poses, int n_views, const reloc_camera *cam,
+                                         const float *targets_dev, const reloc_train_options *opt,
+                                         double *loss_host, void *stream)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    reloc_train_options o;
+    if (opt) o = *opt; else reloc_default_train_options(&o);
+    const double lrs[5] = {o.lr_mean, o.lr_scale, o.lr_quat, o.lr_opacity, o.lr_color};
+    for (double l : lrs)
+        if (!(l >= 0) || !std::isfinite(l)) return fail(RELOC_EINVAL, "bad learning rate");
+    if (!(o.beta1 >= 0 && o.beta1 < 1) || !(o.beta2 >= 0 && o.beta2 < 1) || !(o.eps >= 0))
+        return fail(RELOC_EINVAL, "bad Adam parameters");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    const size_t pbytes = sizeof(float) * 14 * (size_t)ctx->n;
+    CKS(ctx->tgrad.ensure(pbytes));
+    CKS(train_loss_grad(ctx, ranges, n_ranges, poses, n_views, cam, targets_dev, o, ctx->tgrad.as<float>(),
+                        loss_host, st));
+    CKS(ctx->adam_m.ensure(pbytes));
+    CKS(ctx->adam_v.ensure(pbytes));
+    if (ctx->adam_t == 0) {
+        CK(cudaMemsetAsync(ctx->adam_m.p, 0, pbytes, st));
+        CK(cudaMemsetAsync(ctx->adam_v.p, 0, pbytes, st));
+    }
+    ctx->adam_t += 1;
+    AdamParams P;
+    for (int k = 0; k < 5; ++k) P.lr[k] = (float)lrs[k];
+    P.beta1 = (float)o.beta1;
+    P.beta2 = (float)o.beta2;
+    P.eps = (float)o.eps;
+    P.bc1 = (float)(1.0 / (1.0 - std::pow(o.beta1, (double)ctx->adam_t)));
+    P.bc2 = (float)(1.0 / (1.0 - std::pow(o.beta2, (double)ctx->adam_t)));
+    P.o_min = 1e-6f;
+    CK(launch_adam(ctx->mean.as<float>(), ctx->attr.as<float>(), ctx->tgrad.as<float>(), ctx->adam_m.as<float>(),
+                   ctx->adam_v.as<float>(), ctx->n, P, st));
+    CK(cudaStreamSynchronize(st));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_train_reset(reloc_ctx *ctx)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    ctx->adam_t = 0;
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_read_map(reloc_ctx *ctx, float *mean, float *scale, float *quat, float *opacity,
+                                       float *sh)
+{
+    if (!ctx) return fail(RELOC_EINVAL, "NULL context");
+    if (ctx->n == 0) return fail(RELOC_ENOMAP, "no map loaded");
+    if (ctx->precision != RELOC_FP32) return fail(RELOC_EINVAL, "reading the map back needs FP32 attributes");
+    const int64_t n = ctx->n;
+    const int K = (ctx->sh_degree + 1) * (ctx->sh_degree + 1);
+    const size_t nc = attr_components(ctx->sh_degree);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<float> m((size_t)3 * n), a(nc * (size_t)n);
+    CK(cudaMemcpy(m.data(), ctx->mean.p, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(a.data(), ctx->attr.p, sizeof(float) * nc * n, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            if (mean) mean[3 * i + k] = m[(size_t)k * n + i];
+            if (scale) scale[3 * i + k] = a[(size_t)(ATTR_SCALE + k) * n + i];
+        }
+        for (int k = 0; k < 4; ++k)
+            if (quat) quat[4 * i + k] = a[(size_t)(ATTR_QUAT + k) * n + i];
+        if (opacity) opacity[i] = a[(size_t)ATTR_OPAC * n + i];
+        if (sh)
+            for (int k = 0; k < 3 * K; ++k) sh[(size_t)3 * K * i + k] = a[(size_t)(ATTR_SH + k) * n + i];
+    }
     return RELOC_OK;
 }

@@ -176,11 +176,13 @@ inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w 
 cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, const Layout &L, int n_units,
                                 int64_t n_samples, double *scores, int *degenerate, double *coef, cudaStream_t st);
 
-// K6 backward: per (view, Gaussian) gradients of the view's NCC with respect to
-// the projected mean and conic, added into gout[vd_off[v] + i][5] (u, v, a, b, c).
+// K6 backward: per (view, Gaussian) gradients with respect to the projected
+// mean and conic.  gimg null: of the view's NCC (coef from K7), added into
+// gout[vd_off[v] + i][5] (u, v, a, b, c).  gimg [V][3][H][W] = dL/dC of an
+// image loss: added into gout[vd_off[v] + i][9] (u, v, a, b, c, r, g, b, opacity).
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                              const CamParams &cam, const double *coef, float *gout, const int *overflow,
-                              cudaStream_t st);
+                              const CamParams &cam, const double *coef, const float *gimg, float *gout,
+                              const int *overflow, cudaStream_t st);
 
 // Chain of gin to each view's left pose update: out[V][6] (rho, phi);
 // part: n_blocks * V * 6 doubles of scratch.
@@ -188,6 +190,22 @@ cudaError_t launch_pose_chain(const float *mx, const float *my, const float *mz,
                               int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
                               const ViewParams *views, const CamParams &cam, const float *gin, double *part,
                               double *out, cudaStream_t st);
+
+// ---- map training (train.cu) -------------------------------------------------
+// L1 samples: loss += scale * sum |rgb - target|, gimg (=|+=) scale * sign.
+cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, double scale, float *gimg,
+                            bool accumulate, double *loss, cudaStream_t st);
+// gin [VS][9] (launch_blend_grad, image mode) -> gmap [14][n_map] (added):
+// mean xyz, scale xyz, quat wxyz, opacity, rgb.  FP32 attributes only.
+cudaError_t launch_param_chain(const float *mx, const float *my, const float *mz, const float *attr, int64_t n_map,
+                               const uint32_t *gidx, const Layout &L, int n_blocks, const ViewParams *views,
+                               const CamParams &cam, const float *gin, float *gmap, cudaStream_t st);
+struct AdamParams {
+    float lr[5];          // mean, scale, quaternion, opacity, colour
+    float beta1, beta2, eps, bc1, bc2, o_min;
+};
+cudaError_t launch_adam(float *mean, float *attr, const float *grad, float *m1, float *m2, int64_t n,
+                        const AdamParams &P, cudaStream_t st);
 
 // K8: per query, argmax over its views (lowest index on ties):
 // best[q] (index within the query), best_score[q], view_sel[q] (view index).

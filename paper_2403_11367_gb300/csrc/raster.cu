@@ -462,14 +462,19 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 //   dL/d alpha_j = T_j (G . c_j) - (G . C_after) / (1 - alpha_j),
 // G = dNCC/dC of the pixel; alpha = o exp(power) unclamped gives
 // dL/d power = alpha dL/d alpha, and power = -(a dx^2 + 2 b dx dy + c dy^2)/2
-// with dx = x - u.  The warp sums each record's five gradients over its 64
-// pixels and adds them to the (view, Gaussian) entry of gout.
-template <int TW, int TH>
+// with dx = x - u.  The warp sums each record's gradients over its 64 pixels
+// and adds them to the (view, Gaussian) entry of gout.
+// IMG = false: L is the view's NCC (G from coef), five outputs (u, v, a, b, c).
+// IMG = true: G is given per pixel (gimg [V][3][H][W], an image loss's
+// gradient); nine outputs: also dL/d colour = sum w G and dL/d opacity =
+// dL/d alpha exp(power) (alpha unclamped).
+template <int TW, int TH, bool IMG>
 __global__ void __launch_bounds__(32)
 k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
              const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
-             float *__restrict__ gout, const int *__restrict__ overflow)
+             const float *__restrict__ gimg, float *__restrict__ gout, const int *__restrict__ overflow)
 {
+    constexpr int NOUT = IMG ? 9 : 5;
     constexpr int WPT = TW * TH / 64;
     constexpr int WROWS = 64 / TW;
     __shared__ float4 s_a[32], s_b[32], s_c[32];
@@ -557,19 +562,32 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         }
         __syncwarp();
     }
-    // dNCC/dC per pixel
-    const double *cf = coef + 4 * (int64_t)v;
-    const float k_q = (float)cf[0], k_r = (float)cf[1], mr = (float)cf[2], mq = (float)cf[3];
-    const float *query = L.q_img[L.view_q[v]];
+    // dL/dC per pixel
     const int64_t HW = (int64_t)cam.width * cam.height;
     float G[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (IMG) {
+        const float *gi = gimg + (int64_t)v * 3 * HW;
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
-        if (in[p]) {
-            const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
+        for (int p = 0; p < 2; ++p)
+            if (in[p]) {
+                const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
-        }
+                for (int ch = 0; ch < 3; ++ch) G[p][ch] = __ldg(gi + ch * HW + pix);
+            }
+    } else {
+        // NCC: dNCC/dC = (q - mean q) / sqrt(var_r var_q) - NCC (C - mean r) / var_r
+        const double *cf = coef + 4 * (int64_t)v;
+        const float k_q = (float)cf[0], k_r = (float)cf[1], mr = (float)cf[2], mq = (float)cf[3];
+        const float *query = L.q_img[L.view_q[v]];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            if (in[p]) {
+                const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
+            }
+    }
     // pass 2: front to back again, gradients per record
     float Tb[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
     float U[2][3] = {{0, 0, 0}, {0, 0, 0}};
@@ -578,7 +596,10 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k], bb = s_b[k];
-            float g[5] = {0, 0, 0, 0, 0};
+            const float opac = s_a[k].w;
+            float g[NOUT];
+#pragma unroll
+            for (int m = 0; m < NOUT; ++m) g[m] = 0.f;
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 float dx = 0.f, dy = 0.f;
@@ -600,17 +621,27 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                         g[2] += gp * (-0.5f * dx * dx);
                         g[3] += gp * (-dx * dy);
                         g[4] += gp * (-0.5f * dy * dy);
+                        if (IMG) {
+                            g[5] += w * G[p][0];
+                            g[6] += w * G[p][1];
+                            g[7] += w * G[p][2];
+                            g[8] += un ? gal * (al / opac) : 0.f;
+                        }
                         U[p][0] += c.x * w; U[p][1] += c.y * w; U[p][2] += c.z * w;
                         Tb[p] = tn;
                     }
                 }
             }
+            bool any = false;
 #pragma unroll
-            for (int m = 0; m < 5; ++m) g[m] = warp_sum_f(g[m]);
-            if (lane == 0 && (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f || g[4] != 0.f)) {
-                float *o = gout + 5 * (L.vd_off[v] + (int64_t)s_g[k]);
+            for (int m = 0; m < NOUT; ++m) {
+                g[m] = warp_sum_f(g[m]);
+                any = any || g[m] != 0.f;
+            }
+            if (lane == 0 && any) {
+                float *o = gout + NOUT * (L.vd_off[v] + (int64_t)s_g[k]);
 #pragma unroll
-                for (int m = 0; m < 5; ++m) atomicAdd(o + m, g[m]);
+                for (int m = 0; m < NOUT; ++m) atomicAdd(o + m, g[m]);
             }
         }
         __syncwarp();
@@ -619,21 +650,25 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
 
 template <int TW, int TH>
 static cudaError_t blend_grad_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                                const CamParams &cam, const double *coef, float *gout, const int *overflow,
-                                cudaStream_t st)
+                                const CamParams &cam, const double *coef, const float *gimg, float *gout,
+                                const int *overflow, cudaStream_t st)
 {
     dim3 grid(cam.n_tiles * (TW * TH / 64), L.V);
-    k_blend_grad<TW, TH><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gout, overflow);
+    if (gimg)
+        k_blend_grad<TW, TH, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow);
+    else
+        k_blend_grad<TW, TH, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                              const CamParams &cam, const double *coef, float *gout, const int *overflow,
-                              cudaStream_t st)
+                              const CamParams &cam, const double *coef, const float *gimg, float *gout,
+                              const int *overflow, cudaStream_t st)
 {
     if (L.V <= 0) return cudaSuccess;
 #define RELOC_GRAD_CASE(W_, H_) \
-    if (cam.tile_w == W_ && cam.tile_h == H_) return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gout, overflow, st);
+    if (cam.tile_w == W_ && cam.tile_h == H_) \
+        return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow, st);
     RELOC_GRAD_CASE(16, 16)
     RELOC_GRAD_CASE(8, 8)
     RELOC_GRAD_CASE(32, 8)

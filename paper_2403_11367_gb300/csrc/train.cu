@@ -1,0 +1,268 @@
+// train.cu -- map training (Sec. III-B.3): the image loss and its gradient per
+// pixel, the chain rule from per-(view, Gaussian) screen-space gradients to the
+// Gaussians' parameters, and the Adam step on the map.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace reloc {
+
+// ------------------------------------------------------------------ L1 -----
+// L1 part of L_rgb (Eq. 3) over n samples: loss += scale * sum |C - I| and
+// dL/dC = scale * sign(C - I) (sign(0) = +1, the right derivative), written
+// or added (accumulate) to gimg.  One FP64 atomic per block.
+__global__ void __launch_bounds__(256)
+k_photo_l1(const float *__restrict__ rgb, const float *__restrict__ target, int64_t n, float scale, double dscale,
+           float *__restrict__ gimg, int accumulate, double *__restrict__ loss)
+{
+    __shared__ double s_red[8];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const float d = rgb[i] - target[i];
+        acc += (double)fabsf(d);
+        const float g = d >= 0.f ? scale : -scale;
+        gimg[i] = accumulate ? gimg[i] + g : g;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += s_red[w];
+        atomicAdd(loss, s * dscale);
+    }
+}
+
+cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, double scale, float *gimg,
+                            bool accumulate, double *loss, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 256 * 8), 152 * 16);
+    k_photo_l1<<<(int)blocks, 256, 0, st>>>(rgb, target, n, (float)scale, scale, gimg, accumulate ? 1 : 0, loss);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- parameter chain --
+// gin holds, per (view, subset Gaussian), the gradients of the loss with
+// respect to the projected mean (u, v), the conic (a, b, c), the colour and
+// the opacity (k_blend_grad, image mode).  A thread per subset Gaussian walks
+// its query's views and carries them back through the projection (Sec. III-A:
+// Sigma' = J W Sigma W^T J^T + 0.3 I, conic = Sigma'^-1, t = W mu):
+//   dL/dSigma' = -A G_A A                       (G_A = [[ga, gb/2], [gb/2, gc]])
+//   dL/dSigma += T^T dL/dSigma' T, dL/dT = 2 dL/dSigma' T Sigma    (T = J W)
+//   dL/dt from (u, v) and from J(t) (frustum clamp: no term through a clamped
+//   coordinate), dL/dmu += W^T dL/dt;
+// then once: Sigma = M M^T with M = R(q / |q|) diag(s): dL/dM = 2 dL/dSigma M,
+// dL/ds_j = sum_i dL/dM_ij R_ij, dL/dR_ij = dL/dM_ij s_j, through the rotation
+// entries to the unit quaternion and across its normalisation
+// (g_q = (g_qhat - qhat (qhat . g_qhat)) / |q|).  The 14 sums are added to
+// gmap [14][n_map] (mean xyz, scale xyz, quat wxyz, opacity, rgb).
+__global__ void __launch_bounds__(PROJ_THREADS)
+k_param_chain(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
+              const float *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, Layout L,
+              const ViewParams *__restrict__ views, CamParams cam, const float *__restrict__ gin,
+              float *__restrict__ gmap)
+{
+    const int qi = find_segment(L.q_pblk, L.Q, (int)blockIdx.x);
+    const int64_t S = L.q_gsub[qi + 1] - L.q_gsub[qi];
+    const int64_t i = (int64_t)(blockIdx.x - L.q_pblk[qi]) * PROJ_THREADS + threadIdx.x;
+    if (i >= S) return;
+    const int v_begin = L.q_view[qi], V = L.q_view[qi + 1] - v_begin;
+    const int64_t g = gidx[L.q_gsub[qi] + i];
+    const float mu0 = __ldg(mx + g), mu1 = __ldg(my + g), mu2 = __ldg(mz + g);
+    const float sc[3] = {__ldg(attr + (ATTR_SCALE + 0) * n_map + g), __ldg(attr + (ATTR_SCALE + 1) * n_map + g),
+                         __ldg(attr + (ATTR_SCALE + 2) * n_map + g)};
+    const float q0 = __ldg(attr + (ATTR_QUAT + 0) * n_map + g), q1 = __ldg(attr + (ATTR_QUAT + 1) * n_map + g);
+    const float q2 = __ldg(attr + (ATTR_QUAT + 2) * n_map + g), q3 = __ldg(attr + (ATTR_QUAT + 3) * n_map + g);
+    const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    const float qw = q0 / qn, qx = q1 / qn, qy = q2 / qn, qz = q3 / qn;
+    const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                        2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                        2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    float m[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) m[3 * a + b] = r[3 * a + b] * sc[b];
+    float Sm[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Sm[3 * a + b] = m[3 * a] * m[3 * b] + m[3 * a + 1] * m[3 * b + 1] + m[3 * a + 2] * m[3 * b + 2];
+
+    float gmu[3] = {0, 0, 0}, gS[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gcol[3] = {0, 0, 0}, gop = 0.f;
+    bool any = false;
+    for (int vv = 0; vv < V; ++vv) {
+        const int v = v_begin + vv;
+        const float *g9 = gin + 9 * (L.vd_off[v] + i);
+        const float gu = g9[0], gv = g9[1], ga = g9[2], gb = g9[3], gc = g9[4];
+        const float gr = g9[5], gg = g9[6], gbl = g9[7], go = g9[8];
+        if (gu == 0.f && gv == 0.f && ga == 0.f && gb == 0.f && gc == 0.f && gr == 0.f && gg == 0.f &&
+            gbl == 0.f && go == 0.f)
+            continue;
+        any = true;
+        gcol[0] += gr; gcol[1] += gg; gcol[2] += gbl;
+        gop += go;
+        const ViewParams &P = views[v];
+        const float d0 = (mu0 - P.c_hi[0]) - P.c_lo[0], d1 = (mu1 - P.c_hi[1]) - P.c_lo[1];
+        const float d2 = (mu2 - P.c_hi[2]) - P.c_lo[2];
+        const float t[3] = {P.R[0] * d0 + P.R[1] * d1 + P.R[2] * d2, P.R[3] * d0 + P.R[4] * d1 + P.R[5] * d2,
+                            P.R[6] * d0 + P.R[7] * d1 + P.R[8] * d2};
+        const float iz = 1.f / t[2];
+        const float rx = t[0] * iz, ry = t[1] * iz;
+        const bool cx_ = rx < -cam.limx || rx > cam.limx, cy_ = ry < -cam.limy || ry > cam.limy;
+        const float xz = fminf(fmaxf(rx, -cam.limx), cam.limx), yz = fminf(fmaxf(ry, -cam.limy), cam.limy);
+        const float J00 = cam.fx * iz, J02 = -cam.fx * xz * iz, J11 = cam.fy * iz, J12 = -cam.fy * yz * iz;
+        float Tm[6];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Tm[b] = J00 * P.R[b] + J02 * P.R[6 + b];
+            Tm[3 + b] = J11 * P.R[3 + b] + J12 * P.R[6 + b];
+        }
+        float TS[6];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                TS[3 * a + b] = Tm[3 * a] * Sm[b] + Tm[3 * a + 1] * Sm[3 + b] + Tm[3 * a + 2] * Sm[6 + b];
+        const float sa = TS[0] * Tm[0] + TS[1] * Tm[1] + TS[2] * Tm[2] + cam.eps2d;
+        const float sb = TS[0] * Tm[3] + TS[1] * Tm[4] + TS[2] * Tm[5];
+        const float scc = TS[3] * Tm[3] + TS[4] * Tm[4] + TS[5] * Tm[5] + cam.eps2d;
+        const float idet = 1.f / (sa * scc - sb * sb);
+        const float A00 = scc * idet, A01 = -sb * idet, A11 = sa * idet;
+        const float h = 0.5f * gb;
+        const float M00 = A00 * ga + A01 * h, M01 = A00 * h + A01 * gc;
+        const float M10 = A01 * ga + A11 * h, M11 = A01 * h + A11 * gc;
+        const float GS00 = -(M00 * A00 + M01 * A01), GS01 = -(M00 * A01 + M01 * A11);
+        const float GS11 = -(M10 * A01 + M11 * A11);
+        // dL/dSigma += T^T GS T
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float ua = GS00 * Tm[a] + GS01 * Tm[3 + a], wa = GS01 * Tm[a] + GS11 * Tm[3 + a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) gS[3 * a + b] += ua * Tm[b] + wa * Tm[3 + b];
+        }
+        float dT[6];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            dT[b] = 2.f * (GS00 * TS[b] + GS01 * TS[3 + b]);
+            dT[3 + b] = 2.f * (GS01 * TS[b] + GS11 * TS[3 + b]);
+        }
+        const float dJ00 = dT[0] * P.R[0] + dT[1] * P.R[1] + dT[2] * P.R[2];
+        const float dJ02 = dT[0] * P.R[6] + dT[1] * P.R[7] + dT[2] * P.R[8];
+        const float dJ11 = dT[3] * P.R[3] + dT[4] * P.R[4] + dT[5] * P.R[5];
+        const float dJ12 = dT[3] * P.R[6] + dT[4] * P.R[7] + dT[5] * P.R[8];
+        float gt0 = gu * cam.fx * iz, gt1 = gv * cam.fy * iz;
+        float gt2 = -(gu * cam.fx * t[0] + gv * cam.fy * t[1]) * iz * iz;
+        gt2 += -(dJ00 * cam.fx + dJ11 * cam.fy) * iz * iz;
+        gt2 += dJ02 * cam.fx * xz * iz * iz;
+        gt2 += dJ12 * cam.fy * yz * iz * iz;
+        if (!cx_) {
+            gt0 += dJ02 * (-cam.fx * iz * iz);
+            gt2 += dJ02 * (cam.fx * t[0] * iz * iz * iz);
+        }
+        if (!cy_) {
+            gt1 += dJ12 * (-cam.fy * iz * iz);
+            gt2 += dJ12 * (cam.fy * t[1] * iz * iz * iz);
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) gmu[b] += P.R[b] * gt0 + P.R[3 + b] * gt1 + P.R[6 + b] * gt2;
+    }
+    if (!any) return;
+    // dL/dM = 2 dL/dSigma M (dL/dSigma symmetric)
+    float gM[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            gM[3 * a + b] = 2.f * (gS[3 * a] * m[b] + gS[3 * a + 1] * m[3 + b] + gS[3 * a + 2] * m[6 + b]);
+    float gs[3], gR[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gs[b] = gM[b] * r[b] + gM[3 + b] * r[3 + b] + gM[6 + b] * r[6 + b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) gR[3 * a + b] = gM[3 * a + b] * sc[b];
+    // rotation entries -> unit quaternion (w, x, y, z)
+    const float hw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
+    const float hx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
+                            qw * gR[7] - 2.f * qx * gR[8]);
+    const float hy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
+                            qz * gR[7] - 2.f * qy * gR[8]);
+    const float hz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
+                            qy * gR[5] + qx * gR[6] + qy * gR[7]);
+    const float dot = qw * hw + qx * hx + qy * hy + qz * hz;
+    const float gq[4] = {(hw - qw * dot) / qn, (hx - qx * dot) / qn, (hy - qy * dot) / qn, (hz - qz * dot) / qn};
+    const float out[14] = {gmu[0], gmu[1], gmu[2], gs[0], gs[1], gs[2], gq[0], gq[1], gq[2], gq[3],
+                           gop, gcol[0], gcol[1], gcol[2]};
+#pragma unroll
+    for (int k = 0; k < 14; ++k)
+        if (out[k] != 0.f) atomicAdd(gmap + k * n_map + g, out[k]);
+}
+
+cudaError_t launch_param_chain(const float *mx, const float *my, const float *mz, const float *attr, int64_t n_map,
+                               const uint32_t *gidx, const Layout &L, int n_blocks, const ViewParams *views,
+                               const CamParams &cam, const float *gin, float *gmap, cudaStream_t st)
+{
+    if (n_blocks <= 0 || L.V <= 0) return cudaSuccess;
+    k_param_chain<<<n_blocks, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, gin, gmap);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Adam ---
+// One Adam step (Kingma and Ba 2015) over the 14 parameter rows of the map,
+// on 3D Gaussian Splatting's latent parameters: log scale (s = exp(l), so
+// dL/dl = s dL/ds and s' = s exp(-step)), logit opacity (o = sigmoid(z),
+// dL/dz = o (1 - o) dL/do), the rest as stored.  Group k in {mean, scale,
+// quaternion, opacity, colour} has learning rate lr[k]; bc1, bc2 are the bias
+// corrections 1 / (1 - beta^t).
+__global__ void __launch_bounds__(256)
+k_adam(float *__restrict__ mean, float *__restrict__ attr, const float *__restrict__ grad, float *__restrict__ m1,
+       float *__restrict__ m2, int64_t n, AdamParams P)
+{
+    const int64_t total = 14 * n;
+    for (int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * 256) {
+        const int c = (int)(idx / n);
+        const int64_t i = idx - (int64_t)c * n;
+        float *p;
+        int grp;
+        if (c < 3) { p = mean + c * n + i; grp = 0; }
+        else if (c < 6) { p = attr + (ATTR_SCALE + c - 3) * n + i; grp = 1; }
+        else if (c < 10) { p = attr + (ATTR_QUAT + c - 6) * n + i; grp = 2; }
+        else if (c == 10) { p = attr + ATTR_OPAC * n + i; grp = 3; }
+        else { p = attr + (ATTR_SH + c - 11) * n + i; grp = 4; }
+        const float x = *p;
+        float gr = grad[idx];
+        float o = 0.f;
+        if (grp == 1) gr *= x;
+        if (grp == 3) {
+            o = fminf(fmaxf(x, P.o_min), 1.f - P.o_min);
+            gr *= o * (1.f - o);
+        }
+        const float a = P.beta1 * m1[idx] + (1.f - P.beta1) * gr;
+        const float b = P.beta2 * m2[idx] + (1.f - P.beta2) * gr * gr;
+        m1[idx] = a;
+        m2[idx] = b;
+        const float step = P.lr[grp] * (a * P.bc1) / (sqrtf(b * P.bc2) + P.eps);
+        if (grp == 1) {
+            *p = x * expf(-step);
+        } else if (grp == 3) {
+            const float z = logf(o / (1.f - o)) - step;
+            *p = 1.f / (1.f + expf(-z));
+        } else {
+            *p = x - step;
+        }
+    }
+}
+
+cudaError_t launch_adam(float *mean, float *attr, const float *grad, float *m1, float *m2, int64_t n,
+                        const AdamParams &P, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>(ceil_div(14 * n, 256 * 4), 152 * 16);
+    k_adam<<<(int)blocks, 256, 0, st>>>(mean, attr, grad, m1, m2, n, P);
+    return cudaGetLastError();
+}
+
+}  // namespace reloc

@@ -90,6 +90,13 @@ class PnpResult(C.Structure):
                 ("iters", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
+class TrainOptions(C.Structure):
+    _fields_ = [("lambda_dssim", C.c_double), ("w_photo", C.c_double), ("w_reproj", C.c_double),
+                ("lr_mean", C.c_double), ("lr_scale", C.c_double), ("lr_quat", C.c_double),
+                ("lr_opacity", C.c_double), ("lr_color", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double), ("views_per_group", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
 class Counts(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_gauss", C.c_int64), ("n_visible", C.c_int64),
                 ("n_instances", C.c_int64), ("inst_stride", C.c_int64), ("retries", C.c_int32),
@@ -144,6 +151,13 @@ SIGNATURES = {
     "reloc_default_pnp_options": (None, [C.POINTER(PnpOptions)]),
     "reloc_refine_pnp": (C.c_int, [_vp, _dp, _dp, C.POINTER(Camera), _vp, _vp, _vp, C.c_int, C.POINTER(PnpOptions),
                                    C.POINTER(PnpResult), _vp]),
+    "reloc_default_train_options": (None, [C.POINTER(TrainOptions)]),
+    "reloc_train_grad": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp,
+                                   C.POINTER(TrainOptions), _dp, _vp, _vp]),
+    "reloc_train_step": (C.c_int, [_vp, C.POINTER(Range), C.c_int, _dp, C.c_int, C.POINTER(Camera), _vp,
+                                   C.POINTER(TrainOptions), _dp, _vp]),
+    "reloc_train_reset": (C.c_int, [_vp]),
+    "reloc_read_map": (C.c_int, [_vp, _fp, _fp, _fp, _fp, _fp]),
 }
 NOALLOC_MAX_VIEWS = 512
 PROPOSAL_H, PROPOSAL_W, PROPOSAL_CLASSES, PROPOSAL_PARAMS = 47, 176, 64, 1916960
@@ -253,6 +267,7 @@ class Context:
         _check(lib.reloc_load_map(self._h, C.byref(gh), g.n, g.sh_degree, precision))
         self._keep = None
         self.n = g.n
+        self.sh_degree = g.sh_degree
 
     def map_order(self) -> np.ndarray:
         out = np.zeros(self.n, np.int64)
@@ -337,6 +352,52 @@ class Context:
         _check(lib.reloc_score_grad(self._h, ra, nr, pp, V, C.byref(c), _ptr(query), sc.ctypes.data_as(_dp),
                                     gr.ctypes.data_as(_dp), _stream(stream)))
         return sc, gr
+
+    @staticmethod
+    def train_options(**opts) -> TrainOptions:
+        o = TrainOptions()
+        lib.reloc_default_train_options(C.byref(o))
+        for k, v in opts.items():
+            if k not in dict(TrainOptions._fields_):
+                raise TypeError(f"unknown training option {k}")
+            setattr(o, k, v)
+        return o
+
+    def train_grad(self, ranges, poses, cam, targets, grad, stream=None, **opts):
+        """Map-training loss (Sec. III-B.3) over the views at poses [V,4,4]
+        against targets [V,3,H,W] (CUDA float32); its gradient is written to
+        grad [14, n] (CUDA float32, block order).  Returns the loss."""
+        ra, nr = self._ranges(ranges)
+        p, pp, V = _poses(poses)
+        c = camera(cam)
+        o = self.train_options(**opts)
+        loss = C.c_double(0)
+        _check(lib.reloc_train_grad(self._h, ra, nr, pp, V, C.byref(c), _ptr(targets), C.byref(o), C.byref(loss),
+                                    _ptr(grad), _stream(stream)))
+        return loss.value
+
+    def train_step(self, ranges, poses, cam, targets, stream=None, **opts):
+        """One Adam step of map training; returns the loss before the step."""
+        ra, nr = self._ranges(ranges)
+        p, pp, V = _poses(poses)
+        c = camera(cam)
+        o = self.train_options(**opts)
+        loss = C.c_double(0)
+        _check(lib.reloc_train_step(self._h, ra, nr, pp, V, C.byref(c), _ptr(targets), C.byref(o), C.byref(loss),
+                                    _stream(stream)))
+        return loss.value
+
+    def train_reset(self):
+        _check(lib.reloc_train_reset(self._h))
+
+    def read_map(self):
+        """The device map in block order: (mean, scale, quat, opacity, sh)."""
+        K = (self.sh_degree + 1) ** 2
+        out = (np.zeros((self.n, 3), np.float32), np.zeros((self.n, 3), np.float32),
+               np.zeros((self.n, 4), np.float32), np.zeros(self.n, np.float32),
+               np.zeros((self.n, K, 3), np.float32))
+        _check(lib.reloc_read_map(self._h, *(a.ctypes.data_as(_fp) for a in out)))
+        return out
 
     def refine_pnp(self, pose_render, cam, depth, alpha, pairs, pose_init=None, stream=None, **opts):
         """PnP refinement (include/reloc.h): depth/alpha [H,W] and pairs [n,4]
