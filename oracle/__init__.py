@@ -76,7 +76,9 @@ def lib():
             L.or_pnp_backproject.argtypes = [dp, dp, fp, fp, dp, C.c_int64, C.c_double, dp, u8p]
             L.or_pnp_backproject.restype = C.c_int64
             L.or_ncc_pose_grad.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, dp, dp, dp]
-            L.or_photo_loss_jvp.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, C.c_int, dp, dp, dp, dp]
+            L.or_photo_loss_jvp.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, C.c_int, dp, dp, dp,
+                                            C.c_double, dp]
+            L.or_ssim_map.argtypes = [dp, dp, C.c_int, C.c_int, dp]
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
             L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
             L.or_block_select.argtypes = [fp, C.c_int64, C.c_double, C.c_double, C.c_double,
@@ -306,11 +308,12 @@ PARAM_ORDER = ["mean_x", "mean_y", "mean_z", "scale_x", "scale_y", "scale_z", "q
                "quat_z", "opacity", "red", "green", "blue"]
 
 
-def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None):
-    """Map-training loss (Sec. III-B.3, L1 part of L_rgb: mean |render - gt|
-    over all samples of all views) and its derivatives along six directions
-    dirs [n, 14, 6] in the Gaussians' parameters (PARAM_ORDER), forward mode
-    in FP64 (SH degree 0).  Returns (loss, jvp[6])."""
+def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0):
+    """Map-training loss L_photo (Sec. III-B.3, Eqs. 3-4: per view
+    (1 - lam) mean |render - gt| + lam (1 - mean SSIM), averaged over the
+    views) and its derivatives along six directions dirs [n, 14, 6] in the
+    Gaussians' parameters (PARAM_ORDER), forward mode in FP64 (SH degree 0).
+    Returns (loss, jvp[6])."""
     if g.sh_degree != 0:
         raise ValueError("map training needs SH degree 0")
     prm = params() if prm is None else prm
@@ -321,8 +324,19 @@ def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None):
                             _p(sh, C.c_float), g.n, _p(_c(dirs, np.float64), C.c_double),
                             _p(poses, C.c_double), poses.shape[0], _p(camvec(cam), C.c_double),
                             _p(_c(prm, np.float64), C.c_double), _p(_c(gt, np.float64), C.c_double),
-                            _p(out, C.c_double))
+                            float(lam), _p(out, C.c_double))
     return out[0], out[1:]
+
+
+def ssim_map(x, y):
+    """SSIM of one channel at every pixel (Eq. 3's D-SSIM term): x, y [H, W]."""
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    if x.shape != y.shape or x.ndim != 2:
+        raise ValueError("x and y must be equal-sized 2D arrays")
+    out = np.zeros_like(x)
+    lib().or_ssim_map(_p(x, C.c_double), _p(y, C.c_double), x.shape[0], x.shape[1], _p(out, C.c_double))
+    return out
 
 
 def pnp_apply(pose, delta, s=1.0):

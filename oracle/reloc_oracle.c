@@ -17,6 +17,9 @@
  *   - normalised cross-correlation                               (Sec. III-C.1, Eq. ncc)
  *   - block (2D voxel) selection around a coarse pose            (Sec. III-B.2, III-C.1)
  *   - argmax over the candidate grid                             (Sec. III-C.1)
+ *   - map-training loss L_rgb = (1 - lambda) L1 + lambda D-SSIM  (Sec. III-B.3, Eq. 3)
+ *     with SSIM of Wang, Bovik, Sheikh and Simoncelli (2004), and its
+ *     derivatives along parameter directions (forward mode)
  * plus an integer replay of the tile|depth key build and stable sort so the
  * GPU's keys and tile lists can be compared bit for bit.
  *
@@ -1182,25 +1185,131 @@ static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const 
     free(order); free(tmp); free(zkey); free(T); free(done);
 }
 
+/* ---- SSIM (the D-SSIM term of Eq. 3) --------------------------------------
+ * SSIM of Wang, Bovik, Sheikh and Simoncelli (2004) as 3D Gaussian Splatting
+ * uses it: at every pixel the local means, variances and covariance under an
+ * 11 x 11 Gaussian window (standard deviation 1.5 px, weights summing to 1),
+ * samples outside the image counting as 0, and
+ *   SSIM = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+ * sx^2 = E[x^2] - mx^2, sxy = E[xy] - mx my, C1 = 0.01^2, C2 = 0.03^2 (unit
+ * dynamic range).  D-SSIM = 1 - the mean of SSIM over pixels and channels. */
+enum { SSIM_R = 5, SSIM_N = 2 * SSIM_R + 1 };
+static const double SSIM_C1 = 0.01 * 0.01, SSIM_C2 = 0.03 * 0.03;
+
+static void ssim_window(double w[SSIM_N][SSIM_N])
+{
+    double s = 0.0;
+    for (int i = 0; i < SSIM_N; ++i)
+        for (int j = 0; j < SSIM_N; ++j) {
+            const double di = i - SSIM_R, dj = j - SSIM_R;
+            w[i][j] = exp(-(di * di + dj * dj) / (2.0 * 1.5 * 1.5));
+            s += w[i][j];
+        }
+    for (int i = 0; i < SSIM_N; ++i)
+        for (int j = 0; j < SSIM_N; ++j) w[i][j] /= s;
+}
+
+/* SSIM map of one channel: x, y, out [H][W]. */
+void or_ssim_map(const double *x, const double *y, int H, int W, double *out)
+{
+    double w[SSIM_N][SSIM_N];
+    ssim_window(w);
+#pragma omp parallel for schedule(static)
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            double mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+            for (int i = 0; i < SSIM_N; ++i) {
+                const int yy = py + i - SSIM_R;
+                if (yy < 0 || yy >= H) continue;
+                for (int j = 0; j < SSIM_N; ++j) {
+                    const int xx = px + j - SSIM_R;
+                    if (xx < 0 || xx >= W) continue;
+                    const double a = x[(int64_t)yy * W + xx], b = y[(int64_t)yy * W + xx], c = w[i][j];
+                    mx += c * a; my += c * b; exx += c * a * a; eyy += c * b * b; exy += c * a * b;
+                }
+            }
+            const double sx = exx - mx * mx, sy = eyy - my * my, sxy = exy - mx * my;
+            out[(int64_t)py * W + px] = ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) /
+                                        ((mx * mx + my * my + SSIM_C1) * (sx + sy + SSIM_C2));
+        }
+}
+
+/* Sum over the pixels of one channel of SSIM(x, y), x in duals, y fixed. */
+static dual dssim_sum(const dual *x, const double *y, int H, int W)
+{
+    double w[SSIM_N][SSIM_N];
+    ssim_window(w);
+    const int64_t npx = (int64_t)H * W;
+    dual *xx = (dual *)malloc(sizeof(dual) * (npx + 1));
+    dual *rows = (dual *)malloc(sizeof(dual) * (H + 1));
+    for (int64_t k = 0; k < npx; ++k) xx[k] = dmul(x[k], x[k]);
+#pragma omp parallel for schedule(static)
+    for (int py = 0; py < H; ++py) {
+        dual acc = dk(0);
+        for (int px = 0; px < W; ++px) {
+            dual mx = dk(0), exx = dk(0), exy = dk(0);
+            double my = 0, eyy = 0;
+            for (int i = 0; i < SSIM_N; ++i) {
+                const int yy = py + i - SSIM_R;
+                if (yy < 0 || yy >= H) continue;
+                for (int j = 0; j < SSIM_N; ++j) {
+                    const int xc = px + j - SSIM_R;
+                    if (xc < 0 || xc >= W) continue;
+                    const int64_t k = (int64_t)yy * W + xc;
+                    const double c = w[i][j], b = y[k];
+                    mx = dadd(mx, dscale(x[k], c));
+                    exx = dadd(exx, dscale(xx[k], c));
+                    exy = dadd(exy, dscale(x[k], c * b));
+                    my += c * b;
+                    eyy += c * b * b;
+                }
+            }
+            const dual sx = dsub(exx, dmul(mx, mx));
+            const double sy = eyy - my * my;
+            const dual sxy = dsub(exy, dscale(mx, my));
+            const dual num = dmul(dadd(dscale(mx, 2 * my), dk(SSIM_C1)), dadd(dscale(sxy, 2), dk(SSIM_C2)));
+            const dual den = dmul(dadd(dmul(mx, mx), dk(my * my + SSIM_C1)), dadd(sx, dk(sy + SSIM_C2)));
+            acc = dadd(acc, ddiv(num, den));
+        }
+        rows[py] = acc;
+    }
+    dual s = dk(0);
+    for (int py = 0; py < H; ++py) s = dadd(s, rows[py]);
+    free(xx); free(rows);
+    return s;
+}
+
+/* L_photo (Eq. 4 with Eq. 3) averaged over the views:
+ * (1/V) sum_v [(1 - lambda) mean |C_v - I_v| + lambda (1 - mean SSIM(C_v, I_v))],
+ * and its derivatives along six parameter directions.  out[7] = (L, dL[6]). */
 void or_photo_loss_jvp(const float *means, const float *scales, const float *quats, const float *opac,
                        const float *rgb, int64_t n, const double *dirs, const double *poses, int n_views,
-                       const double *cam, const double *p, const double *gt, double *out)
+                       const double *cam, const double *p, const double *gt, double lambda, double *out)
 {
-    const int64_t npx = (int64_t)cam[C_W] * (int64_t)cam[C_H];
+    const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
+    const int64_t npx = (int64_t)Wd * Hd;
     dprec *r = (dprec *)malloc(sizeof(dprec) * (n + 1));
     dual *img = (dual *)malloc(sizeof(dual) * 3 * npx);
     dual loss = dk(0);
-    const double inv = 1.0 / ((double)n_views * 3.0 * (double)npx);
+    const double inv = 1.0 / (3.0 * (double)npx);
     for (int v = 0; v < n_views; ++v) {
         for (int64_t i = 0; i < n; ++i)
             dproject_params(means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], rgb + 3 * i,
                             dirs + (int64_t)NPAR * 6 * i, poses + 16 * v, cam, p, &r[i]);
         dcomposite_view(r, n, cam, p, img);
         const double *I = gt + (int64_t)v * 3 * npx;
+        dual l1 = dk(0);
         for (int64_t k = 0; k < 3 * npx; ++k) {
             dual d = dsub(img[k], dk(I[k]));
-            loss = dadd(loss, dscale(d, (d.v >= 0 ? 1.0 : -1.0) * inv));
+            l1 = dadd(l1, dscale(d, d.v >= 0 ? 1.0 : -1.0));
         }
+        dual lv = dscale(l1, (1.0 - lambda) * inv);
+        if (lambda != 0.0) {
+            dual ss = dk(0);
+            for (int ch = 0; ch < 3; ++ch) ss = dadd(ss, dssim_sum(img + ch * npx, I + ch * npx, Hd, Wd));
+            lv = dadd(lv, dscale(dsub(dk(1.0), dscale(ss, inv)), lambda));
+        }
+        loss = dadd(loss, dscale(lv, 1.0 / n_views));
     }
     out[0] = loss.v;
     for (int k = 0; k < 6; ++k) out[1 + k] = loss.d[k];
