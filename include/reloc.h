@@ -331,8 +331,11 @@ reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_render, const d
  * w_photo and w_reproj; the defaults are 3D Gaussian Splatting's lambda = 0.2
  * and w_photo = w_reproj = 1.  The derivative is that of the render with its
  * inclusion, alpha-skip, clamp and stop decisions fixed, and the right
- * derivative of |x| at 0.  Only lambda = 0 and w_reproj = 0 are accepted
- * (EINVAL otherwise) until the D-SSIM and reprojection terms are added.
+ * derivative of |x| at 0.  D-SSIM = 1 - mean SSIM over the view's pixels
+ * and channels, SSIM of Wang, Bovik, Sheikh and Simoncelli (2004) with an
+ * 11 x 11 Gaussian window (standard deviation 1.5 px), samples outside the
+ * image counting as 0, C1 = 0.01^2, C2 = 0.03^2.  Only w_reproj = 0 is
+ * accepted (EINVAL otherwise) until the reprojection term is added.
  * Adam (Kingma and Ba 2015) updates 3D Gaussian Splatting's latent
  * parameters: mean, log scale, quaternion (as stored; normalised on use),
  * logit opacity, colour, each group with its own learning rate; the scale

@@ -124,7 +124,7 @@ struct reloc_ctx {
     DevBuf pnp_X, pnp_out;
     DevBuf gbuf, gcoef, gpart, gpose;    // NCC pose gradients
     // map training: render and dL/dC scratch, loss, parameter gradients, Adam moments
-    DevBuf trgb, tgimg, tloss, tgrad, adam_m, adam_v;
+    DevBuf trgb, tgimg, tabc, tloss, tgrad, adam_m, adam_v;
     int64_t adam_t = 0;
     PinBuf pin;
     double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
@@ -471,6 +471,7 @@ struct CallOut {
     double *grad = nullptr;                                     // NCC pose gradients [V][6] (device)
     const float *target = nullptr;  // training: target images [V][3][H][W] (device)
     double l1_scale = 0.0;          // training: weight of sum |C - I| in the loss
+    double ssim_scale = 0.0;        // training: weight of sum (1 - SSIM) in the loss
     float *tgrad = nullptr;         // training: dL/dparameters [14][n] (device, accumulated)
     std::vector<double> scores;
     std::vector<int> degen, best;
@@ -705,6 +706,11 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         // map training: the image loss and dL/dC, then back through the blend and the projection
         CK(launch_photo_l1(ctx->trgb.as<float>(), o.target + (int64_t)sb.v0 * 3 * HW, (int64_t)L.V * 3 * HW,
                            o.l1_scale, ctx->tgimg.as<float>(), false, ctx->tloss.as<double>(), st));
+        if (o.ssim_scale > 0) {
+            CK(launch_ssim(ctx->trgb.as<float>(), o.target + (int64_t)sb.v0 * 3 * HW, 3 * L.V, cp.height, cp.width,
+                           o.ssim_scale, ctx->tabc.as<float>(), ctx->tgimg.as<float>(), ctx->tloss.as<double>(), st));
+            launches += 2;
+        }
         CK(cudaMemsetAsync(ctx->gbuf.p, 0, 36 * (size_t)sb.VS, st));
         CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
                              ctx->tgimg.as<float>(), ctx->gbuf.as<float>(), d_overflow, st));
@@ -815,6 +821,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         if (o.target) {
             CKS(ctx->trgb.ensure(12 * (size_t)V * HW));
             CKS(ctx->tgimg.ensure(12 * (size_t)V * HW));
+            if (o.ssim_scale > 0) CKS(ctx->tabc.ensure(36 * (size_t)V * HW));
             CKS(ctx->gbuf.ensure(36 * (size_t)VS));
         }
         if (o.grad) {
@@ -1769,7 +1776,6 @@ static reloc_status train_loss_grad(reloc_ctx *ctx, const reloc_range *ranges, i
     if (!(o.lambda_dssim >= 0 && o.lambda_dssim <= 1) || !(o.w_photo >= 0) || !(o.w_reproj >= 0) ||
         !std::isfinite(o.w_photo) || !std::isfinite(o.w_reproj) || o.views_per_group < 1 || o.views_per_group > 4096)
         return fail(RELOC_EINVAL, "bad training options");
-    if (o.lambda_dssim != 0) return fail(RELOC_EINVAL, "D-SSIM not available yet (lambda_dssim must be 0)");
     if (o.w_reproj != 0) return fail(RELOC_EINVAL, "reprojection loss not available yet (w_reproj must be 0)");
     if (n_ranges < 0 || (n_ranges > 0 && !ranges)) return fail(RELOC_EINVAL, "bad ranges");
     if (cam->width < 1 || cam->height < 1) return fail(RELOC_EINVAL, "bad camera");
@@ -1785,6 +1791,7 @@ static reloc_status train_loss_grad(reloc_ctx *ctx, const reloc_range *ranges, i
     CallOut co;
     co.target = targets_dev;
     co.l1_scale = o.w_photo * (1.0 - o.lambda_dssim) / ((double)n_views * 3.0 * (double)HW);
+    co.ssim_scale = o.w_photo * o.lambda_dssim / ((double)n_views * 3.0 * (double)HW);
     co.tgrad = grad;
     CKS(run_batch(ctx, qs, cam, st, co, false));
     CK(cudaMemcpyAsync(loss_host, ctx->tloss.p, 8, cudaMemcpyDeviceToHost, st));

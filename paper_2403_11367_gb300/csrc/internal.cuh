@@ -195,6 +195,10 @@ cudaError_t launch_pose_chain(const float *mx, const float *my, const float *mz,
 // L1 samples: loss += scale * sum |rgb - target|, gimg (=|+=) scale * sign.
 cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, double scale, float *gimg,
                             bool accumulate, double *loss, cudaStream_t st);
+// D-SSIM over planes channel planes [H][W]: loss += scale * sum (1 - SSIM),
+// gimg += its gradient; abc: 3 * planes * H * W floats of scratch.
+cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H, int W, double scale, float *abc,
+                        float *gimg, double *loss, cudaStream_t st);
 // gin [VS][9] (launch_blend_grad, image mode) -> gmap [14][n_map] (added):
 // mean xyz, scale xyz, quat wxyz, opacity, rgb.  FP32 attributes only.
 cudaError_t launch_param_chain(const float *mx, const float *my, const float *mz, const float *attr, int64_t n_map,

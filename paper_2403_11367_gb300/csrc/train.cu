@@ -2,6 +2,7 @@
 // pixel, the chain rule from per-(view, Gaussian) screen-space gradients to the
 // Gaussians' parameters, and the Adam step on the map.
 #include <algorithm>
+#include <cmath>
 
 #include "internal.cuh"
 
@@ -39,6 +40,170 @@ cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, do
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 256 * 8), 152 * 16);
     k_photo_l1<<<(int)blocks, 256, 0, st>>>(rgb, target, n, (float)scale, scale, gimg, accumulate ? 1 : 0, loss);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- D-SSIM --
+// D-SSIM term of L_rgb (Eq. 3): SSIM of Wang, Bovik, Sheikh and Simoncelli
+// (2004) per channel plane, with local statistics under an 11 x 11 Gaussian
+// window (standard deviation 1.5 px, unit sum; separable, so two 11-tap
+// passes) and samples outside the image counting as 0; C1 = 0.01^2, C2 =
+// 0.03^2.  The loss adds scale * sum over pixels of (1 - SSIM).  A 256-thread
+// block covers a 32 x 8 tile of one plane; its inputs with a 5-pixel halo sit
+// in shared memory.
+constexpr int SS_TW = 32, SS_TH = 8, SS_R = 5, SS_N = 2 * SS_R + 1;
+constexpr int SS_HW = SS_TW + 2 * SS_R, SS_HH = SS_TH + 2 * SS_R;
+constexpr float SS_C1 = 0.01f * 0.01f, SS_C2 = 0.03f * 0.03f;
+
+struct SsimWin {
+    float w[SS_N];   // one-dimensional factor of the window (sums to 1)
+};
+
+static SsimWin ssim_window()
+{
+    double g[SS_N], s = 0.0;
+    for (int k = 0; k < SS_N; ++k) {
+        const double d = k - SS_R;
+        g[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+        s += g[k];
+    }
+    SsimWin w;
+    for (int k = 0; k < SS_N; ++k) w.w[k] = (float)(g[k] / s);
+    return w;
+}
+
+// Forward: per pixel SSIM s and, with dL/ds = -scale, the products of dL/ds
+// with the partial derivatives of s with respect to the local mean of x, the
+// local mean of x^2 and the local mean of x y (A1 = 2 mx my + C1, A2 = 2 sxy +
+// C2, B1 = mx^2 + my^2 + C1, B2 = sx^2 + sy^2 + C2, s = A1 A2 / (B1 B2)):
+//   ds/dmx   = (2 my (A2 - A1) - 2 mx s (B2 - B1)) / (B1 B2)
+//   ds/dE[xx] = -s / B2,  ds/dE[xy] = 2 A1 / (B1 B2),
+// into abc [plane][3][H][W].
+__global__ void __launch_bounds__(SS_TW * SS_TH)
+k_ssim_fwd(const float *__restrict__ x_img, const float *__restrict__ y_img, int H, int W, SsimWin win,
+           float scale, double dscale, float *__restrict__ abc, double *__restrict__ loss)
+{
+    __shared__ float sx[SS_HH][SS_HW], sy[SS_HH][SS_HW];
+    __shared__ float hsum[5][SS_HH][SS_TW];
+    __shared__ double s_red[SS_TW * SS_TH / 32];
+    const int64_t HW = (int64_t)H * W;
+    const int plane = blockIdx.z;
+    const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TH;
+    const float *X = x_img + plane * HW, *Y = y_img + plane * HW;
+    for (int k = threadIdx.x; k < SS_HH * SS_HW; k += SS_TW * SS_TH) {
+        const int r = k / SS_HW, c = k - r * SS_HW;
+        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        sx[r][c] = in ? X[(int64_t)gy * W + gx] : 0.f;
+        sy[r][c] = in ? Y[(int64_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SS_HH * SS_TW; k += SS_TW * SS_TH) {
+        const int r = k / SS_TW, c = k - r * SS_TW;
+        float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+#pragma unroll
+        for (int t = 0; t < SS_N; ++t) {
+            const float a = sx[r][c + t], b = sy[r][c + t], w = win.w[t];
+            m1 = fmaf(w, a, m1);
+            m2 = fmaf(w, b, m2);
+            e11 = fmaf(w * a, a, e11);
+            e22 = fmaf(w * b, b, e22);
+            e12 = fmaf(w * a, b, e12);
+        }
+        hsum[0][r][c] = m1; hsum[1][r][c] = m2; hsum[2][r][c] = e11; hsum[3][r][c] = e22; hsum[4][r][c] = e12;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % SS_TW, ty = threadIdx.x / SS_TW;
+    float q[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < SS_N; ++t) {
+        const float w = win.w[t];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) q[m] = fmaf(w, hsum[m][ty + t][tx], q[m]);
+    }
+    const int gx = x0 + tx, gy = y0 + ty;
+    double contrib = 0.0;
+    if (gx < W && gy < H) {
+        const float mx = q[0], my = q[1];
+        const float vx = q[2] - mx * mx, vy = q[3] - my * my, cxy = q[4] - mx * my;
+        const float A1 = 2.f * mx * my + SS_C1, A2 = 2.f * cxy + SS_C2;
+        const float B1 = mx * mx + my * my + SS_C1, B2 = vx + vy + SS_C2;
+        const float iB = 1.f / (B1 * B2);
+        const float s = A1 * A2 * iB;
+        const float d_m = (2.f * my * (A2 - A1) - 2.f * mx * s * (B2 - B1)) * iB;
+        const float d_xx = -s / B2, d_xy = 2.f * A1 * iB;
+        const int64_t pix = (int64_t)gy * W + gx;
+        float *o = abc + (int64_t)plane * 3 * HW + pix;
+        o[0] = -scale * d_m;
+        o[HW] = -scale * d_xx;
+        o[2 * HW] = -scale * d_xy;
+        contrib = 1.0 - (double)s;
+    }
+    for (int off = 16; off > 0; off >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = contrib;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < SS_TW * SS_TH / 32; ++w) t += s_red[w];
+        atomicAdd(loss, t * dscale);
+    }
+}
+
+// Backward: dL/dx(q) = sum_p w(p - q) (a(p) + 2 x(q) b(p) + y(q) c(p)) over
+// the image's pixels p (the window is symmetric, so the same separable
+// passes), added to gimg.
+__global__ void __launch_bounds__(SS_TW * SS_TH)
+k_ssim_bwd(const float *__restrict__ abc, const float *__restrict__ x_img, const float *__restrict__ y_img, int H,
+           int W, SsimWin win, float *__restrict__ gimg)
+{
+    __shared__ float s3[3][SS_HH][SS_HW];
+    __shared__ float hsum[3][SS_HH][SS_TW];
+    const int64_t HW = (int64_t)H * W;
+    const int plane = blockIdx.z;
+    const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TH;
+    const float *P = abc + (int64_t)plane * 3 * HW;
+    for (int k = threadIdx.x; k < SS_HH * SS_HW; k += SS_TW * SS_TH) {
+        const int r = k / SS_HW, c = k - r * SS_HW;
+        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const int64_t pix = (int64_t)gy * W + gx;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) s3[m][r][c] = in ? P[m * HW + pix] : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SS_HH * SS_TW; k += SS_TW * SS_TH) {
+        const int r = k / SS_TW, c = k - r * SS_TW;
+        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < SS_N; ++t)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) acc[m] = fmaf(win.w[t], s3[m][r][c + t], acc[m]);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) hsum[m][r][c] = acc[m];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % SS_TW, ty = threadIdx.x / SS_TW;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= W || gy >= H) return;
+    float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < SS_N; ++t)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[m] = fmaf(win.w[t], hsum[m][ty + t][tx], acc[m]);
+    const int64_t pix = plane * HW + (int64_t)gy * W + gx;
+    gimg[pix] += acc[0] + 2.f * x_img[pix] * acc[1] + y_img[pix] * acc[2];
+}
+
+cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H, int W, double scale, float *abc,
+                        float *gimg, double *loss, cudaStream_t st)
+{
+    if (planes <= 0) return cudaSuccess;
+    const SsimWin win = ssim_window();
+    dim3 grid((unsigned)ceil_div(W, SS_TW), (unsigned)ceil_div(H, SS_TH), (unsigned)planes);
+    k_ssim_fwd<<<grid, SS_TW * SS_TH, 0, st>>>(rgb, target, H, W, win, (float)scale, scale, abc, loss);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ssim_bwd<<<grid, SS_TW * SS_TH, 0, st>>>(abc, rgb, target, H, W, win, gimg);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@ error; a pair whose inclusion test lies within rounding of its threshold may
 be in one set and not the other, and a sample within rounding of its target
 may take the other sign of |x|); single entries (one-hot directions at the
 Gaussians with the largest gradient of each parameter) within 1e-3 relative.
-The loss equals the oracle's within 1e-4 relative (FP32 render).  Adam steps
+The loss equals the oracle's within 1e-4 relative (FP32 render), with and
+without the D-SSIM term (lambda 0, 0.2, 1).  Adam steps
 lower the loss; the map read back matches what was loaded; invalid maps and
 options fail."""
 import numpy as np
@@ -86,6 +87,24 @@ def test_largest_entries_match_oracle(case):
         for k, (row, i) in enumerate(chunk):
             print(oracle.PARAM_ORDER[row], i, G[row, i], jv[k])
             assert abs(G[row, i] - jv[k]) <= 1e-3 * abs(jv[k])
+
+
+@pytest.mark.parametrize("lam", [0.2, 1.0])
+def test_dssim_loss_and_derivatives_match_oracle(R, case, lam):
+    s, ctx, g, poses, gt32, tg, loss, G = case
+    grad = torch.zeros((14, g.n), device="cuda:0")
+    mine = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, lambda_dssim=lam, w_reproj=0.0)
+    Gl = grad.cpu().numpy().astype(np.float64)
+    r = sg.Rng(91)
+    dirs = (r.u64(g.n * 14 * 6) % np.uint64(3)).astype(np.float64).reshape(g.n, 14, 6) - 1.0
+    ref, jv = oracle.photo_loss_jvp(g, poses, s.camera, gt32, dirs, lam=lam)
+    print("lambda", lam, "loss gpu", mine, "oracle", ref)
+    assert abs(mine - ref) <= 1e-4 * ref
+    for k in range(6):
+        terms = Gl.T * dirs[:, :, k]
+        got, mass = terms.sum(), np.abs(terms).sum()
+        print(k, got, jv[k], mass)
+        assert abs(got - jv[k]) <= 1e-3 * mass + 1e-12
 
 
 def test_gradient_is_zero_outside_the_ranges(R, case):
