@@ -76,8 +76,8 @@ def lib():
             L.or_pnp_backproject.argtypes = [dp, dp, fp, fp, dp, C.c_int64, C.c_double, dp, u8p]
             L.or_pnp_backproject.restype = C.c_int64
             L.or_ncc_pose_grad.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, dp, dp, dp]
-            L.or_photo_loss_jvp.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, C.c_int, dp, dp, dp,
-                                            C.c_double, dp]
+            L.or_train_loss_jvp.argtypes = [fp, fp, fp, fp, fp, C.c_int64, dp, dp, C.c_int, dp, dp, dp,
+                                            C.c_double, C.c_double, C.c_double, C.c_double, dp]
             L.or_ssim_map.argtypes = [dp, dp, C.c_int, C.c_int, dp]
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_int64, u64p]
             L.or_search_order.argtypes = [C.c_uint64, C.c_int64, i32p]
@@ -308,24 +308,31 @@ PARAM_ORDER = ["mean_x", "mean_y", "mean_z", "scale_x", "scale_y", "scale_z", "q
                "quat_z", "opacity", "red", "green", "blue"]
 
 
-def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0):
-    """Map-training loss L_photo (Sec. III-B.3, Eqs. 3-4: per view
-    (1 - lam) mean |render - gt| + lam (1 - mean SSIM), averaged over the
-    views) and its derivatives along six directions dirs [n, 14, 6] in the
-    Gaussians' parameters (PARAM_ORDER), forward mode in FP64 (SH degree 0).
-    Returns (loss, jvp[6])."""
+def train_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0, w_photo=1.0, w_reproj=0.0, alpha_min=0.5):
+    """Map-training loss of Sec. III-B.3 (Eq. 6: w_photo L_photo + w_reproj
+    L_reproj, each an L_rgb of Eq. 3: (1 - lam) mean |x - y| + lam (1 - mean
+    SSIM); L_photo over the views' renders, L_reproj over consecutive view
+    pairs, I_{t+1} re-projected into view t through the rendered depth D / A
+    where A >= alpha_min) and its derivatives along six directions dirs
+    [n, 14, 6] in the Gaussians' parameters (PARAM_ORDER), forward mode in
+    FP64 (SH degree 0).  Returns (loss, jvp[6])."""
     if g.sh_degree != 0:
         raise ValueError("map training needs SH degree 0")
     prm = params() if prm is None else prm
     m, s, q, o, sh = _gauss_ptrs(g)
     poses = _c(poses, np.float64).reshape(-1, 16)
     out = np.zeros(7)
-    lib().or_photo_loss_jvp(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
+    lib().or_train_loss_jvp(_p(m, C.c_float), _p(s, C.c_float), _p(q, C.c_float), _p(o, C.c_float),
                             _p(sh, C.c_float), g.n, _p(_c(dirs, np.float64), C.c_double),
                             _p(poses, C.c_double), poses.shape[0], _p(camvec(cam), C.c_double),
                             _p(_c(prm, np.float64), C.c_double), _p(_c(gt, np.float64), C.c_double),
-                            float(lam), _p(out, C.c_double))
+                            float(lam), float(w_photo), float(w_reproj), float(alpha_min), _p(out, C.c_double))
     return out[0], out[1:]
+
+
+def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0):
+    """L_photo alone (Eqs. 3-4): train_loss_jvp with w_photo = 1, w_reproj = 0."""
+    return train_loss_jvp(g, poses, cam, gt, dirs, prm, lam=lam, w_photo=1.0, w_reproj=0.0)
 
 
 def ssim_map(x, y):

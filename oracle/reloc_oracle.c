@@ -18,6 +18,7 @@
  *   - block (2D voxel) selection around a coarse pose            (Sec. III-B.2, III-C.1)
  *   - argmax over the candidate grid                             (Sec. III-C.1)
  *   - map-training loss L_rgb = (1 - lambda) L1 + lambda D-SSIM  (Sec. III-B.3, Eq. 3)
+ *     in L = w_photo L_photo + w_reproj L_reproj                  (Eqs. 4-6)
  *     with SSIM of Wang, Bovik, Sheikh and Simoncelli (2004), and its
  *     derivatives along parameter directions (forward mode)
  * plus an integer replay of the tile|depth key build and stable sort so the
@@ -1066,7 +1067,7 @@ void or_ncc_pose_grad(const float *means, const float *scales, const float *quat
 /* dirs: [n][14][6] tangents.  out: [7] = loss and its six derivatives.       */
 /* ========================================================================= */
 enum { NPAR = 14 };
-typedef struct { dual u, v, A, B, C, o, col[3]; double z, rx, ry; int vis; } dprec;
+typedef struct { dual u, v, A, B, C, o, col[3], zd; double z, rx, ry; int vis; } dprec;
 
 static void dproject_params(const float *mu, const float *scale, const float *quat, float opac, const float *rgb,
                             const double *dir, const double *W, const double *cam, const double *p, dprec *out)
@@ -1135,13 +1136,15 @@ static void dproject_params(const float *mu, const float *scale, const float *qu
     out->rx = p[P_CUT] * sqrt(a.v); out->ry = p[P_CUT] * sqrt(c.v);
     if (out->u.v + out->rx < 0 || out->u.v - out->rx >= cam[C_W] || out->v.v + out->ry < 0 || out->v.v - out->ry >= cam[C_H])
         return;
-    out->z = t[2].v; out->o = o;
+    out->z = t[2].v; out->zd = t[2]; out->o = o;
     for (int i = 0; i < 3; ++i) out->col[i] = col[i];
     out->vis = 1;
 }
 
-/* Composite one view in duals: img[3][H][W] duals (caller-allocated). */
-static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const double *p, dual *img)
+/* Composite one view in duals: img[3][H][W] duals (caller-allocated); dep and
+ * alp [H][W] (may be NULL): depth D = sum w z and alpha A = sum w. */
+static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const double *p, dual *img, dual *dep,
+                            dual *alp)
 {
     const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
     const int64_t npx = (int64_t)Wd * Hd;
@@ -1156,7 +1159,12 @@ static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const 
     msort_by_double(order, tmp, nv, zkey);
     dual *T = (dual *)malloc(sizeof(dual) * npx);
     uint8_t *done = (uint8_t *)calloc(npx, 1);
-    for (int64_t k = 0; k < npx; ++k) { T[k] = dk(1.0); img[k] = img[npx + k] = img[2 * npx + k] = dk(0); }
+    for (int64_t k = 0; k < npx; ++k) {
+        T[k] = dk(1.0);
+        img[k] = img[npx + k] = img[2 * npx + k] = dk(0);
+        if (dep) dep[k] = dk(0);
+        if (alp) alp[k] = dk(0);
+    }
     const double lim = -0.5 * p[P_CUT] * p[P_CUT];
     for (int64_t j = 0; j < nv; ++j) {
         const dprec *g = &r[order[j]];
@@ -1179,6 +1187,8 @@ static void dcomposite_view(const dprec *r, int64_t n, const double *cam, const 
                 if (tn.v < p[P_T_MIN]) { done[k] = 1; continue; }
                 dual wgt = dmul(al, T[k]);
                 for (int ch = 0; ch < 3; ++ch) img[ch * npx + k] = dadd(img[ch * npx + k], dmul(wgt, g->col[ch]));
+                if (dep) dep[k] = dadd(dep[k], dmul(wgt, g->zd));
+                if (alp) alp[k] = dadd(alp[k], wgt);
                 T[k] = tn;
             }
     }
@@ -1279,39 +1289,104 @@ static dual dssim_sum(const dual *x, const double *y, int H, int W)
     return s;
 }
 
-/* L_photo (Eq. 4 with Eq. 3) averaged over the views:
- * (1/V) sum_v [(1 - lambda) mean |C_v - I_v| + lambda (1 - mean SSIM(C_v, I_v))],
- * and its derivatives along six parameter directions.  out[7] = (L, dL[6]). */
-void or_photo_loss_jvp(const float *means, const float *scales, const float *quats, const float *opac,
-                       const float *rgb, int64_t n, const double *dirs, const double *poses, int n_views,
-                       const double *cam, const double *p, const double *gt, double lambda, double *out)
+/* L_rgb (Eq. 3) of one view's image x (duals, [3][H][W]) against y:
+ * (1 - lambda) mean |x - y| + lambda (1 - mean SSIM(x, y)). */
+static dual drgb_loss(const dual *x, const double *y, int H, int W, double lambda)
+{
+    const int64_t npx = (int64_t)H * W;
+    const double inv = 1.0 / (3.0 * (double)npx);
+    dual l1 = dk(0);
+    for (int64_t k = 0; k < 3 * npx; ++k) {
+        dual d = dsub(x[k], dk(y[k]));
+        l1 = dadd(l1, dscale(d, d.v >= 0 ? 1.0 : -1.0));
+    }
+    dual l = dscale(l1, (1.0 - lambda) * inv);
+    if (lambda != 0.0) {
+        dual ss = dk(0);
+        for (int ch = 0; ch < 3; ++ch) ss = dadd(ss, dssim_sum(x + ch * npx, y + ch * npx, H, W));
+        l = dadd(l, dscale(dsub(dk(1.0), dscale(ss, inv)), lambda));
+    }
+    return l;
+}
+
+/* ---- re-projection (the P of Eq. 5) ---------------------------------------
+ * Reading: the pairs are consecutive training views (t, t+1).  A pixel p of
+ * view t whose rendered alpha A = sum w (1 - T) reaches alpha_min takes the
+ * depth d = D / A of its rendered depth D (the depth equation of Sec. III-A),
+ * is lifted to the camera point d ((p_x + 0.5 - cx) / fx, (p_y + 0.5 - cy) /
+ * fy, 1), carried through the world into view t+1 (poses W_t, W_{t+1}) and
+ * projected to q; when q lies in front of the near plane and its four
+ * bilinear neighbours (pixel centres at +0.5) lie in the image, the
+ * re-projected image at p is I_{t+1} sampled bilinearly at q, otherwise it
+ * keeps I_t(p) (no residual).  out [3][H][W] duals. */
+static void dwarp_view(const dual *dep, const dual *alp, const double *Wt, const double *Wn, const double *cam,
+                       const double *p, double alpha_min, const double *It, const double *In, dual *out)
 {
     const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
     const int64_t npx = (int64_t)Wd * Hd;
+    for (int py = 0; py < Hd; ++py)
+        for (int px = 0; px < Wd; ++px) {
+            const int64_t k = (int64_t)py * Wd + px;
+            for (int ch = 0; ch < 3; ++ch) out[ch * npx + k] = dk(It[ch * npx + k]);
+            if (!(alp[k].v >= alpha_min)) continue;
+            const dual d = ddiv(dep[k], alp[k]);
+            const double ray[3] = {(px + 0.5 - cam[C_CX]) / cam[C_FX], (py + 0.5 - cam[C_CY]) / cam[C_FY], 1.0};
+            dual Pc[3], X[3], Pn[3];
+            for (int i = 0; i < 3; ++i) Pc[i] = dsub(dscale(d, ray[i]), dk(Wt[4 * i + 3]));
+            for (int i = 0; i < 3; ++i)   /* X = R_t^T (P_c - t_t) */
+                X[i] = dadd(dadd(dscale(Pc[0], Wt[i]), dscale(Pc[1], Wt[4 + i])), dscale(Pc[2], Wt[8 + i]));
+            for (int i = 0; i < 3; ++i)
+                Pn[i] = dadd(dadd(dadd(dscale(X[0], Wn[4 * i]), dscale(X[1], Wn[4 * i + 1])), dscale(X[2], Wn[4 * i + 2])),
+                             dk(Wn[4 * i + 3]));
+            if (!(Pn[2].v > p[P_NEAR])) continue;
+            const dual sx = dadd(dscale(ddiv(Pn[0], Pn[2]), cam[C_FX]), dk(cam[C_CX] - 0.5));
+            const dual sy = dadd(dscale(ddiv(Pn[1], Pn[2]), cam[C_FY]), dk(cam[C_CY] - 0.5));
+            const double x0 = floor(sx.v), y0 = floor(sy.v);
+            if (!(x0 >= 0 && x0 <= Wd - 2 && y0 >= 0 && y0 <= Hd - 2)) continue;
+            const dual fx = dsub(sx, dk(x0)), fy = dsub(sy, dk(y0));
+            const dual gx = dsub(dk(1.0), fx), gy = dsub(dk(1.0), fy);
+            const int64_t k00 = (int64_t)y0 * Wd + (int64_t)x0;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double *I = In + ch * npx;
+                out[ch * npx + k] = dadd(dadd(dscale(dmul(gx, gy), I[k00]), dscale(dmul(fx, gy), I[k00 + 1])),
+                                         dadd(dscale(dmul(gx, fy), I[k00 + Wd]), dscale(dmul(fx, fy), I[k00 + Wd + 1])));
+            }
+        }
+}
+
+/* The map-training loss of Eq. 6, L = w_photo L_photo + w_reproj L_reproj:
+ * L_photo = (1/V) sum_t L_rgb(R(G, W_t), I_t) (Eq. 4), L_reproj = (1/(V-1))
+ * sum over consecutive pairs of L_rgb(P(D(G_t), ...), I_t) (Eq. 5, the
+ * re-projection read as above), and its derivatives along six parameter
+ * directions.  out[7] = (L, dL[6]). */
+void or_train_loss_jvp(const float *means, const float *scales, const float *quats, const float *opac,
+                       const float *rgb, int64_t n, const double *dirs, const double *poses, int n_views,
+                       const double *cam, const double *p, const double *gt, double lambda, double w_photo,
+                       double w_reproj, double alpha_min, double *out)
+{
+    const int Wd = (int)cam[C_W], Hd = (int)cam[C_H];
+    const int64_t npx = (int64_t)Wd * Hd;
+    const int reproj = w_reproj != 0.0 && n_views > 1;
     dprec *r = (dprec *)malloc(sizeof(dprec) * (n + 1));
     dual *img = (dual *)malloc(sizeof(dual) * 3 * npx);
+    dual *dep = reproj ? (dual *)malloc(sizeof(dual) * npx) : NULL;
+    dual *alp = reproj ? (dual *)malloc(sizeof(dual) * npx) : NULL;
+    dual *wimg = reproj ? (dual *)malloc(sizeof(dual) * 3 * npx) : NULL;
     dual loss = dk(0);
-    const double inv = 1.0 / (3.0 * (double)npx);
     for (int v = 0; v < n_views; ++v) {
         for (int64_t i = 0; i < n; ++i)
             dproject_params(means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], rgb + 3 * i,
                             dirs + (int64_t)NPAR * 6 * i, poses + 16 * v, cam, p, &r[i]);
-        dcomposite_view(r, n, cam, p, img);
+        const int pair = reproj && v + 1 < n_views;
+        dcomposite_view(r, n, cam, p, img, pair ? dep : NULL, pair ? alp : NULL);
         const double *I = gt + (int64_t)v * 3 * npx;
-        dual l1 = dk(0);
-        for (int64_t k = 0; k < 3 * npx; ++k) {
-            dual d = dsub(img[k], dk(I[k]));
-            l1 = dadd(l1, dscale(d, d.v >= 0 ? 1.0 : -1.0));
+        if (w_photo != 0.0) loss = dadd(loss, dscale(drgb_loss(img, I, Hd, Wd, lambda), w_photo / n_views));
+        if (pair) {
+            dwarp_view(dep, alp, poses + 16 * v, poses + 16 * (v + 1), cam, p, alpha_min, I, I + 3 * npx, wimg);
+            loss = dadd(loss, dscale(drgb_loss(wimg, I, Hd, Wd, lambda), w_reproj / (n_views - 1)));
         }
-        dual lv = dscale(l1, (1.0 - lambda) * inv);
-        if (lambda != 0.0) {
-            dual ss = dk(0);
-            for (int ch = 0; ch < 3; ++ch) ss = dadd(ss, dssim_sum(img + ch * npx, I + ch * npx, Hd, Wd));
-            lv = dadd(lv, dscale(dsub(dk(1.0), dscale(ss, inv)), lambda));
-        }
-        loss = dadd(loss, dscale(lv, 1.0 / n_views));
     }
     out[0] = loss.v;
     for (int k = 0; k < 6; ++k) out[1 + k] = loss.d[k];
-    free(r); free(img);
+    free(r); free(img); free(dep); free(alp); free(wimg);
 }
