@@ -334,8 +334,17 @@ reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_render, const d
  * derivative of |x| at 0.  D-SSIM = 1 - mean SSIM over the view's pixels
  * and channels, SSIM of Wang, Bovik, Sheikh and Simoncelli (2004) with an
  * 11 x 11 Gaussian window (standard deviation 1.5 px), samples outside the
- * image counting as 0, C1 = 0.01^2, C2 = 0.03^2.  Only w_reproj = 0 is
- * accepted (EINVAL otherwise) until the reprojection term is added.
+ * image counting as 0, C1 = 0.01^2, C2 = 0.03^2.  L_reproj (Eq. 5) is read
+ * as: for each pair of consecutive views (t, t+1) in the order given, a
+ * pixel p of view t whose rendered alpha A (= sum w) reaches
+ * reproj_alpha_min takes the depth d = D / A (D = sum w z, the depth
+ * equation of Sec. III-A), is lifted to d ((x + 0.5 - cx) / fx, (y + 0.5 -
+ * cy) / fy, 1), carried into view t+1 by the two poses and projected; in
+ * front of the near plane, with its four bilinear neighbours (pixel centres
+ * at +0.5) inside the image, the re-projected image at p is I_{t+1} sampled
+ * bilinearly there, otherwise I_t(p); L_reproj averages L_rgb(re-projected
+ * image, I_t) over the V - 1 pairs (0 when V = 1).  Its gradient reaches the
+ * map through D and A.
  * Adam (Kingma and Ba 2015) updates 3D Gaussian Splatting's latent
  * parameters: mean, log scale, quaternion (as stored; normalised on use),
  * logit opacity, colour, each group with its own learning rate; the scale
@@ -349,6 +358,7 @@ typedef struct reloc_train_options {
     double lr_opacity;         /* logit per step: 5e-2                                */
     double lr_color;           /* 2.5e-3                                              */
     double beta1, beta2, eps;  /* Adam: 0.9, 0.999, 1e-15                             */
+    double reproj_alpha_min;   /* pixels of L_reproj need rendered alpha >= this: 0.5 */
     int32_t views_per_group;   /* views rendered per group (one gathered copy of the
                                   subset each; bounds the workspace): 16              */
     int32_t reserved[7];

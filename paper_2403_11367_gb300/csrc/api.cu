@@ -125,6 +125,7 @@ struct reloc_ctx {
     DevBuf gbuf, gcoef, gpart, gpose;    // NCC pose gradients
     // map training: render and dL/dC scratch, loss, parameter gradients, Adam moments
     DevBuf trgb, tgimg, tabc, tloss, tgrad, adam_m, adam_v;
+    DevBuf tdep, talp, twarp, tjac, tgw, tgda, trel;     // re-projection loss
     int64_t adam_t = 0;
     PinBuf pin;
     double inst_ratio = 3.0;        // instance capacity per (view, subset Gaussian), learned
@@ -472,6 +473,10 @@ struct CallOut {
     const float *target = nullptr;  // training: target images [V][3][H][W] (device)
     double l1_scale = 0.0;          // training: weight of sum |C - I| in the loss
     double ssim_scale = 0.0;        // training: weight of sum (1 - SSIM) in the loss
+    int n_views_total = 0;          // training: views of the call (pairs are (t, t+1))
+    double rp_l1_scale = 0.0, rp_ssim_scale = 0.0;   // training: re-projection loss weights
+    float rp_alpha_min = 0.5f;
+    const float *rel = nullptr;     // training: relative poses [n_views_total][12] (device)
     float *tgrad = nullptr;         // training: dL/dparameters [14][n] (device, accumulated)
     std::vector<double> scores;
     std::vector<int> degen, best;
@@ -696,9 +701,11 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         launches += 2;
     }
     float *rgb_out = o.target ? ctx->trgb.as<float>() : (o.rgb ? o.rgb + (int64_t)sb.v0 * 3 * HW : nullptr);
+    const bool rp = o.target && o.rel;
+    float *dep_out = rp ? ctx->tdep.as<float>() : (o.depth ? o.depth + (int64_t)sb.v0 * HW : nullptr);
+    float *alp_out = rp ? ctx->talp.as<float>() : (o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr);
     CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
-                    o.score ? ctx->partials.as<double>() : nullptr, rgb_out,
-                    o.depth ? o.depth + (int64_t)sb.v0 * HW : nullptr, o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr,
+                    o.score ? ctx->partials.as<double>() : nullptr, rgb_out, dep_out, alp_out,
                     nullptr, 0, d_overflow, st));
     launches += 1;
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
@@ -711,9 +718,31 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
                            o.ssim_scale, ctx->tabc.as<float>(), ctx->tgimg.as<float>(), ctx->tloss.as<double>(), st));
             launches += 2;
         }
-        CK(cudaMemsetAsync(ctx->gbuf.p, 0, 36 * (size_t)sb.VS, st));
+        if (rp) {
+            // re-projection loss over the pairs (t, t+1) whose first view is in this sub-batch
+            const int np = std::max(0, std::min(L.V, o.n_views_total - 1 - sb.v0));
+            const float *tg = o.target + (int64_t)sb.v0 * 3 * HW;
+            CK(cudaMemsetAsync(ctx->tgda.p, 0, 8 * (size_t)L.V * HW, st));
+            if (np > 0) {
+                CK(launch_reproj_warp(ctx->tdep.as<float>(), ctx->talp.as<float>(), tg, o.rel + 12 * (int64_t)sb.v0,
+                                      np, cp, o.rp_alpha_min, ctx->twarp.as<float>(), ctx->tjac.as<float>(), st));
+                CK(launch_photo_l1(ctx->twarp.as<float>(), tg, (int64_t)np * 3 * HW, o.rp_l1_scale,
+                                   ctx->tgw.as<float>(), false, ctx->tloss.as<double>(), st));
+                launches += 2;
+                if (o.rp_ssim_scale > 0) {
+                    CK(launch_ssim(ctx->twarp.as<float>(), tg, 3 * np, cp.height, cp.width, o.rp_ssim_scale,
+                                   ctx->tabc.as<float>(), ctx->tgw.as<float>(), ctx->tloss.as<double>(), st));
+                    launches += 2;
+                }
+                CK(launch_reproj_back(ctx->tgw.as<float>(), ctx->tjac.as<float>(), ctx->tdep.as<float>(),
+                                      ctx->talp.as<float>(), np, HW, o.rp_alpha_min, ctx->tgda.as<float>(), st));
+                launches += 1;
+            }
+        }
+        CK(cudaMemsetAsync(ctx->gbuf.p, 0, 40 * (size_t)sb.VS, st));
         CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
-                             ctx->tgimg.as<float>(), ctx->gbuf.as<float>(), d_overflow, st));
+                             ctx->tgimg.as<float>(), rp ? ctx->tgda.as<float>() : nullptr, ctx->gbuf.as<float>(),
+                             d_overflow, st));
         CK(launch_param_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
                               ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.as<float>(), ctx->n,
                               ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(), o.tgrad,
@@ -728,7 +757,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         if (o.grad) {
             CK(cudaMemsetAsync(ctx->gbuf.p, 0, 20 * (size_t)sb.VS, st));
             CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
-                                 ctx->gcoef.as<double>(), nullptr, ctx->gbuf.as<float>(), d_overflow, st));
+                                 ctx->gcoef.as<double>(), nullptr, nullptr, ctx->gbuf.as<float>(), d_overflow, st));
             CK(launch_pose_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
                                  ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.p, ctx->precision, ctx->n,
                                  ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(),
@@ -821,8 +850,16 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         if (o.target) {
             CKS(ctx->trgb.ensure(12 * (size_t)V * HW));
             CKS(ctx->tgimg.ensure(12 * (size_t)V * HW));
-            if (o.ssim_scale > 0) CKS(ctx->tabc.ensure(36 * (size_t)V * HW));
-            CKS(ctx->gbuf.ensure(36 * (size_t)VS));
+            CKS(ctx->gbuf.ensure(40 * (size_t)VS));
+            if (o.ssim_scale > 0 || o.rp_ssim_scale > 0) CKS(ctx->tabc.ensure(36 * (size_t)V * HW));
+            if (o.rel) {
+                CKS(ctx->tdep.ensure(4 * (size_t)V * HW));
+                CKS(ctx->talp.ensure(4 * (size_t)V * HW));
+                CKS(ctx->twarp.ensure(12 * (size_t)V * HW));
+                CKS(ctx->tjac.ensure(12 * (size_t)V * HW));
+                CKS(ctx->tgw.ensure(12 * (size_t)V * HW));
+                CKS(ctx->tgda.ensure(8 * (size_t)V * HW));
+            }
         }
         if (o.grad) {
             int64_t pb = 1;
@@ -1760,6 +1797,7 @@ extern "C" void reloc_default_train_options(reloc_train_options *opt)
     opt->beta1 = 0.9;
     opt->beta2 = 0.999;
     opt->eps = 1e-15;
+    opt->reproj_alpha_min = 0.5;
     opt->views_per_group = 16;
 }
 
@@ -1776,7 +1814,8 @@ static reloc_status train_loss_grad(reloc_ctx *ctx, const reloc_range *ranges, i
     if (!(o.lambda_dssim >= 0 && o.lambda_dssim <= 1) || !(o.w_photo >= 0) || !(o.w_reproj >= 0) ||
         !std::isfinite(o.w_photo) || !std::isfinite(o.w_reproj) || o.views_per_group < 1 || o.views_per_group > 4096)
         return fail(RELOC_EINVAL, "bad training options");
-    if (o.w_reproj != 0) return fail(RELOC_EINVAL, "reprojection loss not available yet (w_reproj must be 0)");
+    if (!(o.reproj_alpha_min > 0) || !std::isfinite(o.reproj_alpha_min))
+        return fail(RELOC_EINVAL, "reproj_alpha_min must be > 0");
     if (n_ranges < 0 || (n_ranges > 0 && !ranges)) return fail(RELOC_EINVAL, "bad ranges");
     if (cam->width < 1 || cam->height < 1) return fail(RELOC_EINVAL, "bad camera");
     const int64_t HW = (int64_t)cam->width * cam->height;
@@ -1792,6 +1831,31 @@ static reloc_status train_loss_grad(reloc_ctx *ctx, const reloc_range *ranges, i
     co.target = targets_dev;
     co.l1_scale = o.w_photo * (1.0 - o.lambda_dssim) / ((double)n_views * 3.0 * (double)HW);
     co.ssim_scale = o.w_photo * o.lambda_dssim / ((double)n_views * 3.0 * (double)HW);
+    co.n_views_total = n_views;
+    if (o.w_reproj > 0 && n_views > 1) {
+        // relative pose of each view to the next: P_{t+1} = R_rel P_t + t_rel
+        std::vector<float> rel((size_t)12 * n_views, 0.f);
+        for (int t = 0; t + 1 < n_views; ++t) {
+            const double *A = poses + 16 * (size_t)t, *B = poses + 16 * (size_t)(t + 1);
+            for (int k = 0; k < 16; ++k)
+                if (!std::isfinite(A[k]) || !std::isfinite(B[k])) return fail(RELOC_ENUMERIC, "non-finite pose");
+            double R[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    R[3 * i + j] = B[4 * i] * A[4 * j] + B[4 * i + 1] * A[4 * j + 1] + B[4 * i + 2] * A[4 * j + 2];
+            for (int i = 0; i < 9; ++i) rel[12 * (size_t)t + i] = (float)R[i];
+            for (int i = 0; i < 3; ++i)
+                rel[12 * (size_t)t + 9 + i] =
+                    (float)(B[4 * i + 3] - (R[3 * i] * A[3] + R[3 * i + 1] * A[7] + R[3 * i + 2] * A[11]));
+        }
+        CKS(ctx->trel.ensure(sizeof(float) * rel.size()));
+        CK(cudaMemcpyAsync(ctx->trel.p, rel.data(), sizeof(float) * rel.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        co.rel = ctx->trel.as<float>();
+        co.rp_l1_scale = o.w_reproj * (1.0 - o.lambda_dssim) / ((double)(n_views - 1) * 3.0 * (double)HW);
+        co.rp_ssim_scale = o.w_reproj * o.lambda_dssim / ((double)(n_views - 1) * 3.0 * (double)HW);
+        co.rp_alpha_min = (float)o.reproj_alpha_min;
+    }
     co.tgrad = grad;
     CKS(run_batch(ctx, qs, cam, st, co, false));
     CK(cudaMemcpyAsync(loss_host, ctx->tloss.p, 8, cudaMemcpyDeviceToHost, st));

@@ -179,10 +179,11 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // K6 backward: per (view, Gaussian) gradients with respect to the projected
 // mean and conic.  gimg null: of the view's NCC (coef from K7), added into
 // gout[vd_off[v] + i][5] (u, v, a, b, c).  gimg [V][3][H][W] = dL/dC of an
-// image loss: added into gout[vd_off[v] + i][9] (u, v, a, b, c, r, g, b, opacity).
+// image loss (gda [V][2][H][W] = dL/d(depth, alpha), may be null): added into
+// gout[vd_off[v] + i][10] (u, v, a, b, c, r, g, b, opacity, z).
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                              const CamParams &cam, const double *coef, const float *gimg, float *gout,
-                              const int *overflow, cudaStream_t st);
+                              const CamParams &cam, const double *coef, const float *gimg, const float *gda,
+                              float *gout, const int *overflow, cudaStream_t st);
 
 // Chain of gin to each view's left pose update: out[V][6] (rho, phi);
 // part: n_blocks * V * 6 doubles of scratch.
@@ -199,7 +200,15 @@ cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, do
 // gimg += its gradient; abc: 3 * planes * H * W floats of scratch.
 cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H, int W, double scale, float *abc,
                         float *gimg, double *loss, cudaStream_t st);
-// gin [VS][9] (launch_blend_grad, image mode) -> gmap [14][n_map] (added):
+// Re-projection of Eq. 5 for n_views consecutive pairs: targets holds views
+// 0 .. n_views (n_views + 1 images), rel [n_views][12] the relative poses;
+// warped, jac [n_views][3][H][W]; then gda [n_views][2][H][W] = dL/d(D, A).
+cudaError_t launch_reproj_warp(const float *dep, const float *alp, const float *targets, const float *rel,
+                               int n_views, const CamParams &cam, float alpha_min, float *warped, float *jac,
+                               cudaStream_t st);
+cudaError_t launch_reproj_back(const float *gw, const float *jac, const float *dep, const float *alp, int n_views,
+                               int64_t HW, float alpha_min, float *gda, cudaStream_t st);
+// gin [VS][10] (launch_blend_grad, image mode) -> gmap [14][n_map] (added):
 // mean xyz, scale xyz, quat wxyz, opacity, rgb.  FP32 attributes only.
 cudaError_t launch_param_chain(const float *mx, const float *my, const float *mz, const float *attr, int64_t n_map,
                                const uint32_t *gidx, const Layout &L, int n_blocks, const ViewParams *views,

@@ -466,15 +466,19 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // and adds them to the (view, Gaussian) entry of gout.
 // IMG = false: L is the view's NCC (G from coef), five outputs (u, v, a, b, c).
 // IMG = true: G is given per pixel (gimg [V][3][H][W], an image loss's
-// gradient); nine outputs: also dL/d colour = sum w G and dL/d opacity =
-// dL/d alpha exp(power) (alpha unclamped).
+// gradient), and optionally the gradients G_D, G_A with respect to the
+// pixel's depth D = sum w z and alpha A = sum w (gda [V][2][H][W]), which
+// enter dL/d alpha_j like two more channels with values z_j and 1; ten
+// outputs: also dL/d colour = sum w G, dL/d opacity = dL/d alpha exp(power)
+// (alpha unclamped) and dL/dz = sum w G_D.
 template <int TW, int TH, bool IMG>
 __global__ void __launch_bounds__(32)
 k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
              const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
-             const float *__restrict__ gimg, float *__restrict__ gout, const int *__restrict__ overflow)
+             const float *__restrict__ gimg, const float *__restrict__ gda, float *__restrict__ gout,
+             const int *__restrict__ overflow)
 {
-    constexpr int NOUT = IMG ? 9 : 5;
+    constexpr int NOUT = IMG ? 10 : 5;
     constexpr int WPT = TW * TH / 64;
     constexpr int WROWS = 64 / TW;
     __shared__ float4 s_a[32], s_b[32], s_c[32];
@@ -538,11 +542,13 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     // pass 1: final colour of the pixel pair
     float T[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
     float C[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float DA[2][2] = {{0, 0}, {0, 0}};     // depth and alpha of the pixel (image mode)
     for (int b = r.x; b < r.y; b += 32) {
         if (__all_sync(0xffffffffu, T[0] == 0.f && T[1] == 0.f)) break;
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k];
+            const float zk = s_a[k].z;
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 float dx, dy;
@@ -555,6 +561,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                     } else {
                         const float w = al * T[p];
                         C[p][0] += c.x * w; C[p][1] += c.y * w; C[p][2] += c.z * w;
+                        if (IMG) { DA[p][0] += zk * w; DA[p][1] += w; }
                         T[p] = tn;
                     }
                 }
@@ -565,6 +572,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     // dL/dC per pixel
     const int64_t HW = (int64_t)cam.width * cam.height;
     float G[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float GDA[2][2] = {{0, 0}, {0, 0}};
     if (IMG) {
         const float *gi = gimg + (int64_t)v * 3 * HW;
 #pragma unroll
@@ -573,6 +581,10 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) G[p][ch] = __ldg(gi + ch * HW + pix);
+                if (gda) {
+                    GDA[p][0] = __ldg(gda + (int64_t)v * 2 * HW + pix);
+                    GDA[p][1] = __ldg(gda + (int64_t)v * 2 * HW + HW + pix);
+                }
             }
     } else {
         // NCC: dNCC/dC = (q - mean q) / sqrt(var_r var_q) - NCC (C - mean r) / var_r
@@ -591,12 +603,13 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     // pass 2: front to back again, gradients per record
     float Tb[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
     float U[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float UDA[2][2] = {{0, 0}, {0, 0}};
     for (int b = r.x; b < r.y; b += 32) {
         if (__all_sync(0xffffffffu, Tb[0] == 0.f && Tb[1] == 0.f)) break;
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k], bb = s_b[k];
-            const float opac = s_a[k].w;
+            const float opac = s_a[k].w, zk = s_a[k].z;
             float g[NOUT];
 #pragma unroll
             for (int m = 0; m < NOUT; ++m) g[m] = 0.f;
@@ -613,8 +626,12 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                         const float w = al * Tb[p];
                         const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
                                              C[p][2] - U[p][2] - c.z * w};
-                        const float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
-                                          (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) / (1.f - al);
+                        float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
+                                    (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) / (1.f - al);
+                        if (IMG) {
+                            const float da = DA[p][0] - UDA[p][0] - zk * w, aa = DA[p][1] - UDA[p][1] - w;
+                            gal += Tb[p] * (GDA[p][0] * zk + GDA[p][1]) - (GDA[p][0] * da + GDA[p][1] * aa) / (1.f - al);
+                        }
                         const float gp = un ? gal * al : 0.f;
                         g[0] += gp * (bb.x * dx + bb.y * dy);
                         g[1] += gp * (bb.y * dx + bb.z * dy);
@@ -626,6 +643,9 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                             g[6] += w * G[p][1];
                             g[7] += w * G[p][2];
                             g[8] += un ? gal * (al / opac) : 0.f;
+                            g[9] += w * GDA[p][0];
+                            UDA[p][0] += zk * w;
+                            UDA[p][1] += w;
                         }
                         U[p][0] += c.x * w; U[p][1] += c.y * w; U[p][2] += c.z * w;
                         Tb[p] = tn;
@@ -650,25 +670,27 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
 
 template <int TW, int TH>
 static cudaError_t blend_grad_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                                const CamParams &cam, const double *coef, const float *gimg, float *gout,
-                                const int *overflow, cudaStream_t st)
+                                const CamParams &cam, const double *coef, const float *gimg, const float *gda,
+                                float *gout, const int *overflow, cudaStream_t st)
 {
     dim3 grid(cam.n_tiles * (TW * TH / 64), L.V);
     if (gimg)
-        k_blend_grad<TW, TH, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow);
+        k_blend_grad<TW, TH, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout,
+                                                        overflow);
     else
-        k_blend_grad<TW, TH, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow);
+        k_blend_grad<TW, TH, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout,
+                                                         overflow);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
-                              const CamParams &cam, const double *coef, const float *gimg, float *gout,
-                              const int *overflow, cudaStream_t st)
+                              const CamParams &cam, const double *coef, const float *gimg, const float *gda,
+                              float *gout, const int *overflow, cudaStream_t st)
 {
     if (L.V <= 0) return cudaSuccess;
 #define RELOC_GRAD_CASE(W_, H_) \
     if (cam.tile_w == W_ && cam.tile_h == H_) \
-        return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gimg, gout, overflow, st);
+        return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout, overflow, st);
     RELOC_GRAD_CASE(16, 16)
     RELOC_GRAD_CASE(8, 8)
     RELOC_GRAD_CASE(32, 8)

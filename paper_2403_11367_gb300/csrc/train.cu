@@ -207,10 +207,116 @@ cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------- re-projection --
+// The P of Eq. 5 for the consecutive training views (t, t+1): a pixel p of
+// view t whose rendered alpha A reaches alpha_min takes the depth d = D / A,
+// is lifted to d * ray(p) (ray = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1))
+// and carried into view t+1 by the relative pose (rel[12] = R_rel row-major,
+// t_rel: P = R_rel d ray + t_rel); in front of the near plane, with the four
+// bilinear neighbours of q = (fx P_x / P_z + cx, fy P_y / P_z + cy) (pixel
+// centres at +0.5) inside the image, the re-projected image takes I_{t+1}
+// sampled there and jac the derivative of that sample with respect to d;
+// otherwise it keeps I_t(p) and jac = 0.  A thread per pixel.
+__global__ void __launch_bounds__(256)
+k_reproj_warp(const float *__restrict__ dep, const float *__restrict__ alp, const float *__restrict__ targets,
+              const float *__restrict__ rel, int n_views, int H, int W, float fx, float fy, float cx, float cy,
+              float near_plane, float alpha_min, float *__restrict__ warped, float *__restrict__ jac)
+{
+    const int64_t HW = (int64_t)H * W;
+    const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (idx >= (int64_t)n_views * HW) return;
+    const int v = (int)(idx / HW);
+    const int64_t pix = idx - (int64_t)v * HW;
+    const int py = (int)(pix / W), px = (int)(pix - (int64_t)py * W);
+    const float *It = targets + (int64_t)v * 3 * HW, *In = It + 3 * HW;
+    float *wo = warped + (int64_t)v * 3 * HW + pix, *jo = jac + (int64_t)v * 3 * HW + pix;
+    const float A = alp[idx];
+    bool ok = A >= alpha_min;
+    float out[3] = {It[pix], It[HW + pix], It[2 * HW + pix]}, dj[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+        const float d = dep[idx] / A;
+        const float r0 = ((float)px + 0.5f - cx) / fx, r1 = ((float)py + 0.5f - cy) / fy;
+        const float *M = rel + 12 * v;
+        const float m0 = M[0] * r0 + M[1] * r1 + M[2], m1 = M[3] * r0 + M[4] * r1 + M[5];
+        const float m2 = M[6] * r0 + M[7] * r1 + M[8];
+        const float P0 = fmaf(d, m0, M[9]), P1 = fmaf(d, m1, M[10]), P2 = fmaf(d, m2, M[11]);
+        ok = P2 > near_plane;
+        if (ok) {
+            const float iz = 1.f / P2;
+            const float sx = fx * P0 * iz + (cx - 0.5f), sy = fy * P1 * iz + (cy - 0.5f);
+            const float x0 = floorf(sx), y0 = floorf(sy);
+            ok = x0 >= 0.f && x0 <= (float)(W - 2) && y0 >= 0.f && y0 <= (float)(H - 2);
+            if (ok) {
+                const float ax = sx - x0, ay = sy - y0;
+                const float dsx = fx * (m0 * P2 - P0 * m2) * iz * iz, dsy = fy * (m1 * P2 - P1 * m2) * iz * iz;
+                const int64_t k00 = (int64_t)y0 * W + (int64_t)x0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float *I = In + c * HW;
+                    const float i00 = I[k00], i01 = I[k00 + 1], i10 = I[k00 + W], i11 = I[k00 + W + 1];
+                    out[c] = (1.f - ax) * (1.f - ay) * i00 + ax * (1.f - ay) * i01 + (1.f - ax) * ay * i10 +
+                             ax * ay * i11;
+                    const float gx = (1.f - ay) * (i01 - i00) + ay * (i11 - i10);
+                    const float gy = (1.f - ax) * (i10 - i00) + ax * (i11 - i01);
+                    dj[c] = gx * dsx + gy * dsy;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        wo[c * HW] = out[c];
+        jo[c * HW] = dj[c];
+    }
+}
+
+// dL/dD = g_d / A and dL/dA = -g_d D / A^2 with g_d = sum_c dL/dwarped_c *
+// jac_c (d = D / A), into gda [v][2][H][W]; 0 where the pixel had no sample.
+__global__ void __launch_bounds__(256)
+k_reproj_back(const float *__restrict__ gw, const float *__restrict__ jac, const float *__restrict__ dep,
+              const float *__restrict__ alp, int n_views, int64_t HW, float alpha_min, float *__restrict__ gda)
+{
+    const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (idx >= (int64_t)n_views * HW) return;
+    const int v = (int)(idx / HW);
+    const int64_t pix = idx - (int64_t)v * HW;
+    const float *g = gw + (int64_t)v * 3 * HW + pix, *j = jac + (int64_t)v * 3 * HW + pix;
+    const float gd = g[0] * j[0] + g[HW] * j[HW] + g[2 * HW] * j[2 * HW];
+    const float A = alp[idx];
+    float gD = 0.f, gA = 0.f;
+    if (A >= alpha_min && gd != 0.f) {
+        gD = gd / A;
+        gA = -gd * dep[idx] / (A * A);
+    }
+    gda[(int64_t)v * 2 * HW + pix] = gD;
+    gda[(int64_t)v * 2 * HW + HW + pix] = gA;
+}
+
+cudaError_t launch_reproj_warp(const float *dep, const float *alp, const float *targets, const float *rel,
+                               int n_views, const CamParams &cam, float alpha_min, float *warped, float *jac,
+                               cudaStream_t st)
+{
+    const int64_t n = (int64_t)n_views * cam.width * cam.height;
+    if (n <= 0) return cudaSuccess;
+    k_reproj_warp<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(dep, alp, targets, rel, n_views, cam.height, cam.width,
+                                                              cam.fx, cam.fy, cam.cx, cam.cy, cam.near_plane,
+                                                              alpha_min, warped, jac);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reproj_back(const float *gw, const float *jac, const float *dep, const float *alp, int n_views,
+                               int64_t HW, float alpha_min, float *gda, cudaStream_t st)
+{
+    const int64_t n = (int64_t)n_views * HW;
+    if (n <= 0) return cudaSuccess;
+    k_reproj_back<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(gw, jac, dep, alp, n_views, HW, alpha_min, gda);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------- parameter chain --
 // gin holds, per (view, subset Gaussian), the gradients of the loss with
-// respect to the projected mean (u, v), the conic (a, b, c), the colour and
-// the opacity (k_blend_grad, image mode).  A thread per subset Gaussian walks
+// respect to the projected mean (u, v), the conic (a, b, c), the colour, the
+// opacity and the camera depth z = t_z (k_blend_grad, image mode).  A thread per subset Gaussian walks
 // its query's views and carries them back through the projection (Sec. III-A:
 // Sigma' = J W Sigma W^T J^T + 0.3 I, conic = Sigma'^-1, t = W mu):
 //   dL/dSigma' = -A G_A A                       (G_A = [[ga, gb/2], [gb/2, gc]])
@@ -260,11 +366,11 @@ k_param_chain(const float *__restrict__ mx, const float *__restrict__ my, const 
     bool any = false;
     for (int vv = 0; vv < V; ++vv) {
         const int v = v_begin + vv;
-        const float *g9 = gin + 9 * (L.vd_off[v] + i);
-        const float gu = g9[0], gv = g9[1], ga = g9[2], gb = g9[3], gc = g9[4];
-        const float gr = g9[5], gg = g9[6], gbl = g9[7], go = g9[8];
+        const float *g10 = gin + 10 * (L.vd_off[v] + i);
+        const float gu = g10[0], gv = g10[1], ga = g10[2], gb = g10[3], gc = g10[4];
+        const float gr = g10[5], gg = g10[6], gbl = g10[7], go = g10[8], gz = g10[9];
         if (gu == 0.f && gv == 0.f && ga == 0.f && gb == 0.f && gc == 0.f && gr == 0.f && gg == 0.f &&
-            gbl == 0.f && go == 0.f)
+            gbl == 0.f && go == 0.f && gz == 0.f)
             continue;
         any = true;
         gcol[0] += gr; gcol[1] += gg; gcol[2] += gbl;
@@ -319,7 +425,7 @@ k_param_chain(const float *__restrict__ mx, const float *__restrict__ my, const 
         const float dJ11 = dT[3] * P.R[3] + dT[4] * P.R[4] + dT[5] * P.R[5];
         const float dJ12 = dT[3] * P.R[6] + dT[4] * P.R[7] + dT[5] * P.R[8];
         float gt0 = gu * cam.fx * iz, gt1 = gv * cam.fy * iz;
-        float gt2 = -(gu * cam.fx * t[0] + gv * cam.fy * t[1]) * iz * iz;
+        float gt2 = gz - (gu * cam.fx * t[0] + gv * cam.fy * t[1]) * iz * iz;
         gt2 += -(dJ00 * cam.fx + dJ11 * cam.fy) * iz * iz;
         gt2 += dJ02 * cam.fx * xz * iz * iz;
         gt2 += dJ12 * cam.fy * yz * iz * iz;

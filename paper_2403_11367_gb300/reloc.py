@@ -94,7 +94,8 @@ class TrainOptions(C.Structure):
     _fields_ = [("lambda_dssim", C.c_double), ("w_photo", C.c_double), ("w_reproj", C.c_double),
                 ("lr_mean", C.c_double), ("lr_scale", C.c_double), ("lr_quat", C.c_double),
                 ("lr_opacity", C.c_double), ("lr_color", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
-                ("eps", C.c_double), ("views_per_group", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("eps", C.c_double), ("reproj_alpha_min", C.c_double), ("views_per_group", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class Counts(C.Structure):

@@ -10,7 +10,9 @@ be in one set and not the other, and a sample within rounding of its target
 may take the other sign of |x|); single entries (one-hot directions at the
 Gaussians with the largest gradient of each parameter) within 1e-3 relative.
 The loss equals the oracle's within 1e-4 relative (FP32 render), with and
-without the D-SSIM term (lambda 0, 0.2, 1).  Adam steps
+without the D-SSIM term (lambda 0, 0.2, 1), for the re-projection term alone
+and for the weighted total of Eq. 6 (which does not depend on how the views
+are grouped).  Adam steps
 lower the loss; the map read back matches what was loaded; invalid maps and
 options fail."""
 import numpy as np
@@ -107,6 +109,42 @@ def test_dssim_loss_and_derivatives_match_oracle(R, case, lam):
         assert abs(got - jv[k]) <= 1e-3 * mass + 1e-12
 
 
+def _check_against_oracle(ctx, g, poses, s, tg, gt32, seed, **opts):
+    grad = torch.zeros((14, g.n), device="cuda:0")
+    mine = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, **opts)
+    Gl = grad.cpu().numpy().astype(np.float64)
+    r = sg.Rng(seed)
+    dirs = (r.u64(g.n * 14 * 6) % np.uint64(3)).astype(np.float64).reshape(g.n, 14, 6) - 1.0
+    ref, jv = oracle.train_loss_jvp(g, poses, s.camera, gt32, dirs, lam=opts["lambda_dssim"],
+                                    w_photo=opts["w_photo"], w_reproj=opts["w_reproj"])
+    print(opts, "loss gpu", mine, "oracle", ref)
+    assert abs(mine - ref) <= 1e-4 * ref
+    for k in range(6):
+        terms = Gl.T * dirs[:, :, k]
+        got, mass = terms.sum(), np.abs(terms).sum()
+        print(k, got, jv[k], mass)
+        assert abs(got - jv[k]) <= 1e-3 * mass + 1e-12
+    return mine, Gl
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_reprojection_loss_and_derivatives_match_oracle(R, case, lam):
+    s, ctx, g, poses, gt32, tg, loss, G = case
+    _check_against_oracle(ctx, g, poses, s, tg, gt32, 101, lambda_dssim=lam, w_photo=0.0, w_reproj=1.0)
+
+
+def test_total_loss_matches_oracle_and_groups_do_not_matter(R, case):
+    s, ctx, g, poses, gt32, tg, loss, G = case
+    opts = dict(lambda_dssim=0.2, w_photo=0.7, w_reproj=1.3)
+    L, Gl = _check_against_oracle(ctx, g, poses, s, tg, gt32, 103, **opts)
+    # one view per group: each pair's two views fall in different groups
+    grad = torch.zeros((14, g.n), device="cuda:0")
+    L1 = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, views_per_group=1, **opts)
+    G1 = grad.cpu().numpy().astype(np.float64)
+    assert abs(L1 - L) <= 1e-6 * L
+    assert np.abs(G1 - Gl).max() <= 1e-4 * np.abs(Gl).max()
+
+
 def test_gradient_is_zero_outside_the_ranges(R, case):
     s, ctx, g, poses, gt32, tg, loss, G = case
     half = ctx.n // 2
@@ -158,6 +196,13 @@ def test_invalid_training_calls(R):
     with pytest.raises(R.RelocError) as e:
         ctx.train_step([(0, ctx.n)], poses, s.camera, tg, **dict(L1_ONLY, beta1=1.0))
     assert e.value.status == R.EINVAL
+    with pytest.raises(R.RelocError) as e:
+        ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, reproj_alpha_min=0.0)
+    assert e.value.status == R.EINVAL
+    # one view: no pair, the re-projection term is 0 and the call is valid
+    L0 = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, lambda_dssim=0.2, w_reproj=0.0)
+    L1 = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, lambda_dssim=0.2, w_reproj=1.0)
+    assert L0 == L1
     street = sg.street_gaussians(20000, seed=3, sh_degree=3)
     ctx.load_map(street)
     with pytest.raises(R.RelocError) as e:
