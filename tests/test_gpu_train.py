@@ -202,7 +202,7 @@ def test_invalid_training_calls(R):
     # one view: no pair, the re-projection term is 0 and the call is valid
     L0 = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, lambda_dssim=0.2, w_reproj=0.0)
     L1 = ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, grad, lambda_dssim=0.2, w_reproj=1.0)
-    assert L0 == L1
+    assert abs(L0 - L1) <= 1e-12 * L0          # FP64 atomic sums: order varies
     street = sg.street_gaussians(20000, seed=3, sh_degree=3)
     ctx.load_map(street)
     with pytest.raises(R.RelocError) as e:
