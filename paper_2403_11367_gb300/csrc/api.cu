@@ -741,8 +741,9 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         }
         CK(cudaMemsetAsync(ctx->gbuf.p, 0, 40 * (size_t)sb.VS, st));
         CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
-                             ctx->tgimg.as<float>(), rp ? ctx->tgda.as<float>() : nullptr, ctx->gbuf.as<float>(),
-                             d_overflow, st));
+                             ctx->tgimg.as<float>(), rp ? ctx->tgda.as<float>() : nullptr, ctx->trgb.as<float>(),
+                             rp ? ctx->tdep.as<float>() : nullptr, rp ? ctx->talp.as<float>() : nullptr,
+                             ctx->gbuf.as<float>(), d_overflow, st));
         CK(launch_param_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
                               ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.as<float>(), ctx->n,
                               ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(), o.tgrad,
@@ -757,7 +758,8 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         if (o.grad) {
             CK(cudaMemsetAsync(ctx->gbuf.p, 0, 20 * (size_t)sb.VS, st));
             CK(launch_blend_grad(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
-                                 ctx->gcoef.as<double>(), nullptr, nullptr, ctx->gbuf.as<float>(), d_overflow, st));
+                                 ctx->gcoef.as<double>(), nullptr, nullptr, nullptr, nullptr, nullptr,
+                                 ctx->gbuf.as<float>(), d_overflow, st));
             CK(launch_pose_chain(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n,
                                  ctx->mean.as<float>() + 2 * ctx->n, ctx->attr.p, ctx->precision, ctx->n,
                                  ctx->gidx.as<uint32_t>(), L, sb.pblk, sb.d_views, cp, ctx->gbuf.as<float>(),

@@ -180,10 +180,13 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // mean and conic.  gimg null: of the view's NCC (coef from K7), added into
 // gout[vd_off[v] + i][5] (u, v, a, b, c).  gimg [V][3][H][W] = dL/dC of an
 // image loss (gda [V][2][H][W] = dL/d(depth, alpha), may be null): added into
-// gout[vd_off[v] + i][10] (u, v, a, b, c, r, g, b, opacity, z).
+// gout[vd_off[v] + i][10] (u, v, a, b, c, r, g, b, opacity, z); cimg (may be
+// null) [V][3][H][W] the views' forward render (cdep, calp [V][H][W] its depth
+// and alpha, needed with gda) so the colour need not be composited again.
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                               const CamParams &cam, const double *coef, const float *gimg, const float *gda,
-                              float *gout, const int *overflow, cudaStream_t st);
+                              const float *cimg, const float *cdep, const float *calp, float *gout,
+                              const int *overflow, cudaStream_t st);
 
 // Chain of gin to each view's left pose update: out[V][6] (rho, phi);
 // part: n_blocks * V * 6 doubles of scratch.

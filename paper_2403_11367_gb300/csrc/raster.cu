@@ -28,6 +28,31 @@ __device__ __forceinline__ float warp_sum_f(float x)
     return x;
 }
 
+// Warp reduce-scatter of NP values per lane (NP a power of two, 2 .. 16):
+// recursive halving, each step exchanging half of the remaining values with
+// the partner lane (offsets 16, 8, ...), then a plain sum over the last
+// 32 / NP lanes.  Returns the warp's total of value (lane / (32 / NP)) on
+// every lane: (NP - 1) + log2(32 / NP) shuffles instead of 5 NP for NP
+// separate sums.
+template <int NP>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NP], int lane)
+{
+#pragma unroll
+    for (int n = NP, o = 16; n > 1; n >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float send = up ? v[i] : v[n / 2 + i];
+            const float keep = up ? v[n / 2 + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    float x = v[0];
+#pragma unroll
+    for (int o = 16 / NP; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 // Fixed grid and fixed reduction order: the sums are deterministic.
 // grid (QS_BLOCKS, Q): block (b, q) sums its share of query q.
 __global__ void __launch_bounds__(QS_THREADS) k_query_stats(Layout L, int64_t n, double *part)
@@ -471,14 +496,20 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // enter dL/d alpha_j like two more channels with values z_j and 1; ten
 // outputs: also dL/d colour = sum w G, dL/d opacity = dL/d alpha exp(power)
 // (alpha unclamped) and dL/dz = sum w G_D.
+// cimg (image mode, may be null): the forward's render of the views
+// ([V][3][H][W], with cdep, calp [V][H][W] when gda is given) replaces the
+// first walk.
 template <int TW, int TH, bool IMG>
 __global__ void __launch_bounds__(32)
 k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
              const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
-             const float *__restrict__ gimg, const float *__restrict__ gda, float *__restrict__ gout,
+             const float *__restrict__ gimg, const float *__restrict__ gda, const float *__restrict__ cimg,
+             const float *__restrict__ cdep, const float *__restrict__ calp, float *__restrict__ gout,
              const int *__restrict__ overflow)
 {
     constexpr int NOUT = IMG ? 10 : 5;
+    constexpr int NP = IMG ? 16 : 8;           // NOUT padded to a power of two
+    constexpr int GRP = 32 / NP;                // lanes holding each total
     constexpr int WPT = TW * TH / 64;
     constexpr int WROWS = 64 / TW;
     __shared__ float4 s_a[32], s_b[32], s_c[32];
@@ -539,11 +570,25 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         return al >= cam.alpha_min ? al : 0.f;
     };
 
+    const int64_t HW = (int64_t)cam.width * cam.height;
     // pass 1: final colour of the pixel pair
     float T[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
     float C[2][3] = {{0, 0, 0}, {0, 0, 0}};
     float DA[2][2] = {{0, 0}, {0, 0}};     // depth and alpha of the pixel (image mode)
-    for (int b = r.x; b < r.y; b += 32) {
+    if (IMG && cimg) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            if (in[p]) {
+                const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) C[p][ch] = __ldg(cimg + ((int64_t)v * 3 + ch) * HW + pix);
+                if (gda) {
+                    DA[p][0] = __ldg(cdep + (int64_t)v * HW + pix);
+                    DA[p][1] = __ldg(calp + (int64_t)v * HW + pix);
+                }
+            }
+    }
+    for (int b = r.x; b < ((IMG && cimg) ? r.x : r.y); b += 32) {
         if (__all_sync(0xffffffffu, T[0] == 0.f && T[1] == 0.f)) break;
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
@@ -570,7 +615,6 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         __syncwarp();
     }
     // dL/dC per pixel
-    const int64_t HW = (int64_t)cam.width * cam.height;
     float G[2][3] = {{0, 0, 0}, {0, 0, 0}};
     float GDA[2][2] = {{0, 0}, {0, 0}};
     if (IMG) {
@@ -610,9 +654,10 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k], bb = s_b[k];
             const float opac = s_a[k].w, zk = s_a[k].z;
-            float g[NOUT];
+            float g[NP];
 #pragma unroll
-            for (int m = 0; m < NOUT; ++m) g[m] = 0.f;
+            for (int m = 0; m < NP; ++m) g[m] = 0.f;
+            bool touched = false;
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 float dx = 0.f, dy = 0.f;
@@ -623,6 +668,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                     if (tn < cam.t_min) {
                         Tb[p] = 0.f;
                     } else {
+                        touched = true;
                         const float w = al * Tb[p];
                         const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
                                              C[p][2] - U[p][2] - c.z * w};
@@ -652,17 +698,11 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                     }
                 }
             }
-            bool any = false;
-#pragma unroll
-            for (int m = 0; m < NOUT; ++m) {
-                g[m] = warp_sum_f(g[m]);
-                any = any || g[m] != 0.f;
-            }
-            if (lane == 0 && any) {
-                float *o = gout + NOUT * (L.vd_off[v] + (int64_t)s_g[k]);
-#pragma unroll
-                for (int m = 0; m < NOUT; ++m) atomicAdd(o + m, g[m]);
-            }
+            if (!__any_sync(0xffffffffu, touched)) continue;
+            const float tot = warp_reduce_scatter<NP>(g, lane);
+            const int m = lane / GRP;
+            if (lane % GRP == 0 && m < NOUT && tot != 0.f)
+                atomicAdd(gout + NOUT * (L.vd_off[v] + (int64_t)s_g[k]) + m, tot);
         }
         __syncwarp();
     }
@@ -671,26 +711,29 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
 template <int TW, int TH>
 static cudaError_t blend_grad_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                                 const CamParams &cam, const double *coef, const float *gimg, const float *gda,
-                                float *gout, const int *overflow, cudaStream_t st)
+                                const float *cimg, const float *cdep, const float *calp, float *gout,
+                                const int *overflow, cudaStream_t st)
 {
     dim3 grid(cam.n_tiles * (TW * TH / 64), L.V);
     if (gimg)
-        k_blend_grad<TW, TH, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout,
-                                                        overflow);
+        k_blend_grad<TW, TH, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, cimg, cdep,
+                                                        calp, gout, overflow);
     else
-        k_blend_grad<TW, TH, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout,
-                                                         overflow);
+        k_blend_grad<TW, TH, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, nullptr,
+                                                         nullptr, nullptr, gout, overflow);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_grad(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                               const CamParams &cam, const double *coef, const float *gimg, const float *gda,
-                              float *gout, const int *overflow, cudaStream_t st)
+                              const float *cimg, const float *cdep, const float *calp, float *gout,
+                              const int *overflow, cudaStream_t st)
 {
     if (L.V <= 0) return cudaSuccess;
 #define RELOC_GRAD_CASE(W_, H_) \
     if (cam.tile_w == W_ && cam.tile_h == H_) \
-        return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, gout, overflow, st);
+        return blend_grad_t<W_, H_>(rec, L, inst_gauss, ranges, cam, coef, gimg, gda, cimg, cdep, calp, gout, \
+                                    overflow, st);
     RELOC_GRAD_CASE(16, 16)
     RELOC_GRAD_CASE(8, 8)
     RELOC_GRAD_CASE(32, 8)
