@@ -500,7 +500,7 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // ([V][3][H][W], with cdep, calp [V][H][W] when gda is given) replaces the
 // first walk.
 template <int TW, int TH, bool IMG>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32, IMG ? 24 : 32)     // NCC mode: 64 registers, no spills
 k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
              const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
              const float *__restrict__ gimg, const float *__restrict__ gda, const float *__restrict__ cimg,
@@ -558,13 +558,15 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         return __popc(keep);
     };
     // alpha of a kept record at pixel p (0 if excluded), unclamped flag
-    auto alpha_at = [&](int k, int p, float &dx, float &dy, bool &unclamped) -> float {
+    // ex = exp(power) = alpha / o while unclamped
+    auto alpha_at = [&](int k, int p, float &dx, float &dy, bool &unclamped, float &ex) -> float {
         const float4 a = s_a[k], b = s_b[k];
         dx = fxp - a.x;
         dy = fyp[p] - a.y;
         const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
         if (!(power >= lim)) return 0.f;
-        const float raw = a.w * __expf(power);
+        ex = __expf(power);
+        const float raw = a.w * ex;
         unclamped = raw < cam.alpha_max;
         const float al = fminf(cam.alpha_max, raw);
         return al >= cam.alpha_min ? al : 0.f;
@@ -598,7 +600,8 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             for (int p = 0; p < 2; ++p) {
                 float dx, dy;
                 bool un = false;
-                const float al = T[p] > 0.f ? alpha_at(k, p, dx, dy, un) : 0.f;
+                float ex = 0.f;
+                const float al = T[p] > 0.f ? alpha_at(k, p, dx, dy, un, ex) : 0.f;
                 if (al > 0.f) {
                     const float tn = T[p] * (1.f - al);
                     if (tn < cam.t_min) {
@@ -653,7 +656,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k], bb = s_b[k];
-            const float opac = s_a[k].w, zk = s_a[k].z;
+            const float zk = s_a[k].z;
             float g[NP];
 #pragma unroll
             for (int m = 0; m < NP; ++m) g[m] = 0.f;
@@ -662,7 +665,8 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             for (int p = 0; p < 2; ++p) {
                 float dx = 0.f, dy = 0.f;
                 bool un = false;
-                const float al = Tb[p] > 0.f ? alpha_at(k, p, dx, dy, un) : 0.f;
+                float ex = 0.f;
+                const float al = Tb[p] > 0.f ? alpha_at(k, p, dx, dy, un, ex) : 0.f;
                 if (al > 0.f) {
                     const float tn = Tb[p] * (1.f - al);
                     if (tn < cam.t_min) {
@@ -672,11 +676,13 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                         const float w = al * Tb[p];
                         const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
                                              C[p][2] - U[p][2] - c.z * w};
+                        // 1 / (1 - alpha), alpha <= alpha_max < 1: fast reciprocal (2 ulp)
+                        const float r1a = __fdividef(1.f, 1.f - al);
                         float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
-                                    (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) / (1.f - al);
+                                    (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) * r1a;
                         if (IMG) {
                             const float da = DA[p][0] - UDA[p][0] - zk * w, aa = DA[p][1] - UDA[p][1] - w;
-                            gal += Tb[p] * (GDA[p][0] * zk + GDA[p][1]) - (GDA[p][0] * da + GDA[p][1] * aa) / (1.f - al);
+                            gal += Tb[p] * (GDA[p][0] * zk + GDA[p][1]) - (GDA[p][0] * da + GDA[p][1] * aa) * r1a;
                         }
                         const float gp = un ? gal * al : 0.f;
                         g[0] += gp * (bb.x * dx + bb.y * dy);
@@ -688,7 +694,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                             g[5] += w * G[p][0];
                             g[6] += w * G[p][1];
                             g[7] += w * G[p][2];
-                            g[8] += un ? gal * (al / opac) : 0.f;
+                            g[8] += un ? gal * ex : 0.f;
                             g[9] += w * GDA[p][0];
                             UDA[p][0] += zk * w;
                             UDA[p][1] += w;
