@@ -647,24 +647,15 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                     G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
             }
     }
-    // pass 2: front to back again, gradients per record.  Per pixel, with
-    // S_j = G . c_j (+ G_D z_j + G_A in image mode) the record's value seen
-    // through G, K = sum over the contributors after j of w S, so that
-    // dL/d alpha_j = T_j S_j - K / (1 - alpha_j); K starts at G . C (+ G_D D +
-    // G_A A) and loses w_j S_j at record j.  The derivatives by u, v, a, b, c
-    // are summed as raw moments (sum gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2,
-    // gp = dL/d power) and turned into gradients once per record.
+    // pass 2: front to back again, gradients per record
     float Tb[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
-    float K[2];
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-        K[p] = G[p][0] * C[p][0] + G[p][1] * C[p][1] + G[p][2] * C[p][2] +
-               (IMG ? GDA[p][0] * DA[p][0] + GDA[p][1] * DA[p][1] : 0.f);
+    float U[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float UDA[2][2] = {{0, 0}, {0, 0}};
     for (int b = r.x; b < r.y; b += 32) {
         if (__all_sync(0xffffffffu, Tb[0] == 0.f && Tb[1] == 0.f)) break;
         const int nk = stage(b);
         for (int k = 0; k < nk; ++k) {
-            const float4 c = s_c[k];
+            const float4 c = s_c[k], bb = s_b[k];
             const float zk = s_a[k].z;
             float g[NP];
 #pragma unroll
@@ -683,40 +674,39 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                     } else {
                         touched = true;
                         const float w = al * Tb[p];
-                        float S = G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z;
-                        if (IMG) S += GDA[p][0] * zk + GDA[p][1];
-                        K[p] -= w * S;
+                        const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
+                                             C[p][2] - U[p][2] - c.z * w};
                         // 1 / (1 - alpha), alpha <= alpha_max < 1: fast reciprocal (2 ulp)
-                        const float gal = Tb[p] * S - K[p] * __fdividef(1.f, 1.f - al);
+                        const float r1a = __fdividef(1.f, 1.f - al);
+                        float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
+                                    (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) * r1a;
+                        if (IMG) {
+                            const float da = DA[p][0] - UDA[p][0] - zk * w, aa = DA[p][1] - UDA[p][1] - w;
+                            gal += Tb[p] * (GDA[p][0] * zk + GDA[p][1]) - (GDA[p][0] * da + GDA[p][1] * aa) * r1a;
+                        }
                         const float gp = un ? gal * al : 0.f;
-                        const float gx = gp * dx, gy = gp * dy;
-                        g[0] += gx;
-                        g[1] += gy;
-                        g[2] += gx * dx;
-                        g[3] += gx * dy;
-                        g[4] += gy * dy;
+                        g[0] += gp * (bb.x * dx + bb.y * dy);
+                        g[1] += gp * (bb.y * dx + bb.z * dy);
+                        g[2] += gp * (-0.5f * dx * dx);
+                        g[3] += gp * (-dx * dy);
+                        g[4] += gp * (-0.5f * dy * dy);
                         if (IMG) {
                             g[5] += w * G[p][0];
                             g[6] += w * G[p][1];
                             g[7] += w * G[p][2];
                             g[8] += un ? gal * ex : 0.f;
                             g[9] += w * GDA[p][0];
+                            UDA[p][0] += zk * w;
+                            UDA[p][1] += w;
                         }
+                        U[p][0] += c.x * w; U[p][1] += c.y * w; U[p][2] += c.z * w;
                         Tb[p] = tn;
                     }
                 }
             }
             if (!__any_sync(0xffffffffu, touched)) continue;
-            float tot = warp_reduce_scatter<NP>(g, lane);
-            // moments -> gradients: d power/du = a dx + b dy, d/dv = b dx + c dy,
-            // d/da = -dx^2 / 2, d/db = -dx dy, d/dc = -dy^2 / 2
-            const float other = __shfl_xor_sync(0xffffffffu, tot, GRP);
+            const float tot = warp_reduce_scatter<NP>(g, lane);
             const int m = lane / GRP;
-            const float4 bb = s_b[k];
-            if (m == 0) tot = bb.x * tot + bb.y * other;
-            else if (m == 1) tot = bb.y * other + bb.z * tot;
-            else if (m == 2 || m == 4) tot *= -0.5f;
-            else if (m == 3) tot = -tot;
             if (lane % GRP == 0 && m < NOUT && tot != 0.f)
                 atomicAdd(gout + NOUT * (L.vd_off[v] + (int64_t)s_g[k]) + m, tot);
         }
