@@ -779,6 +779,22 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_leg(args):
+    import torch
+    from paper_2403_11367_gb300.build import build
+    build()
+    import scenegen as sg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cam = sg.street_camera()
+    stream = torch.cuda.current_stream(dev)
+    if args.leg == "map_training":
+        out = run_train_leg(cam, dev, stream, steps=args.steps, warmup=args.warmup)
+    else:
+        out = run_ascent_leg(cam, dev, stream)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -787,8 +803,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batching, learned-proposal and precision legs")
+    ap.add_argument("--leg", choices=["map_training", "pose_ascent"],
+                    help="run one self-contained leg alone on cuda:0 and print its JSON object")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.leg:
+        run_leg(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
