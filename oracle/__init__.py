@@ -120,9 +120,9 @@ def _c(a, dt):
 DEFAULT_PARAMS = dict(near=0.2, fov_clamp=1.3, eps2d=0.3, alpha_min=1.0 / 255.0, alpha_max=0.99,
                       t_min=1e-4, cut=3.0, tile_w=16, tile_h=16,
                       flag_power=1e-5, flag_alpha=1e-5, flag_t=1e-3, flag_depth=1e-6, flag_sig=1e-5,
-                      flag_pos=2e-4)
+                      flag_pos=2e-4, ncc_gray=0)
 _PORDER = ["near", "fov_clamp", "eps2d", "alpha_min", "alpha_max", "t_min", "cut", "tile_w", "tile_h",
-           "flag_power", "flag_alpha", "flag_t", "flag_depth", "flag_sig", "flag_pos"]
+           "flag_power", "flag_alpha", "flag_t", "flag_depth", "flag_sig", "flag_pos", "ncc_gray"]
 
 
 def params(**over) -> np.ndarray:

@@ -39,7 +39,8 @@
  *   - SH degree 0 is plain RGB; degree >= 1 is max(0, sum c_lm Y_lm(dir) + 0.5)
  *     with real orthonormal SH (Condon-Shortley phase), dir = mu - camera centre;
  *   - depth order: ascending camera depth, ties by Gaussian index;
- *   - NCC over all 3*H*W samples as one vector with one mean each.
+ *   - NCC over all 3*H*W samples as one vector with one mean each (or, with
+ *     the P_NCC_GRAY parameter, over the H*W gray values (R + G + B) / 3).
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC (no fast-math: IEEE FP64 throughout).
  */
@@ -60,6 +61,7 @@ enum {
     P_NEAR = 0, P_FOV_CLAMP, P_EPS2D, P_ALPHA_MIN, P_ALPHA_MAX, P_T_MIN, P_CUT,
     P_TILE_W, P_TILE_H,
     P_FLAG_POWER, P_FLAG_ALPHA, P_FLAG_T, P_FLAG_DEPTH, P_FLAG_SIG, P_FLAG_POS,
+    P_NCC_GRAY,           /* != 0: NCC over the gray values (R + G + B) / 3 */
     P_COUNT = 16
 };
 
@@ -665,7 +667,17 @@ void or_render_views(const float *means, const float *scales, const float *quats
         }
         if (query && scores) {
             int dg = 0;
-            scores[v] = or_ncc(img, query, 3 * npx, &dg);
+            if (p[P_NCC_GRAY] != 0) {
+                double *gi = (double *)malloc(sizeof(double) * (npx + 1)), *gq = (double *)malloc(sizeof(double) * (npx + 1));
+                for (int64_t k = 0; k < npx; ++k) {
+                    gi[k] = (img[k] + img[npx + k] + img[2 * npx + k]) / 3.0;
+                    gq[k] = (query[k] + query[npx + k] + query[2 * npx + k]) / 3.0;
+                }
+                scores[v] = or_ncc(gi, gq, npx, &dg);
+                free(gi); free(gq);
+            } else {
+                scores[v] = or_ncc(img, query, 3 * npx, &dg);
+            }
             if (degenerate) degenerate[v] = dg;
         }
         if (!rgb) free(img);
@@ -1031,21 +1043,35 @@ void or_ncc_pose_grad(const float *means, const float *scales, const float *quat
                 s->T = tn;
             }
     }
-    /* NCC over all 3 H W samples, two-pass, in duals (query constant) */
-    const int64_t ns = 3 * npx;
+    /* NCC over all 3 H W samples (or the H W gray values), two-pass, in duals
+     * (query constant) */
+    const int gray = p[P_NCC_GRAY] != 0;
+    const int nch = gray ? 1 : 3;
+    const int64_t ns = nch * npx;
+    dual *rs = (dual *)malloc(sizeof(dual) * (ns + 1));
+    double *qs = (double *)malloc(sizeof(double) * (ns + 1));
+    for (int ch = 0; ch < nch; ++ch)
+        for (int64_t k = 0; k < npx; ++k) {
+            if (gray) {
+                rs[k] = dscale(dadd(dadd(px[k].c[0], px[k].c[1]), px[k].c[2]), 1.0 / 3.0);
+                qs[k] = (query[k] + query[npx + k] + query[2 * npx + k]) / 3.0;
+            } else {
+                rs[ch * npx + k] = px[k].c[ch];
+                qs[ch * npx + k] = query[ch * npx + k];
+            }
+        }
     dual mr = dk(0); double mq = 0;
-    for (int ch = 0; ch < 3; ++ch)
-        for (int64_t k = 0; k < npx; ++k) { mr = dadd(mr, px[k].c[ch]); mq += query[ch * npx + k]; }
+    for (int64_t k = 0; k < ns; ++k) { mr = dadd(mr, rs[k]); mq += qs[k]; }
     mr = dscale(mr, 1.0 / ns); mq /= ns;
     dual sab = dk(0), saa = dk(0); double sbb = 0;
-    for (int ch = 0; ch < 3; ++ch)
-        for (int64_t k = 0; k < npx; ++k) {
-            dual da = dsub(px[k].c[ch], mr);
-            const double db = query[ch * npx + k] - mq;
-            sab = dadd(sab, dscale(da, db));
-            saa = dadd(saa, dmul(da, da));
-            sbb += db * db;
-        }
+    for (int64_t k = 0; k < ns; ++k) {
+        dual da = dsub(rs[k], mr);
+        const double db = qs[k] - mq;
+        sab = dadd(sab, dscale(da, db));
+        saa = dadd(saa, dmul(da, da));
+        sbb += db * db;
+    }
+    free(rs); free(qs);
     out[0] = 0;
     for (int k = 0; k < 6; ++k) out[1 + k] = 0;
     if (saa.v > 1e-12 * ns && sbb > 1e-12 * ns) {
@@ -1057,10 +1083,11 @@ void or_ncc_pose_grad(const float *means, const float *scales, const float *quat
 }
 
 /* ========================================================================= */
-/* Map training loss (Sec. III-B.3): L_photo = L_rgb(R(G), I) with           */
-/* L_rgb(I1, I2) = (1 - lambda) L1(I1, I2) + lambda L_D-SSIM(I1, I2), here   */
-/* with its L1 part, the mean absolute difference over all 3 H W samples of   */
-/* every view.  Directional derivatives of the loss along six directions in  */
+/* Map training loss (Sec. III-B.3): L = w_photo L_photo + w_reproj L_reproj */
+/* with L_rgb(I1, I2) = (1 - lambda) L1(I1, I2) + lambda L_D-SSIM(I1, I2),    */
+/* L1 the mean absolute difference over all 3 H W samples of a view (the     */
+/* SSIM and re-projection parts follow below).                               */
+/* Directional derivatives of the loss along six directions in               */
 /* the space of all Gaussian parameters -- mean (3), scale (3), quaternion    */
 /* (4), opacity (1), RGB (3): 14 per Gaussian, SH degree 0 -- by forward-mode */
 /* duals through the same projection and compositing as above.               */
