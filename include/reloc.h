@@ -61,7 +61,10 @@ typedef struct reloc_config {
     int64_t inst_capacity;     /* tile instances per view to start with; 0 = from the
                                   subset size (learned ratio): 0                       */
     int32_t blend_rpl;         /* blend: records staged per lane per warp step (1, 2): 1 */
-    int32_t reserved[7];
+    int32_t ncc_gray;          /* NCC samples (Eq. ncc, "intensity"): 0 = all 3 H W RGB
+                                  samples as one vector; 1 = the H W gray values
+                                  (R + G + B) / 3 of render and query: 0             */
+    int32_t reserved[6];
 } reloc_config;
 
 typedef struct reloc_camera {

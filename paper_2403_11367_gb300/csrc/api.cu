@@ -179,6 +179,7 @@ extern "C" void reloc_default_config(reloc_config *cfg)
     cfg->block_size = 20.0;
     cfg->inst_capacity = 0;
     cfg->blend_rpl = 1;
+    cfg->ncc_gray = 0;
 }
 
 static bool tile_ok(int w, int h)
@@ -192,7 +193,8 @@ static reloc_status check_config(const reloc_config &c)
     if (!tile_ok(c.tile_w, c.tile_h)) return fail(RELOC_EINVAL, "tile %dx%d not supported", c.tile_w, c.tile_h);
     if (!(c.near_plane > 0) || !(c.fov_clamp > 0) || !(c.eps2d >= 0) || !(c.alpha_min > 0) ||
         !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1) || !(c.t_min > 0) || !(c.t_min < 1) || !(c.cut > 0) ||
-        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 0 || c.blend_rpl < 1 || c.blend_rpl > 2)
+        !(c.det_fp64 >= 0) || !(c.block_size > 0) || c.inst_capacity < 0 || c.blend_rpl < 1 || c.blend_rpl > 2 ||
+        c.ncc_gray < 0 || c.ncc_gray > 1)
         return fail(RELOC_EINVAL, "invalid constant in reloc_config");
     return RELOC_OK;
 }
@@ -431,6 +433,7 @@ static reloc_status make_cam(const reloc_ctx *ctx, const reloc_camera *cam, CamP
     cp.alpha_max = c.alpha_max;
     cp.t_min = c.t_min;
     cp.blend_rpl = c.blend_rpl;
+    cp.ncc_gray = c.ncc_gray;
     return RELOC_OK;
 }
 
@@ -697,7 +700,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     const uint32_t *fgauss = ctx->inst.as<uint32_t>();
     stage_mark(ctx, sbi, RELOC_STAGE_BLEND, st, capturing);
     if (o.score) {
-        CK(launch_query_stats(L, 3 * HW, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
+        CK(launch_query_stats(L, HW, cp.ncc_gray != 0, ctx->qpart.as<double>(), ctx->qstats.as<double>(), st));
         launches += 2;
     }
     float *rgb_out = o.target ? ctx->trgb.as<float>() : (o.rgb ? o.rgb + (int64_t)sb.v0 * 3 * HW : nullptr);
@@ -751,7 +754,8 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         launches += 3;
     }
     if (o.score) {
-        CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, blend_units(cp), 3 * HW,
+        CK(launch_ncc_finalize(ctx->partials.as<double>(), ctx->qstats.as<double>(), L, blend_units(cp),
+                               cp.ncc_gray ? HW : 3 * HW,
                                ctx->scores.as<double>() + sb.v0, ctx->degen.as<int>() + sb.v0,
                                o.grad ? ctx->gcoef.as<double>() : nullptr, st));
         launches += 1;

@@ -40,6 +40,7 @@ struct CamParams {
     float near_plane, eps2d, cut, det_fp64;
     float alpha_min, alpha_max, t_min;
     int blend_rpl;     // records per lane per warp step in K6 (1 or 2)
+    int ncc_gray;      // NCC over gray values (R + G + B) / 3 instead of RGB samples
     int bin_chunk;     // depth-ordered Gaussians per tile-binning chunk (K3, K4)
 };
 
@@ -156,7 +157,9 @@ cudaError_t launch_fill_tiles(const int2 *ranges_view, int n_tiles, uint32_t *ti
 
 // Query statistics S_q, S_qq over n samples of each of the Q query images
 // -> qstats[Q][2] (double).  block_scratch: Q * 2 * 152 doubles.
-cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch, double *qstats,
+// Query sums (sum q, sum q^2) over its 3 H W samples, or over its H W gray
+// values (R + G + B) / 3 when gray.
+cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *block_scratch, double *qstats,
                                cudaStream_t st);
 
 // K6 (+ K7 partials): blend every (view, tile) of the layout, a warp per

@@ -55,13 +55,14 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NP], int lane)
 
 // Fixed grid and fixed reduction order: the sums are deterministic.
 // grid (QS_BLOCKS, Q): block (b, q) sums its share of query q.
-__global__ void __launch_bounds__(QS_THREADS) k_query_stats(Layout L, int64_t n, double *part)
+__global__ void __launch_bounds__(QS_THREADS) k_query_stats(Layout L, int64_t HW, int gray, double *part)
 {
     __shared__ double s[2][QS_THREADS / 32];
     const float *q = L.q_img[blockIdx.y];
+    const int64_t n = gray ? HW : 3 * HW;
     double a = 0, b = 0;
     for (int64_t j = (int64_t)blockIdx.x * QS_THREADS + threadIdx.x; j < n; j += (int64_t)QS_BLOCKS * QS_THREADS) {
-        double x = q[j];
+        const double x = gray ? ((double)q[j] + (double)q[HW + j] + (double)q[2 * HW + j]) / 3.0 : (double)q[j];
         a += x;
         b += x * x;
     }
@@ -91,10 +92,11 @@ __global__ void k_query_stats_final(const double *part, int Q, double *qstats)
     qstats[2 * q + 1] = B;
 }
 
-cudaError_t launch_query_stats(const Layout &L, int64_t n, double *block_scratch, double *qstats, cudaStream_t st)
+cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *block_scratch, double *qstats,
+                               cudaStream_t st)
 {
     if (L.Q <= 0) return cudaSuccess;
-    k_query_stats<<<dim3(QS_BLOCKS, L.Q), QS_THREADS, 0, st>>>(L, n, block_scratch);
+    k_query_stats<<<dim3(QS_BLOCKS, L.Q), QS_THREADS, 0, st>>>(L, HW, gray ? 1 : 0, block_scratch);
     k_query_stats_final<<<(L.Q + 127) / 128, 128, 0, st>>>(block_scratch, L.Q, qstats);
     return cudaGetLastError();
 }
@@ -365,11 +367,21 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     if (partials) {
         const float *query = L.q_img[L.view_q[v]];
         // pixels outside the image have zero colour and contribute nothing
-        float sr = R0 + G0 + B0 + R1 + G1 + B1;
-        float srr = R0 * R0 + G0 * G0 + B0 * B0 + R1 * R1 + G1 * G1 + B1 * B1;
-        float srq = 0.f;
-        if (in0) srq += R0 * __ldg(query + pix0) + G0 * __ldg(query + HW + pix0) + B0 * __ldg(query + 2 * HW + pix0);
-        if (in1) srq += R1 * __ldg(query + pix1) + G1 * __ldg(query + HW + pix1) + B1 * __ldg(query + 2 * HW + pix1);
+        float sr, srr, srq = 0.f;
+        if (cam.ncc_gray) {
+            // gray values (R + G + B) / 3 of render and query
+            const float third = 1.f / 3.f;
+            const float r0 = (R0 + G0 + B0) * third, r1 = (R1 + G1 + B1) * third;
+            sr = r0 + r1;
+            srr = r0 * r0 + r1 * r1;
+            if (in0) srq += r0 * ((__ldg(query + pix0) + __ldg(query + HW + pix0) + __ldg(query + 2 * HW + pix0)) * third);
+            if (in1) srq += r1 * ((__ldg(query + pix1) + __ldg(query + HW + pix1) + __ldg(query + 2 * HW + pix1)) * third);
+        } else {
+            sr = R0 + G0 + B0 + R1 + G1 + B1;
+            srr = R0 * R0 + G0 * G0 + B0 * B0 + R1 * R1 + G1 * G1 + B1 * B1;
+            if (in0) srq += R0 * __ldg(query + pix0) + G0 * __ldg(query + HW + pix0) + B0 * __ldg(query + 2 * HW + pix0);
+            if (in1) srq += R1 * __ldg(query + pix1) + G1 * __ldg(query + HW + pix1) + B1 * __ldg(query + 2 * HW + pix1);
+        }
         sr = warp_sum_f(sr);
         srr = warp_sum_f(srr);
         srq = warp_sum_f(srq);
@@ -642,9 +654,17 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         for (int p = 0; p < 2; ++p)
             if (in[p]) {
                 const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
+                if (cam.ncc_gray) {
+                    // gray NCC: dNCC/dC_ch = dNCC/d gray / 3
+                    const float qg = (__ldg(query + pix) + __ldg(query + HW + pix) + __ldg(query + 2 * HW + pix)) / 3.f;
+                    const float rg = (C[p][0] + C[p][1] + C[p][2]) / 3.f;
+                    const float gg = (k_q * (qg - mq) - k_r * (rg - mr)) / 3.f;
+                    G[p][0] = G[p][1] = G[p][2] = gg;
+                } else {
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-                    G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
+                    for (int ch = 0; ch < 3; ++ch)
+                        G[p][ch] = k_q * (__ldg(query + ch * HW + pix) - mq) - k_r * (C[p][ch] - mr);
+                }
             }
     }
     // pass 2: front to back again, gradients per record

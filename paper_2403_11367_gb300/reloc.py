@@ -31,7 +31,7 @@ class Config(C.Structure):
                 ("fov_clamp", C.c_float), ("eps2d", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("t_min", C.c_float), ("cut", C.c_float), ("det_fp64", C.c_float),
                 ("block_size", C.c_double), ("inst_capacity", C.c_int64), ("blend_rpl", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("ncc_gray", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Camera(C.Structure):
