@@ -227,10 +227,6 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     const bool in0 = px < cam.width && py0 < cam.height;
     const bool in1 = px < cam.width && py1 < cam.height;
     const float fxp = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
-    // pixel-centre extent of this warp's block
-    const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
-    const float wy0 = (float)(ty * TH + warp * WROWS) + 0.5f, wy1 = wy0 + (float)(WROWS - 1);
-
     int2 r = make_int2(0, 0);
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
@@ -264,10 +260,21 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         gnext[q] = j1 < r.y ? __ldg(list + j1) : 0u;
     }
     for (int b = r.x; b < r.y; b += CH) {
+        // pixel-centre box of the pixels still compositing (a stopped pixel has
+        // T = 0 exactly and takes nothing more, so records that miss this box
+        // would add nothing)
+        float bx0, bx1, by0, by1;
         {
             float t0, t1;
             upk(T2, t0, t1);
-            if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+            const bool a0 = t0 > 0.f, a1 = t1 > 0.f;
+            if (__all_sync(0xffffffffu, !a0 && !a1)) break;
+            const unsigned rlo = __reduce_min_sync(0xffffffffu, a0 ? (unsigned)py0 : (a1 ? (unsigned)py1 : 0xffffu));
+            const unsigned rhi = __reduce_max_sync(0xffffffffu, a1 ? (unsigned)py1 : (a0 ? (unsigned)py0 : 0u));
+            const unsigned clo = __reduce_min_sync(0xffffffffu, (a0 || a1) ? (unsigned)px : 0xffffu);
+            const unsigned chi = __reduce_max_sync(0xffffffffu, (a0 || a1) ? (unsigned)px : 0u);
+            bx0 = (float)clo + 0.5f; bx1 = (float)chi + 0.5f;
+            by0 = (float)rlo + 0.5f; by1 = (float)rhi + 0.5f;
         }
         int nk = 0;
 #pragma unroll
@@ -287,7 +294,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
                 if (thr < 0.f) {
                     // keep iff the ellipse {power >= thr} (widened 1%) meets the block
-                    const float qmin = quad_min_rect(pb.x, pb.y, pb.z, wx0 - pa.x, wx1 - pa.x, wy0 - pa.y, wy1 - pa.y);
+                    const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
                     hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
                 }
             }
@@ -535,8 +542,6 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
     const bool in[2] = {px < cam.width && py0 < cam.height, px < cam.width && py0 + 1 < cam.height};
     const float fxp = (float)px + 0.5f, fyp[2] = {(float)py0 + 0.5f, (float)py0 + 1.5f};
-    const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
-    const float wy0 = (float)(ty * TH + warp * WROWS) + 0.5f, wy1 = wy0 + (float)(WROWS - 1);
     if (*overflow) return;
     const int2 r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
@@ -545,8 +550,16 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const float lamin = __logf(cam.alpha_min);
     const unsigned lt = lanemask_lt_u();
 
-    // the same per-warp cull and compaction as the forward, one step of 32 records
-    auto stage = [&](int b) -> int {
+    // the same per-warp cull and compaction as the forward, one step of 32
+    // records, against the box of the pixels still compositing (t0, t1 > 0)
+    auto stage = [&](int b, float t0, float t1) -> int {
+        const bool a0 = t0 > 0.f, a1 = t1 > 0.f;
+        const unsigned rlo = __reduce_min_sync(0xffffffffu, a0 ? (unsigned)py0 : (a1 ? (unsigned)py0 + 1u : 0xffffu));
+        const unsigned rhi = __reduce_max_sync(0xffffffffu, a1 ? (unsigned)py0 + 1u : (a0 ? (unsigned)py0 : 0u));
+        const unsigned clo = __reduce_min_sync(0xffffffffu, (a0 || a1) ? (unsigned)px : 0xffffu);
+        const unsigned chi = __reduce_max_sync(0xffffffffu, (a0 || a1) ? (unsigned)px : 0u);
+        const float bx0 = (float)clo + 0.5f, bx1 = (float)chi + 0.5f;
+        const float by0 = (float)rlo + 0.5f, by1 = (float)rhi + 0.5f;
         const int j = b + lane;
         bool hit = false;
         float4 pa = make_float4(0, 0, 0, 0), pb = pa, pc = pa;
@@ -557,7 +570,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             pa = __ldg(p); pb = __ldg(p + 1); pc = __ldg(p + 2);
             const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
             if (thr < 0.f) {
-                const float qmin = quad_min_rect(pb.x, pb.y, pb.z, wx0 - pa.x, wx1 - pa.x, wy0 - pa.y, wy1 - pa.y);
+                const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
                 hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
             }
         }
@@ -604,7 +617,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     }
     for (int b = r.x; b < ((IMG && cimg) ? r.x : r.y); b += 32) {
         if (__all_sync(0xffffffffu, T[0] == 0.f && T[1] == 0.f)) break;
-        const int nk = stage(b);
+        const int nk = stage(b, T[0], T[1]);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k];
             const float zk = s_a[k].z;
@@ -673,7 +686,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     float UDA[2][2] = {{0, 0}, {0, 0}};
     for (int b = r.x; b < r.y; b += 32) {
         if (__all_sync(0xffffffffu, Tb[0] == 0.f && Tb[1] == 0.f)) break;
-        const int nk = stage(b);
+        const int nk = stage(b, Tb[0], Tb[1]);
         for (int k = 0; k < nk; ++k) {
             const float4 c = s_c[k], bb = s_b[k];
             const float zk = s_a[k].z;
