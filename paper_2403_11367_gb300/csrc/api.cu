@@ -116,7 +116,7 @@ struct reloc_ctx {
     std::vector<int64_t> order;
     BlockIndex blocks;
     // workspace (sized for the largest sub-batch of a call)
-    DevBuf gidx, tables, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums;
+    DevBuf gidx, tables, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums, dtot;
     DevBuf srect, bhist, inst, ranges, partials, qpart, qstats;
     // per-call results (all views / queries of the call)
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
@@ -661,6 +661,10 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         p.total_chunks = sb.c1;
         p.hist = ctx->hist1.as<uint32_t>();
         p.mask = 0xFF;
+        // per (view, digit) totals, one slice per pass
+        uint32_t *dtot = ctx->dtot.as<uint32_t>();
+        CK(cudaMemsetAsync(dtot, 0, 16 * (size_t)RADIX * L.V, st));
+        p.dtot = dtot;
         uint32_t *ka = ctx->k1a.as<uint32_t>(), *va = ctx->v1a.as<uint32_t>();
         uint32_t *kb = ctx->k1b.as<uint32_t>(), *vb = ctx->v1b.as<uint32_t>();
         // pass 0: dense (view, Gaussian) arrays; culled pairs are dropped
@@ -679,6 +683,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         p.len_out = nullptr;
         for (int pass = 1; pass < 4; ++pass) {
             p.shift = 8 * pass;
+            p.dtot = dtot + (size_t)pass * RADIX * L.V;
             p.keys_in = (pass & 1) ? ka : kb;
             p.vals_in = (pass & 1) ? va : vb;
             p.keys_out = (pass & 1) ? kb : ka;
@@ -848,6 +853,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->k1b.ensure(4 * (size_t)VS));
         CKS(ctx->v1b.ensure(4 * (size_t)VS));
         CKS(ctx->hist1.ensure(4 * (size_t)RADIX * c1));
+        CKS(ctx->dtot.ensure(16 * (size_t)RADIX * V));
         CKS(ctx->srect.ensure(8 * (size_t)VS));
         CKS(ctx->bhist.ensure(4 * (size_t)cp.n_tiles * cb));
         CKS(ctx->inst.ensure(4 * (size_t)VI));

@@ -116,6 +116,7 @@ cudaError_t launch_project(const float *mx, const float *my, const float *mz, co
 struct RadixPass {
     const uint32_t *keys_in, *vals_in, *filt, *len;
     uint32_t *keys_out, *vals_out, *len_out, *hist;
+    uint32_t *dtot;    // per (segment, digit) totals of the pass, zeroed by the caller
     const int64_t *seg_off;
     const int32_t *chunk_base;
     int n_seg, total_chunks, shift;

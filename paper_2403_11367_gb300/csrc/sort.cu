@@ -90,42 +90,51 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
         if (valid && (peers & lt) == 0) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    p.hist[(int64_t)RADIX * p.chunk_base[s] + (int64_t)threadIdx.x * cps + k] = s_h[threadIdx.x];
+    const uint32_t cnt = s_h[threadIdx.x];
+    p.hist[(int64_t)RADIX * p.chunk_base[s] + (int64_t)threadIdx.x * cps + k] = cnt;
+    if (cnt) atomicAdd(p.dtot + (int64_t)RADIX * s + threadIdx.x, cnt);
 }
 
-// --------------------------------------------------- segment scan ----------
-// In-place exclusive scan of `count` words per segment; total_out[s] = sum.
-// In-place exclusive scan of segment s = data[mult*base[s], mult*base[s+1]);
-// total_out[s] = its sum.  One block per segment walks it in tiles of
-// SCAN_THREADS * 4 words (each thread 4 consecutive words, coalesced),
-// carrying the running total from tile to tile.
-constexpr int SCAN_THREADS = 512;
-constexpr int SCAN_IPT = 4;
-__global__ void __launch_bounds__(SCAN_THREADS)
-k_seg_scan(uint32_t *data, const int32_t *__restrict__ base, int mult, uint32_t *total_out)
+// ------------------------------------------------------- digit offsets -----
+// Exclusive offsets of one pass in place: the segment's counts are stored
+// digit-major ([digit][chunk]), so the offset of (d, k) is the total of all
+// smaller digits (dtot, summed by the upsweep) plus the counts of digit d in
+// the chunks before k.  A warp per (segment, digit) takes the first from
+// dtot and scans the second 32 chunks at a time; len_out[s] (may be null) =
+// the segment's total.
+constexpr int DSCAN_WARPS = 8;
+__global__ void __launch_bounds__(32 * DSCAN_WARPS)
+k_digit_scan(uint32_t *hist, const uint32_t *__restrict__ dtot, const int32_t *__restrict__ chunk_base,
+             uint32_t *len_out)
 {
-    __shared__ uint32_t s_tmp[33];
-    uint32_t *a = data + (int64_t)mult * base[blockIdx.x];
-    const int64_t count = (int64_t)mult * (base[blockIdx.x + 1] - base[blockIdx.x]);
-    uint32_t carry = 0;
-    for (int64_t t0 = 0; t0 < count; t0 += SCAN_THREADS * SCAN_IPT) {
-        const int64_t i0 = t0 + (int64_t)threadIdx.x * SCAN_IPT;
-        uint32_t v[SCAN_IPT], sum = 0;
-#pragma unroll
-        for (int j = 0; j < SCAN_IPT; ++j) {
-            v[j] = i0 + j < count ? a[i0 + j] : 0u;
-            sum += v[j];
-        }
-        uint32_t tot;
-        uint32_t run = carry + block_excl_scan(sum, s_tmp, &tot);
-#pragma unroll
-        for (int j = 0; j < SCAN_IPT; ++j) {
-            if (i0 + j < count) a[i0 + j] = run;
-            run += v[j];
-        }
-        carry += tot;
+    const int s = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d = blockIdx.y * DSCAN_WARPS + warp;
+    const uint32_t *dt = dtot + (int64_t)RADIX * s;
+    uint32_t below = 0, all = 0;
+    for (int i = lane; i < RADIX; i += 32) {
+        const uint32_t x = dt[i];
+        below += i < d ? x : 0u;
+        all += x;
     }
-    if (total_out && threadIdx.x == 0) total_out[blockIdx.x] = carry;
+    below = __reduce_add_sync(0xffffffffu, below);
+    all = __reduce_add_sync(0xffffffffu, all);
+    if (len_out && d == 0 && lane == 0) len_out[s] = all;
+    const int cps = chunk_base[s + 1] - chunk_base[s];
+    uint32_t *h = hist + (int64_t)RADIX * chunk_base[s] + (int64_t)d * cps;
+    uint32_t carry = below;
+    for (int k0 = 0; k0 < cps; k0 += 32) {
+        const int k = k0 + lane;
+        const uint32_t x = k < cps ? h[k] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (k < cps) h[k] = carry + inc - x;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
 }
 
 // ------------------------------------------------------------ scatter ------
@@ -219,7 +228,8 @@ cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st)
 {
     if (p.n_seg <= 0 || p.total_chunks <= 0) return cudaSuccess;
     k_radix_upsweep<<<p.total_chunks, SORT_THREADS, 0, st>>>(p);
-    k_seg_scan<<<p.n_seg, SCAN_THREADS, 0, st>>>(p.hist, p.chunk_base, RADIX, p.len_out);
+    k_digit_scan<<<dim3(p.n_seg, RADIX / DSCAN_WARPS), 32 * DSCAN_WARPS, 0, st>>>(p.hist, p.dtot, p.chunk_base,
+                                                                                   p.len_out);
     k_radix_scatter<<<p.total_chunks, SORT_THREADS, 0, st>>>(p);
     return cudaGetLastError();
 }
