@@ -49,10 +49,14 @@ cudaError_t launch_photo_l1(const float *rgb, const float *target, int64_t n, do
 // window (standard deviation 1.5 px, unit sum; separable, so two 11-tap
 // passes) and samples outside the image counting as 0; C1 = 0.01^2, C2 =
 // 0.03^2.  The loss adds scale * sum over pixels of (1 - SSIM).  A 256-thread
-// block covers a 32 x 8 tile of one plane; its inputs with a 5-pixel halo sit
-// in shared memory.
-constexpr int SS_TW = 32, SS_TH = 8, SS_R = 5, SS_N = 2 * SS_R + 1;
-constexpr int SS_HW = SS_TW + 2 * SS_R, SS_HH = SS_TH + 2 * SS_R;
+// block covers a 32 x 32 tile of one plane; its inputs with a 5-pixel halo
+// sit in shared memory, and each thread slides the window over four
+// neighbouring outputs from registers (14 loads per source for 4 outputs)
+// in both passes.
+constexpr int SS_T = 32, SS_R = 5, SS_N = 2 * SS_R + 1, SS_H = SS_T + 2 * SS_R;
+constexpr int SS_THREADS = 256, SS_OUT = 4, SS_WIN = SS_OUT + 2 * SS_R;
+constexpr int SS_IN_STRIDE = 45;     // input rows: 8 lanes at stride 4 per row, rows 45 apart: no bank conflict
+constexpr int SS_H_STRIDE = 33;      // pass-1 rows: (row + column) spreads the lanes over the banks
 constexpr float SS_C1 = 0.01f * 0.01f, SS_C2 = 0.03f * 0.03f;
 
 struct SsimWin {
@@ -72,6 +76,21 @@ static SsimWin ssim_window()
     return w;
 }
 
+// Load a (SS_H x SS_H) halo tile of NQ planes (src[m] + plane offset) into
+// dst[m][row * SS_IN_STRIDE + col], 0 outside the image.
+template <int NQ>
+__device__ __forceinline__ void ssim_load(float (*dst)[SS_H * SS_IN_STRIDE], const float *const (&src)[NQ], int H,
+                                          int W, int x0, int y0)
+{
+    for (int k = threadIdx.x; k < SS_H * SS_H; k += SS_THREADS) {
+        const int r = k / SS_H, c = k - r * SS_H;
+        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) dst[m][r * SS_IN_STRIDE + c] = in ? src[m][(int64_t)gy * W + gx] : 0.f;
+    }
+}
+
 // Forward: per pixel SSIM s and, with dL/ds = -scale, the products of dL/ds
 // with the partial derivatives of s with respect to the local mean of x, the
 // local mean of x^2 and the local mean of x y (A1 = 2 mx my + C1, A2 = 2 sxy +
@@ -79,72 +98,89 @@ static SsimWin ssim_window()
 //   ds/dmx   = (2 my (A2 - A1) - 2 mx s (B2 - B1)) / (B1 B2)
 //   ds/dE[xx] = -s / B2,  ds/dE[xy] = 2 A1 / (B1 B2),
 // into abc [plane][3][H][W].
-__global__ void __launch_bounds__(SS_TW * SS_TH)
+__global__ void __launch_bounds__(SS_THREADS)
 k_ssim_fwd(const float *__restrict__ x_img, const float *__restrict__ y_img, int H, int W, SsimWin win,
            float scale, double dscale, float *__restrict__ abc, double *__restrict__ loss)
 {
-    __shared__ float sx[SS_HH][SS_HW], sy[SS_HH][SS_HW];
-    __shared__ float hsum[5][SS_HH][SS_TW];
-    __shared__ double s_red[SS_TW * SS_TH / 32];
+    __shared__ float sin_[2][SS_H * SS_IN_STRIDE];
+    __shared__ float hsum[5][SS_H * SS_H_STRIDE];
+    __shared__ double s_red[SS_THREADS / 32];
     const int64_t HW = (int64_t)H * W;
     const int plane = blockIdx.z;
-    const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TH;
-    const float *X = x_img + plane * HW, *Y = y_img + plane * HW;
-    for (int k = threadIdx.x; k < SS_HH * SS_HW; k += SS_TW * SS_TH) {
-        const int r = k / SS_HW, c = k - r * SS_HW;
-        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sx[r][c] = in ? X[(int64_t)gy * W + gx] : 0.f;
-        sy[r][c] = in ? Y[(int64_t)gy * W + gx] : 0.f;
-    }
+    const int x0 = blockIdx.x * SS_T, y0 = blockIdx.y * SS_T;
+    const float *const src[2] = {x_img + plane * HW, y_img + plane * HW};
+    ssim_load<2>(sin_, src, H, W, x0, y0);
     __syncthreads();
-    for (int k = threadIdx.x; k < SS_HH * SS_TW; k += SS_TW * SS_TH) {
-        const int r = k / SS_TW, c = k - r * SS_TW;
-        float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+    // pass 1 (along x): item = (row, group of 4 output columns)
+    for (int it = threadIdx.x; it < SS_H * (SS_T / SS_OUT); it += SS_THREADS) {
+        const int r = it / (SS_T / SS_OUT), c0 = (it - r * (SS_T / SS_OUT)) * SS_OUT;
+        float a[SS_WIN], b[SS_WIN];
 #pragma unroll
-        for (int t = 0; t < SS_N; ++t) {
-            const float a = sx[r][c + t], b = sy[r][c + t], w = win.w[t];
-            m1 = fmaf(w, a, m1);
-            m2 = fmaf(w, b, m2);
-            e11 = fmaf(w * a, a, e11);
-            e22 = fmaf(w * b, b, e22);
-            e12 = fmaf(w * a, b, e12);
+        for (int i = 0; i < SS_WIN; ++i) {
+            a[i] = sin_[0][r * SS_IN_STRIDE + c0 + i];
+            b[i] = sin_[1][r * SS_IN_STRIDE + c0 + i];
         }
-        hsum[0][r][c] = m1; hsum[1][r][c] = m2; hsum[2][r][c] = e11; hsum[3][r][c] = e22; hsum[4][r][c] = e12;
+#pragma unroll
+        for (int o = 0; o < SS_OUT; ++o) {
+            float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+#pragma unroll
+            for (int t = 0; t < SS_N; ++t) {
+                const float w = win.w[t], xa = a[o + t], yb = b[o + t];
+                const float wx = w * xa, wy = w * yb;
+                m1 += wx;
+                m2 += wy;
+                e11 = fmaf(wx, xa, e11);
+                e22 = fmaf(wy, yb, e22);
+                e12 = fmaf(wx, yb, e12);
+            }
+            const int h = r * SS_H_STRIDE + c0 + o;
+            hsum[0][h] = m1; hsum[1][h] = m2; hsum[2][h] = e11; hsum[3][h] = e22; hsum[4][h] = e12;
+        }
     }
     __syncthreads();
-    const int tx = threadIdx.x % SS_TW, ty = threadIdx.x / SS_TW;
-    float q[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // pass 2 (along y): thread = (column, group of 4 output rows)
+    const int col = threadIdx.x % SS_T, r0 = (threadIdx.x / SS_T) * SS_OUT;
+    float q[5][SS_OUT];
 #pragma unroll
-    for (int t = 0; t < SS_N; ++t) {
-        const float w = win.w[t];
+    for (int m = 0; m < 5; ++m) {
+        float v[SS_WIN];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) q[m] = fmaf(w, hsum[m][ty + t][tx], q[m]);
+        for (int i = 0; i < SS_WIN; ++i) v[i] = hsum[m][(r0 + i) * SS_H_STRIDE + col];
+#pragma unroll
+        for (int o = 0; o < SS_OUT; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < SS_N; ++t) acc = fmaf(win.w[t], v[o + t], acc);
+            q[m][o] = acc;
+        }
     }
-    const int gx = x0 + tx, gy = y0 + ty;
     double contrib = 0.0;
-    if (gx < W && gy < H) {
-        const float mx = q[0], my = q[1];
-        const float vx = q[2] - mx * mx, vy = q[3] - my * my, cxy = q[4] - mx * my;
-        const float A1 = 2.f * mx * my + SS_C1, A2 = 2.f * cxy + SS_C2;
-        const float B1 = mx * mx + my * my + SS_C1, B2 = vx + vy + SS_C2;
-        const float iB = 1.f / (B1 * B2);
-        const float s = A1 * A2 * iB;
-        const float d_m = (2.f * my * (A2 - A1) - 2.f * mx * s * (B2 - B1)) * iB;
-        const float d_xx = -s / B2, d_xy = 2.f * A1 * iB;
-        const int64_t pix = (int64_t)gy * W + gx;
-        float *o = abc + (int64_t)plane * 3 * HW + pix;
-        o[0] = -scale * d_m;
-        o[HW] = -scale * d_xx;
-        o[2 * HW] = -scale * d_xy;
-        contrib = 1.0 - (double)s;
+    const int gx = x0 + col;
+#pragma unroll
+    for (int o = 0; o < SS_OUT; ++o) {
+        const int gy = y0 + r0 + o;
+        if (gx < W && gy < H) {
+            const float mx = q[0][o], my = q[1][o];
+            const float vx = q[2][o] - mx * mx, vy = q[3][o] - my * my, cxy = q[4][o] - mx * my;
+            const float A1 = 2.f * mx * my + SS_C1, A2 = 2.f * cxy + SS_C2;
+            const float B1 = mx * mx + my * my + SS_C1, B2 = vx + vy + SS_C2;
+            const float iB = 1.f / (B1 * B2);
+            const float s = A1 * A2 * iB;
+            const float d_m = (2.f * my * (A2 - A1) - 2.f * mx * s * (B2 - B1)) * iB;
+            const float d_xx = -s / B2, d_xy = 2.f * A1 * iB;
+            float *po = abc + (int64_t)plane * 3 * HW + (int64_t)gy * W + gx;
+            po[0] = -scale * d_m;
+            po[HW] = -scale * d_xx;
+            po[2 * HW] = -scale * d_xy;
+            contrib += 1.0 - (double)s;
+        }
     }
     for (int off = 16; off > 0; off >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = contrib;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < SS_TW * SS_TH / 32; ++w) t += s_red[w];
+        for (int w = 0; w < SS_THREADS / 32; ++w) t += s_red[w];
         atomicAdd(loss, t * dscale);
     }
 }
@@ -152,46 +188,60 @@ k_ssim_fwd(const float *__restrict__ x_img, const float *__restrict__ y_img, int
 // Backward: dL/dx(q) = sum_p w(p - q) (a(p) + 2 x(q) b(p) + y(q) c(p)) over
 // the image's pixels p (the window is symmetric, so the same separable
 // passes), added to gimg.
-__global__ void __launch_bounds__(SS_TW * SS_TH)
+__global__ void __launch_bounds__(SS_THREADS)
 k_ssim_bwd(const float *__restrict__ abc, const float *__restrict__ x_img, const float *__restrict__ y_img, int H,
            int W, SsimWin win, float *__restrict__ gimg)
 {
-    __shared__ float s3[3][SS_HH][SS_HW];
-    __shared__ float hsum[3][SS_HH][SS_TW];
+    __shared__ float sin_[3][SS_H * SS_IN_STRIDE];
+    __shared__ float hsum[3][SS_H * SS_H_STRIDE];
     const int64_t HW = (int64_t)H * W;
     const int plane = blockIdx.z;
-    const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TH;
+    const int x0 = blockIdx.x * SS_T, y0 = blockIdx.y * SS_T;
     const float *P = abc + (int64_t)plane * 3 * HW;
-    for (int k = threadIdx.x; k < SS_HH * SS_HW; k += SS_TW * SS_TH) {
-        const int r = k / SS_HW, c = k - r * SS_HW;
-        const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const int64_t pix = (int64_t)gy * W + gx;
+    const float *const src[3] = {P, P + HW, P + 2 * HW};
+    ssim_load<3>(sin_, src, H, W, x0, y0);
+    __syncthreads();
+    for (int it = threadIdx.x; it < SS_H * (SS_T / SS_OUT); it += SS_THREADS) {
+        const int r = it / (SS_T / SS_OUT), c0 = (it - r * (SS_T / SS_OUT)) * SS_OUT;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) s3[m][r][c] = in ? P[m * HW + pix] : 0.f;
+        for (int m = 0; m < 3; ++m) {
+            float a[SS_WIN];
+#pragma unroll
+            for (int i = 0; i < SS_WIN; ++i) a[i] = sin_[m][r * SS_IN_STRIDE + c0 + i];
+#pragma unroll
+            for (int o = 0; o < SS_OUT; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < SS_N; ++t) acc = fmaf(win.w[t], a[o + t], acc);
+                hsum[m][r * SS_H_STRIDE + c0 + o] = acc;
+            }
+        }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < SS_HH * SS_TW; k += SS_TW * SS_TH) {
-        const int r = k / SS_TW, c = k - r * SS_TW;
-        float acc[3] = {0.f, 0.f, 0.f};
+    const int col = threadIdx.x % SS_T, r0 = (threadIdx.x / SS_T) * SS_OUT;
+    float q[3][SS_OUT];
 #pragma unroll
-        for (int t = 0; t < SS_N; ++t)
+    for (int m = 0; m < 3; ++m) {
+        float v[SS_WIN];
 #pragma unroll
-            for (int m = 0; m < 3; ++m) acc[m] = fmaf(win.w[t], s3[m][r][c + t], acc[m]);
+        for (int i = 0; i < SS_WIN; ++i) v[i] = hsum[m][(r0 + i) * SS_H_STRIDE + col];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) hsum[m][r][c] = acc[m];
+        for (int o = 0; o < SS_OUT; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < SS_N; ++t) acc = fmaf(win.w[t], v[o + t], acc);
+            q[m][o] = acc;
+        }
     }
-    __syncthreads();
-    const int tx = threadIdx.x % SS_TW, ty = threadIdx.x / SS_TW;
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= W || gy >= H) return;
-    float acc[3] = {0.f, 0.f, 0.f};
+    const int gx = x0 + col;
 #pragma unroll
-    for (int t = 0; t < SS_N; ++t)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) acc[m] = fmaf(win.w[t], hsum[m][ty + t][tx], acc[m]);
-    const int64_t pix = plane * HW + (int64_t)gy * W + gx;
-    gimg[pix] += acc[0] + 2.f * x_img[pix] * acc[1] + y_img[pix] * acc[2];
+    for (int o = 0; o < SS_OUT; ++o) {
+        const int gy = y0 + r0 + o;
+        if (gx < W && gy < H) {
+            const int64_t pix = plane * HW + (int64_t)gy * W + gx;
+            gimg[pix] += q[0][o] + 2.f * x_img[pix] * q[1][o] + y_img[pix] * q[2][o];
+        }
+    }
 }
 
 cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H, int W, double scale, float *abc,
@@ -199,11 +249,11 @@ cudaError_t launch_ssim(const float *rgb, const float *target, int planes, int H
 {
     if (planes <= 0) return cudaSuccess;
     const SsimWin win = ssim_window();
-    dim3 grid((unsigned)ceil_div(W, SS_TW), (unsigned)ceil_div(H, SS_TH), (unsigned)planes);
-    k_ssim_fwd<<<grid, SS_TW * SS_TH, 0, st>>>(rgb, target, H, W, win, (float)scale, scale, abc, loss);
+    dim3 grid((unsigned)ceil_div(W, SS_T), (unsigned)ceil_div(H, SS_T), (unsigned)planes);
+    k_ssim_fwd<<<grid, SS_THREADS, 0, st>>>(rgb, target, H, W, win, (float)scale, scale, abc, loss);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_ssim_bwd<<<grid, SS_TW * SS_TH, 0, st>>>(abc, rgb, target, H, W, win, gimg);
+    k_ssim_bwd<<<grid, SS_THREADS, 0, st>>>(abc, rgb, target, H, W, win, gimg);
     return cudaGetLastError();
 }
 

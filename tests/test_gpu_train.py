@@ -208,3 +208,29 @@ def test_invalid_training_calls(R):
     with pytest.raises(R.RelocError) as e:
         ctx.train_grad([(0, ctx.n)], poses, s.camera, tg, torch.zeros((14, street.n), device="cuda:0"), **L1_ONLY)
     assert e.value.status == R.EINVAL
+
+
+def test_sub_batches_do_not_change_the_loss_or_gradient(R):
+    """A 64 MiB workspace budget puts each view of a 400k-Gaussian street
+    subset in its own sub-batch, so the re-projection pairs straddle
+    sub-batches; loss and gradient equal those of one sub-batch (up to the
+    order of the atomic sums)."""
+    g = sg.street_gaussians(400_000, seed=5, sh_degree=0)
+    cam = sg.street_camera(704, 188, 276.0)
+    x0 = float(np.median(g.mean[:, 0]))
+    poses = np.stack([sg.pose_from_xyz_yaw(x0 + k, 0.0, 1.6, 0.0) for k in range(4)])
+    tg = torch.tensor(np.stack([sg.random_image(70 + k, 3, cam.height, cam.width) for k in range(4)]),
+                      dtype=torch.float32, device="cuda:0")
+    out = []
+    for budget, vpg in ((16 << 30, 16), (64 << 20, 1)):
+        ctx = R.Context()
+        ctx.set_batch_options(mem_budget=budget)
+        ctx.load_map(g)
+        grad = torch.zeros((14, g.n), device="cuda:0")
+        L = ctx.train_grad([(0, ctx.n)], poses, cam, tg, grad, views_per_group=vpg)
+        out.append((L, grad.cpu().numpy()))
+        ctx.close()
+    (La, Ga), (Lb, Gb) = out
+    print("loss", La, Lb, "max |dG|", np.abs(Ga - Gb).max(), "max |G|", np.abs(Ga).max())
+    assert abs(La - Lb) <= 1e-9 * La
+    assert np.abs(Ga - Gb).max() <= 1e-5 * np.abs(Ga).max()
