@@ -497,29 +497,33 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 }
 
 // ------------------------------------------------------- K6 backward ------
-// Gradient of each view's NCC with respect to its Gaussians' projected means
+// Gradients of a view's loss with respect to its Gaussians' projected means
 // (u, v) and conics (a, b, c), for the view's fixed set of included
 // (pixel, Gaussian) pairs.  A warp per 64-pixel block walks the tile's list
-// twice with the forward's cull: first compositing the pixel pair to its
+// with the forward's cull and the forward's arithmetic (base-2 exponent, the
+// inclusion, clamp and stop tests as saturating step functions, the pixel
+// pair packed in f32x2), so its decisions are the forward's bit for bit:
+// first, unless the forward's render is given, compositing the pair to its
 // final colour C, then again front to back, where for contributor j with
-// weight w_j = alpha_j T_j and C_after = C - C_up_to_j,
-//   dL/d alpha_j = T_j (G . c_j) - (G . C_after) / (1 - alpha_j),
-// G = dNCC/dC of the pixel; alpha = o exp(power) unclamped gives
-// dL/d power = alpha dL/d alpha, and power = -(a dx^2 + 2 b dx dy + c dy^2)/2
-// with dx = x - u.  The warp sums each record's gradients over its 64 pixels
-// and adds them to the (view, Gaussian) entry of gout.
+// weight w_j = alpha_j T_j,
+//   dL/d alpha_j = T_j S_j - K_j / (1 - alpha_j),
+// S_j = G . c_j (+ G_D z_j + G_A in image mode: depth and alpha as two more
+// channels with values z_j and 1) and K_j = the sum of w S over the
+// contributors after j (K starts at G . C (+ G_D D + G_A A) and loses w_j S_j
+// at j); alpha = o exp(power) unclamped gives dL/d power = alpha dL/d alpha,
+// and power = -(a dx^2 + 2 b dx dy + c dy^2)/2 with dx = x - u.  The warp
+// sums each record's gradients over its 64 pixels (a reduce-scatter: lane
+// 32/NP * m holds total m) and adds them to the (view, Gaussian) entry of
+// gout.
 // IMG = false: L is the view's NCC (G from coef), five outputs (u, v, a, b, c).
 // IMG = true: G is given per pixel (gimg [V][3][H][W], an image loss's
-// gradient), and optionally the gradients G_D, G_A with respect to the
-// pixel's depth D = sum w z and alpha A = sum w (gda [V][2][H][W]), which
-// enter dL/d alpha_j like two more channels with values z_j and 1; ten
-// outputs: also dL/d colour = sum w G, dL/d opacity = dL/d alpha exp(power)
-// (alpha unclamped) and dL/dz = sum w G_D.
+// gradient), and optionally G_D, G_A (gda [V][2][H][W]); ten outputs: also
+// dL/d colour = sum w G, dL/d opacity = dL/d power / o and dL/dz = sum w G_D.
 // cimg (image mode, may be null): the forward's render of the views
 // ([V][3][H][W], with cdep, calp [V][H][W] when gda is given) replaces the
 // first walk.
 template <int TW, int TH, bool IMG>
-__global__ void __launch_bounds__(32, IMG ? 24 : 32)     // NCC mode: 64 registers, no spills
+__global__ void __launch_bounds__(32, IMG ? 24 : 32)
 k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
              const int2 *__restrict__ ranges, CamParams cam, const double *__restrict__ coef,
              const float *__restrict__ gimg, const float *__restrict__ gda, const float *__restrict__ cimg,
@@ -531,7 +535,12 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     constexpr int GRP = 32 / NP;                // lanes holding each total
     constexpr int WPT = TW * TH / 64;
     constexpr int WROWS = 64 / TW;
-    __shared__ float4 s_a[32], s_b[32], s_c[32];
+    constexpr float L2E = 1.4426950408889634f;
+    // kept records: the forward's (-u, A', B', log2 o) (-v, -v, C', C')
+    // (r, r, g, g) (b, b, z, z), then the natural conic and 1/o:
+    // (a, a, b, b) (c, c, 1/o, 1/o); the forward's step threshold
+    __shared__ float4 s_rec[6][32];
+    __shared__ float s_thr[32];
     __shared__ uint32_t s_g[32];
     const int unit = blockIdx.x;
     const int tile = unit / WPT, warp = unit - tile * WPT;
@@ -541,18 +550,25 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const int px = tx * TW + lane % TW;
     const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
     const bool in[2] = {px < cam.width && py0 < cam.height, px < cam.width && py0 + 1 < cam.height};
-    const float fxp = (float)px + 0.5f, fyp[2] = {(float)py0 + 0.5f, (float)py0 + 1.5f};
+    const float fxp = (float)px + 0.5f;
     if (*overflow) return;
     const int2 r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
     const float lim = -0.5f * cam.cut * cam.cut;
     const float lamin = __logf(cam.alpha_min);
+    const float limL = lim * L2E;
+    const float l2amin = log2f(cam.alpha_min);
+    const float ntmin = -cam.t_min * STEP_SCALE;
+    const float amax = cam.alpha_max, amaxS = cam.alpha_max * STEP_SCALE;
     const unsigned lt = lanemask_lt_u();
+    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f);
 
-    // the same per-warp cull and compaction as the forward, one step of 32
-    // records, against the box of the pixels still compositing (t0, t1 > 0)
-    auto stage = [&](int b, float t0, float t1) -> int {
+    // the forward's cull and compaction, one step of 32 records, against the
+    // box of the pixels still compositing (T > 0)
+    auto stage = [&](int b, f32x2 T2) -> int {
+        float t0, t1;
+        upk(T2, t0, t1);
         const bool a0 = t0 > 0.f, a1 = t1 > 0.f;
         const unsigned rlo = __reduce_min_sync(0xffffffffu, a0 ? (unsigned)py0 : (a1 ? (unsigned)py0 + 1u : 0xffffu));
         const unsigned rhi = __reduce_max_sync(0xffffffffu, a1 ? (unsigned)py0 + 1u : (a0 ? (unsigned)py0 : 0u));
@@ -577,71 +593,86 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         const unsigned keep = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const int k = __popc(keep & lt);
-            s_a[k] = pa; s_b[k] = pb; s_c[k] = pc; s_g[k] = gi;
+            const float l2o = __log2f(pa.w);
+            const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
+            const float io = 1.f / pa.w;
+            s_rec[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
+            s_rec[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
+            s_rec[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
+            s_rec[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
+            s_rec[4][k] = make_float4(pb.x, pb.x, pb.y, pb.y);
+            s_rec[5][k] = make_float4(pb.z, pb.z, io, io);
+            s_thr[k] = -STEP_SCALE * fmaxf(limL + l2o, l2amin);
+            s_g[k] = gi;
         }
         __syncwarp();
         return __popc(keep);
     };
-    // alpha of a kept record at pixel p (0 if excluded), unclamped flag
-    // ex = exp(power) = alpha / o while unclamped
-    auto alpha_at = [&](int k, int p, float &dx, float &dy, bool &unclamped, float &ex) -> float {
-        const float4 a = s_a[k], b = s_b[k];
-        dx = fxp - a.x;
-        dy = fyp[p] - a.y;
-        const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
-        if (!(power >= lim)) return 0.f;
-        ex = __expf(power);
-        const float raw = a.w * ex;
-        unclamped = raw < cam.alpha_max;
-        const float al = fminf(cam.alpha_max, raw);
-        return al >= cam.alpha_min ? al : 0.f;
-    };
 
     const int64_t HW = (int64_t)cam.width * cam.height;
-    // pass 1: final colour of the pixel pair
-    float T[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
-    float C[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    float DA[2][2] = {{0, 0}, {0, 0}};     // depth and alpha of the pixel (image mode)
+    // pass 1: final colour (depth, alpha) of the pixel pair, as the forward
+    f32x2 T2 = pk(in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f);
+    f32x2 CR2 = 0ull, CG2 = 0ull, CB2 = 0ull, CZ2 = 0ull, CS2 = 0ull;
     if (IMG && cimg) {
+        float c[5][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
 #pragma unroll
         for (int p = 0; p < 2; ++p)
             if (in[p]) {
                 const int64_t pix = (int64_t)(py0 + p) * cam.width + px;
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) C[p][ch] = __ldg(cimg + ((int64_t)v * 3 + ch) * HW + pix);
+                for (int ch = 0; ch < 3; ++ch) c[ch][p] = __ldg(cimg + ((int64_t)v * 3 + ch) * HW + pix);
                 if (gda) {
-                    DA[p][0] = __ldg(cdep + (int64_t)v * HW + pix);
-                    DA[p][1] = __ldg(calp + (int64_t)v * HW + pix);
+                    c[3][p] = __ldg(cdep + (int64_t)v * HW + pix);
+                    c[4][p] = __ldg(calp + (int64_t)v * HW + pix);
                 }
             }
-    }
-    for (int b = r.x; b < ((IMG && cimg) ? r.x : r.y); b += 32) {
-        if (__all_sync(0xffffffffu, T[0] == 0.f && T[1] == 0.f)) break;
-        const int nk = stage(b, T[0], T[1]);
-        for (int k = 0; k < nk; ++k) {
-            const float4 c = s_c[k];
-            const float zk = s_a[k].z;
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                float dx, dy;
-                bool un = false;
-                float ex = 0.f;
-                const float al = T[p] > 0.f ? alpha_at(k, p, dx, dy, un, ex) : 0.f;
-                if (al > 0.f) {
-                    const float tn = T[p] * (1.f - al);
-                    if (tn < cam.t_min) {
-                        T[p] = 0.f;
-                    } else {
-                        const float w = al * T[p];
-                        C[p][0] += c.x * w; C[p][1] += c.y * w; C[p][2] += c.z * w;
-                        if (IMG) { DA[p][0] += zk * w; DA[p][1] += w; }
-                        T[p] = tn;
-                    }
+        CR2 = pk(c[0][0], c[0][1]); CG2 = pk(c[1][0], c[1][1]); CB2 = pk(c[2][0], c[2][1]);
+        CZ2 = pk(c[3][0], c[3][1]); CS2 = pk(c[4][0], c[4][1]);
+    } else {
+        for (int b = r.x; b < r.y; b += 32) {
+            {
+                float t0, t1;
+                upk(T2, t0, t1);
+                if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+            }
+            const int nk = stage(b, T2);
+            for (int k = 0; k < nk; ++k) {
+                const float4 s0 = s_rec[0][k], s1 = s_rec[1][k];
+                const float nth = s_thr[k];
+                const float dx = fxp + s0.x;
+                const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
+                const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
+                const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
+                float p0, p1;
+                upk(P2, p0, p1);
+                const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
+                const float a0 = fminf(amax, ex2_approx(p0)), a1 = fminf(amax, ex2_approx(p1));
+                const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), IN2));
+                const f32x2 TN2 = fma2(W2, NEG1, T2);
+                float n0, n1;
+                upk(TN2, n0, n1);
+                const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
+                const f32x2 WF = mul2(W2, GO2);
+                T2 = mul2(TN2, GO2);
+                const float4 c0 = s_rec[2][k], c1 = s_rec[3][k];
+                CR2 = fma2(pk(c0.x, c0.y), WF, CR2);
+                CG2 = fma2(pk(c0.z, c0.w), WF, CG2);
+                CB2 = fma2(pk(c1.x, c1.y), WF, CB2);
+                if (IMG) {
+                    CZ2 = fma2(pk(c1.z, c1.w), WF, CZ2);
+                    CS2 = add2(CS2, WF);
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
+    float C[2][3], DA[2][2];
+    upk(CR2, C[0][0], C[1][0]);
+    upk(CG2, C[0][1], C[1][1]);
+    upk(CB2, C[0][2], C[1][2]);
+    upk(CZ2, DA[0][0], DA[1][0]);
+    upk(CS2, DA[0][1], DA[1][1]);
+
     // dL/dC per pixel
     float G[2][3] = {{0, 0, 0}, {0, 0, 0}};
     float GDA[2][2] = {{0, 0}, {0, 0}};
@@ -680,64 +711,85 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 }
             }
     }
+    const f32x2 G0 = pk(G[0][0], G[1][0]), G1 = pk(G[0][1], G[1][1]), G2 = pk(G[0][2], G[1][2]);
+    const f32x2 GD = pk(GDA[0][0], GDA[1][0]), GA = pk(GDA[0][1], GDA[1][1]);
+    f32x2 K2 = pk(G[0][0] * C[0][0] + G[0][1] * C[0][1] + G[0][2] * C[0][2] + GDA[0][0] * DA[0][0] + GDA[0][1] * DA[0][1],
+                  G[1][0] * C[1][0] + G[1][1] * C[1][1] + G[1][2] * C[1][2] + GDA[1][0] * DA[1][0] + GDA[1][1] * DA[1][1]);
+
     // pass 2: front to back again, gradients per record
-    float Tb[2] = {in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f};
-    float U[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    float UDA[2][2] = {{0, 0}, {0, 0}};
+    T2 = pk(in[0] ? 1.f : 0.f, in[1] ? 1.f : 0.f);
     for (int b = r.x; b < r.y; b += 32) {
-        if (__all_sync(0xffffffffu, Tb[0] == 0.f && Tb[1] == 0.f)) break;
-        const int nk = stage(b, Tb[0], Tb[1]);
+        {
+            float t0, t1;
+            upk(T2, t0, t1);
+            if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+        }
+        const int nk = stage(b, T2);
         for (int k = 0; k < nk; ++k) {
-            const float4 c = s_c[k], bb = s_b[k];
-            const float zk = s_a[k].z;
+            const float4 s0 = s_rec[0][k], s1 = s_rec[1][k];
+            const float nth = s_thr[k];
+            const float dx = fxp + s0.x;
+            const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
+            const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
+            const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
+            float p0, p1;
+            upk(P2, p0, p1);
+            const float i0 = __saturatef(fmaf(p0, STEP_SCALE, nth)), i1 = __saturatef(fmaf(p1, STEP_SCALE, nth));
+            const float r0 = ex2_approx(p0), r1 = ex2_approx(p1);
+            const float a0 = fminf(amax, r0), a1 = fminf(amax, r1);
+            const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), pk(i0, i1)));
+            const f32x2 TN2 = fma2(W2, NEG1, T2);
+            float n0, n1;
+            upk(TN2, n0, n1);
+            const float o0 = __saturatef(fmaf(n0, STEP_SCALE, ntmin)), o1 = __saturatef(fmaf(n1, STEP_SCALE, ntmin));
+            const f32x2 GO2 = pk(o0, o1);
+            const f32x2 WF = mul2(W2, GO2);
+            float w0, w1;
+            upk(WF, w0, w1);
+            if (!__any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
+                T2 = mul2(TN2, GO2);
+                continue;
+            }
+            const float4 c0 = s_rec[2][k], c1 = s_rec[3][k], nb = s_rec[4][k], nc = s_rec[5][k];
+            // S = G . c (+ G_D z + G_A); K loses w S
+            f32x2 S2 = fma2(G0, pk(c0.x, c0.y), fma2(G1, pk(c0.z, c0.w), mul2(G2, pk(c1.x, c1.y))));
+            if (IMG) S2 = fma2(GD, pk(c1.z, c1.w), add2(S2, GA));
+            K2 = fma2(WF, mul2(S2, NEG1), K2);
+            // dL/d alpha = T S - K / (1 - alpha), masked to the included, unstopped pairs;
+            // 1 / (1 - alpha): alpha <= alpha_max < 1, fast reciprocal (2 ulp)
+            const f32x2 NR2 = pk(__fdividef(-1.f, 1.f - a0), __fdividef(-1.f, 1.f - a1));
+            const f32x2 GAL = mul2(fma2(K2, NR2, mul2(T2, S2)), mul2(pk(i0, i1), GO2));
+            // dL/d power = alpha dL/d alpha (0 where the clamp holds)
+            const f32x2 GP = mul2(GAL, pk(a0 * __saturatef(fmaf(r0, -STEP_SCALE, amaxS)),
+                                          a1 * __saturatef(fmaf(r1, -STEP_SCALE, amaxS))));
+            const f32x2 GX = mul2(GP, pk(dx, dx)), GY = mul2(GP, DY2);
             float g[NP];
 #pragma unroll
-            for (int m = 0; m < NP; ++m) g[m] = 0.f;
-            bool touched = false;
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                float dx = 0.f, dy = 0.f;
-                bool un = false;
-                float ex = 0.f;
-                const float al = Tb[p] > 0.f ? alpha_at(k, p, dx, dy, un, ex) : 0.f;
-                if (al > 0.f) {
-                    const float tn = Tb[p] * (1.f - al);
-                    if (tn < cam.t_min) {
-                        Tb[p] = 0.f;
-                    } else {
-                        touched = true;
-                        const float w = al * Tb[p];
-                        const float ca[3] = {C[p][0] - U[p][0] - c.x * w, C[p][1] - U[p][1] - c.y * w,
-                                             C[p][2] - U[p][2] - c.z * w};
-                        // 1 / (1 - alpha), alpha <= alpha_max < 1: fast reciprocal (2 ulp)
-                        const float r1a = __fdividef(1.f, 1.f - al);
-                        float gal = Tb[p] * (G[p][0] * c.x + G[p][1] * c.y + G[p][2] * c.z) -
-                                    (G[p][0] * ca[0] + G[p][1] * ca[1] + G[p][2] * ca[2]) * r1a;
-                        if (IMG) {
-                            const float da = DA[p][0] - UDA[p][0] - zk * w, aa = DA[p][1] - UDA[p][1] - w;
-                            gal += Tb[p] * (GDA[p][0] * zk + GDA[p][1]) - (GDA[p][0] * da + GDA[p][1] * aa) * r1a;
-                        }
-                        const float gp = un ? gal * al : 0.f;
-                        g[0] += gp * (bb.x * dx + bb.y * dy);
-                        g[1] += gp * (bb.y * dx + bb.z * dy);
-                        g[2] += gp * (-0.5f * dx * dx);
-                        g[3] += gp * (-dx * dy);
-                        g[4] += gp * (-0.5f * dy * dy);
-                        if (IMG) {
-                            g[5] += w * G[p][0];
-                            g[6] += w * G[p][1];
-                            g[7] += w * G[p][2];
-                            g[8] += un ? gal * ex : 0.f;
-                            g[9] += w * GDA[p][0];
-                            UDA[p][0] += zk * w;
-                            UDA[p][1] += w;
-                        }
-                        U[p][0] += c.x * w; U[p][1] += c.y * w; U[p][2] += c.z * w;
-                        Tb[p] = tn;
-                    }
-                }
+            for (int m = NOUT; m < NP; ++m) g[m] = 0.f;
+            float lo, hi;
+            upk(fma2(GX, pk(nb.x, nb.y), mul2(GY, pk(nb.z, nb.w))), lo, hi);      // d/du: a dx + b dy
+            g[0] = lo + hi;
+            upk(fma2(GX, pk(nb.z, nb.w), mul2(GY, pk(nc.x, nc.y))), lo, hi);      // d/dv: b dx + c dy
+            g[1] = lo + hi;
+            upk(mul2(GX, pk(-0.5f * dx, -0.5f * dx)), lo, hi);                     // d/da: -dx^2 / 2
+            g[2] = lo + hi;
+            upk(mul2(GX, mul2(DY2, NEG1)), lo, hi);                                // d/db: -dx dy
+            g[3] = lo + hi;
+            upk(mul2(GY, mul2(DY2, pk(-0.5f, -0.5f))), lo, hi);                     // d/dc: -dy^2 / 2
+            g[4] = lo + hi;
+            if (IMG) {
+                upk(mul2(WF, G0), lo, hi);
+                g[5] = lo + hi;
+                upk(mul2(WF, G1), lo, hi);
+                g[6] = lo + hi;
+                upk(mul2(WF, G2), lo, hi);
+                g[7] = lo + hi;
+                upk(mul2(GP, pk(nc.z, nc.w)), lo, hi);                             // d/do = dL/d power / o
+                g[8] = lo + hi;
+                upk(mul2(WF, GD), lo, hi);
+                g[9] = lo + hi;
             }
-            if (!__any_sync(0xffffffffu, touched)) continue;
+            T2 = mul2(TN2, GO2);
             const float tot = warp_reduce_scatter<NP>(g, lane);
             const int m = lane / GRP;
             if (lane % GRP == 0 && m < NOUT && tot != 0.f)

@@ -233,4 +233,7 @@ def test_sub_batches_do_not_change_the_loss_or_gradient(R):
     (La, Ga), (Lb, Gb) = out
     print("loss", La, Lb, "max |dG|", np.abs(Ga - Gb).max(), "max |G|", np.abs(Ga).max())
     assert abs(La - Lb) <= 1e-9 * La
-    assert np.abs(Ga - Gb).max() <= 1e-5 * np.abs(Ga).max()
+    # the per-Gaussian FP32 sums regroup (views per thread, atomics across groups):
+    # rounding of cancelling terms reaches ~2e-5 of the largest entry; a pair lost
+    # or doubled across sub-batches would be of the order of the entry itself
+    assert np.abs(Ga - Gb).max() <= 1e-4 * np.abs(Ga).max()
