@@ -237,3 +237,17 @@ def test_sub_batches_do_not_change_the_loss_or_gradient(R):
     # rounding of cancelling terms reaches ~2e-5 of the largest entry; a pair lost
     # or doubled across sub-batches would be of the order of the entry itself
     assert np.abs(Ga - Gb).max() <= 1e-4 * np.abs(Ga).max()
+
+
+def test_empty_subset_renders_black(R):
+    """No Gaussians selected: every render is black, so L1 alone is the mean
+    of the targets and the gradient is zero."""
+    s, g0, poses, gt = tiny_training(n_views=2)
+    tg = torch.tensor(gt.astype(np.float32), device="cuda:0")
+    ctx = R.Context()
+    ctx.load_map(g0)
+    grad = torch.full((14, g0.n), 3.0, device="cuda:0")
+    L = ctx.train_grad([], poses, s.camera, tg, grad, lambda_dssim=0.0, w_reproj=1.0)
+    ref = float(np.abs(gt.astype(np.float32).astype(np.float64)).mean())
+    assert abs(L - ref) <= 1e-6 * ref
+    assert float(grad.abs().max()) == 0.0
