@@ -1749,7 +1749,7 @@ extern "C" reloc_status reloc_refine_pnp(reloc_ctx *ctx, const double *pose_rend
             return fail(RELOC_ENUMERIC, "non-finite pose");
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
-    CKS(ctx->pnp_X.ensure(32 * (size_t)n_pairs));
+    CKS(ctx->pnp_X.ensure(32 * (size_t)n_pairs + (256 << 10)));   // points, then per-block sums and state
     CKS(ctx->pnp_out.ensure(sizeof(double) * 20));
     CK(launch_refine_pnp(pose_render, pose_init, cam->fx, cam->fy, cam->cx, cam->cy, cam->width, cam->height,
                          depth_dev, alpha_dev, pairs_dev, n_pairs, o.max_iters, o.huber_px, o.alpha_min, o.tol,

@@ -143,8 +143,9 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 // Allow K4 its largest shared-memory footprint (once per device, before any capture).
 cudaError_t configure_tile_kernels();
 
-// Pose refinement by PnP on one view's depth (pnp.cu): out_dev[20] = pose[16],
-// rms, cost, n_used, iterations; X_scratch: 4 doubles per pair.
+// Pose refinement by PnP on one view's depth (pnp.cu), one cooperative launch:
+// out_dev[20] = pose[16], rms, cost, n_used, iterations; X_scratch: 4 doubles
+// per pair, then per-block sums and the solver state (under 256 KB).
 cudaError_t launch_refine_pnp(const double *pose_render, const double *pose_init, double fx, double fy, double cx,
                               double cy, int width, int height, const float *depth, const float *alpha,
                               const float *pairs, int n, int max_iters, double huber, double alpha_min, double tol,

@@ -9,9 +9,17 @@
 // point P = R X + t is [I | -[P]x] and of its pixel
 // J_pi = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]].
 //
-// The problem is small (thousands of pairs, a 6 x 6 system per iteration), so
-// one block does it all: the pairs are spread over its threads, the normal
-// equations are summed with a block reduction and one thread factors them.
+// The problem is small (thousands of pairs, a 6 x 6 system per iteration)
+// but FP64, whose rate per SM is low on this GPU, so the pairs are spread
+// over up to one block per SM in one cooperative launch: every pass over the
+// pairs writes one partial sum per block, block 0 adds them in block order
+// (the result does not depend on timing) and factors the system, and grid
+// barriers separate the phases.  The solver state (pose, trial pose, step,
+// decision) lives in global memory and is read past L1 after each barrier.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace reloc {
@@ -28,8 +36,14 @@ struct PnpArgs {
     const float *depth, *alpha;
     const float4 *pairs;
     double4 *X;                          // scratch [n]: world point, w = 1 if used
+    double *part;                        // scratch [gridDim.x][PNP_ACC]: per-block sums
+    double *st;                          // scratch [PNP_STATE]: solver state
     double *out;                         // [16 pose, rms, cost, n_used, iters, status]
 };
+
+// solver state in global memory
+enum { PS_POSE = 0, PS_TRIAL = 12, PS_DELTA = 24, PS_COST = 30, PS_STEP = 31, PS_FLAG = 32, PS_NUSED = 33,
+       PNP_STATE = 34 };
 
 __device__ __forceinline__ double warp_sum_dbl(double x)
 {
@@ -64,7 +78,7 @@ template <bool GRAD, bool RMS>
 __device__ void pnp_accumulate(const PnpArgs &a, const double *R, const double *t, double *acc)
 {
     for (int j = 0; j < PNP_ACC; ++j) acc[j] = 0.0;
-    for (int i = threadIdx.x; i < a.n; i += PNP_THREADS) {
+    for (int i = blockIdx.x * PNP_THREADS + threadIdx.x; i < a.n; i += gridDim.x * PNP_THREADS) {
         const double4 X = a.X[i];
         if (X.w == 0.0) continue;
         const float4 q = a.pairs[i];
@@ -159,18 +173,39 @@ __device__ bool solve6(const double *Hu, const double *g, double *x)
     return true;
 }
 
+// This block's sums of v[0..m) into part[blockIdx.x][0..m).
+__device__ void block_partial(const PnpArgs &a, const double *v, int m, double (*s_red)[PNP_ACC], double *s_sum)
+{
+    block_sum(v, m, s_red, s_sum);
+    if (threadIdx.x < m) a.part[(int64_t)blockIdx.x * PNP_ACC + threadIdx.x] = s_sum[threadIdx.x];
+}
+
+// Block 0: totals of the per-block sums of entries [j0, j0 + m), in block order.
+__device__ void grid_total(const PnpArgs &a, int j0, int m, double *out)
+{
+    if (threadIdx.x < m) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(a.part + (int64_t)b * PNP_ACC + j0 + threadIdx.x);
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(PNP_THREADS) k_refine_pnp(PnpArgs a)
 {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
     __shared__ double s_red[PNP_THREADS / 32][PNP_ACC];
     __shared__ double s_sum[PNP_ACC];
-    __shared__ double s_pose[12], s_trial[12], s_delta[6];
-    __shared__ double s_cost, s_step;
-    __shared__ int s_state;                          // 0 going, 1 accepted, 2 stop
+    __shared__ double s_tot[PNP_ACC];
+    __shared__ double s_pose[12];
     double acc[PNP_ACC];
+    double *st = a.st;
+    const bool lead = blockIdx.x == 0;
 
     // back-projection of every pair with the rendered depth
     double used = 0.0;
-    for (int i = threadIdx.x; i < a.n; i += PNP_THREADS) {
+    for (int i = blockIdx.x * PNP_THREADS + threadIdx.x; i < a.n; i += gridDim.x * PNP_THREADS) {
         const float4 p = a.pairs[i];
         double4 X = make_double4(0.0, 0.0, 0.0, 0.0);
         const double sx = (double)p.x - 0.5, sy = (double)p.y - 0.5;
@@ -198,60 +233,96 @@ __global__ void __launch_bounds__(PNP_THREADS) k_refine_pnp(PnpArgs a)
         }
         a.X[i] = X;
     }
-    if (threadIdx.x < 12) s_pose[threadIdx.x] = a.W0[threadIdx.x];
-    block_sum(&used, 1, s_red, s_sum);
-    const double n_used = s_sum[0];
+    block_partial(a, &used, 1, s_red, s_sum);
+    grid.sync();
+    if (lead) {
+        grid_total(a, 0, 1, s_tot);
+        if (threadIdx.x < 12) st[PS_POSE + threadIdx.x] = a.W0[threadIdx.x];
+        if (threadIdx.x == 0) st[PS_NUSED] = s_tot[0];
+    }
+    grid.sync();
+    const double n_used = __ldcg(st + PS_NUSED);
+    // load a 12-entry pose from the state into shared memory
+    auto load_pose = [&](int off) {
+        if (threadIdx.x < 12) s_pose[threadIdx.x] = __ldcg(st + off + threadIdx.x);
+        __syncthreads();
+    };
     int it = 0;
     if (n_used >= 3.0) {
         for (; it < a.max_iters; ++it) {
+            load_pose(PS_POSE);
             pnp_accumulate<true, false>(a, s_pose, s_pose + 9, acc);
-            block_sum(acc, PNP_ACC, s_red, s_sum);
-            if (threadIdx.x == 0) {
-                s_cost = s_sum[27];
-                s_state = solve6(s_sum, s_sum + 21, s_delta) ? 0 : 2;
-                s_step = 1.0;
-            }
-            __syncthreads();
-            if (s_state == 2) break;
-            for (int bt = 0; bt <= 10; ++bt) {      // backtrack until the cost drops
-                if (threadIdx.x == 0) apply_update(s_pose, s_delta, s_step, s_trial);
-                __syncthreads();
-                pnp_accumulate<false, false>(a, s_trial, s_trial + 9, acc);
-                block_sum(acc + 27, 1, s_red, s_sum);
+            block_partial(a, acc, PNP_ACC, s_red, s_sum);
+            grid.sync();
+            if (lead) {
+                grid_total(a, 0, PNP_ACC, s_tot);
                 if (threadIdx.x == 0) {
-                    if (s_sum[0] < s_cost) {
-                        for (int j = 0; j < 12; ++j) s_pose[j] = s_trial[j];
-                        s_state = 1;
-                    } else {
-                        s_step *= 0.5;
+                    double delta[6];
+                    const bool ok = solve6(s_tot, s_tot + 21, delta);
+                    for (int j = 0; j < 6; ++j) st[PS_DELTA + j] = delta[j];
+                    st[PS_COST] = s_tot[27];
+                    st[PS_STEP] = 1.0;
+                    st[PS_FLAG] = ok ? 0.0 : 2.0;
+                }
+            }
+            grid.sync();
+            if (__ldcg(st + PS_FLAG) == 2.0) break;
+            for (int bt = 0; bt <= 10; ++bt) {      // backtrack until the cost drops
+                if (lead && threadIdx.x == 0) {
+                    double W[12], d[6], Wt[12];
+                    for (int j = 0; j < 12; ++j) W[j] = st[PS_POSE + j];
+                    for (int j = 0; j < 6; ++j) d[j] = st[PS_DELTA + j];
+                    apply_update(W, d, st[PS_STEP], Wt);
+                    for (int j = 0; j < 12; ++j) st[PS_TRIAL + j] = Wt[j];
+                }
+                grid.sync();
+                load_pose(PS_TRIAL);
+                pnp_accumulate<false, false>(a, s_pose, s_pose + 9, acc);
+                block_partial(a, acc + 27, 1, s_red, s_sum);
+                grid.sync();
+                if (lead) {
+                    grid_total(a, 0, 1, s_tot);
+                    if (threadIdx.x == 0) {
+                        if (s_tot[0] < st[PS_COST]) {
+                            for (int j = 0; j < 12; ++j) st[PS_POSE + j] = st[PS_TRIAL + j];
+                            st[PS_FLAG] = 1.0;
+                        } else {
+                            st[PS_STEP] *= 0.5;
+                        }
                     }
                 }
-                __syncthreads();
-                if (s_state == 1) break;
+                grid.sync();
+                if (__ldcg(st + PS_FLAG) == 1.0) break;
             }
-            if (s_state != 1) break;                 // no step lowers the cost: converged
+            if (__ldcg(st + PS_FLAG) != 1.0) break;  // no step lowers the cost: converged
             double dmax = 0.0;
-            for (int j = 0; j < 6; ++j) dmax = fmax(dmax, fabs(s_step * s_delta[j]));
+            const double step = __ldcg(st + PS_STEP);
+            for (int j = 0; j < 6; ++j) dmax = fmax(dmax, fabs(step * __ldcg(st + PS_DELTA + j)));
             if (dmax < a.tol) {
                 ++it;
                 break;
             }
         }
     }
+    load_pose(PS_POSE);
     pnp_accumulate<false, true>(a, s_pose, s_pose + 9, acc);
     acc[2] = acc[27];
-    block_sum(acc, 3, s_red, s_sum);
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) a.out[4 * r + c] = s_pose[3 * r + c];
-            a.out[4 * r + 3] = s_pose[9 + r];
+    block_partial(a, acc, 3, s_red, s_sum);
+    grid.sync();
+    if (lead) {
+        grid_total(a, 0, 3, s_tot);
+        if (threadIdx.x == 0) {
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) a.out[4 * r + c] = s_pose[3 * r + c];
+                a.out[4 * r + 3] = s_pose[9 + r];
+            }
+            a.out[12] = a.out[13] = a.out[14] = 0.0;
+            a.out[15] = 1.0;
+            a.out[16] = s_tot[1] > 0.0 ? sqrt(s_tot[0] / s_tot[1]) : 0.0;
+            a.out[17] = s_tot[2];
+            a.out[18] = n_used;
+            a.out[19] = (double)it;
         }
-        a.out[12] = a.out[13] = a.out[14] = 0.0;
-        a.out[15] = 1.0;
-        a.out[16] = s_sum[1] > 0.0 ? sqrt(s_sum[0] / s_sum[1]) : 0.0;
-        a.out[17] = s_sum[2];
-        a.out[18] = n_used;
-        a.out[19] = (double)it;
     }
 }
 
@@ -276,8 +347,17 @@ cudaError_t launch_refine_pnp(const double *pose_render, const double *pose_init
     a.pairs = reinterpret_cast<const float4 *>(pairs);
     a.X = reinterpret_cast<double4 *>(X_scratch);
     a.out = out_dev;
-    k_refine_pnp<<<1, PNP_THREADS, 0, st>>>(a);
-    return cudaGetLastError();
+    // one block per SM at most (all resident: the launch is cooperative)
+    int dev = 0, n_sm = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(n_sm, ceil_div(n, PNP_THREADS)));
+    a.part = X_scratch + 4 * (int64_t)n;
+    a.st = a.part + (int64_t)nb * PNP_ACC;
+    void *args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void *)k_refine_pnp, dim3(nb), dim3(PNP_THREADS), args, 0, st);
+    return e;
 }
 
 }  // namespace reloc
