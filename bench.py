@@ -335,6 +335,7 @@ def run_refine_leg(ctx, cam, dev, stream, n_queries=8, iters=3):
     gen = torch.Generator(device=dev)
     gen.manual_seed(72)
     before, after, lib_ms, n_pairs = [], [], [], []
+    render_ms, pnp_ms = [], []
     for i in range(n_queries):
         Wh = sg.pose_from_xyz_yaw(*hidden[i])
         runs, _, _ = ctx.select_block(hidden[i][0], hidden[i][1], RADIUS)
@@ -361,6 +362,8 @@ def run_refine_leg(ctx, cam, dev, stream, n_queries=8, iters=3):
             Wk = np.array(out.pose).reshape(4, 4)
             if it > 0:
                 lib_ms.append(1e3 * ((t1 - t0) + (t3 - t2)))
+                render_ms.append(1e3 * (t1 - t0))
+            pnp_ms.append(1e3 * (t3 - t2))
             n_pairs.append(int(pairs.shape[0]))
         after.append(_pose_error(Wk, Wh))
     b, a = np.array(before), np.array(after)
@@ -369,7 +372,9 @@ def run_refine_leg(ctx, cam, dev, stream, n_queries=8, iters=3):
             "error_before_m_deg": [float(np.median(b[:, 0])), float(np.median(b[:, 1]))],
             "error_after_m_deg": [float(np.median(a[:, 0])), float(np.median(a[:, 1]))],
             "max_error_after_m_deg": [float(a[:, 0].max()), float(a[:, 1].max())],
-            "library_ms_per_iteration": float(np.mean(lib_ms)) if lib_ms else None}
+            "library_ms_per_iteration": float(np.mean(lib_ms)) if lib_ms else None,
+            "render_ms_per_iteration": float(np.mean(render_ms)) if render_ms else None,
+            "pnp_ms_per_solve": float(np.mean(pnp_ms)) if pnp_ms else None}
 
 
 def run_ascent_leg(cam, dev, stream, n_queries=4, iters=15):

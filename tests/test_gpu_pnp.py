@@ -49,6 +49,21 @@ def test_pnp_matches_oracle(R, noise, outliers):
     assert abs(res.rms_px - ref["rms_px"]) <= 1e-6 * max(1.0, ref["rms_px"])
 
 
+def test_pnp_many_pairs_matches_oracle(R):
+    """Every pixel of the tiny view as a pair (~25k pairs, so the solve spreads
+    over about a hundred blocks): the same pose as the oracle's FP64 solve."""
+    s, Wq, Wr = tiny_views()
+    depth, alpha, pairs = make_pairs(s, Wq, Wr, step=1, noise_px=0.3, outlier_frac=0.1, seed=5)
+    ref = oracle.refine_pnp(Wr, s.camera, depth, alpha, pairs)
+    ctx = R.Context()
+    res = ctx.refine_pnp(Wr, s.camera, dev(depth), dev(alpha), dev(pairs))
+    dt, dr = pose_error(np.array(res.pose).reshape(4, 4), ref["pose"])
+    print(len(pairs), "pairs; gpu vs oracle", dt, dr, res.iters, ref["iters"])
+    assert len(pairs) > 20000 and res.n_used == ref["n_used"]
+    assert dt < 1e-9 and dr < 1e-10
+    assert abs(res.rms_px - ref["rms_px"]) <= 1e-6 * max(1.0, ref["rms_px"])
+
+
 def test_pnp_invalid_calls(R):
     s, Wq, Wr = tiny_views()
     depth, alpha, pairs = make_pairs(s, Wq, Wr)
