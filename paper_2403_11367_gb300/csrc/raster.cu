@@ -186,10 +186,13 @@ __device__ __forceinline__ float ex2_approx(float x)
 //   p' = A' dx^2 + B' dx dy + C' dy^2 + log2(o) = power * log2(e) + log2(o),
 // so alpha = min(alpha_max, 2^p') = min(alpha_max, o exp(power)).  The 3-sigma
 // rule (power >= -cut^2/2) and alpha >= alpha_min become one threshold on p':
-// p' >= max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)).  A pixel that stops
-// (T (1 - alpha) < t_min, the stopping Gaussian not added) gets T = 0, so
-// later weights vanish without a flag; its alpha output is the sum of its
-// weights, which telescopes to 1 - T before the stop.  Both tests are step
+// p' >= max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)).  The transmittance
+// is carried as T' = prod (1 - alpha) past the stop: T' only decreases, so a
+// pixel's stop (T (1 - alpha) < t_min, the stopping Gaussian not added) is the
+// first record where T' falls below t_min, and a weight is kept while T' after
+// it is >= t_min -- no flag, and one multiply per record on the dependency
+// chain; the alpha output is the sum of the kept weights, which telescopes to
+// 1 - T before the stop.  Both tests are step
 // functions sat((x - t) 2^60), one saturating fused multiply-add per pixel:
 // any positive float difference times 2^60 saturates to 1, a negative one to
 // 0 (only x == t exactly falls on the other side of a >= test).
@@ -244,7 +247,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     // depth and weight sums
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
-    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
+    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
     const float ntmin = -cam.t_min * STEP_SCALE;
 
     // software pipeline: list indices two steps ahead, records one step ahead
@@ -260,14 +263,14 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         gnext[q] = j1 < r.y ? __ldg(list + j1) : 0u;
     }
     for (int b = r.x; b < r.y; b += CH) {
-        // pixel-centre box of the pixels still compositing (a stopped pixel has
-        // T = 0 exactly and takes nothing more, so records that miss this box
+        // pixel-centre box of the pixels still compositing (a pixel has stopped
+        // once T < t_min and takes nothing more, so records that miss this box
         // would add nothing)
         float bx0, bx1, by0, by1;
         {
             float t0, t1;
             upk(T2, t0, t1);
-            const bool a0 = t0 > 0.f, a1 = t1 > 0.f;
+            const bool a0 = t0 >= cam.t_min && in0, a1 = t1 >= cam.t_min && in1;
             if (__all_sync(0xffffffffu, !a0 && !a1)) break;
             const unsigned rlo = __reduce_min_sync(0xffffffffu, a0 ? (unsigned)py0 : (a1 ? (unsigned)py1 : 0xffffu));
             const unsigned rhi = __reduce_max_sync(0xffffffffu, a1 ? (unsigned)py1 : (a0 ? (unsigned)py0 : 0u));
@@ -326,14 +329,17 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
             const float a0 = fminf(cam.alpha_max, ex2_approx(p0));
             const float a1 = fminf(cam.alpha_max, ex2_approx(p1));
-            const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), IN2));
-            const f32x2 TN2 = fma2(W2, NEG1, T2);
+            // T' = T (1 - alpha) carries on past the stop: it only decreases, so
+            // T' >= t_min holds up to the stop and never after; the weight is
+            // kept while it holds (one multiply on the dependency chain)
+            const f32x2 AIN = mul2(pk(a0, a1), IN2);
+            const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
             float n0, n1;
             upk(TN2, n0, n1);
             // T (1 - alpha) >= t_min
             const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
-            const f32x2 WF = mul2(W2, GO2);
-            T2 = mul2(TN2, GO2);
+            const f32x2 WF = mul2(mul2(T2, AIN), GO2);
+            T2 = TN2;
             const float4 c0 = sw[2][k];
             R2 = fma2(pk(c0.x, c0.y), WF, R2);
             G2 = fma2(pk(c0.z, c0.w), WF, G2);
@@ -562,14 +568,14 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const float ntmin = -cam.t_min * STEP_SCALE;
     const float amax = cam.alpha_max, amaxS = cam.alpha_max * STEP_SCALE;
     const unsigned lt = lanemask_lt_u();
-    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f);
+    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
 
     // the forward's cull and compaction, one step of 32 records, against the
     // box of the pixels still compositing (T > 0)
     auto stage = [&](int b, f32x2 T2) -> int {
         float t0, t1;
         upk(T2, t0, t1);
-        const bool a0 = t0 > 0.f, a1 = t1 > 0.f;
+        const bool a0 = t0 >= cam.t_min && in[0], a1 = t1 >= cam.t_min && in[1];
         const unsigned rlo = __reduce_min_sync(0xffffffffu, a0 ? (unsigned)py0 : (a1 ? (unsigned)py0 + 1u : 0xffffu));
         const unsigned rhi = __reduce_max_sync(0xffffffffu, a1 ? (unsigned)py0 + 1u : (a0 ? (unsigned)py0 : 0u));
         const unsigned clo = __reduce_min_sync(0xffffffffu, (a0 || a1) ? (unsigned)px : 0xffffu);
@@ -633,7 +639,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             {
                 float t0, t1;
                 upk(T2, t0, t1);
-                if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+                if (__all_sync(0xffffffffu, !(t0 >= cam.t_min && in[0]) && !(t1 >= cam.t_min && in[1]))) break;
             }
             const int nk = stage(b, T2);
             for (int k = 0; k < nk; ++k) {
@@ -647,13 +653,13 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 upk(P2, p0, p1);
                 const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
                 const float a0 = fminf(amax, ex2_approx(p0)), a1 = fminf(amax, ex2_approx(p1));
-                const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), IN2));
-                const f32x2 TN2 = fma2(W2, NEG1, T2);
+                const f32x2 AIN = mul2(pk(a0, a1), IN2);
+                const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
                 float n0, n1;
                 upk(TN2, n0, n1);
                 const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
-                const f32x2 WF = mul2(W2, GO2);
-                T2 = mul2(TN2, GO2);
+                const f32x2 WF = mul2(mul2(T2, AIN), GO2);
+                T2 = TN2;
                 const float4 c0 = s_rec[2][k], c1 = s_rec[3][k];
                 CR2 = fma2(pk(c0.x, c0.y), WF, CR2);
                 CG2 = fma2(pk(c0.z, c0.w), WF, CG2);
@@ -722,7 +728,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         {
             float t0, t1;
             upk(T2, t0, t1);
-            if (__all_sync(0xffffffffu, t0 == 0.f && t1 == 0.f)) break;
+            if (__all_sync(0xffffffffu, !(t0 >= cam.t_min && in[0]) && !(t1 >= cam.t_min && in[1]))) break;
         }
         const int nk = stage(b, T2);
         for (int k = 0; k < nk; ++k) {
@@ -737,17 +743,17 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             const float i0 = __saturatef(fmaf(p0, STEP_SCALE, nth)), i1 = __saturatef(fmaf(p1, STEP_SCALE, nth));
             const float r0 = ex2_approx(p0), r1 = ex2_approx(p1);
             const float a0 = fminf(amax, r0), a1 = fminf(amax, r1);
-            const f32x2 W2 = mul2(T2, mul2(pk(a0, a1), pk(i0, i1)));
-            const f32x2 TN2 = fma2(W2, NEG1, T2);
+            const f32x2 AIN = mul2(pk(a0, a1), pk(i0, i1));
+            const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
             float n0, n1;
             upk(TN2, n0, n1);
             const float o0 = __saturatef(fmaf(n0, STEP_SCALE, ntmin)), o1 = __saturatef(fmaf(n1, STEP_SCALE, ntmin));
             const f32x2 GO2 = pk(o0, o1);
-            const f32x2 WF = mul2(W2, GO2);
+            const f32x2 WF = mul2(mul2(T2, AIN), GO2);
             float w0, w1;
             upk(WF, w0, w1);
             if (!__any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
-                T2 = mul2(TN2, GO2);
+                T2 = TN2;
                 continue;
             }
             const float4 c0 = s_rec[2][k], c1 = s_rec[3][k], nb = s_rec[4][k], nc = s_rec[5][k];
@@ -789,7 +795,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 upk(mul2(WF, GD), lo, hi);
                 g[9] = lo + hi;
             }
-            T2 = mul2(TN2, GO2);
+            T2 = TN2;
             const float tot = warp_reduce_scatter<NP>(g, lane);
             const int m = lane / GRP;
             if (lane % GRP == 0 && m < NOUT && tot != 0.f)
