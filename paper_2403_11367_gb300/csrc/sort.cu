@@ -78,16 +78,22 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
     const int n = (int)max64(0, min64(SORT_CHUNK, seg_len - begin));
     const int64_t base = p.seg_off[s] + begin;
     const unsigned lt = lanemask_lt();
-    for (int b = 0; b < n; b += SORT_THREADS) {
-        const int idx = b + threadIdx.x;
-        bool valid = idx < n;
-        uint32_t d = RADIX;
-        if (valid) {
-            if (p.filt) valid = p.filt[base + idx] != 0;
-            if (valid) d = (p.keys_in[base + idx] >> p.shift) & p.mask;
+    // all of this thread's loads first (independent, in flight together), then the counts
+    uint32_t d[SORT_IPT];
+#pragma unroll
+    for (int r = 0; r < SORT_IPT; ++r) {
+        const int idx = r * SORT_THREADS + threadIdx.x;
+        d[r] = RADIX;
+        if (idx < n) {
+            const uint32_t k = p.keys_in[base + idx];
+            const bool keep = p.filt ? p.filt[base + idx] != 0 : true;
+            d[r] = keep ? (k >> p.shift) & p.mask : (uint32_t)RADIX;
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lt) == 0) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    }
+#pragma unroll
+    for (int r = 0; r < SORT_IPT; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+        if (d[r] != (uint32_t)RADIX && (peers & lt) == 0) atomicAdd(&s_h[d[r]], (uint32_t)__popc(peers));
     }
     __syncthreads();
     const uint32_t cnt = s_h[threadIdx.x];
@@ -169,16 +175,24 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
     const int64_t base = p.seg_off[s] + begin;
     const unsigned lt = lanemask_lt();
     uint32_t key[SORT_IPT], val[SORT_IPT], rank[SORT_IPT];
+    bool vld[SORT_IPT];
+    // all of this thread's loads first (independent, in flight together), then the ranks
 #pragma unroll
     for (int r = 0; r < SORT_IPT; ++r) {
         const int idx = warp * (32 * SORT_IPT) + r * 32 + lane;
-        bool valid = idx < n;
-        uint32_t kk = 0, vv = 0;
-        if (valid) {
-            if (p.filt) valid = p.filt[base + idx] != 0;
-            kk = p.keys_in[base + idx];
-            vv = p.vals_in ? p.vals_in[base + idx] : (uint32_t)(begin + idx);
+        vld[r] = idx < n;
+        key[r] = 0u;
+        val[r] = 0u;
+        if (vld[r]) {
+            key[r] = p.keys_in[base + idx];
+            val[r] = p.vals_in ? p.vals_in[base + idx] : (uint32_t)(begin + idx);
+            if (p.filt) vld[r] = p.filt[base + idx] != 0;
         }
+    }
+#pragma unroll
+    for (int r = 0; r < SORT_IPT; ++r) {
+        const bool valid = vld[r];
+        const uint32_t kk = key[r], vv = val[r];
         const uint32_t d = valid ? (kk >> p.shift) & p.mask : (uint32_t)RADIX;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = 0;
