@@ -82,12 +82,26 @@ template <int NQ>
 __device__ __forceinline__ void ssim_load(float (*dst)[SS_H * SS_IN_STRIDE], const float *const (&src)[NQ], int H,
                                           int W, int x0, int y0)
 {
-    for (int k = threadIdx.x; k < SS_H * SS_H; k += SS_THREADS) {
+    // every load of the thread first (all in flight together), then the stores
+    constexpr int PER = (SS_H * SS_H + SS_THREADS - 1) / SS_THREADS;
+    float v[PER][NQ];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int k = u * SS_THREADS + threadIdx.x;
         const int r = k / SS_H, c = k - r * SS_H;
         const int gy = y0 + r - SS_R, gx = x0 + c - SS_R;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const bool in = k < SS_H * SS_H && gy >= 0 && gy < H && gx >= 0 && gx < W;
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) dst[m][r * SS_IN_STRIDE + c] = in ? src[m][(int64_t)gy * W + gx] : 0.f;
+        for (int m = 0; m < NQ; ++m) v[u][m] = in ? src[m][(int64_t)gy * W + gx] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int k = u * SS_THREADS + threadIdx.x;
+        if (k < SS_H * SS_H) {
+            const int r = k / SS_H, c = k - r * SS_H;
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) dst[m][r * SS_IN_STRIDE + c] = v[u][m];
+        }
     }
 }
 
