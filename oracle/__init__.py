@@ -330,6 +330,41 @@ def train_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0, w_photo=1.0, w_re
     return out[0], out[1:]
 
 
+def map_params(g) -> np.ndarray:
+    """The Gaussians' 14 training parameters per row, in PARAM_ORDER (FP64)."""
+    if g.sh_degree != 0:
+        raise ValueError("map training needs SH degree 0")
+    return np.concatenate([g.mean, g.scale, g.quat, g.opacity[:, None], g.sh[:, 0, :]], 1).astype(np.float64)
+
+
+def adam_step(prm, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-15, o_min=1e-6):
+    """One Adam step (Kingma and Ba 2015, Algorithm 1) on 3D Gaussian
+    Splatting's latent parameters of a [n, 14] parameter array (PARAM_ORDER,
+    activated values): the scale through its log (s = exp(l), dL/dl = s dL/ds),
+    the opacity through its logit (o = sigmoid(z), o first clamped to
+    [o_min, 1 - o_min], dL/dz = o (1 - o) dL/do), mean, quaternion and colour
+    as they are.  lr = (mean, scale, quaternion, opacity, colour); t = the step
+    number (1 for the first).  Returns (params, m, v), FP64."""
+    prm = np.asarray(prm, np.float64)
+    g = np.asarray(grad, np.float64).copy()
+    group = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4])
+    o = np.clip(prm[:, 10], o_min, 1.0 - o_min)
+    g[:, 3:6] *= prm[:, 3:6]
+    g[:, 10] *= o * (1.0 - o)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    step = np.asarray(lr, np.float64)[group][None, :] * mhat / (np.sqrt(vhat) + eps)
+    out = prm.copy()
+    for c in (0, 1, 2, 6, 7, 8, 9, 11, 12, 13):
+        out[:, c] = prm[:, c] - step[:, c]
+    out[:, 3:6] = prm[:, 3:6] * np.exp(-step[:, 3:6])
+    z = np.log(o / (1.0 - o)) - step[:, 10]
+    out[:, 10] = 1.0 / (1.0 + np.exp(-z))
+    return out, m, v
+
+
 def photo_loss_jvp(g, poses, cam, gt, dirs, prm=None, lam=0.0):
     """L_photo alone (Eqs. 3-4): train_loss_jvp with w_photo = 1, w_reproj = 0."""
     return train_loss_jvp(g, poses, cam, gt, dirs, prm, lam=lam, w_photo=1.0, w_reproj=0.0)
