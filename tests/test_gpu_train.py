@@ -251,3 +251,43 @@ def test_empty_subset_renders_black(R):
     ref = float(np.abs(gt.astype(np.float32).astype(np.float64)).mean())
     assert abs(L - ref) <= 1e-6 * ref
     assert float(grad.abs().max()) == 0.0
+
+
+def test_adam_step_matches_oracle(R):
+    """One reloc_train_step from fresh Adam state equals the oracle's Adam
+    step applied to the oracle's gradient, for 16 Gaussians of view 0: the
+    full gradient of those Gaussians from one-hot forward-mode derivatives
+    (L1 loss over 2 views).  The first step moves each latent parameter by
+    lr * sign(g), so entries whose oracle gradient is within rounding of 0
+    (where the FP32 sign may differ) are left out."""
+    s, g0, poses, gt = tiny_training(n_views=2, seed=51)
+    tg = torch.tensor(gt.astype(np.float32), device="cuda:0")
+    ctx = R.Context()
+    ctx.load_map(g0)
+    g = g0.subset(ctx.map_order())
+    recs = oracle.project(g, poses[0], s.camera)
+    idx = np.nonzero(recs[:, oracle.F["visible"]] > 0)[0][::97][:16]
+    assert len(idx) == 16
+    opts = dict(lambda_dssim=0.0, w_reproj=0.0)
+    o = R.Context.train_options(**opts)
+    ctx.train_step([(0, ctx.n)], poses, s.camera, tg, **opts)
+    m, sc, q, op, sh = ctx.read_map()
+    after = np.concatenate([m, sc, q, op[:, None], sh[:, 0, :]], 1).astype(np.float64)[idx]
+    gt32 = gt.astype(np.float32).astype(np.float64)
+    G = np.zeros((len(idx), 14))
+    cols = [(j, c) for j in range(len(idx)) for c in range(14)]
+    for k0 in range(0, len(cols), 6):
+        D = np.zeros((g.n, 14, 6))
+        for k, (j, c) in enumerate(cols[k0:k0 + 6]):
+            D[idx[j], c, k] = 1.0
+        _, jv = oracle.train_loss_jvp(g, poses, s.camera, gt32, D, lam=0.0, w_photo=1.0, w_reproj=0.0)
+        for k, (j, c) in enumerate(cols[k0:k0 + 6]):
+            G[j, c] = jv[k]
+    before = oracle.map_params(g)[idx]
+    lr = [o.lr_mean, o.lr_scale, o.lr_quat, o.lr_opacity, o.lr_color]
+    ref, _, _ = oracle.adam_step(before, G, np.zeros_like(G), np.zeros_like(G), 1, lr, o.beta1, o.beta2, o.eps)
+    sure = np.abs(G) > 1e-6 * np.abs(G).max()
+    err = np.abs(after - ref)
+    print("checked", int(sure.sum()), "of", G.size, "max err", err[sure].max())
+    assert sure.sum() > 0.8 * G.size
+    assert np.all(err[sure] <= 1e-6 * np.abs(ref[sure]) + 1e-7)
