@@ -192,14 +192,24 @@ __device__ __forceinline__ float ex2_approx(float x)
 // first record where T' falls below t_min, and a weight is kept while T' after
 // it is >= t_min -- no flag, and one multiply per record on the dependency
 // chain; the alpha output is the sum of the kept weights, which telescopes to
-// 1 - T before the stop.  Both tests are step
-// functions sat((x - t) 2^60), one saturating fused multiply-add per pixel:
-// any positive float difference times 2^60 saturates to 1, a negative one to
-// 0 (only x == t exactly falls on the other side of a >= test).
+// 1 - T before the stop.  Both tests are 0/1 factors from one float compare
+// each (set.ge), which runs on the ALU pipe beside the FMA-bound arithmetic.
 // The column terms dx, A' dx^2 + log2(o) and B' dx are shared by the pixel
 // pair and computed once (scalar); the row terms run packed.  DA: accumulate
 // depth and alpha too (image export); the scoring launches need colour only.
-constexpr float STEP_SCALE = 1152921504606846976.f;   // 2^60
+// 1.0f if a >= b (a < b) else 0.0f: one float compare, on the ALU pipe
+__device__ __forceinline__ float step_ge(float a, float b)
+{
+    float d;
+    asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float step_lt(float a, float b)
+{
+    float d;
+    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
 template <int TW, int TH, int RPL, bool DA>
 __global__ void __launch_bounds__(32, RPL == 1 ? 32 : 24)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
@@ -212,7 +222,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     constexpr int CH = 32 * RPL;             // records per warp step
     static_assert(WPT >= 1 && TH % WROWS == 0, "tile shape");
     // kept records compacted: (-u,A',B',log2 o) (-v,-v,C',C') (r,r,g,g)
-    // (b,b,z,z) and -2^60 times the p' threshold
+    // (b,b,z,z) and the p' threshold
     __shared__ float4 s_rec[4][CH];
     __shared__ float s_thr[CH];
 
@@ -248,7 +258,6 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
     const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
-    const float ntmin = -cam.t_min * STEP_SCALE;
 
     // software pipeline: list indices two steps ahead, records one step ahead
     uint32_t gnext[RPL];
@@ -310,7 +319,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 sw[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
                 sw[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
                 sw[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
-                sthr[k] = -STEP_SCALE * fmaxf(limL + l2o, l2amin);
+                sthr[k] = fmaxf(limL + l2o, l2amin);
             }
             nk += __popc(keep);
         }
@@ -326,7 +335,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             float p0, p1;
             upk(P2, p0, p1);
             // p' >= threshold
-            const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
+            const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
             const float a0 = fminf(cam.alpha_max, ex2_approx(p0));
             const float a1 = fminf(cam.alpha_max, ex2_approx(p1));
             // T' = T (1 - alpha) carries on past the stop: it only decreases, so
@@ -337,7 +346,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             float n0, n1;
             upk(TN2, n0, n1);
             // T (1 - alpha) >= t_min
-            const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
+            const f32x2 GO2 = pk(step_ge(n0, cam.t_min), step_ge(n1, cam.t_min));
             const f32x2 WF = mul2(mul2(T2, AIN), GO2);
             T2 = TN2;
             const float4 c0 = sw[2][k];
@@ -565,8 +574,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const float lamin = __logf(cam.alpha_min);
     const float limL = lim * L2E;
     const float l2amin = log2f(cam.alpha_min);
-    const float ntmin = -cam.t_min * STEP_SCALE;
-    const float amax = cam.alpha_max, amaxS = cam.alpha_max * STEP_SCALE;
+    const float amax = cam.alpha_max;
     const unsigned lt = lanemask_lt_u();
     const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
 
@@ -608,7 +616,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             s_rec[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
             s_rec[4][k] = make_float4(pb.x, pb.x, pb.y, pb.y);
             s_rec[5][k] = make_float4(pb.z, pb.z, io, io);
-            s_thr[k] = -STEP_SCALE * fmaxf(limL + l2o, l2amin);
+            s_thr[k] = fmaxf(limL + l2o, l2amin);
             s_g[k] = gi;
         }
         __syncwarp();
@@ -651,13 +659,13 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
                 float p0, p1;
                 upk(P2, p0, p1);
-                const f32x2 IN2 = pk(__saturatef(fmaf(p0, STEP_SCALE, nth)), __saturatef(fmaf(p1, STEP_SCALE, nth)));
+                const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
                 const float a0 = fminf(amax, ex2_approx(p0)), a1 = fminf(amax, ex2_approx(p1));
                 const f32x2 AIN = mul2(pk(a0, a1), IN2);
                 const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
                 float n0, n1;
                 upk(TN2, n0, n1);
-                const f32x2 GO2 = pk(__saturatef(fmaf(n0, STEP_SCALE, ntmin)), __saturatef(fmaf(n1, STEP_SCALE, ntmin)));
+                const f32x2 GO2 = pk(step_ge(n0, cam.t_min), step_ge(n1, cam.t_min));
                 const f32x2 WF = mul2(mul2(T2, AIN), GO2);
                 T2 = TN2;
                 const float4 c0 = s_rec[2][k], c1 = s_rec[3][k];
@@ -740,14 +748,14 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
             float p0, p1;
             upk(P2, p0, p1);
-            const float i0 = __saturatef(fmaf(p0, STEP_SCALE, nth)), i1 = __saturatef(fmaf(p1, STEP_SCALE, nth));
+            const float i0 = step_ge(p0, nth), i1 = step_ge(p1, nth);
             const float r0 = ex2_approx(p0), r1 = ex2_approx(p1);
             const float a0 = fminf(amax, r0), a1 = fminf(amax, r1);
             const f32x2 AIN = mul2(pk(a0, a1), pk(i0, i1));
             const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
             float n0, n1;
             upk(TN2, n0, n1);
-            const float o0 = __saturatef(fmaf(n0, STEP_SCALE, ntmin)), o1 = __saturatef(fmaf(n1, STEP_SCALE, ntmin));
+            const float o0 = step_ge(n0, cam.t_min), o1 = step_ge(n1, cam.t_min);
             const f32x2 GO2 = pk(o0, o1);
             const f32x2 WF = mul2(mul2(T2, AIN), GO2);
             float w0, w1;
@@ -766,8 +774,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             const f32x2 NR2 = pk(__fdividef(-1.f, 1.f - a0), __fdividef(-1.f, 1.f - a1));
             const f32x2 GAL = mul2(fma2(K2, NR2, mul2(T2, S2)), mul2(pk(i0, i1), GO2));
             // dL/d power = alpha dL/d alpha (0 where the clamp holds)
-            const f32x2 GP = mul2(GAL, pk(a0 * __saturatef(fmaf(r0, -STEP_SCALE, amaxS)),
-                                          a1 * __saturatef(fmaf(r1, -STEP_SCALE, amaxS))));
+            const f32x2 GP = mul2(GAL, pk(a0 * step_lt(r0, amax), a1 * step_lt(r1, amax)));
             const f32x2 GX = mul2(GP, pk(dx, dx)), GY = mul2(GP, DY2);
             float g[NP];
 #pragma unroll
