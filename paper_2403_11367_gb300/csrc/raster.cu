@@ -159,16 +159,21 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
 // Minimum over the rectangle [x0,x1] x [y0,y1] (offsets from the ellipse
 // centre) of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 for a positive-definite
 // conic: 0 if the centre is inside, else the least of the four edge minima
-// (each a clamped 1D quadratic).
+// (each a clamped 1D quadratic).  The edge minimisers -b dx / c and -b dy / a
+// use the fast reciprocal: any dy in the edge gives q at or above the edge's
+// minimum, and a minimiser off by a few ulp raises it by c (delta dy)^2 --
+// orders below the callers' widening of the threshold -- so the value stays
+// a minimum up to that and the cull stays conservative.
 __device__ __forceinline__ float quad_min_rect(float a, float b, float c, float x0, float x1, float y0, float y1)
 {
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
+    const float rc = __fdividef(-b, c), ra = __fdividef(-b, a);
     auto edge_x = [&](float dx) {      // dx fixed, dy free in [y0, y1]
-        const float dy = fminf(fmaxf(-b * dx / c, y0), y1);
+        const float dy = fminf(fmaxf(rc * dx, y0), y1);
         return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
     };
     auto edge_y = [&](float dy) {      // dy fixed, dx free in [x0, x1]
-        const float dx = fminf(fmaxf(-b * dy / a, x0), x1);
+        const float dx = fminf(fmaxf(ra * dy, x0), x1);
         return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
     };
     return fminf(fminf(edge_x(x0), edge_x(x1)), fminf(edge_y(y0), edge_y(y1)));
@@ -244,7 +249,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
-    constexpr float L2E = 1.4426950408889634f;
+    constexpr float L2E = 1.4426950408889634f, LN2 = 0.6931471805599453f;
     const float lim = -0.5f * cam.cut * cam.cut;
     const float lamin = __logf(cam.alpha_min);
     const float limL = lim * L2E;
@@ -301,9 +306,11 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 qa[q] = __ldg(p); qb[q] = __ldg(p + 1); qc[q] = __ldg(p + 2);
             }
             gnext[q] = jnn < r.y ? __ldg(list + jnn) : 0u;
+            // log2 o: the threshold below and the staged record
+            const float l2o = __log2f(pa.w);
             if (j < r.y) {
                 // pa: u v z o | pb: conic a b c, Sigma'_xx | pc: rgb, Sigma'_yy
-                const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
+                const float thr = fmaxf(lim, lamin - LN2 * l2o - 1e-3f);
                 if (thr < 0.f) {
                     // keep iff the ellipse {power >= thr} (widened 1%) meets the block
                     const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
@@ -313,7 +320,6 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             const unsigned keep = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int k = nk + __popc(keep & lt);
-                const float l2o = __log2f(pa.w);
                 const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
                 sw[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
                 sw[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
@@ -550,7 +556,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     constexpr int GRP = 32 / NP;                // lanes holding each total
     constexpr int WPT = TW * TH / 64;
     constexpr int WROWS = 64 / TW;
-    constexpr float L2E = 1.4426950408889634f;
+    constexpr float L2E = 1.4426950408889634f, LN2 = 0.6931471805599453f;
     // kept records: the forward's (-u, A', B', log2 o) (-v, -v, C', C')
     // (r, r, g, g) (b, b, z, z), then the natural conic and 1/o:
     // (a, a, b, b) (c, c, 1/o, 1/o); the forward's step threshold
@@ -598,7 +604,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             gi = __ldg(list + j);
             const float4 *p = vrec + 3 * (int64_t)gi;
             pa = __ldg(p); pb = __ldg(p + 1); pc = __ldg(p + 2);
-            const float thr = fmaxf(lim, lamin - __logf(pa.w) - 1e-3f);
+            const float thr = fmaxf(lim, lamin - LN2 * __log2f(pa.w) - 1e-3f);
             if (thr < 0.f) {
                 const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
                 hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
