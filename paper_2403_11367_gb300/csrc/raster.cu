@@ -158,25 +158,26 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
 
 // Minimum over the rectangle [x0,x1] x [y0,y1] (offsets from the ellipse
 // centre) of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 for a positive-definite
-// conic: 0 if the centre is inside, else the least of the four edge minima
-// (each a clamped 1D quadratic).  The edge minimisers -b dx / c and -b dy / a
-// use the fast reciprocal: any dy in the edge gives q at or above the edge's
-// minimum, and a minimiser off by a few ulp raises it by c (delta dy)^2 --
-// orders below the callers' widening of the threshold -- so the value stays
-// a minimum up to that and the cull stays conservative.
+// conic.  q is strictly convex with its minimum 0 at the centre, so unless the
+// centre is inside, the rectangle's minimum lies on a side facing the centre
+// (from any other point q falls along the segment towards the centre without
+// leaving the rectangle).  Those sides are x = X and y = Y with X, Y the
+// coordinates of the rectangle nearest 0; where 0 lies between x0 and x1 the
+// segment x = 0 crosses the rectangle and only bounds the minimum from above.
+// So the minimum is the lesser of the two 1D minima along x = X and y = Y
+// (each a clamped quadratic), and 0 when the centre is inside (X = Y = 0).
+// The minimisers -b X / c and -b Y / a use the fast reciprocal: any point of
+// a side gives q at or above that side's minimum, and one off by a few ulp
+// raises it by c (delta)^2, orders below the callers' widening of the
+// threshold, so the cull stays conservative.
 __device__ __forceinline__ float quad_min_rect(float a, float b, float c, float x0, float x1, float y0, float y1)
 {
-    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
-    const float rc = __fdividef(-b, c), ra = __fdividef(-b, a);
-    auto edge_x = [&](float dx) {      // dx fixed, dy free in [y0, y1]
-        const float dy = fminf(fmaxf(rc * dx, y0), y1);
-        return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
-    };
-    auto edge_y = [&](float dy) {      // dy fixed, dx free in [x0, x1]
-        const float dx = fminf(fmaxf(ra * dy, x0), x1);
-        return a * dx * dx + 2.f * b * dx * dy + c * dy * dy;
-    };
-    return fminf(fminf(edge_x(x0), edge_x(x1)), fminf(edge_y(y0), edge_y(y1)));
+    const float X = fminf(fmaxf(0.f, x0), x1), Y = fminf(fmaxf(0.f, y0), y1);
+    const float dy = fminf(fmaxf(__fdividef(-b, c) * X, y0), y1);   // along x = X
+    const float dx = fminf(fmaxf(__fdividef(-b, a) * Y, x0), x1);   // along y = Y
+    const float qx = fmaf(X, fmaf(a, X, 2.f * b * dy), c * dy * dy);
+    const float qy = fmaf(dx, fmaf(a, dx, 2.f * b * Y), c * Y * Y);
+    return fminf(qx, qy);
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
