@@ -196,8 +196,10 @@ __device__ __forceinline__ float ex2_approx(float x)
 // is carried as T' = prod (1 - alpha) past the stop: T' only decreases, so a
 // pixel's stop (T (1 - alpha) < t_min, the stopping Gaussian not added) is the
 // first record where T' falls below t_min, and a weight is kept while T' after
-// it is >= t_min -- no flag, and one multiply per record on the dependency
-// chain; the alpha output is the sum of the kept weights, which telescopes to
+// it is >= t_min -- no flag, and one fused T + T (-alpha) per record on the
+// dependency chain (rounded once).  The kernel carries -alpha and minus the
+// weights, so that update is a single FMA, and negates the sums at the end;
+// the alpha output is the sum of the kept weights, which telescopes to
 // 1 - T before the stop.  Both tests are 0/1 factors from one float compare
 // each (set.ge), which runs on the ALU pipe beside the FMA-bound arithmetic.
 // The column terms dx, A' dx^2 + log2(o) and B' dx are shared by the pixel
@@ -263,7 +265,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     // depth and weight sums
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
-    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
+    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
 
     // software pipeline: list indices two steps ahead, records one step ahead
     uint32_t gnext[RPL];
@@ -343,41 +345,44 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             upk(P2, p0, p1);
             // p' >= threshold
             const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
-            const float a0 = fminf(cam.alpha_max, ex2_approx(p0));
-            const float a1 = fminf(cam.alpha_max, ex2_approx(p1));
-            // T' = T (1 - alpha) carries on past the stop: it only decreases, so
-            // T' >= t_min holds up to the stop and never after; the weight is
-            // kept while it holds (one multiply on the dependency chain)
-            const f32x2 AIN = mul2(pk(a0, a1), IN2);
-            const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
+            // -alpha = max(-alpha_max, -2^p') (exact negation of the clamp)
+            const float na0 = fmaxf(-cam.alpha_max, -ex2_approx(p0));
+            const float na1 = fmaxf(-cam.alpha_max, -ex2_approx(p1));
+            // T' = T (1 - alpha), formed as one fused T + T (-alpha), carries on
+            // past the stop: it only decreases, so T' >= t_min holds up to the
+            // stop and never after; the weight is kept while it holds (one
+            // instruction on the dependency chain)
+            const f32x2 NAIN = mul2(pk(na0, na1), IN2);
+            const f32x2 TN2 = fma2(T2, NAIN, T2);
             float n0, n1;
             upk(TN2, n0, n1);
             // T (1 - alpha) >= t_min
             const f32x2 GO2 = pk(step_ge(n0, cam.t_min), step_ge(n1, cam.t_min));
-            const f32x2 WF = mul2(mul2(T2, AIN), GO2);
+            // minus the weight: the sums below accumulate negated
+            const f32x2 NWF = mul2(mul2(T2, NAIN), GO2);
             T2 = TN2;
             const float4 c0 = sw[2][k];
-            R2 = fma2(pk(c0.x, c0.y), WF, R2);
-            G2 = fma2(pk(c0.z, c0.w), WF, G2);
+            R2 = fma2(pk(c0.x, c0.y), NWF, R2);
+            G2 = fma2(pk(c0.z, c0.w), NWF, G2);
             if (DA) {
                 const float4 c1 = sw[3][k];
-                B2 = fma2(pk(c1.x, c1.y), WF, B2);
-                Z2 = fma2(pk(c1.z, c1.w), WF, Z2);
-                S2 = add2(S2, WF);
+                B2 = fma2(pk(c1.x, c1.y), NWF, B2);
+                Z2 = fma2(pk(c1.z, c1.w), NWF, Z2);
+                S2 = add2(S2, NWF);
             } else {
                 const float2 c1 = *reinterpret_cast<const float2 *>(&sw[3][k]);
-                B2 = fma2(pk(c1.x, c1.y), WF, B2);
+                B2 = fma2(pk(c1.x, c1.y), NWF, B2);
             }
         }
         __syncwarp();
     }
 
     float R0, R1, G0, G1, B0, B1, D0, D1, A0, A1;
-    upk(R2, R0, R1);
-    upk(G2, G0, G1);
-    upk(B2, B0, B1);
-    upk(Z2, D0, D1);
-    upk(S2, A0, A1);
+    upk(mul2(R2, NEG1), R0, R1);
+    upk(mul2(G2, NEG1), G0, G1);
+    upk(mul2(B2, NEG1), B0, B1);
+    upk(mul2(Z2, NEG1), D0, D1);
+    upk(mul2(S2, NEG1), A0, A1);
     const int64_t HW = (int64_t)cam.width * cam.height;
     const int64_t pix0 = (int64_t)py0 * cam.width + px, pix1 = pix0 + cam.width;
     if (rgb) {
@@ -583,7 +588,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     const float l2amin = log2f(cam.alpha_min);
     const float amax = cam.alpha_max;
     const unsigned lt = lanemask_lt_u();
-    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f), ONE2 = pk(1.f, 1.f);
+    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f);
 
     // the forward's cull and compaction, one step of 32 records, against the
     // box of the pixels still compositing (T > 0)
@@ -667,25 +672,28 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 float p0, p1;
                 upk(P2, p0, p1);
                 const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
-                const float a0 = fminf(amax, ex2_approx(p0)), a1 = fminf(amax, ex2_approx(p1));
-                const f32x2 AIN = mul2(pk(a0, a1), IN2);
-                const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
+                const float na0 = fmaxf(-amax, -ex2_approx(p0)), na1 = fmaxf(-amax, -ex2_approx(p1));
+                const f32x2 NAIN = mul2(pk(na0, na1), IN2);
+                const f32x2 TN2 = fma2(T2, NAIN, T2);
                 float n0, n1;
                 upk(TN2, n0, n1);
                 const f32x2 GO2 = pk(step_ge(n0, cam.t_min), step_ge(n1, cam.t_min));
-                const f32x2 WF = mul2(mul2(T2, AIN), GO2);
+                const f32x2 NWF = mul2(mul2(T2, NAIN), GO2);
                 T2 = TN2;
                 const float4 c0 = s_rec[2][k], c1 = s_rec[3][k];
-                CR2 = fma2(pk(c0.x, c0.y), WF, CR2);
-                CG2 = fma2(pk(c0.z, c0.w), WF, CG2);
-                CB2 = fma2(pk(c1.x, c1.y), WF, CB2);
+                CR2 = fma2(pk(c0.x, c0.y), NWF, CR2);
+                CG2 = fma2(pk(c0.z, c0.w), NWF, CG2);
+                CB2 = fma2(pk(c1.x, c1.y), NWF, CB2);
                 if (IMG) {
-                    CZ2 = fma2(pk(c1.z, c1.w), WF, CZ2);
-                    CS2 = add2(CS2, WF);
+                    CZ2 = fma2(pk(c1.z, c1.w), NWF, CZ2);
+                    CS2 = add2(CS2, NWF);
                 }
             }
             __syncwarp();
         }
+        // the sums ran over minus the weights
+        CR2 = mul2(CR2, NEG1); CG2 = mul2(CG2, NEG1); CB2 = mul2(CB2, NEG1);
+        CZ2 = mul2(CZ2, NEG1); CS2 = mul2(CS2, NEG1);
     }
     float C[2][3], DA[2][2];
     upk(CR2, C[0][0], C[1][0]);
@@ -757,17 +765,19 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             upk(P2, p0, p1);
             const float i0 = step_ge(p0, nth), i1 = step_ge(p1, nth);
             const float r0 = ex2_approx(p0), r1 = ex2_approx(p1);
-            const float a0 = fminf(amax, r0), a1 = fminf(amax, r1);
-            const f32x2 AIN = mul2(pk(a0, a1), pk(i0, i1));
-            const f32x2 TN2 = mul2(T2, fma2(AIN, NEG1, ONE2));
+            // the forward's arithmetic: -alpha, T' = T + T (-alpha) fused, minus the weight
+            const float na0 = fmaxf(-amax, -r0), na1 = fmaxf(-amax, -r1);
+            const float a0 = -na0, a1 = -na1;
+            const f32x2 NAIN = mul2(pk(na0, na1), pk(i0, i1));
+            const f32x2 TN2 = fma2(T2, NAIN, T2);
             float n0, n1;
             upk(TN2, n0, n1);
             const float o0 = step_ge(n0, cam.t_min), o1 = step_ge(n1, cam.t_min);
             const f32x2 GO2 = pk(o0, o1);
-            const f32x2 WF = mul2(mul2(T2, AIN), GO2);
+            const f32x2 NWF = mul2(mul2(T2, NAIN), GO2);
             float w0, w1;
-            upk(WF, w0, w1);
-            if (!__any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
+            upk(NWF, w0, w1);
+            if (!__any_sync(0xffffffffu, w0 < 0.f || w1 < 0.f)) {
                 T2 = TN2;
                 continue;
             }
@@ -775,7 +785,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             // S = G . c (+ G_D z + G_A); K loses w S
             f32x2 S2 = fma2(G0, pk(c0.x, c0.y), fma2(G1, pk(c0.z, c0.w), mul2(G2, pk(c1.x, c1.y))));
             if (IMG) S2 = fma2(GD, pk(c1.z, c1.w), add2(S2, GA));
-            K2 = fma2(WF, mul2(S2, NEG1), K2);
+            K2 = fma2(NWF, S2, K2);
             // dL/d alpha = T S - K / (1 - alpha), masked to the included, unstopped pairs;
             // 1 / (1 - alpha): alpha <= alpha_max < 1, fast reciprocal (2 ulp)
             const f32x2 NR2 = pk(__fdividef(-1.f, 1.f - a0), __fdividef(-1.f, 1.f - a1));
@@ -798,16 +808,17 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             upk(mul2(GY, mul2(DY2, pk(-0.5f, -0.5f))), lo, hi);                     // d/dc: -dy^2 / 2
             g[4] = lo + hi;
             if (IMG) {
-                upk(mul2(WF, G0), lo, hi);
-                g[5] = lo + hi;
-                upk(mul2(WF, G1), lo, hi);
-                g[6] = lo + hi;
-                upk(mul2(WF, G2), lo, hi);
-                g[7] = lo + hi;
+                // colour and depth: w G, from minus the weight
+                upk(mul2(NWF, G0), lo, hi);
+                g[5] = -lo - hi;
+                upk(mul2(NWF, G1), lo, hi);
+                g[6] = -lo - hi;
+                upk(mul2(NWF, G2), lo, hi);
+                g[7] = -lo - hi;
                 upk(mul2(GP, pk(nc.z, nc.w)), lo, hi);                             // d/do = dL/d power / o
                 g[8] = lo + hi;
-                upk(mul2(WF, GD), lo, hi);
-                g[9] = lo + hi;
+                upk(mul2(NWF, GD), lo, hi);
+                g[9] = -lo - hi;
             }
             T2 = TN2;
             const float tot = warp_reduce_scatter<NP>(g, lane);
