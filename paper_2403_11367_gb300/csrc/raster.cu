@@ -230,7 +230,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     constexpr int CH = 32 * RPL;             // records per warp step
     static_assert(WPT >= 1 && TH % WROWS == 0, "tile shape");
     // kept records compacted: (-u,A',B',log2 o) (-v,-v,C',C') (r,r,g,g)
-    // (b,b,z,z) and the p' threshold
+    // (b,b,z,z) and the p' threshold; colour only: (b,b,thr,thr)
     __shared__ float4 s_rec[4][CH];
     __shared__ float s_thr[CH];
 
@@ -327,8 +327,14 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 sw[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
                 sw[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
                 sw[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
-                sw[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
-                sthr[k] = fmaxf(limL + l2o, l2amin);
+                const float nth = fmaxf(limL + l2o, l2amin);
+                if (DA) {
+                    sw[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
+                    sthr[k] = nth;
+                } else {
+                    // colour only: the threshold rides in the blue record
+                    sw[3][k] = make_float4(pc.z, pc.z, nth, nth);
+                }
             }
             nk += __popc(keep);
         }
@@ -336,7 +342,8 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
 #pragma unroll 4
         for (int k = 0; k < nk; ++k) {
             const float4 s0 = sw[0][k], s1 = sw[1][k];
-            const float nth = sthr[k];
+            const float4 c1 = sw[3][k];
+            const float nth = DA ? sthr[k] : c1.z;
             const float dx = fxp + s0.x;
             const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
             const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
@@ -364,14 +371,10 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             const float4 c0 = sw[2][k];
             R2 = fma2(pk(c0.x, c0.y), NWF, R2);
             G2 = fma2(pk(c0.z, c0.w), NWF, G2);
+            B2 = fma2(pk(c1.x, c1.y), NWF, B2);
             if (DA) {
-                const float4 c1 = sw[3][k];
-                B2 = fma2(pk(c1.x, c1.y), NWF, B2);
                 Z2 = fma2(pk(c1.z, c1.w), NWF, Z2);
                 S2 = add2(S2, NWF);
-            } else {
-                const float2 c1 = *reinterpret_cast<const float2 *>(&sw[3][k]);
-                B2 = fma2(pk(c1.x, c1.y), NWF, B2);
             }
         }
         __syncwarp();
