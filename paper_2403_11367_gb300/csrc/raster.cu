@@ -531,8 +531,9 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // (u, v) and conics (a, b, c), for the view's fixed set of included
 // (pixel, Gaussian) pairs.  A warp per 64-pixel block walks the tile's list
 // with the forward's cull and the forward's arithmetic (base-2 exponent, the
-// inclusion, clamp and stop tests as saturating step functions, the pixel
-// pair packed in f32x2), so its decisions are the forward's bit for bit:
+// inclusion, clamp and stop tests as exact 0/1 compares, the fused
+// transmittance update, the pixel pair packed in f32x2), so its decisions are
+// the forward's bit for bit:
 // first, unless the forward's render is given, compositing the pair to its
 // final colour C, then again front to back, where for contributor j with
 // weight w_j = alpha_j T_j,
