@@ -240,6 +240,66 @@ def test_single_view_single_gaussian(R):
     compare_images(rgb, depth, alpha, ref, 5.0)
 
 
+def _rot(axis, ang):
+    c, s_ = math.cos(ang), math.sin(ang)
+    i, j = [(1, 2), (2, 0), (0, 1)][axis]
+    m = np.eye(3)
+    m[i, i] = m[j, j] = c
+    m[i, j], m[j, i] = -s_, s_
+    return m
+
+
+def test_thin_footprints_cull_is_exact_across_block_shapes(R):
+    """Needle-like Gaussians (one long axis of 0.3-1.5 m, two of 4 mm) at random
+    orientations project to footprints up to ~430 px long and ~3 px wide that
+    cross the warp blocks at every angle, graze their corners and run along
+    their edges.  The blend keeps a record for a block only if the ellipse at
+    the record's own threshold meets the box of the block's still-compositing
+    pixels, so it may drop only records that no pixel of the block takes.  The
+    per-pixel arithmetic and the order of the records at a pixel do not depend
+    on the tile shape (warp blocks of 16x4, 8x8, 32x2, 8x8 pixels for 16x16,
+    8x8, 32x8, 8x16 tiles) nor on the records staged per step, only the cull
+    does: the images must be equal across those launches, value for value.
+    (Against the FP64 oracle such footprints sit outside the FP32 parity bar:
+    a*dx^2 + 2b*dx*dy + c*dy^2 cancels terms of ~1e4-1e5 to a few units along a
+    long diagonal footprint, so its FP32 value carries errors near 1e-2; the
+    paper's per-pixel evaluation is FP32 and so is this one.)"""
+    r = sg.Rng(41)
+    n = 1500
+    mean = np.stack([r.uniform(n, -4.0, 4.0), r.uniform(n, -2.5, 2.5), r.uniform(n, 3.0, 12.0)], 1)
+    scale = np.stack([np.exp(r.uniform(n, math.log(0.3), math.log(1.5))),
+                      np.full(n, 0.004), np.full(n, 0.004)], 1)
+    quat = r.normal(4 * n).reshape(n, 4)
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    opacity = 1.0 / (1.0 + np.exp(-r.normal(n, 0.0, 1.5)))
+    rgb = r.uniform(3 * n).reshape(n, 1, 3)
+    g = sg.Gaussians(mean.astype(np.float32), scale.astype(np.float32), quat.astype(np.float32),
+                     opacity.astype(np.float32), rgb.astype(np.float32), 0)
+    cam = sg.Camera(200, 120, 150.0, 150.0, 100.0, 60.0)          # ragged 16-px tiles in x and y
+    poses = []
+    for ax, ay, tx in ((0.0, 0.0, 0.0), (0.1, -0.15, 0.3), (-0.08, 0.2, -0.4), (0.05, 0.05, 0.1)):
+        W = np.eye(4)
+        W[:3, :3] = _rot(0, ax) @ _rot(1, ay)
+        W[:3, 3] = (tx, 0.0, 0.0)
+        poses.append(W)
+    poses = np.stack(poses)
+    noise = sg.Rng(42).normal(3 * cam.height * cam.width, 0.0, 0.02).reshape(3, cam.height, cam.width)
+    q = torch.tensor((np.clip(noise + 0.5, 0.0, 1.0)).astype(np.float32), device="cuda:0").contiguous()
+    base = None
+    for tile, rpl in (((16, 16), 1), ((16, 16), 2), ((8, 8), 1), ((32, 8), 1), ((8, 16), 1)):
+        ctx = make_ctx(R, g, tile_w=tile[0], tile_h=tile[1], blend_rpl=rpl)
+        imgs = gpu_render(ctx, full_range(ctx), poses, cam)
+        sc, dg = ctx.score(full_range(ctx), poses, cam, q)
+        if base is None:
+            base = imgs, sc
+            assert float(imgs[2].max()) > 0.9 and float((imgs[2] > 0).mean()) > 0.5
+            continue
+        for x, y in zip(imgs, base[0]):
+            assert np.array_equal(x, y), (tile, rpl, float(np.abs(x - y).max()))
+        # scores: the same pixels, NCC partial sums grouped by warp block
+        assert np.abs(sc - base[1]).max() <= TOL_NCC, (tile, rpl)
+
+
 def test_overflow_grow_and_retry_is_exact(R, tiny):
     a = make_ctx(R, tiny.gaussians)
     b = make_ctx(R, tiny.gaussians, inst_capacity=64)
