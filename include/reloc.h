@@ -533,9 +533,14 @@ reloc_status reloc_stage_times(reloc_ctx *ctx, double *ms_out, int64_t *calls_ou
 
 /* Copy intermediate results of the LAST render/score/localize call, for
  * parity checks (device pointers, any may be NULL; sizes from reloc_last_counts):
- *   records_dev [n_views][n_gauss][12] float: u, v, depth, opacity,
- *                conic a, b, c, Sigma'_xx, red, green, blue, Sigma'_yy
-                (conic = inverse of the dilated Sigma'; valid where visible)
+ *   records_dev [n_views][n_gauss][12] float: u, v, depth, log2(opacity),
+ *                k alpha_x, k alpha_y, k beta_x, k beta_y, red, green, blue, 0
+ *                (alpha, beta: the footprint's principal axes scaled by the
+ *                inverse square roots of the dilated Sigma''s eigenvalues,
+ *                so that the conic Sigma'^-1 = alpha alpha^T + beta beta^T
+ *                and the power is -((alpha . d)^2 + (beta . d)^2) / 2;
+ *                k = sqrt(log2(e) / 2), the blend's base-2 scale; valid where
+ *                visible)
  *   rects_dev   [n_views][n_gauss][4] int32: tile rectangle tx0, ty0, tx1, ty1
  *                inclusive; all -1 where not visible
  *   inst_tiles_dev / inst_gauss_dev [n_views][inst_stride] uint32: the sorted
@@ -549,27 +554,6 @@ reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rec
                                 uint32_t *inst_tiles_dev, uint32_t *inst_gauss_dev,
                                 int64_t *inst_count_host, int32_t *ranges_dev, void *stream);
 
-/* NCC of already-rendered images against a query, without allocating.
- * The paper has no counterpart: this entry point is for callers that must not
- * allocate device memory after start-up -- e.g. a real-time relocalization
- * loop whose memory is reserved up front (cudaMalloc/cudaFree may synchronise
- * the whole device and take milliseconds) or a process whose device memory
- * belongs to another framework's pool.  It computes what the scoring stage of
- * reloc_score computes (Eq. ncc over all 3*H*W samples, FP64 sums, 0 and
- * degenerate = 1 for a zero-variance image) for images the caller rendered.
- *   images_dev      [n_views][3][height][width] float32, device, caller-owned
- *   query_dev       [3][height][width] float32, device, caller-owned
- *   scores_dev      [n_views] double, device, written (caller-owned)
- *   degenerate_dev  [n_views] int, device, written (may be NULL)
- * Its only scratch is a fixed 393,728-byte device array inside the library,
- * held by every GPU that loads the library until the process exits; no
- * cudaMalloc, cudaFree or allocating library routine is called.  The first
- * call on a device looks up that array's device address (with the device
- * current) and should come before any stream capture.  Asynchronous on
- * `stream`.  All calls share the one array: calls that overlap on the GPU
- * race and must be ordered by the caller.  Errors: EINVAL (NULL pointer,
- * n_views outside 1..RELOC_NOALLOC_MAX_VIEWS, image size outside 1..16383),
- * ECUDA. */
 /* Measured arithmetic throughput of `device`, the denominators of the
  * projection's and the blend's rooflines.  The paper has no counterpart: it
  * is a measurement utility.  Register-resident microbenchmarks (independent
@@ -583,6 +567,31 @@ reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rec
 reloc_status reloc_measure_peaks(int device, double *fp32_scalar_tflops, double *fp32_packed_tflops,
                                  double *ex2_gops);
 
+/* NCC of already-rendered images against a query, without allocating.
+ * The paper has no counterpart: this entry point is for callers that must not
+ * allocate device memory after start-up -- e.g. a real-time relocalization
+ * loop whose memory is reserved up front (cudaMalloc/cudaFree may synchronise
+ * the whole device and take milliseconds) or a process whose device memory
+ * belongs to another framework's pool.  For images the caller rendered it
+ * computes the Pearson correlation of each image with the query over all
+ * 3*H*W samples (the RGB score of reloc_score with ncc_gray = 0; the gray
+ * option is not offered here), with every per-sample sum in FP64, and score 0
+ * with degenerate = 1 for a zero-variance image.  reloc_score sums each
+ * 64-pixel block in compensated FP32 before its FP64 combine, so the two agree
+ * to rounding (within 2e-6), not bit for bit.
+ *   images_dev      [n_views][3][height][width] float32, device, caller-owned
+ *   query_dev       [3][height][width] float32, device, caller-owned
+ *   scores_dev      [n_views] double, device, written (caller-owned)
+ *   degenerate_dev  [n_views] int, device, written (may be NULL)
+ * Its only scratch is a fixed 393,728-byte device array inside the library,
+ * held by every GPU that loads the library until the process exits; no
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on a device looks up that array's device address (with the device
+ * current) and should come before any stream capture.  Asynchronous on
+ * `stream`.  All calls share the one array: calls that overlap on the GPU
+ * race and must be ordered by the caller.  Errors: EINVAL (NULL pointer,
+ * n_views outside 1..RELOC_NOALLOC_MAX_VIEWS, image size outside 1..16383),
+ * ECUDA. */
 #define RELOC_NOALLOC_MAX_VIEWS 512
 reloc_status reloc_ncc_images_noalloc(const float *images_dev, int n_views, int height, int width,
                                       const float *query_dev, double *scores_dev, int *degenerate_dev,

@@ -78,6 +78,59 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
 
 constexpr int PROJ_VIEW_BATCH = 128;
 
+// Principal-axis form of a footprint.  N = T M (2 x 3) holds the projected
+// scaled axes of the Gaussian (T = J R_w, M = R S), so Sigma' = N N^T + eps I.
+// With the eigenpairs (l1 >= l2, e1 orthogonal to e2) of Sigma',
+//   -1/2 d^T Sigma'^-1 d = -1/2 (U^2 + V^2),  U = alpha . d,  V = beta . d,
+//   alpha = e1 / sqrt(l1),  beta = e2 / sqrt(l2),
+// which is what the record carries instead of the conic.  det(N N^T) is the
+// squared norm of the cross product of N's rows (Lagrange's identity), a sum
+// of squares: det(Sigma') = det(N N^T) + eps tr(N N^T) + eps^2 and
+// l2 = det / l1 keep their relative precision for long thin footprints, where
+// Sigma'_xx Sigma'_yy - Sigma'_xy^2 cancels.  The eigenvector is taken from
+// the row of Sigma' - l1 I without cancellation (A - C and the root have the
+// same sign).  Returns false unless Sigma' is positive definite; sxx, syy are
+// the diagonal of Sigma' (the 3-sigma bounding box).  In FP32 the root that
+// sets the eigenvector's direction is IEEE; the normalisation, l2 and the
+// inverse square roots only scale the axes (by 1 + a few ulp, which moves the
+// form by as little) and use the fast reciprocal (square root).
+__device__ __forceinline__ float fp_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fp_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fp_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fp_div(double a, double b) { return a / b; }
+template <typename F>
+__device__ __forceinline__ bool footprint_axes(const F (&n)[6], F eps, F &sxx, F &syy, F &det, F (&ab)[4])
+{
+    const F A0 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    const F C0 = n[3] * n[3] + n[4] * n[4] + n[5] * n[5];
+    const F B0 = n[0] * n[3] + n[1] * n[4] + n[2] * n[5];
+    const F x = n[1] * n[5] - n[2] * n[4];
+    const F y = n[2] * n[3] - n[0] * n[5];
+    const F z = n[0] * n[4] - n[1] * n[3];
+    sxx = A0 + eps;
+    syy = C0 + eps;
+    det = (x * x + y * y + z * z) + eps * (A0 + C0 + eps);
+    if (!(det > F(0))) return false;
+    const F dd = A0 - C0;
+    const F sq = sqrt(dd * dd + F(4) * B0 * B0);
+    const F l1 = F(0.5) * (sxx + syy + sq);
+    const F l2 = fp_div(det, l1);
+    F ex, ey;
+    if (dd >= F(0)) { ex = dd + sq; ey = F(2) * B0; }
+    else { ex = F(2) * B0; ey = sq - dd; }
+    const F en2 = ex * ex + ey * ey;
+    if (en2 > F(0)) {
+        const F ien = fp_rsqrt(en2);
+        ex = ex * ien; ey = ey * ien;
+    } else {
+        ex = F(1); ey = F(0);
+    }
+    const F r1 = fp_rsqrt(l1), r2 = fp_rsqrt(l2);
+    ab[0] = ex * r1; ab[1] = ey * r1;
+    ab[2] = -ey * r2; ab[3] = ex * r2;
+    return true;
+}
+
 template <typename T, int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS)
 k_project(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
@@ -97,7 +150,7 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
 
     // ---- per-Gaussian quantities, loaded and formed once ------------------
     float mu0 = 0, mu1 = 0, mu2 = 0, opac = 0;
-    float S00 = 0, S01 = 0, S02 = 0, S11 = 0, S12 = 0, S22 = 0;
+    float m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // M = R S, row-major
     float sh[3 * K];
     if (active) {
         const int64_t g = gidx[L.q_gsub[qi] + i];
@@ -118,16 +171,10 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
         float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
         float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
         float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
-        // M = R S, Sigma = M M^T
-        float m00 = r00 * s0, m01 = r01 * s1, m02 = r02 * s2;
-        float m10 = r10 * s0, m11 = r11 * s1, m12 = r12 * s2;
-        float m20 = r20 * s0, m21 = r21 * s1, m22 = r22 * s2;
-        S00 = m00 * m00 + m01 * m01 + m02 * m02;
-        S01 = m00 * m10 + m01 * m11 + m02 * m12;
-        S02 = m00 * m20 + m01 * m21 + m02 * m22;
-        S11 = m10 * m10 + m11 * m11 + m12 * m12;
-        S12 = m10 * m20 + m11 * m21 + m12 * m22;
-        S22 = m20 * m20 + m21 * m21 + m22 * m22;
+        // M = R S (Sigma = M M^T): column k is the k-th scaled axis
+        m[0] = r00 * s0; m[1] = r01 * s1; m[2] = r02 * s2;
+        m[3] = r10 * s0; m[4] = r11 * s1; m[5] = r12 * s2;
+        m[6] = r20 * s0; m[7] = r21 * s1; m[8] = r22 * s2;
     }
     const float cut2 = cam.cut;
     const float inv_tw = 1.0f / cam.tile_w, inv_th = 1.0f / cam.tile_h;
@@ -161,41 +208,31 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
                 // T = J R_w (2x3)
                 float t00 = j00 * P.R[0] + j02 * P.R[6], t01 = j00 * P.R[1] + j02 * P.R[7], t02 = j00 * P.R[2] + j02 * P.R[8];
                 float t10 = j11 * P.R[3] + j12 * P.R[6], t11 = j11 * P.R[4] + j12 * P.R[7], t12 = j11 * P.R[5] + j12 * P.R[8];
-                // Sigma' = T Sigma T^T
-                float u0 = t00 * S00 + t01 * S01 + t02 * S02;
-                float u1 = t00 * S01 + t01 * S11 + t02 * S12;
-                float u2 = t00 * S02 + t01 * S12 + t02 * S22;
-                float w0 = t10 * S00 + t11 * S01 + t12 * S02;
-                float w1 = t10 * S01 + t11 * S11 + t12 * S12;
-                float w2 = t10 * S02 + t11 * S12 + t12 * S22;
-                float ca = u0 * t00 + u1 * t01 + u2 * t02 + cam.eps2d;
-                float cb = u0 * t10 + u1 * t11 + u2 * t12;
-                float cc = w0 * t10 + w1 * t11 + w2 * t12 + cam.eps2d;
-                float det = ca * cc - cb * cb;
-                float ia, ib, ic;
-                bool ok;
+                // N = T M: the projected scaled axes (Sigma' = N N^T + eps I)
+                float nn[6];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    nn[k] = t00 * m[k] + t01 * m[3 + k] + t02 * m[6 + k];
+                    nn[3 + k] = t10 * m[k] + t11 * m[3 + k] + t12 * m[6 + k];
+                }
+                float ca, cc, det, ab[4];
+                bool ok = footprint_axes(nn, cam.eps2d, ca, cc, det, ab);
                 if (det < cam.det_fp64) {
-                    // near-degenerate footprint: form Sigma' and its inverse in FP64
-                    double T0[3] = {(double)t00, (double)t01, (double)t02};
-                    double T1[3] = {(double)t10, (double)t11, (double)t12};
-                    double Sg[9] = {S00, S01, S02, S01, S11, S12, S02, S12, S22};
-                    double A = 0, B = 0, Cc = 0;
+                    // near-degenerate footprint: N, Sigma' and its axes in FP64
+                    const double T0[3] = {(double)t00, (double)t01, (double)t02};
+                    const double T1[3] = {(double)t10, (double)t11, (double)t12};
+                    double nd[6];
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k) {
+                        nd[k] = T0[0] * (double)m[k] + T0[1] * (double)m[3 + k] + T0[2] * (double)m[6 + k];
+                        nd[3 + k] = T1[0] * (double)m[k] + T1[1] * (double)m[3 + k] + T1[2] * (double)m[6 + k];
+                    }
+                    double sxd, syd, dd, abd[4];
+                    ok = footprint_axes(nd, (double)cam.eps2d, sxd, syd, dd, abd);
+                    ca = (float)sxd; cc = (float)syd;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            A += T0[r] * Sg[3 * r + c] * T0[c];
-                            B += T0[r] * Sg[3 * r + c] * T1[c];
-                            Cc += T1[r] * Sg[3 * r + c] * T1[c];
-                        }
-                    A += cam.eps2d; Cc += cam.eps2d;
-                    double dd = A * Cc - B * B;
-                    ok = dd > 0;
-                    ia = (float)(Cc / dd); ib = (float)(-B / dd); ic = (float)(A / dd);
-                    ca = (float)A; cc = (float)Cc;
-                } else {
-                    ok = det > 0;
-                    ia = cc / det; ib = -cb / det; ic = ca / det;
+                    for (int k = 0; k < 4; ++k) ab[k] = (float)abd[k];
+                    ok = ok && isfinite(ab[2]) && isfinite(ab[3]);
                 }
                 if (ok) {
                     float u = cam.fx * tx / tz + cam.cx;
@@ -225,10 +262,14 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
                             }
                             cr = fmaxf(cr, 0.f); cg = fmaxf(cg, 0.f); cbl = fmaxf(cbl, 0.f);
                         }
+                        // the blend's form: log2(o) and the axes scaled by
+                        // sqrt(log2(e) / 2), so that the base-2 exponent is
+                        // log2(o) - (alpha' . d)^2 - (beta' . d)^2
+                        constexpr float KAPPA = 0.8493218002880191f;
                         float4 *rp = rec + 3 * o;
-                        rp[0] = make_float4(u, vpx, tz, opac);
-                        rp[1] = make_float4(ia, ib, ic, ca);
-                        rp[2] = make_float4(cr, cg, cbl, cc);
+                        rp[0] = make_float4(u, vpx, tz, __log2f(opac));
+                        rp[1] = make_float4(KAPPA * ab[0], KAPPA * ab[1], KAPPA * ab[2], KAPPA * ab[3]);
+                        rp[2] = make_float4(cr, cg, cbl, 0.f);
                     }
                 }
             }

@@ -21,11 +21,50 @@ __device__ __forceinline__ double warp_sum_d(double x)
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     return x;
 }
-__device__ __forceinline__ float warp_sum_f(float x)
+
+// Compensated FP32 sums (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005: Sum2 and Dot2).  A sum is carried as hi + lo; TwoSum gives
+// the exact rounding error of each addition and TwoProd (one FMA) that of
+// each product, and the errors are summed into lo, so the result is as if
+// computed in twice the working precision and then rounded.  The _rn
+// intrinsics keep the compiler from fusing or reordering these steps.
+struct CSum {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void cs_add(CSum &c, float x)
+{
+    float s, e;
+    two_sum(c.hi, x, s, e);
+    c.hi = s;
+    c.lo = __fadd_rn(c.lo, e);
+}
+__device__ __forceinline__ void cs_add_prod(CSum &c, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);           // a b - p, exactly
+    float s, e;
+    two_sum(c.hi, p, s, e);
+    c.hi = s;
+    c.lo = __fadd_rn(c.lo, __fadd_rn(e, pe));
+}
+// butterfly over the warp: every lane ends with the warp's total
+__device__ __forceinline__ double cs_warp_total(CSum c)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    return x;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, c.hi, o), l = __shfl_xor_sync(0xffffffffu, c.lo, o);
+        float s, e;
+        two_sum(c.hi, h, s, e);
+        c.hi = s;
+        c.lo = __fadd_rn(__fadd_rn(c.lo, l), e);
+    }
+    return (double)c.hi + (double)c.lo;
 }
 
 // Warp reduce-scatter of NP values per lane (NP a power of two, 2 .. 16):
@@ -156,29 +195,78 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
     return d;
 }
 
+// Records carry (u, v, depth, log2 o | a1, a2, b1, b2 | r, g, b, -): the
+// footprint in principal-axis form, scaled for base 2: with d the offset of a
+// pixel centre from the projected mean, U = a1 dx + a2 dy and V = b1 dx + b2 dy,
+// the exponent is p' = log2(o) + power log2(e) = log2(o) - (U^2 + V^2), so
+// alpha = min(alpha_max, 2^p') = min(alpha_max, o exp(power)).
+// q(d) = U^2 + V^2 = qa dx^2 + 2 qb dx dy + qc dy^2 is the scaled conic.
+struct Conic {
+    float a, b, c;
+};
+__device__ __forceinline__ Conic conic_of(float4 ab)
+{
+    return {fmaf(ab.x, ab.x, ab.z * ab.z), fmaf(ab.x, ab.y, ab.z * ab.w), fmaf(ab.y, ab.y, ab.w * ab.w)};
+}
+
 // Minimum over the rectangle [x0,x1] x [y0,y1] (offsets from the ellipse
-// centre) of q(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 for a positive-definite
-// conic.  q is strictly convex with its minimum 0 at the centre, so unless the
-// centre is inside, the rectangle's minimum lies on a side facing the centre
-// (from any other point q falls along the segment towards the centre without
-// leaving the rectangle).  Those sides are x = X and y = Y with X, Y the
-// coordinates of the rectangle nearest 0; where 0 lies between x0 and x1 the
-// segment x = 0 crosses the rectangle and only bounds the minimum from above.
-// So the minimum is the lesser of the two 1D minima along x = X and y = Y
-// (each a clamped quadratic), and 0 when the centre is inside (X = Y = 0).
-// The minimisers -b X / c and -b Y / a use the fast reciprocal: any point of
-// a side gives q at or above that side's minimum, and one off by a few ulp
-// raises it by c (delta)^2, orders below the callers' widening of the
-// threshold, so the cull stays conservative.
-__device__ __forceinline__ float quad_min_rect(float a, float b, float c, float x0, float x1, float y0, float y1)
+// centre) of q.  q is strictly convex with its minimum 0 at the centre, so
+// unless the centre is inside, the rectangle's minimum lies on a side facing
+// the centre (from any other point q falls along the segment towards the
+// centre without leaving the rectangle).  Those sides are x = X and y = Y with
+// X, Y the coordinates of the rectangle nearest 0; where 0 lies between x0 and
+// x1 the segment x = 0 crosses the rectangle and only bounds the minimum from
+// above.  So the minimum is the lesser of the two 1D minima along x = X and
+// y = Y (each a clamped quadratic), and 0 when the centre is inside
+// (X = Y = 0).  The minimisers -qb X / qc and -qb Y / qa use the fast
+// reciprocal: any point of a side gives q at or above that side's minimum, and
+// one off by a few ulp raises it by qc (delta)^2, orders below the callers'
+// widening of the bound, so the cull stays conservative.  q is evaluated at
+// those points as U^2 + V^2, which does not cancel along long thin
+// footprints (the conic form does, by orders of magnitude).
+__device__ __forceinline__ float quad_min_rect(float4 ab, Conic q, float x0, float x1, float y0, float y1)
 {
     const float X = fminf(fmaxf(0.f, x0), x1), Y = fminf(fmaxf(0.f, y0), y1);
-    const float dy = fminf(fmaxf(__fdividef(-b, c) * X, y0), y1);   // along x = X
-    const float dx = fminf(fmaxf(__fdividef(-b, a) * Y, x0), x1);   // along y = Y
-    const float qx = fmaf(X, fmaf(a, X, 2.f * b * dy), c * dy * dy);
-    const float qy = fmaf(dx, fmaf(a, dx, 2.f * b * Y), c * Y * Y);
-    return fminf(qx, qy);
+    const float dy = fminf(fmaxf(__fdividef(-q.b, q.c) * X, y0), y1);   // along x = X
+    const float dx = fminf(fmaxf(__fdividef(-q.b, q.a) * Y, x0), x1);   // along y = Y
+    const float u1 = fmaf(ab.x, X, ab.y * dy), v1 = fmaf(ab.z, X, ab.w * dy);
+    const float u2 = fmaf(ab.x, dx, ab.y * Y), v2 = fmaf(ab.z, dx, ab.w * Y);
+    return fminf(fmaf(u1, u1, v1 * v1), fmaf(u2, u2, v2 * v2));
 }
+
+// Block-centred staging of a kept record for one warp block whose pixel
+// centres lie around (ocx, ocy).  With the block centre's offset from the mean
+// d_b and a pixel's fixed offset delta from the block centre,
+//   p'(delta) = P0 + Gx dx + Gy dy - (qa dx^2 + 2 qb dx dy + qc dy^2),
+// P0 = log2(o) - Ub^2 - Vb^2 the exponent at the block centre and
+// G = -2 (Ub (a1, a2) + Vb (b1, b2)) its gradient there, Ub and Vb the axis
+// coordinates of d_b.  P0 and G come from the axes (no cancellation however
+// far the centre lies along a long footprint), and the quadratic term only
+// sees offsets within the block (|delta| <= 8 px), so the conic form's
+// cancellation stays at that scale.  Per pixel pair this costs three scalar
+// and two packed FMAs.
+//   s0 = (-qa, Gx, -2 qb, Gy), s1 = (-qc, -qc, P0, thr)
+__device__ __forceinline__ void block_stage(float4 pa, float4 ab, Conic q, float thr, float ocx, float ocy,
+                                            float4 &s0, float4 &s1)
+{
+    const float dbx = ocx - pa.x, dby = ocy - pa.y;
+    const float Ub = fmaf(ab.x, dbx, ab.y * dby), Vb = fmaf(ab.z, dbx, ab.w * dby);
+    const float P0 = fmaf(-Vb, Vb, fmaf(-Ub, Ub, pa.w));
+    const float Gx = -2.f * fmaf(Ub, ab.x, Vb * ab.z), Gy = -2.f * fmaf(Ub, ab.y, Vb * ab.w);
+    s0 = make_float4(-q.a, Gx, -2.f * q.b, Gy);
+    s1 = make_float4(-q.c, -q.c, P0, thr);
+}
+
+// Warp blocks: 64 pixels, BW x BH with BW = min(TW, 16), each lane owning two
+// vertically adjacent pixels; a TW x TH tile holds (TW / BW) x (TH / BH) of them.
+template <int TW, int TH>
+struct BlockGeom {
+    static constexpr int BW = TW < 16 ? TW : 16;
+    static constexpr int BH = 64 / BW;
+    static constexpr int NBX = TW / BW;
+    static constexpr int WPT = TW * TH / 64;
+    static_assert(WPT >= 1 && TW % BW == 0 && TH % BH == 0, "tile shape");
+};
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -187,12 +275,11 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Pixel arithmetic in base 2: with A' = -a/2 log2(e), B' = -b log2(e),
-// C' = -c/2 log2(e) and dx, dy the pixel's offset from the mean,
-//   p' = A' dx^2 + B' dx dy + C' dy^2 + log2(o) = power * log2(e) + log2(o),
-// so alpha = min(alpha_max, 2^p') = min(alpha_max, o exp(power)).  The 3-sigma
+// Pixel arithmetic in base 2 (block_stage): p' = power log2(e) + log2(o),
+// alpha = min(alpha_max, 2^p') = min(alpha_max, o exp(power)).  The 3-sigma
 // rule (power >= -cut^2/2) and alpha >= alpha_min become one threshold on p':
-// p' >= max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)).  The transmittance
+// p' >= thr = max(-cut^2/2 log2(e) + log2(o), log2(alpha_min)), i.e.
+// q <= min(cut^2/2 log2(e), log2(o) - log2(alpha_min)).  The transmittance
 // is carried as T' = prod (1 - alpha) past the stop: T' only decreases, so a
 // pixel's stop (T (1 - alpha) < t_min, the stopping Gaussian not added) is the
 // first record where T' falls below t_min, and a weight is kept while T' after
@@ -202,9 +289,10 @@ __device__ __forceinline__ float ex2_approx(float x)
 // the alpha output is the sum of the kept weights, which telescopes to
 // 1 - T before the stop.  Both tests are 0/1 factors from one float compare
 // each (set.ge), which runs on the ALU pipe beside the FMA-bound arithmetic.
-// The column terms dx, A' dx^2 + log2(o) and B' dx are shared by the pixel
-// pair and computed once (scalar); the row terms run packed.  DA: accumulate
-// depth and alpha too (image export); the scoring launches need colour only.
+// The column terms P0 + Gx dx - qa dx^2 and Gy - 2 qb dx are shared by the
+// pixel pair and computed once (scalar); the row terms run packed.  DA:
+// accumulate depth and alpha too (image export); the scoring launches need
+// colour only.
 // 1.0f if a >= b (a < b) else 0.0f: one float compare, on the ALU pipe
 __device__ __forceinline__ float step_ge(float a, float b)
 {
@@ -218,21 +306,23 @@ __device__ __forceinline__ float step_lt(float a, float b)
     asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
     return d;
 }
+// Register budget: 64 per thread (32 one-warp blocks per SM) for the scoring
+// launches; the export launches (DA) carry depth and alpha sums too and get
+// 72 (28 blocks per SM) rather than spill (same-box A/B: winner export
+// 0.233 -> 0.208 ms).
 template <int TW, int TH, int RPL, bool DA>
-__global__ void __launch_bounds__(32, RPL == 1 ? 32 : 24)
+__global__ void __launch_bounds__(32, RPL == 1 ? (DA ? 28 : 32) : 24)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
         const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
         float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
         const int *__restrict__ overflow)
 {
-    constexpr int WPT = TW * TH / 64;        // warps (64-pixel blocks) per tile
-    constexpr int WROWS = 64 / TW;           // pixel rows per warp
+    using GM = BlockGeom<TW, TH>;
+    constexpr int BW = GM::BW, BH = GM::BH, WPT = GM::WPT;
     constexpr int CH = 32 * RPL;             // records per warp step
-    static_assert(WPT >= 1 && TH % WROWS == 0, "tile shape");
-    // kept records compacted: (-u,A',B',log2 o) (-v,-v,C',C') (r,r,g,g)
-    // (b,b,z,z) and the p' threshold; colour only: (b,b,thr,thr)
+    // kept records compacted: (-qa, Gx, -2 qb, Gy) (-qc, -qc, P0, thr)
+    // (r, r, g, g) (b, b, z, z)
     __shared__ float4 s_rec[4][CH];
-    __shared__ float s_thr[CH];
 
     // one warp per block: (tile, warp block) units, so a warp that finishes
     // early frees its slot instead of waiting for the tile's slowest warp
@@ -242,30 +332,32 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     const int out_v = blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     const int lane = threadIdx.x;
-    const int px = tx * TW + lane % TW;
-    const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
+    const int bx0p = tx * TW + (warp % GM::NBX) * BW, by0p = ty * TH + (warp / GM::NBX) * BH;
+    const int px = bx0p + lane % BW;
+    const int py0 = by0p + 2 * (lane / BW);
     const int py1 = py0 + 1;
     const bool in0 = px < cam.width && py0 < cam.height;
     const bool in1 = px < cam.width && py1 < cam.height;
-    const float fxp = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
+    // centre of the block's pixel centres and this lane's offsets from it (exact)
+    const float ocx = (float)bx0p + 0.5f * BW, ocy = (float)by0p + 0.5f * BH;
+    const float DX = (float)(lane % BW) + 0.5f - 0.5f * BW;
+    const float dy0 = (float)(2 * (lane / BW)) + 0.5f - 0.5f * BH;
+    const f32x2 DY2 = pk(dy0, dy0 + 1.f);
     int2 r = make_int2(0, 0);
     if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
-    constexpr float L2E = 1.4426950408889634f, LN2 = 0.6931471805599453f;
-    const float lim = -0.5f * cam.cut * cam.cut;
-    const float lamin = __logf(cam.alpha_min);
-    const float limL = lim * L2E;
+    constexpr float L2E = 1.4426950408889634f;
+    const float limL = -0.5f * cam.cut * cam.cut * L2E;
     const float l2amin = log2f(cam.alpha_min);
     float4(*const sw)[CH] = s_rec;
-    float *const sthr = s_thr;
     const unsigned lt = lanemask_lt_u();
 
     // pixel pair state (low = row y, high = row y + 1): transmittance, colour,
     // depth and weight sums
     f32x2 T2 = pk(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f);
     f32x2 R2 = 0ull, G2 = 0ull, B2 = 0ull, Z2 = 0ull, S2 = 0ull;
-    const f32x2 FY2 = pk(fy0, fy1), NEG1 = pk(-1.f, -1.f);
+    const f32x2 NEG1 = pk(-1.f, -1.f);
 
     // software pipeline: list indices two steps ahead, records one step ahead
     uint32_t gnext[RPL];
@@ -309,32 +401,25 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
                 qa[q] = __ldg(p); qb[q] = __ldg(p + 1); qc[q] = __ldg(p + 2);
             }
             gnext[q] = jnn < r.y ? __ldg(list + jnn) : 0u;
-            // log2 o: the threshold below and the staged record
-            const float l2o = __log2f(pa.w);
-            if (j < r.y) {
-                // pa: u v z o | pb: conic a b c, Sigma'_xx | pc: rgb, Sigma'_yy
-                const float thr = fmaxf(lim, lamin - LN2 * l2o - 1e-3f);
-                if (thr < 0.f) {
-                    // keep iff the ellipse {power >= thr} (widened 1%) meets the block
-                    const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
-                    hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
-                }
+            // pa: u v z log2(o) | pb: scaled axes | pc: rgb.  A pixel counts iff
+            // q <= min(-limL, log2 o - log2 alpha_min); keep the record iff the
+            // ellipse at that bound (plus a margin for the float arithmetic,
+            // widened 1%) meets the box
+            const Conic cq = conic_of(pb);
+            const float qbound = fminf(-limL, pa.w - l2amin + 1.5e-3f);
+            if (j < r.y && qbound > 0.f) {
+                const float qmin = quad_min_rect(pb, cq, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
+                hit = qmin <= qbound * 1.01f + 1e-3f;
             }
             const unsigned keep = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const int k = nk + __popc(keep & lt);
-                const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
-                sw[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
-                sw[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
+                float4 t0, t1;
+                block_stage(pa, pb, cq, fmaxf(limL + pa.w, l2amin), ocx, ocy, t0, t1);
+                sw[0][k] = t0;
+                sw[1][k] = t1;
                 sw[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
-                const float nth = fmaxf(limL + l2o, l2amin);
-                if (DA) {
-                    sw[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
-                    sthr[k] = nth;
-                } else {
-                    // colour only: the threshold rides in the blue record
-                    sw[3][k] = make_float4(pc.z, pc.z, nth, nth);
-                }
+                sw[3][k] = DA ? make_float4(pc.z, pc.z, pa.z, pa.z) : make_float4(pc.z, pc.z, 0.f, 0.f);
             }
             nk += __popc(keep);
         }
@@ -342,16 +427,12 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
 #pragma unroll 4
         for (int k = 0; k < nk; ++k) {
             const float4 s0 = sw[0][k], s1 = sw[1][k];
-            const float4 c1 = sw[3][k];
-            const float nth = DA ? sthr[k] : c1.z;
-            const float dx = fxp + s0.x;
-            const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
-            const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
-            const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
+            const float k1 = fmaf(s0.z, DX, s0.w), k0 = fmaf(fmaf(s0.x, DX, s0.y), DX, s1.z);
+            const f32x2 P2 = fma2(DY2, fma2(pk(s1.x, s1.y), DY2, pk(k1, k1)), pk(k0, k0));
             float p0, p1;
             upk(P2, p0, p1);
             // p' >= threshold
-            const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
+            const f32x2 IN2 = pk(step_ge(p0, s1.w), step_ge(p1, s1.w));
             // -alpha = max(-alpha_max, -2^p') (exact negation of the clamp)
             const float na0 = fmaxf(-cam.alpha_max, -ex2_approx(p0));
             const float na1 = fmaxf(-cam.alpha_max, -ex2_approx(p1));
@@ -368,7 +449,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
             // minus the weight: the sums below accumulate negated
             const f32x2 NWF = mul2(mul2(T2, NAIN), GO2);
             T2 = TN2;
-            const float4 c0 = sw[2][k];
+            const float4 c0 = sw[2][k], c1 = sw[3][k];
             R2 = fma2(pk(c0.x, c0.y), NWF, R2);
             G2 = fma2(pk(c0.z, c0.w), NWF, G2);
             B2 = fma2(pk(c1.x, c1.y), NWF, B2);
@@ -403,30 +484,43 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     }
     if (partials) {
         const float *query = L.q_img[L.view_q[v]];
-        // pixels outside the image have zero colour and contribute nothing
-        float sr, srr, srq = 0.f;
+        // pixels outside the image have zero colour and contribute nothing;
+        // the block's S_r, S_rr and S_rq are compensated FP32 sums
+        CSum sr = {0.f, 0.f}, srr = {0.f, 0.f}, srq = {0.f, 0.f};
         if (cam.ncc_gray) {
             // gray values (R + G + B) / 3 of render and query
             const float third = 1.f / 3.f;
             const float r0 = (R0 + G0 + B0) * third, r1 = (R1 + G1 + B1) * third;
-            sr = r0 + r1;
-            srr = r0 * r0 + r1 * r1;
-            if (in0) srq += r0 * ((__ldg(query + pix0) + __ldg(query + HW + pix0) + __ldg(query + 2 * HW + pix0)) * third);
-            if (in1) srq += r1 * ((__ldg(query + pix1) + __ldg(query + HW + pix1) + __ldg(query + 2 * HW + pix1)) * third);
+            cs_add(sr, r0);
+            cs_add(sr, r1);
+            cs_add_prod(srr, r0, r0);
+            cs_add_prod(srr, r1, r1);
+            if (in0) cs_add_prod(srq, r0, (__ldg(query + pix0) + __ldg(query + HW + pix0) + __ldg(query + 2 * HW + pix0)) * third);
+            if (in1) cs_add_prod(srq, r1, (__ldg(query + pix1) + __ldg(query + HW + pix1) + __ldg(query + 2 * HW + pix1)) * third);
         } else {
-            sr = R0 + G0 + B0 + R1 + G1 + B1;
-            srr = R0 * R0 + G0 * G0 + B0 * B0 + R1 * R1 + G1 * G1 + B1 * B1;
-            if (in0) srq += R0 * __ldg(query + pix0) + G0 * __ldg(query + HW + pix0) + B0 * __ldg(query + 2 * HW + pix0);
-            if (in1) srq += R1 * __ldg(query + pix1) + G1 * __ldg(query + HW + pix1) + B1 * __ldg(query + 2 * HW + pix1);
+            const float c[6] = {R0, G0, B0, R1, G1, B1};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                cs_add(sr, c[k]);
+                cs_add_prod(srr, c[k], c[k]);
+            }
+            if (in0) {
+                cs_add_prod(srq, R0, __ldg(query + pix0));
+                cs_add_prod(srq, G0, __ldg(query + HW + pix0));
+                cs_add_prod(srq, B0, __ldg(query + 2 * HW + pix0));
+            }
+            if (in1) {
+                cs_add_prod(srq, R1, __ldg(query + pix1));
+                cs_add_prod(srq, G1, __ldg(query + HW + pix1));
+                cs_add_prod(srq, B1, __ldg(query + 2 * HW + pix1));
+            }
         }
-        sr = warp_sum_f(sr);
-        srr = warp_sum_f(srr);
-        srq = warp_sum_f(srq);
+        const double tr = cs_warp_total(sr), trr = cs_warp_total(srr), trq = cs_warp_total(srq);
         if (lane == 0) {
             double *o = partials + ((int64_t)blockIdx.y * cam.n_tiles * WPT + unit) * 3;
-            o[0] = sr;
-            o[1] = srr;
-            o[2] = srq;
+            o[0] = tr;
+            o[1] = trr;
+            o[2] = trq;
         }
     }
 }
@@ -542,7 +636,12 @@ cudaError_t launch_ncc_finalize(const double *partials, const double *qstats, co
 // channels with values z_j and 1) and K_j = the sum of w S over the
 // contributors after j (K starts at G . C (+ G_D D + G_A A) and loses w_j S_j
 // at j); alpha = o exp(power) unclamped gives dL/d power = alpha dL/d alpha,
-// and power = -(a dx^2 + 2 b dx dy + c dy^2)/2 with dx = x - u.  The warp
+// and power = -(a dx^2 + 2 b dx dy + c dy^2)/2 with dx = x - u, so
+// d power/du = a dx + b dy and d power/dv = b dx + c dy, taken as the
+// gradient at the block centre (-G / 2, from the axes, no cancellation) plus
+// the conic times the pixel's offset within the block, in the scaled units of
+// the staging (divided by log2(e) / 2); d power/da = -dx^2/2, d/db = -dx dy,
+// d/dc = -dy^2/2.  The warp
 // sums each record's gradients over its 64 pixels (a reduce-scatter: lane
 // 32/NP * m holds total m) and adds them to the (view, Gaussian) entry of
 // gout.
@@ -564,35 +663,38 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
     constexpr int NOUT = IMG ? 10 : 5;
     constexpr int NP = IMG ? 16 : 8;           // NOUT padded to a power of two
     constexpr int GRP = 32 / NP;                // lanes holding each total
-    constexpr int WPT = TW * TH / 64;
-    constexpr int WROWS = 64 / TW;
-    constexpr float L2E = 1.4426950408889634f, LN2 = 0.6931471805599453f;
-    // kept records: the forward's (-u, A', B', log2 o) (-v, -v, C', C')
-    // (r, r, g, g) (b, b, z, z), then the natural conic and 1/o:
-    // (a, a, b, b) (c, c, 1/o, 1/o); the forward's step threshold
+    using GM = BlockGeom<TW, TH>;
+    constexpr int BW = GM::BW, BH = GM::BH, WPT = GM::WPT;
+    constexpr float L2E = 1.4426950408889634f;
+    // kept records: the forward's (-qa, Gx, -2 qb, Gy) (-qc, -qc, P0, thr)
+    // (r, r, g, g) (b, b, z, z), then the block centre's offset from the mean
+    // and 1/o: (dbx, 1/o, dby, dby), and the scaled conic (qa, qb, qc, -)
     __shared__ float4 s_rec[6][32];
-    __shared__ float s_thr[32];
     __shared__ uint32_t s_g[32];
     const int unit = blockIdx.x;
     const int tile = unit / WPT, warp = unit - tile * WPT;
     const int v = blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     const int lane = threadIdx.x;
-    const int px = tx * TW + lane % TW;
-    const int py0 = ty * TH + warp * WROWS + 2 * (lane / TW);
+    const int bx0p = tx * TW + (warp % GM::NBX) * BW, by0p = ty * TH + (warp / GM::NBX) * BH;
+    const int px = bx0p + lane % BW;
+    const int py0 = by0p + 2 * (lane / BW);
     const bool in[2] = {px < cam.width && py0 < cam.height, px < cam.width && py0 + 1 < cam.height};
-    const float fxp = (float)px + 0.5f;
+    const float ocx = (float)bx0p + 0.5f * BW, ocy = (float)by0p + 0.5f * BH;
+    const float DX = (float)(lane % BW) + 0.5f - 0.5f * BW;
+    const float dy0 = (float)(2 * (lane / BW)) + 0.5f - 0.5f * BH;
+    const f32x2 DY2 = pk(dy0, dy0 + 1.f);
     if (*overflow) return;
     const int2 r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
-    const float lim = -0.5f * cam.cut * cam.cut;
-    const float lamin = __logf(cam.alpha_min);
-    const float limL = lim * L2E;
+    const float limL = -0.5f * cam.cut * cam.cut * L2E;
     const float l2amin = log2f(cam.alpha_min);
     const float amax = cam.alpha_max;
     const unsigned lt = lanemask_lt_u();
-    const f32x2 FY2 = pk((float)py0 + 0.5f, (float)py0 + 1.5f), NEG1 = pk(-1.f, -1.f);
+    const f32x2 NEG1 = pk(-1.f, -1.f);
+    // the natural conic is the scaled one over log2(e) / 2
+    constexpr float IK2 = 2.f / L2E;
 
     // the forward's cull and compaction, one step of 32 records, against the
     // box of the pixels still compositing (T > 0)
@@ -609,30 +711,30 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         const int j = b + lane;
         bool hit = false;
         float4 pa = make_float4(0, 0, 0, 0), pb = pa, pc = pa;
+        Conic cq = {0.f, 0.f, 0.f};
         uint32_t gi = 0;
         if (j < r.y) {
             gi = __ldg(list + j);
             const float4 *p = vrec + 3 * (int64_t)gi;
             pa = __ldg(p); pb = __ldg(p + 1); pc = __ldg(p + 2);
-            const float thr = fmaxf(lim, lamin - LN2 * __log2f(pa.w) - 1e-3f);
-            if (thr < 0.f) {
-                const float qmin = quad_min_rect(pb.x, pb.y, pb.z, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
-                hit = qmin <= -2.f * thr * 1.01f + 1e-3f;
+            cq = conic_of(pb);
+            const float qbound = fminf(-limL, pa.w - l2amin + 1.5e-3f);
+            if (qbound > 0.f) {
+                const float qmin = quad_min_rect(pb, cq, bx0 - pa.x, bx1 - pa.x, by0 - pa.y, by1 - pa.y);
+                hit = qmin <= qbound * 1.01f + 1e-3f;
             }
         }
         const unsigned keep = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const int k = __popc(keep & lt);
-            const float l2o = __log2f(pa.w);
-            const float Ap = -0.5f * L2E * pb.x, Bp = -L2E * pb.y, Cp = -0.5f * L2E * pb.z;
-            const float io = 1.f / pa.w;
-            s_rec[0][k] = make_float4(-pa.x, Ap, Bp, l2o);
-            s_rec[1][k] = make_float4(-pa.y, -pa.y, Cp, Cp);
+            float4 t0, t1;
+            block_stage(pa, pb, cq, fmaxf(limL + pa.w, l2amin), ocx, ocy, t0, t1);
+            s_rec[0][k] = t0;
+            s_rec[1][k] = t1;
             s_rec[2][k] = make_float4(pc.x, pc.x, pc.y, pc.y);
             s_rec[3][k] = make_float4(pc.z, pc.z, pa.z, pa.z);
-            s_rec[4][k] = make_float4(pb.x, pb.x, pb.y, pb.y);
-            s_rec[5][k] = make_float4(pb.z, pb.z, io, io);
-            s_thr[k] = fmaxf(limL + l2o, l2amin);
+            s_rec[4][k] = make_float4(ocx - pa.x, ex2_approx(-pa.w), ocy - pa.y, ocy - pa.y);
+            s_rec[5][k] = make_float4(cq.a, cq.b, cq.c, 0.f);
             s_g[k] = gi;
         }
         __syncwarp();
@@ -668,14 +770,11 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             const int nk = stage(b, T2);
             for (int k = 0; k < nk; ++k) {
                 const float4 s0 = s_rec[0][k], s1 = s_rec[1][k];
-                const float nth = s_thr[k];
-                const float dx = fxp + s0.x;
-                const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
-                const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
-                const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
+                const float k1 = fmaf(s0.z, DX, s0.w), k0 = fmaf(fmaf(s0.x, DX, s0.y), DX, s1.z);
+                const f32x2 P2 = fma2(DY2, fma2(pk(s1.x, s1.y), DY2, pk(k1, k1)), pk(k0, k0));
                 float p0, p1;
                 upk(P2, p0, p1);
-                const f32x2 IN2 = pk(step_ge(p0, nth), step_ge(p1, nth));
+                const f32x2 IN2 = pk(step_ge(p0, s1.w), step_ge(p1, s1.w));
                 const float na0 = fmaxf(-amax, -ex2_approx(p0)), na1 = fmaxf(-amax, -ex2_approx(p1));
                 const f32x2 NAIN = mul2(pk(na0, na1), IN2);
                 const f32x2 TN2 = fma2(T2, NAIN, T2);
@@ -760,14 +859,11 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
         const int nk = stage(b, T2);
         for (int k = 0; k < nk; ++k) {
             const float4 s0 = s_rec[0][k], s1 = s_rec[1][k];
-            const float nth = s_thr[k];
-            const float dx = fxp + s0.x;
-            const float k1 = s0.z * dx, k0 = fmaf(s0.y * dx, dx, s0.w);
-            const f32x2 DY2 = add2(FY2, pk(s1.x, s1.y));
-            const f32x2 P2 = fma2(DY2, fma2(pk(s1.z, s1.w), DY2, pk(k1, k1)), pk(k0, k0));
+            const float k1 = fmaf(s0.z, DX, s0.w), k0 = fmaf(fmaf(s0.x, DX, s0.y), DX, s1.z);
+            const f32x2 P2 = fma2(DY2, fma2(pk(s1.x, s1.y), DY2, pk(k1, k1)), pk(k0, k0));
             float p0, p1;
             upk(P2, p0, p1);
-            const float i0 = step_ge(p0, nth), i1 = step_ge(p1, nth);
+            const float i0 = step_ge(p0, s1.w), i1 = step_ge(p1, s1.w);
             const float r0 = ex2_approx(p0), r1 = ex2_approx(p1);
             // the forward's arithmetic: -alpha, T' = T + T (-alpha) fused, minus the weight
             const float na0 = fmaxf(-amax, -r0), na1 = fmaxf(-amax, -r1);
@@ -785,7 +881,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 T2 = TN2;
                 continue;
             }
-            const float4 c0 = s_rec[2][k], c1 = s_rec[3][k], nb = s_rec[4][k], nc = s_rec[5][k];
+            const float4 c0 = s_rec[2][k], c1 = s_rec[3][k], db = s_rec[4][k], cn = s_rec[5][k];
             // S = G . c (+ G_D z + G_A); K loses w S
             f32x2 S2 = fma2(G0, pk(c0.x, c0.y), fma2(G1, pk(c0.z, c0.w), mul2(G2, pk(c1.x, c1.y))));
             if (IMG) S2 = fma2(GD, pk(c1.z, c1.w), add2(S2, GA));
@@ -796,20 +892,25 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
             const f32x2 GAL = mul2(fma2(K2, NR2, mul2(T2, S2)), mul2(pk(i0, i1), GO2));
             // dL/d power = alpha dL/d alpha (0 where the clamp holds)
             const f32x2 GP = mul2(GAL, pk(a0 * step_lt(r0, amax), a1 * step_lt(r1, amax)));
-            const f32x2 GX = mul2(GP, pk(dx, dx)), GY = mul2(GP, DY2);
+            // offsets of the pixels from the mean: dx = dbx + DX, dy = dby + dy_lane
+            const float dx = db.x + DX;
+            const f32x2 DYM = add2(pk(db.z, db.w), DY2);
+            const f32x2 GX = mul2(GP, pk(dx, dx)), GY = mul2(GP, DYM), GK = mul2(GP, pk(IK2, IK2));
+            // d power/du, d power/dv in scaled units: -G/2 + (qa dx + qb dy, qb dx + qc dy) over the block offsets
+            const float cu = fmaf(cn.x, DX, -0.5f * s0.y), cv = fmaf(cn.y, DX, -0.5f * s0.w);
             float g[NP];
 #pragma unroll
             for (int m = NOUT; m < NP; ++m) g[m] = 0.f;
             float lo, hi;
-            upk(fma2(GX, pk(nb.x, nb.y), mul2(GY, pk(nb.z, nb.w))), lo, hi);      // d/du: a dx + b dy
+            upk(mul2(GK, fma2(pk(cn.y, cn.y), DY2, pk(cu, cu))), lo, hi);        // d/du: a dx + b dy
             g[0] = lo + hi;
-            upk(fma2(GX, pk(nb.z, nb.w), mul2(GY, pk(nc.x, nc.y))), lo, hi);      // d/dv: b dx + c dy
+            upk(mul2(GK, fma2(pk(cn.z, cn.z), DY2, pk(cv, cv))), lo, hi);        // d/dv: b dx + c dy
             g[1] = lo + hi;
             upk(mul2(GX, pk(-0.5f * dx, -0.5f * dx)), lo, hi);                     // d/da: -dx^2 / 2
             g[2] = lo + hi;
-            upk(mul2(GX, mul2(DY2, NEG1)), lo, hi);                                // d/db: -dx dy
+            upk(mul2(GX, mul2(DYM, NEG1)), lo, hi);                                // d/db: -dx dy
             g[3] = lo + hi;
-            upk(mul2(GY, mul2(DY2, pk(-0.5f, -0.5f))), lo, hi);                     // d/dc: -dy^2 / 2
+            upk(mul2(GY, mul2(DYM, pk(-0.5f, -0.5f))), lo, hi);                     // d/dc: -dy^2 / 2
             g[4] = lo + hi;
             if (IMG) {
                 // colour and depth: w G, from minus the weight
@@ -819,7 +920,7 @@ k_blend_grad(const float4 *__restrict__ rec, Layout L, const uint32_t *__restric
                 g[6] = -lo - hi;
                 upk(mul2(NWF, G2), lo, hi);
                 g[7] = -lo - hi;
-                upk(mul2(GP, pk(nc.z, nc.w)), lo, hi);                             // d/do = dL/d power / o
+                upk(mul2(GP, pk(db.y, db.y)), lo, hi);                             // d/do = dL/d power / o
                 g[8] = lo + hi;
                 upk(mul2(NWF, GD), lo, hi);
                 g[9] = -lo - hi;
