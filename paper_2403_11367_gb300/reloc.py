@@ -184,13 +184,36 @@ def _check(status):
         raise RelocError(status, lib.reloc_last_error().decode())
 
 
-def _ptr(t):
-    """Device pointer of a torch CUDA tensor (or None)."""
+_F32, _F64, _I32, _U16 = ("float32",), ("float64",), ("int32",), ("bfloat16", "int16", "uint16")
+
+
+def _ptr(t, dtype=None, numel=None, shape=None, name="buffer"):
+    """Device pointer of a torch CUDA tensor (or None), after checking what the
+    C call will read or write through it: its dtype (one of the names in
+    ``dtype``), its exact shape or at least ``numel`` elements, contiguity and
+    placement on the current CUDA device.  A wrong buffer raises ValueError
+    here, before any launch could read or write past it."""
     if t is None:
         return None
-    if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("device buffers must be contiguous CUDA tensors")
+    if dtype is not None and str(t.dtype).replace("torch.", "") not in dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {' or '.join(dtype)}")
+    if shape is not None and tuple(t.shape) != tuple(int(x) for x in shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(int(x) for x in shape)}")
+    if numel is not None and t.numel() < int(numel):
+        raise ValueError(f"{name}: {t.numel()} elements, at least {int(numel)} needed")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: device buffers must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: device buffers must be CUDA tensors")
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
     return C.c_void_p(t.data_ptr())
+
+
+def _qptr(q, c, name="query"):
+    """A [3][H][W] float32 image on the device for camera c."""
+    return _ptr(q, _F32, shape=(3, c.height, c.width), name=name)
 
 
 def _stream(stream):
@@ -221,9 +244,13 @@ def reloc_ncc_images_noalloc(images, query, scores_out, degenerate_out=None, str
     """NCC of rendered images [V,3,H,W] against query [3,H,W] into scores_out
     [V] (float64) and degenerate_out [V] (int32), all CUDA tensors; the library
     allocates nothing for this call (see include/reloc.h)."""
+    if images.dim() != 4 or images.shape[1] != 3:
+        raise ValueError(f"images: shape {tuple(images.shape)}, expected (V, 3, H, W)")
     V, _, H, W = images.shape
-    _check(lib.reloc_ncc_images_noalloc(_ptr(images), V, H, W, _ptr(query), _ptr(scores_out),
-                                        _ptr(degenerate_out), _stream(stream)))
+    _check(lib.reloc_ncc_images_noalloc(_ptr(images, _F32, name="images"), V, H, W,
+                                        _ptr(query, _F32, shape=(3, H, W), name="query"),
+                                        _ptr(scores_out, _F64, numel=V, name="scores_out"),
+                                        _ptr(degenerate_out, _I32, numel=V, name="degenerate_out"), _stream(stream)))
 
 
 def reloc_measure_peaks(device: int = 0) -> dict:
@@ -248,6 +275,8 @@ class Context:
         self._h = _vp()
         _check(lib.reloc_create(C.byref(cfg) if cfg is not None else None, device, C.byref(self._h)))
         self.n = 0
+        self._cfg = cfg if cfg is not None else reloc_default_config()
+        self._cam = None                 # camera of the last rendering call (export_debug sizes)
 
     def close(self):
         if self._h:
@@ -292,7 +321,10 @@ class Context:
         ra, nr = self._ranges(ranges)
         p, pp, V = _poses(poses)
         c = camera(cam)
-        _check(lib.reloc_render(self._h, ra, nr, pp, V, C.byref(c), _ptr(rgb), _ptr(depth), _ptr(alpha),
+        hw = c.height * c.width
+        self._cam = c
+        _check(lib.reloc_render(self._h, ra, nr, pp, V, C.byref(c), _ptr(rgb, _F32, V * 3 * hw, name="rgb"),
+                                _ptr(depth, _F32, V * hw, name="depth"), _ptr(alpha, _F32, V * hw, name="alpha"),
                                 _stream(stream)))
 
     def score(self, ranges, poses, cam, query, stream=None):
@@ -301,7 +333,8 @@ class Context:
         c = camera(cam)
         sc = np.zeros(V)
         dg = np.zeros(V, np.int32)
-        _check(lib.reloc_score(self._h, ra, nr, pp, V, C.byref(c), _ptr(query), sc.ctypes.data_as(_dp),
+        self._cam = c
+        _check(lib.reloc_score(self._h, ra, nr, pp, V, C.byref(c), _qptr(query, c), sc.ctypes.data_as(_dp),
                                dg.ctypes.data_as(_ip), _stream(stream)))
         return sc, dg
 
@@ -313,9 +346,13 @@ class Context:
         res = Result()
         V = g.nx * g.ny * g.nyaw
         sc = np.zeros(V) if want_scores else None
-        _check(lib.reloc_localize(self._h, _ptr(query), cp.ctypes.data_as(_dp), radius, C.byref(g), C.byref(c),
+        hw = c.height * c.width
+        self._cam = c
+        _check(lib.reloc_localize(self._h, _qptr(query, c), cp.ctypes.data_as(_dp), radius, C.byref(g), C.byref(c),
                                   C.byref(res), sc.ctypes.data_as(_dp) if sc is not None else None,
-                                  _ptr(best_rgb), _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
+                                  _ptr(best_rgb, _F32, 3 * hw, name="best_rgb"),
+                                  _ptr(best_depth, _F32, hw, name="best_depth"),
+                                  _ptr(best_alpha, _F32, hw, name="best_alpha"), _stream(stream)))
         return res, sc
 
     def localize_random(self, query, coarse_pose, radius, grid, cam, fraction=0.2, ncc_stop=float("inf"), batch=64,
@@ -336,10 +373,14 @@ class Context:
         res = Result()
         n = g.nx * g.ny * g.nyaw
         sc = np.zeros(n) if want_scores else None
-        _check(lib.reloc_localize_random(self._h, _ptr(query), cp.ctypes.data_as(_dp), radius, C.byref(g),
+        hw = c.height * c.width
+        self._cam = c
+        _check(lib.reloc_localize_random(self._h, _qptr(query, c), cp.ctypes.data_as(_dp), radius, C.byref(g),
                                          C.byref(c), C.byref(opt), C.byref(res),
-                                         sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
-                                         _ptr(best_depth), _ptr(best_alpha), _stream(stream)))
+                                         sc.ctypes.data_as(_dp) if sc is not None else None,
+                                         _ptr(best_rgb, _F32, 3 * hw, name="best_rgb"),
+                                         _ptr(best_depth, _F32, hw, name="best_depth"),
+                                         _ptr(best_alpha, _F32, hw, name="best_alpha"), _stream(stream)))
         return res, sc
 
     def score_grad(self, ranges, poses, cam, query, stream=None):
@@ -350,7 +391,8 @@ class Context:
         c = camera(cam)
         sc = np.zeros(V)
         gr = np.zeros((V, 6))
-        _check(lib.reloc_score_grad(self._h, ra, nr, pp, V, C.byref(c), _ptr(query), sc.ctypes.data_as(_dp),
+        self._cam = c
+        _check(lib.reloc_score_grad(self._h, ra, nr, pp, V, C.byref(c), _qptr(query, c), sc.ctypes.data_as(_dp),
                                     gr.ctypes.data_as(_dp), _stream(stream)))
         return sc, gr
 
@@ -373,8 +415,11 @@ class Context:
         c = camera(cam)
         o = self.train_options(**opts)
         loss = C.c_double(0)
-        _check(lib.reloc_train_grad(self._h, ra, nr, pp, V, C.byref(c), _ptr(targets), C.byref(o), C.byref(loss),
-                                    _ptr(grad), _stream(stream)))
+        self._cam = c
+        _check(lib.reloc_train_grad(self._h, ra, nr, pp, V, C.byref(c),
+                                    _ptr(targets, _F32, shape=(V, 3, c.height, c.width), name="targets"),
+                                    C.byref(o), C.byref(loss), _ptr(grad, _F32, 14 * self.n, name="grad"),
+                                    _stream(stream)))
         return loss.value
 
     def train_step(self, ranges, poses, cam, targets, stream=None, **opts):
@@ -384,8 +429,10 @@ class Context:
         c = camera(cam)
         o = self.train_options(**opts)
         loss = C.c_double(0)
-        _check(lib.reloc_train_step(self._h, ra, nr, pp, V, C.byref(c), _ptr(targets), C.byref(o), C.byref(loss),
-                                    _stream(stream)))
+        self._cam = c
+        _check(lib.reloc_train_step(self._h, ra, nr, pp, V, C.byref(c),
+                                    _ptr(targets, _F32, shape=(V, 3, c.height, c.width), name="targets"),
+                                    C.byref(o), C.byref(loss), _stream(stream)))
         return loss.value
 
     def train_reset(self):
@@ -411,8 +458,12 @@ class Context:
         pi = pr if pose_init is None else np.ascontiguousarray(pose_init, np.float64).reshape(16)
         c = camera(cam)
         res = PnpResult()
+        hw = c.height * c.width
+        if pairs.dim() != 2 or pairs.shape[1] != 4:
+            raise ValueError(f"pairs: shape {tuple(pairs.shape)}, expected (n, 4)")
         _check(lib.reloc_refine_pnp(self._h, pr.ctypes.data_as(_dp), pi.ctypes.data_as(_dp), C.byref(c),
-                                    _ptr(depth), _ptr(alpha), _ptr(pairs), int(pairs.shape[0]), C.byref(o),
+                                    _ptr(depth, _F32, hw, name="depth"), _ptr(alpha, _F32, hw, name="alpha"),
+                                    _ptr(pairs, _F32, name="pairs"), int(pairs.shape[0]), C.byref(o),
                                     C.byref(res), _stream(stream)))
         return res
 
@@ -422,28 +473,31 @@ class Context:
         n = len(queries)
         arr = (Query * n)()
         counts = []
+        c = camera(cam)
         for i, (img, pose, radius, grid) in enumerate(queries):
-            arr[i].query_dev = _ptr(img).value
+            arr[i].query_dev = _qptr(img, c, name=f"queries[{i}]").value
             arr[i].coarse_pose = (C.c_double * 16)(*np.asarray(pose, np.float64).reshape(16))
             arr[i].radius = float(radius)
             arr[i].grid = Grid(*grid) if not isinstance(grid, Grid) else grid
             counts.append(arr[i].grid.nx * arr[i].grid.ny * arr[i].grid.nyaw)
         res = (Result * n)()
         sc = np.zeros(sum(counts)) if want_scores else None
-        c = camera(cam)
+        hw = c.height * c.width
+        self._cam = c
         _check(lib.reloc_localize_batch(self._h, arr, n, C.byref(c), res,
-                                        sc.ctypes.data_as(_dp) if sc is not None else None, _ptr(best_rgb),
-                                        _ptr(best_depth), _stream(stream)))
+                                        sc.ctypes.data_as(_dp) if sc is not None else None,
+                                        _ptr(best_rgb, _F32, n * 3 * hw, name="best_rgb"),
+                                        _ptr(best_depth, _F32, n * hw, name="best_depth"), _stream(stream)))
         split = None
         if sc is not None:
             split = np.split(sc, np.cumsum(counts)[:-1])
         return list(res), split
 
     @staticmethod
-    def _queries(queries):
+    def _queries(queries, c):
         arr = (Query * len(queries))()
         for i, (img, pose, radius, grid) in enumerate(queries):
-            arr[i].query_dev = _ptr(img).value
+            arr[i].query_dev = _qptr(img, c, name=f"queries[{i}]").value
             arr[i].coarse_pose = (C.c_double * 16)(*np.asarray(pose, np.float64).reshape(16))
             arr[i].radius = float(radius)
             arr[i].grid = Grid(*grid) if not isinstance(grid, Grid) else grid
@@ -452,7 +506,7 @@ class Context:
     def autotune(self, sample, cam, table_path=None, force=False, stream=None) -> TuneResult:
         out = TuneResult()
         c = camera(cam)
-        _check(lib.reloc_autotune(self._h, self._queries(sample), len(sample), C.byref(c),
+        _check(lib.reloc_autotune(self._h, self._queries(sample, c), len(sample), C.byref(c),
                                   table_path.encode() if table_path else None, 1 if force else 0, C.byref(out),
                                   _stream(stream)))
         return out
@@ -471,19 +525,25 @@ class Context:
         c = camera(cam)
         res = Result()
 
-        def hp(a):
+        hw = c.height * c.width
+
+        def hp(a, n, name):
             if a is None:
                 return None
             if hasattr(a, "data_ptr"):
-                if a.is_cuda or not a.is_contiguous():
-                    raise ValueError("host buffers must be contiguous CPU tensors")
+                if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float32":
+                    raise ValueError(f"{name}: host buffers must be contiguous float32 CPU tensors")
+                if a.numel() < n:
+                    raise ValueError(f"{name}: {a.numel()} elements, at least {n} needed")
                 return C.c_void_p(a.data_ptr())
             if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
-                raise ValueError("host buffers must be contiguous float32")
+                raise ValueError(f"{name}: host buffers must be contiguous float32")
+            if a.size < n:
+                raise ValueError(f"{name}: {a.size} elements, at least {n} needed")
             return C.c_void_p(a.ctypes.data)
-        _check(lib.reloc_localize_host(self._h, hp(query_host), cp.ctypes.data_as(_dp), radius, C.byref(g),
-                                       C.byref(c), C.byref(res), hp(best_rgb_host), hp(best_depth_host),
-                                       _stream(stream)))
+        _check(lib.reloc_localize_host(self._h, hp(query_host, 3 * hw, "query_host"), cp.ctypes.data_as(_dp), radius,
+                                       C.byref(g), C.byref(c), C.byref(res), hp(best_rgb_host, 3 * hw, "best_rgb_host"),
+                                       hp(best_depth_host, hw, "best_depth_host"), _stream(stream)))
         return res
 
     # -- learned proposal ------------------------------------------------------------
@@ -502,15 +562,20 @@ class Context:
 
     def proposal_make_input(self, query, coarse_rgb, cam, out, stream=None):
         c = camera(cam)
-        _check(lib.reloc_proposal_make_input(self._h, _ptr(query), _ptr(coarse_rgb), C.byref(c), _ptr(out),
+        _check(lib.reloc_proposal_make_input(self._h, _qptr(query, c), _qptr(coarse_rgb, c, name="coarse_rgb"),
+                                             C.byref(c), _ptr(out, _U16, PROPOSAL_H * PROPOSAL_W * 2, name="out"),
                                              _stream(stream)))
 
     def proposal_forward(self, inputs, logits, stream=None):
-        _check(lib.reloc_proposal_forward(self._h, _ptr(inputs), inputs.shape[0], _ptr(logits), _stream(stream)))
+        B = inputs.shape[0]
+        _check(lib.reloc_proposal_forward(self._h, _ptr(inputs, _U16, shape=(B, PROPOSAL_H, PROPOSAL_W, 2), name="inputs"),
+                                          B, _ptr(logits, _F32, B * PROPOSAL_CLASSES, name="logits"), _stream(stream)))
 
     def proposal_train_step(self, inputs, labels, lr, update=True, stream=None) -> float:
         loss = C.c_float(0)
-        _check(lib.reloc_proposal_train_step(self._h, _ptr(inputs), _ptr(labels), inputs.shape[0], lr,
+        B = inputs.shape[0]
+        _check(lib.reloc_proposal_train_step(self._h, _ptr(inputs, _U16, shape=(B, PROPOSAL_H, PROPOSAL_W, 2), name="inputs"),
+                                             _ptr(labels, _I32, shape=(B,), name="labels"), B, lr,
                                              1 if update else 0, C.byref(loss), _stream(stream)))
         return float(loss.value)
 
@@ -518,8 +583,9 @@ class Context:
         """C[M,N] (float32) = A[M,K] @ B[N,K]^T for bfloat16 CUDA tensors."""
         M, K = A.shape
         N = B.shape[0]
-        _check(lib.reloc_gemm_bf16(self._h, _ptr(A), _ptr(B), _ptr(bias), _ptr(C), M, N, K, 1 if relu else 0,
-                                   split_k, _stream(stream)))
+        _check(lib.reloc_gemm_bf16(self._h, _ptr(A, _U16, shape=(M, K), name="A"), _ptr(B, _U16, shape=(N, K), name="B"),
+                                   _ptr(bias, _F32, N, name="bias"), _ptr(C, _F32, M * N, name="C"), M, N, K,
+                                   1 if relu else 0, split_k, _stream(stream)))
 
     def set_proposal(self, enabled=True, top_k=8, margin=0.0):
         _check(lib.reloc_set_proposal(self._h, 1 if enabled else 0, top_k, margin))
@@ -541,7 +607,21 @@ class Context:
 
     def export_debug(self, records=None, rects=None, inst_tiles=None, inst_gauss=None, ranges=None, n_views=None,
                      stream=None):
-        cnt = np.zeros(max(1, n_views or 1), np.int64)
-        _check(lib.reloc_export_debug(self._h, _ptr(records), _ptr(rects), _ptr(inst_tiles), _ptr(inst_gauss),
-                                      cnt.ctypes.data_as(_i64p), _ptr(ranges), _stream(stream)))
+        k = self.last_counts()
+        V, S = k.n_views, k.n_gauss
+        if n_views is not None and n_views != V:
+            raise ValueError(f"n_views {n_views}, the last call rendered {V} views")
+        cnt = np.zeros(max(1, V), np.int64)
+        ntiles = 0
+        if ranges is not None:
+            if self._cam is None:
+                raise ValueError("ranges: no rendering call yet")
+            tw, th = self._cfg.tile_w, self._cfg.tile_h
+            ntiles = ((self._cam.width + tw - 1) // tw) * ((self._cam.height + th - 1) // th)
+        _check(lib.reloc_export_debug(self._h, _ptr(records, _F32, V * S * 12, name="records"),
+                                      _ptr(rects, _I32, V * S * 4, name="rects"),
+                                      _ptr(inst_tiles, _I32, V * k.inst_stride, name="inst_tiles"),
+                                      _ptr(inst_gauss, _I32, V * k.inst_stride, name="inst_gauss"),
+                                      cnt.ctypes.data_as(_i64p),
+                                      _ptr(ranges, _I32, V * 2 * ntiles, name="ranges"), _stream(stream)))
         return cnt
