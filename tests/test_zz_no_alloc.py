@@ -7,9 +7,12 @@ through this entry point; its only scratch is a fixed array inside the
 library.  This test renders candidate views with reloc_render, scores them
 with the new entry point twice in a row (different view sets, so stale
 scratch from the first call would show), and checks both against the scores
-of the existing entry point reloc_score for the same poses, within the NCC
-tolerance of the parity tests.  It is collected last (file name) and needs
-no state from the other tests.
+of the existing entry point reloc_score for the same poses and against the
+FP64 oracle's NCC of the same images, within the NCC tolerance of the parity
+tests.  It also runs the largest accepted call (RELOC_NOALLOC_MAX_VIEWS
+views, which fills the last scratch row), a zero-variance image (score 0,
+degenerate 1) and a call without the degenerate output.  It is collected
+last (file name) and needs no state from the other tests.
 """
 import numpy as np
 import pytest
@@ -43,6 +46,8 @@ def test_noalloc_ncc_matches_reloc_score_on_two_calls():
     ctx.render(ranges, s.candidate_poses, cam, rgb=imgs)
     ref, ref_dg = ctx.score(ranges, s.candidate_poses, cam, qd)
 
+    imgs_np = imgs.cpu().numpy()
+    ref_or = np.array([oracle.ncc(imgs_np[v], q)[0] for v in range(V)])
     for sel in (np.arange(V), np.arange(V)[::-2].copy()):
         sub = imgs[torch.as_tensor(sel, device="cuda:0")].contiguous()
         scores = torch.full((len(sel),), float("nan"), dtype=torch.float64, device="cuda:0")
@@ -52,7 +57,24 @@ def test_noalloc_ncc_matches_reloc_score_on_two_calls():
         got = scores.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.abs(got - ref[sel]).max() <= TOL_NCC, (got, ref[sel])
+        assert np.abs(got - ref_or[sel]).max() <= 1e-9, (got, ref_or[sel])
         assert np.array_equal(dg.cpu().numpy(), ref_dg[sel])
+
+    # the largest accepted call: one view tiled to RELOC_NOALLOC_MAX_VIEWS,
+    # with a zero-variance image in the last slot, no degenerate output
+    n = R.NOALLOC_MAX_VIEWS
+    many = imgs[3:4].expand(n, -1, -1, -1).contiguous()
+    many[n - 1] = 0.25
+    scores = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda:0")
+    R.reloc_ncc_images_noalloc(many, qd, scores, None)
+    got = scores.cpu().numpy()
+    assert np.abs(got[:-1] - ref_or[3]).max() <= 1e-9
+    assert got[-1] == 0.0
+    dg = torch.full((2,), -1, dtype=torch.int32, device="cuda:0")
+    two = torch.stack([imgs[3], many[n - 1]]).contiguous()
+    scores2 = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda:0")
+    R.reloc_ncc_images_noalloc(two, qd, scores2, dg)
+    assert dg.cpu().numpy().tolist() == [0, 1] and scores2.cpu().numpy()[1] == 0.0
 
     # sizes beyond the fixed scratch are rejected before any launch
     big = torch.empty((1, 3, 2, 2), device="cuda:0")
