@@ -36,11 +36,16 @@ N_GAUSS = 2_000_000
 GRID = (4, 4, 4, 0.5, 2.0)
 RADIUS = 40.0
 N_QUERIES = 4
-FLOPS_PER_EVAL = 24          # FP32 ops per included (pixel, Gaussian) pair (plus one exp)
+# FP32 operations per evaluated (pixel, Gaussian) pair, plus one exponential:
+# the quadratic form and the threshold (~8), alpha with its clamp (~3), the
+# transmittance update and stop test (~3), the weighted colour (3 FMAs, 6)
+# and the weight (~2) -- the algorithmic count of the method, not of any
+# particular kernel's instruction mix
+FLOPS_PER_EVAL = 22
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this
-# workload's 64-view k_blend<16,16,1,false> launch (query 0: 628.4 MB + 15.6 MB);
-# to be re-taken whenever that kernel changes
-BLEND_DRAM_BYTES_PER_LAUNCH = 643_978_496
+# workload's 64-view k_blend<16,16,1,false> launch of query 0 on the current
+# kernel; None until taken (the roofline's "traffic" is then null)
+BLEND_DRAM_BYTES_PER_LAUNCH = None
 WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
             "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
 
@@ -279,11 +284,27 @@ def run_random_leg(ctx, cam, dev, stream, n_queries=8):
         fyaw = -np.degrees(off[i, 2]) / syaw + 0.5 * (nyaw - 1)
         near += int(abs(ix - fx) <= 1 and abs(iy - fy) <= 1 and abs(iyaw - fyaw) <= 1)
     scored = sum(rr.n_scored for rr in res)
+    # the early stop at thresholds the synthetic street reaches (its best NCC
+    # over 20% of the paper grid is ~0.70-0.75, below the 0.8 above)
+    sweep = {}
+    for thr in (0.72, 0.7, 0.65):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rs = [ctx.localize_random(img, pose, RADIUS, PAPER_GRID, cam, fraction=SEARCH_FRACTION, ncc_stop=thr,
+                                  batch=SEARCH_BATCH, seed=100 + i, stream=stream, want_scores=False)[0]
+              for i, (img, pose) in enumerate(jobs)]
+        torch.cuda.synchronize()
+        d1 = time.perf_counter() - t1
+        sc1 = sum(x.n_scored for x in rs)
+        sweep[str(thr)] = {"stopped_early": sum(x.stopped_early for x in rs), "mean_scored_per_query": sc1 / n_queries,
+                           "queries_per_s": n_queries / d1, "candidates_per_s": sc1 / d1,
+                           "best_equal_to_full_20pct": sum(int(x.best_index == y.best_index) for x, y in zip(rs, res))}
     return {"grid": "15 x 15 x 36 cells, 2 m / 10 deg (8100)", "fraction": SEARCH_FRACTION,
             "ncc_stop": SEARCH_STOP, "batch": SEARCH_BATCH, "queries": n_queries, "candidates_scored": scored,
             "candidates_per_s": scored / dt, "queries_per_s": n_queries / dt,
             "mean_scored_per_query": scored / n_queries, "stopped_early": sum(rr.stopped_early for rr in res),
-            "best_within_one_cell_of_hidden": near, "best_ncc": [round(rr.best_score, 4) for rr in res]}
+            "best_within_one_cell_of_hidden": near, "best_ncc": [round(rr.best_score, 4) for rr in res],
+            "stop_at_reachable_thresholds": sweep}
 
 
 def _stand_in_pairs(W_render, W_query, cam, depth, alpha, gen, step=8, noise=0.5, outliers=0.1):
@@ -498,22 +519,35 @@ def _apply_left(W, delta):
     return out
 
 
-def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best):
-    """FP16 / BF16 attribute storage on the driving workload: candidates/s and
-    deviation of every NCC score and winner from the FP32 path."""
+def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best, orc0=None):
+    """FP32 / FP16 / BF16 attribute storage on the driving workload:
+    candidates/s, deviation of every NCC score and winner from the FP32 path,
+    and each storage's error against the FP64 oracle of the FP32 map: all 64
+    NCC scores of query 0, and every pixel of the FP32 winner's view of query 0
+    (RGB max-abs over all pixels and over the pixels the oracle does not flag
+    as threshold-adjacent)."""
     import numpy as np
     import torch
+    import oracle
     from paper_2403_11367_gb300 import reloc as R
     out = {}
     V = GRID[0] * GRID[1] * GRID[2]
-    for name, prec in (("fp16", R.FP16), ("bf16", R.BF16)):
+    pix_ref = None
+    if orc0 is not None:
+        _, _, _, _, oscores, sub, poses, _ = orc0
+        wpose = poses[ref_best[0]][None]
+        pix_ref = oracle.render_views(sub, wpose, cam)
+    for name, prec in (("fp32", R.FP32), ("fp16", R.FP16), ("bf16", R.BF16)):
         ctx = R.Context(R.reloc_default_config())
         ctx.load_map(g, prec)
         dev_sc, agree = 0.0, 0
+        scores0 = None
         for k in range(len(queries)):
             res, sc = ctx.localize(queries[k], seed_poses[k], RADIUS, GRID, cam, stream=stream)
             dev_sc = max(dev_sc, float(np.abs(sc - ref_scores[k]).max()))
             agree += int(res.best_index == ref_best[k])
+            if k == 0:
+                scores0 = sc
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -524,9 +558,29 @@ def run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_
         torch.cuda.synchronize()
         out[name] = {"candidates_per_s": 8 * V / (e0.elapsed_time(e1) / 1e3), "max_ncc_dev_vs_fp32": dev_sc,
                      "winner_agreement_vs_fp32": agree / len(queries),
-                     "map_bytes_per_gaussian": 12 + 2 * (8 + 3 * 16)}
+                     "map_bytes_per_gaussian": 12 + (4 if prec == R.FP32 else 2) * (8 + 3 * 16)}
+        if pix_ref is not None:
+            runs, _, _ = ctx.select_block(seeds_xy(seed_poses[0])[0], seeds_xy(seed_poses[0])[1], RADIUS)
+            rgb = torch.empty((1, 3, cam.height, cam.width), device=dev)
+            ctx.render(runs, wpose, cam, rgb=rgb, stream=stream)
+            torch.cuda.synchronize()
+            e = np.abs(rgb.cpu().numpy().astype(np.float64) - pix_ref["rgb"]).max(axis=1)
+            mask = pix_ref["flags"] == 0
+            out[name]["vs_fp64_oracle"] = {
+                "ncc_max_abs_err_64_views": float(np.abs(scores0 - oscores).max()),
+                "winner_equal": bool(int(np.argmax(scores0)) == int(oracle.argmax(oscores))),
+                "rgb_max_abs_err_unflagged": float(e[mask].max(initial=0)),
+                "rgb_max_abs_err_all": float(e.max()), "flagged_fraction": float(1 - mask.mean()),
+                "view": "query 0, the FP32 winner's pose, 1408x376"}
         ctx.close()
     return out
+
+
+def seeds_xy(pose):
+    """Camera centre (x, y) of a world-to-camera pose."""
+    import numpy as np
+    c = -np.asarray(pose)[:3, :3].T @ np.asarray(pose)[:3, 3]
+    return float(c[0]), float(c[1])
 
 
 def rank_queries(rank: int = 0):
@@ -565,9 +619,11 @@ def job_throughput(world: int, units_per_rank: float, slowest_s: float) -> float
 
 # ---------------------------------------------------------------- oracle ----
 
-def oracle_sample(g, cam, hidden, seeds, n_cand: int, query_index: int = 0, with_counts=True):
-    """Oracle (FP64, OpenMP over views) on n_cand candidates of one query:
-    block select, render, NCC.  Returns (seconds, threads, counts)."""
+def oracle_sample(g, cam, hidden, seeds, n_cand: int, query_index: int = 0, images=False):
+    """Oracle (FP64, OpenMP over views) on the first n_cand grid candidates of
+    one query: block select, render, NCC.  Returns (seconds of the render and
+    NCC, threads, per-view counts (n_vis, n_inst, n_eval), seconds of the block
+    selection and query render, scores, the subset, the poses, the query)."""
     import numpy as np
 
     import oracle
@@ -582,10 +638,10 @@ def oracle_sample(g, cam, hidden, seeds, n_cand: int, query_index: int = 0, with
                                                                                     cam.width)
     t1 = time.perf_counter()
     poses = oracle.grid_poses(seed_pose, *GRID)[:n_cand]
-    out = oracle.render_views(sub, poses, cam, query=q, images=False, flags=False)
+    out = oracle.render_views(sub, poses, cam, query=q, images=images, flags=images)
     oracle.argmax(out["scores"])
     t2 = time.perf_counter()
-    return t2 - t1, oracle.max_threads(), out["counts"], t1 - t0, np.asarray(out["scores"])
+    return t2 - t1, oracle.max_threads(), out["counts"], t1 - t0, np.asarray(out["scores"]), sub, poses, q
 
 
 def run_reference(args):
@@ -715,8 +771,13 @@ def run_ours(args):
         res, sc = ctx.localize(queries[k], seed_poses[k], RADIUS, GRID, cam, stream=stream)
         ref_scores.append(sc)
         ref_best.append(res.best_index)
-    precision = run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best) \
-        if not args.no_batch else None
+
+    # the oracle on exactly the timed views: all 64 candidates of each query
+    # (the algorithmic counts of the roofline); query 0's render is also the
+    # CPU baseline sample
+    orc = [oracle_sample(g, cam, hidden, seeds, V, k) for k in range(N_QUERIES)] if rank == 0 else None
+    precision = run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best,
+                                  orc[0] if orc else None) if not args.no_batch else None
     batch = run_batch_leg(ctx, cam, dev, stream) if not args.no_batch else None
     learned = run_learned_leg(ctx, cam, dev, stream) if not args.no_batch else None
     random_search = run_random_leg(ctx, cam, dev, stream) if not args.no_batch else None
@@ -731,11 +792,14 @@ def run_ours(args):
 
     clocks = clk.summary()
     blend_ms = stage_ms["blend"] / max(1, stage_calls["blend"])
-    # algorithmic work of the blend: included (pixel, Gaussian) pairs, counted
-    # exactly by the oracle for the same views (cpu_baseline leg below)
-    cpu_s, cores, ocounts, _, _ = oracle_sample(g, cam, hidden, seeds, 16, 0)
-    n_eval_per_view = float(ocounts[:, 2].mean())
-    flops = n_eval_per_view * V * FLOPS_PER_EVAL
+    # algorithmic work of the blend over the timed steps: evaluated (pixel,
+    # Gaussian) pairs of every view, counted exactly by the oracle for the
+    # views each step rendered (step k: query k mod 4, all 64 candidates)
+    cpu_s, cores = orc[0][0], orc[0][1]
+    n_eval_q = [float(o[2][:, 2].sum()) for o in orc]
+    n_eval_steps = sum(n_eval_q[k % N_QUERIES] for k in range(args.steps))
+    n_eval_per_view = n_eval_steps / (args.steps * V)
+    flops = n_eval_steps * FLOPS_PER_EVAL / args.steps
     peak = max(peaks["fp32_scalar_tflops"], peaks["fp32_packed_tflops"])
     achieved = flops / (blend_ms / 1e3) / 1e12
     per_stage = {k: v / max(1, stage_calls[k]) for k, v in stage_ms.items()}
@@ -755,14 +819,19 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_blend", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": BLEND_DRAM_BYTES_PER_LAUNCH,
-                     "traffic_gbs": BLEND_DRAM_BYTES_PER_LAUNCH / (blend_ms / 1e3) / 1e9,
+                     "traffic_gbs": (BLEND_DRAM_BYTES_PER_LAUNCH / (blend_ms / 1e3) / 1e9
+                                     if BLEND_DRAM_BYTES_PER_LAUNCH else None),
                      "peak_source": "measured on this GPU before the timed region: register-resident "
                                     "FP32 FMA microbenchmark (reloc_measure_peaks), the larger of scalar "
                                     f"{peaks['fp32_scalar_tflops']:.1f} and packed f32x2 "
                                     f"{peaks['fp32_packed_tflops']:.1f} TFLOP/s",
-                     "work": f"{n_eval_per_view:.4g} included pixel-Gaussian pairs/view x {V} views x "
-                             f"{FLOPS_PER_EVAL} flop (oracle count)",
-                     "launch_ms": blend_ms},
+                     "work": f"{n_eval_per_view:.6g} evaluated pixel-Gaussian pairs/view (oracle count over the "
+                             f"timed steps' views: queries {N_QUERIES} x {V} candidates, step k = query k mod "
+                             f"{N_QUERIES}) x {V} views x {FLOPS_PER_EVAL} flop",
+                     "n_eval_per_query": n_eval_q, "flop_per_launch": flops,
+                     "launch_ms": blend_ms,
+                     "recompute": "achieved = flop_per_launch / (launch_ms / 1e3) / 1e12; launch_ms = "
+                                  "stage_ms.blend (query statistics + the scoring blend, mean over the timed steps)"},
         "stage_ms": per_stage,
         "stage_roofline": stage_rooflines(per_stage, S_sub, V, counts.n_visible, counts.n_instances,
                                           n_eval_per_view, peak, peaks["ex2_gops"], _peaks().get("hbm_gbs")),
@@ -774,8 +843,8 @@ def run_ours(args):
         "pose_ascent": ascent,
         "map_training": train,
         "precision": precision,
-        "cpu_baseline": {"value": 16 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "16 of the 64 candidates of query 0 (FP64 render + NCC)"},
+        "cpu_baseline": {"value": V / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the {V} candidates of query 0 (FP64 render + NCC)"},
         "clocks": clocks,
         "peaks": {"hbm_gbs": _peaks().get("hbm_gbs"), "bf16_tflops": _peaks().get("bf16_tflops"), **peaks},
     }

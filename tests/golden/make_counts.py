@@ -4,8 +4,11 @@ seeded workloads, per candidate view (FP64 projection and compositing):
   n_vis   Gaussians in front of the near plane whose 3-sigma rectangle meets
           the image (Sec. III-A projection, the tile binning's input)
   n_inst  (tile, Gaussian) instances of 16x16 tiles (the rectangle's tiles)
-  n_eval  included (pixel, Gaussian) pairs: power >= -4.5, alpha >= 1/255,
-          before the pixel's transmittance stop (Eq. 3 compositing)
+  n_eval  evaluated (pixel, Gaussian) pairs: the pixel centre inside the
+          3-sigma ellipse (power >= -4.5), up to and including the Gaussian
+          at which the pixel's transmittance stops (Eq. 3 compositing); pairs
+          then skipped for alpha < 1/255 are counted too, since their alpha
+          had to be computed
 
 Workloads: the tiny scene (10k Gaussians, 352x94, 16 candidates) and the
 driving street's first query (2M-Gaussian map, 40 m block selection around
