@@ -239,6 +239,71 @@ def run_learned_leg(ctx, cam, dev, stream, n_queries=256):
     return out
 
 
+# the proposal network's layers: (C_in, C_out, H_out, W_out) of the five 3x3
+# stride-2 convolutions, then the two fully connected layers (in, out)
+PROPOSAL_CONVS = [(2, 32, 24, 88), (32, 64, 12, 44), (64, 64, 6, 22), (64, 128, 3, 11), (128, 128, 2, 6)]
+PROPOSAL_FCS = [(1536, 1024), (1024, 64)]
+
+
+def proposal_train_flop_per_sample():
+    """Algorithmic FLOPs of one training sample's contractions: forward, the
+    weight gradient (the same products) and the input gradient (all layers but
+    the first), 2 per multiply-add, without the GEMMs' K padding."""
+    fwd = [2 * ho * wo * co * 9 * ci for ci, co, ho, wo in PROPOSAL_CONVS] + [2 * i * o for i, o in PROPOSAL_FCS]
+    return 2 * sum(fwd) + sum(fwd[1:])
+
+
+def run_gemm_leg(ctx, dev, stream, batch=256, steps=10):
+    """The tensor-core GEMM (tcgen05, TMA-fed, BF16 in, FP32 accumulate):
+    proposal training throughput (samples/s and the contraction TFLOP/s of the
+    steps, against the sustained BF16 peak), and single launches timed alone on
+    the network's largest GEMM at a large batch and on a square GEMM (TFLOP/s
+    against the burst BF16 peak)."""
+    import torch
+    from paper_2403_11367_gb300 import reloc as R
+    pk = _peaks()
+    out = {}
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.randn((batch, R.PROPOSAL_H, R.PROPOSAL_W, 2), generator=gen).to(torch.bfloat16).to(dev).contiguous()
+    y = torch.randint(0, R.PROPOSAL_CLASSES, (batch,), generator=gen, dtype=torch.int32).to(dev)
+    ctx.proposal_init(3)
+    for _ in range(3):
+        ctx.proposal_train_step(x, y, 1e-4, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.proposal_train_step(x, y, 1e-4, stream=stream)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    fl = proposal_train_flop_per_sample() * batch
+    out["proposal_training"] = {"batch": batch, "ms_per_step": dt * 1e3, "samples_per_s": batch / dt,
+                                "gemm_tflops": fl / dt / 1e12, "flop_per_step": fl,
+                                "peak_tflops": pk.get("bf16_tflops_sustained"),
+                                "frac": fl / dt / 1e12 / pk["bf16_tflops_sustained"] if pk.get("bf16_tflops_sustained")
+                                else None,
+                                "note": "host-synchronised steps (loss read back), many small launches"}
+    for name, (M, N, K) in (("fc1_batch8192", (8192, 1024, 1536)), ("square8192", (8192, 8192, 8192))):
+        A = torch.randn((M, K), generator=gen).to(torch.bfloat16).to(dev)
+        B = torch.randn((N, K), generator=gen).to(torch.bfloat16).to(dev)
+        C = torch.empty((M, N), device=dev)
+        for _ in range(3):
+            ctx.gemm_bf16(A, B, C, stream=stream)
+        ms = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.gemm_bf16(A, B, C, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = min(ms) / 1e3
+        tf = 2.0 * M * N * K / t / 1e12
+        out[name] = {"M": M, "N": N, "K": K, "ms": t * 1e3, "tflops": tf, "peak_tflops": pk.get("bf16_tflops"),
+                     "frac": tf / pk["bf16_tflops"] if pk.get("bf16_tflops") else None}
+        del A, B, C
+    return out
+
+
 PAPER_GRID = (15, 15, 36, 2.0, 10.0)   # 2 m x 10 deg over (-15, 15) m and a full turn: 8100 cells
 SEARCH_FRACTION, SEARCH_BATCH, SEARCH_STOP = 0.2, 64, 0.8
 
@@ -784,6 +849,7 @@ def run_ours(args):
     refine = run_refine_leg(ctx, cam, dev, stream) if not args.no_batch else None
     ascent = run_ascent_leg(cam, dev, stream) if not args.no_batch else None
     train = run_train_leg(cam, dev, stream) if not args.no_batch else None
+    gemm = run_gemm_leg(ctx, dev, stream) if not args.no_batch else None
 
     if rank != 0:
         if dist is not None:
@@ -833,8 +899,14 @@ def run_ours(args):
                      "recompute": "achieved = flop_per_launch / (launch_ms / 1e3) / 1e12; launch_ms = "
                                   "stage_ms.blend (query statistics + the scoring blend, mean over the timed steps)"},
         "stage_ms": per_stage,
-        "stage_roofline": stage_rooflines(per_stage, S_sub, V, counts.n_visible, counts.n_instances,
-                                          n_eval_per_view, peak, peaks["ex2_gops"], _peaks().get("hbm_gbs")),
+        "stage_roofline": {**stage_rooflines(per_stage, S_sub, V, counts.n_visible, counts.n_instances,
+                                             n_eval_per_view, peak, peaks["ex2_gops"], _peaks().get("hbm_gbs")),
+                           **({"k_gemm_bf16": {"bound": "tensor", "unit": "TFLOP/s",
+                                               "achieved_tflops": gemm["square8192"]["tflops"],
+                                               "peak_tflops": gemm["square8192"]["peak_tflops"],
+                                               "frac": gemm["square8192"]["frac"],
+                                               "work": "8192^3 BF16 GEMM, 2 M N K flop, one launch timed alone "
+                                                       "(burst peak)"}} if gemm else {})},
         "counts": {"n_gauss": counts.n_gauss, "n_visible": counts.n_visible, "n_instances": counts.n_instances},
         "batch": batch,
         "learned": learned,
@@ -842,6 +914,7 @@ def run_ours(args):
         "refine": refine,
         "pose_ascent": ascent,
         "map_training": train,
+        "tensor_gemm": gemm,
         "precision": precision,
         "cpu_baseline": {"value": V / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"the {V} candidates of query 0 (FP64 render + NCC)"},

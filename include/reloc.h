@@ -554,6 +554,25 @@ reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, int32_t *rec
                                 uint32_t *inst_tiles_dev, uint32_t *inst_gauss_dev,
                                 int64_t *inst_count_host, int32_t *ranges_dev, void *stream);
 
+/* Fault injection for failure-detection tests.  The paper has no
+ * counterpart: it lets a test make the library's failure paths run without
+ * faulting the GPU.  Process-wide; count = 0 clears a kind.
+ *   RELOC_FAULT_GEMM_WAIT  the next `count` tensor-core GEMM launches (the
+ *                          proposal's and reloc_gemm_bf16's) have their MMA
+ *                          lanes wait on a barrier that nothing completes:
+ *                          each CTA gives up after the wait limit (about a
+ *                          second), issues no MMA, waits for its own copies
+ *                          in flight, frees its tensor memory and records the
+ *                          failure; the call returns RELOC_ETIMEOUT and the
+ *                          context stays usable.
+ *   RELOC_FAULT_ALLOC      the next `count` device allocations fail; the call
+ *                          that needed them returns RELOC_ENOMEM and the
+ *                          context stays usable.
+ * Errors: EINVAL (unknown kind, count < 0). */
+#define RELOC_FAULT_GEMM_WAIT 1
+#define RELOC_FAULT_ALLOC 2
+reloc_status reloc_inject_faults(int kind, int count);
+
 /* Measured arithmetic throughput of `device`, the denominators of the
  * projection's and the blend's rooflines.  The paper has no counterpart: it
  * is a measurement utility.  Register-resident microbenchmarks (independent

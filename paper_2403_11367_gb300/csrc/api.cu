@@ -8,6 +8,7 @@
 // check workspace capacity).  If a view produced more tile instances than
 // the workspace holds, the call grows the workspace to the size the device
 // reported and re-runs the call.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,17 @@
 #include "reloc.h"
 
 using namespace reloc;
+
+// Pending injected faults (reloc_inject_faults; tests only), process-wide.
+static std::atomic<int> g_faults[FAULT_KINDS];
+
+bool reloc::take_fault(int kind)
+{
+    int n = g_faults[kind].load();
+    while (n > 0)
+        if (g_faults[kind].compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
 
 namespace {
 
@@ -58,6 +70,7 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
+        if (take_fault(FAULT_ALLOC)) return fail(RELOC_ENOMEM, "device allocation failed (injected)");
         size_t want = n < 256 ? 256 : n;
         cudaError_t e = cudaMalloc(&p, want);
         if (e != cudaSuccess) {
@@ -1703,6 +1716,14 @@ extern "C" reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, i
     if (inst_count_host)
         for (int v = 0; v < ctx->last_V; ++v) inst_count_host[v] = ctx->last_ninst[v];
     CK(cudaStreamSynchronize(st));
+    return RELOC_OK;
+}
+
+extern "C" reloc_status reloc_inject_faults(int kind, int count)
+{
+    if (count < 0 || (kind != RELOC_FAULT_GEMM_WAIT && kind != RELOC_FAULT_ALLOC))
+        return fail(RELOC_EINVAL, "inject_faults: kind RELOC_FAULT_GEMM_WAIT or RELOC_FAULT_ALLOC, count >= 0");
+    g_faults[kind == RELOC_FAULT_GEMM_WAIT ? FAULT_GEMM_WAIT : FAULT_ALLOC].store(count);
     return RELOC_OK;
 }
 

@@ -7,32 +7,54 @@
 // contraction of the learned candidate proposal (convolutions via im2col and
 // the MLP, forward and backward).
 //
-// One CTA of 128 threads computes a 128 x BN tile (BN in {16, 32, ..., 128}).
-// Per K step of 64 the threads copy the A and B tiles into shared memory in
-// the canonical no-swizzle K-major layout (8-row x 16-byte core matrices;
-// core matrices adjacent in K are LBO bytes apart, adjacent in M/N 128 bytes
-// apart), one elected thread issues four tcgen05.mma (K = 16 each) and commits
-// them to an mbarrier, and every thread waits on it before the tiles are
-// overwritten.  The epilogue reads the accumulator with tcgen05.ld (each warp
-// its 32 TMEM lanes) and applies bias and ReLU.  With split_k > 1, CTA z
-// covers the K range [z*Ks, (z+1)*Ks) and writes FP32 partials
-// C[z][M][N], summed later in a fixed order.
+// One CTA of 128 threads computes a 128 x BN tile (BN in {16, 32, ..., 256}),
+// warp-specialised over a ring of GEMM_STAGES shared-memory stages:
+//   - one lane of warp 0 loads the A (128 x 64) and B (BN x 64) tiles of each
+//     K step with TMA (cp.async.bulk.tensor, one 16-byte-wide box per 8-wide
+//     K chunk, so the tiles land in the canonical no-swizzle K-major layout:
+//     8-row x 16-byte core matrices, K-adjacent ones LBO bytes apart, M/N-
+//     adjacent ones 128 bytes apart) and signals the stage's "full" mbarrier
+//     through the copies' transaction count;
+//   - one lane of warp 1 waits for a full stage, issues its four
+//     tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to
+//     the stage's "empty" mbarrier, which releases the stage to the loader
+//     once the MMAs have read it; after the last K step it commits to a
+//     "done" mbarrier;
+//   - all four warps wait for "done" and read the accumulator with
+//     tcgen05.ld (each warp its 32 TMEM lanes), applying bias and ReLU.
+// So the loads of the next stages are in flight while the tensor cores work
+// on the current one.  With split_k > 1, CTA z covers the K range
+// [z*Ks, (z+1)*Ks) and writes FP32 partials C[z][M][N], summed later in a
+// fixed order.
 //
-// Every mbarrier wait is bounded: past the limit the CTA records an error in
-// *status, stops issuing MMAs, and still frees its tensor memory.
+// Every mbarrier wait is bounded (GEMM_WAIT_NS of the global timer): past it
+// the CTA records an error in *status and stops issuing; the loader then
+// waits (bounded) for its own copies in flight, the MMA lane commits "done"
+// (which tracks every MMA it issued) and all threads wait for it (bounded)
+// before the tensor memory is freed, so nothing the CTA started still writes
+// shared or tensor memory when it exits.
 #include "internal.cuh"
+
+#include <cuda.h>
 
 namespace reloc {
 
 constexpr int GEMM_THREADS = 128;
 constexpr int GEMM_BM = 128;
 constexpr int GEMM_BK = 64;
-constexpr int GEMM_BN_MAX = 128;
-constexpr unsigned GEMM_WAIT_LIMIT = 1u << 22;   // try_wait polls before giving up
+constexpr int GEMM_STAGES = 4;
+constexpr unsigned long long GEMM_WAIT_NS = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major (tcgen05 format:
@@ -55,9 +77,11 @@ __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Wait until the phase of the given parity has completed, or GEMM_WAIT_NS.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
-    for (unsigned it = 0; it < GEMM_WAIT_LIMIT; ++it) {
+    const unsigned long long deadline = global_ns() + GEMM_WAIT_NS;
+    for (;;) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -66,30 +90,56 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
                      : "r"(mbar), "r"(parity)
                      : "memory");
         if (done) return true;
+        if (global_ns() > deadline) return false;
     }
-    return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 2D TMA load of one box at (x, y) into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar)
+                 : "memory");
 }
 
 struct GemmArgs {
-    const __nv_bfloat16 *A, *B;
     const float *bias;          // [N] or null
     float *Cf;                  // FP32 output (or split-K partials) or null
     __nv_bfloat16 *Cb;          // BF16 output or null
     int M, N, K;                // K multiple of 64
-    int lda, ldb, ldc;          // row strides (elements)
+    int ldc;                    // row stride of C (elements)
     int relu;
     int split_k;                // >= 1; > 1 writes partials Cf[z][M][ldc]
+    int inject;                 // test only: the MMA lane waits on a barrier nothing arrives at
     int *status;                // error flag (1: an mbarrier wait gave up)
 };
 
 template <int BN>
-__global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(GemmArgs g)
+struct GemmSmem {
+    static constexpr uint32_t A_BYTES = GEMM_BM * GEMM_BK * 2;
+    static constexpr uint32_t B_BYTES = BN * GEMM_BK * 2;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr size_t TOTAL = (size_t)GEMM_STAGES * STAGE + 1024;   // + alignment slack
+};
+
+template <int BN>
+__global__ void __launch_bounds__(GEMM_THREADS)
+k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    // A tile: 8 K-chunks x (128/8) row blocks x 128 B; B tile: 8 x (BN/8) x 128 B
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + GEMM_BM * GEMM_BK * 2;
-    __shared__ __align__(8) uint64_t mbar;
+    using SM = GemmSmem<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar_full[GEMM_STAGES], bar_empty[GEMM_STAGES], bar_done, bar_never;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
@@ -97,9 +147,10 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(GemmArgs g)
     const int m0 = blockIdx.x * GEMM_BM, n0 = blockIdx.y * BN;
     const int kz = blockIdx.z;
     const int k_per = g.K / g.split_k;                  // multiple of 64 by construction
-    const int kbeg = kz * k_per, kend = kbeg + k_per;
+    const int kbeg = kz * k_per;
+    const int n_k = k_per / GEMM_BK;
     constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;   // power of two >= 32
-    constexpr uint32_t LBO_A = (GEMM_BM / 8) * 128, LBO_B = (BN / 8) * 128, SBO = 128;
+    constexpr uint32_t LBO_A = GEMM_BM * 16, LBO_B = BN * 16, SBO = 128;
     constexpr uint32_t IDESC = instr_desc_bf16(GEMM_BM, BN);
 
     if (warp == 0) {
@@ -108,69 +159,105 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(GemmArgs g)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
+    if (tid == 32) {
         abort_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        for (int s = 0; s < GEMM_STAGES; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        mbar_init(smem_u32(&bar_never), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_s;
-    const uint32_t aA = smem_u32(sA), aB = smem_u32(sB), mb = smem_u32(&mbar);
+    const uint32_t sbase = smem_u32(smem);
 
-    uint32_t phase = 0;
-    bool any = false;
-    for (int k0 = kbeg; k0 < kend; k0 += GEMM_BK) {
-        // ---- stage A (128 x 64) and B (BN x 64) as 16-byte core-matrix rows
-        for (int c = tid; c < GEMM_BM * (GEMM_BK / 8); c += GEMM_THREADS) {
-            const int r = c / (GEMM_BK / 8), kc = c % (GEMM_BK / 8);
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m0 + r < g.M) v = *reinterpret_cast<const uint4 *>(g.A + (int64_t)(m0 + r) * g.lda + k0 + kc * 8);
-            *reinterpret_cast<uint4 *>(sA + kc * LBO_A + (r >> 3) * SBO + (r & 7) * 16) = v;
+    if (tid == 0) {
+        // ---- loader: K step it into stage it % GEMM_STAGES ------------------
+        int issued = 0;
+        for (int it = 0; it < n_k; ++it) {
+            const int s = it % GEMM_STAGES;
+            const uint32_t ph = (uint32_t)(it / GEMM_STAGES) & 1u;
+            // the stage is free once the MMAs of K step it - GEMM_STAGES have read it
+            if (it >= GEMM_STAGES && !mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1u)) {
+                abort_s = 1;
+                if (g.status) atomicExch(g.status, 1);
+                break;
+            }
+            if (abort_s) break;
+            const uint32_t sa = sbase + s * SM::STAGE, sb = sa + SM::A_BYTES;
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, SM::STAGE);
+            const int k0 = kbeg + it * GEMM_BK;
+#pragma unroll
+            for (int kc = 0; kc < GEMM_BK / 8; ++kc) {
+                tma_load_2d(sa + kc * LBO_A, &tmA, k0 + kc * 8, m0, fb);
+                tma_load_2d(sb + kc * LBO_B, &tmB, k0 + kc * 8, n0, fb);
+            }
+            ++issued;
         }
-        for (int c = tid; c < BN * (GEMM_BK / 8); c += GEMM_THREADS) {
-            const int r = c / (GEMM_BK / 8), kc = c % (GEMM_BK / 8);
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (n0 + r < g.N) v = *reinterpret_cast<const uint4 *>(g.B + (int64_t)(n0 + r) * g.ldb + k0 + kc * 8);
-            *reinterpret_cast<uint4 *>(sB + kc * LBO_B + (r >> 3) * SBO + (r & 7) * 16) = v;
+        // copies still in flight land before the CTA may exit: the last one
+        // issued on each stage completes that stage's current phase
+        for (int it = issued - GEMM_STAGES < 0 ? 0 : issued - GEMM_STAGES; it < issued; ++it)
+            if (!mbar_wait(smem_u32(&bar_full[it % GEMM_STAGES]), (uint32_t)(it / GEMM_STAGES) & 1u) && g.status)
+                atomicExch(g.status, 1);
+    } else if (tid == 32) {
+        // ---- MMA issuer ----------------------------------------------------------
+        if (g.inject) {
+            // test only: a wait that nothing completes runs out
+            if (!mbar_wait(smem_u32(&bar_never), 0u)) {
+                abort_s = 1;
+                if (g.status) atomicExch(g.status, 1);
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (abort_s) break;
-        if (tid == 0) {
+        for (int it = 0; it < n_k && !abort_s; ++it) {
+            const int s = it % GEMM_STAGES;
+            const uint32_t ph = (uint32_t)(it / GEMM_STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&bar_full[s]), ph)) {
+                abort_s = 1;
+                if (g.status) atomicExch(g.status, 1);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = sbase + s * SM::STAGE, sb = sa + SM::A_BYTES;
 #pragma unroll
             for (int j = 0; j < GEMM_BK / 16; ++j) {
                 // K step j covers two core-matrix columns: advance by 2 * LBO
-                const uint64_t da = smem_desc(aA + 2 * j * LBO_A, LBO_A, SBO);
-                const uint64_t db = smem_desc(aB + 2 * j * LBO_B, LBO_B, SBO);
-                const uint32_t acc = (any || j > 0) ? 1u : 0u;
+                const uint64_t da = smem_desc(sa + 2 * j * LBO_A, LBO_A, SBO);
+                const uint64_t db = smem_desc(sb + 2 * j * LBO_B, LBO_B, SBO);
+                const uint32_t acc = (it > 0 || j > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\t"
                              "setp.ne.u32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
                              "l"(da), "l"(db), "r"(IDESC), "r"(acc)
                              : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&bar_empty[s]))
                          : "memory");
         }
-        any = true;
-        // every thread waits until the MMAs have consumed this stage
-        if (!mbar_wait(mb, phase)) {
-            abort_s = 1;
-            if (g.status) atomicExch(g.status, 1);
-        }
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (abort_s) break;
+        // "done" completes once every MMA this lane issued has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&bar_done))
+                     : "memory");
     }
+    __syncwarp();
+    __syncthreads();
+    if (!mbar_wait(smem_u32(&bar_done), 0u)) {
+        abort_s = 1;
+        if (g.status) atomicExch(g.status, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
 
     // ---- epilogue: TMEM -> registers -> global ------------------------------
     if (!abort_s) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const bool any = n_k > 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -220,45 +307,92 @@ __global__ void k_gemm_reduce(const float *__restrict__ part, int split, int M, 
     if (Cb) Cb[(int64_t)row * ldc + col] = __float2bfloat16_rn(v);
 }
 
-template <int BN>
-static cudaError_t gemm_t(const GemmArgs &g, cudaStream_t st)
+// ---- tensor maps ---------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
 {
-    // 96 KB of dynamic shared memory keeps at most two CTAs per SM, so their
-    // tensor memory (<= 2 x 128 columns) always fits the SM's 512 columns.
-    constexpr size_t SMEM = 96 * 1024;
-    static_assert((GEMM_BM + BN) * GEMM_BK * 2 <= SMEM, "tiles fit");
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Row-major BF16 matrix [rows][ld] (K = cols used), boxes of 8 K-elements
+// (16 bytes) by box_rows rows; rows beyond `rows` and K beyond `cols` read 0.
+static cudaError_t make_map(CUtensorMap *map, const __nv_bfloat16 *base, int rows, int cols, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dim, stride, box, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN>
+static cudaError_t gemm_t(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int lda, int ldb, const GemmArgs &g,
+                          cudaStream_t st)
+{
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, A, g.M, g.K, lda, GEMM_BM);
+    if (e == cudaSuccess) e = make_map(&mb, B, g.N, g.K, ldb, BN);
+    if (e != cudaSuccess) return e;
+    constexpr size_t SMEM = GemmSmem<BN>::TOTAL;
+    e = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)ceil_div(g.M, GEMM_BM), (unsigned)ceil_div(g.N, BN), (unsigned)g.split_k);
-    k_gemm_bf16<BN><<<grid, GEMM_THREADS, SMEM, st>>>(g);
+    k_gemm_bf16<BN><<<grid, GEMM_THREADS, SMEM, st>>>(ma, mb, g);
     return cudaGetLastError();
 }
 
 // C = A B^T (+ bias, ReLU).  Requirements: K % 64 == 0, K / split_k % 64 == 0,
 // lda, ldb multiples of 8 (16-byte rows), 16-byte aligned A and B.
-// split_k > 1 needs `partials` (split_k * M * ldc floats).
+// split_k > 1 needs `partials` (split_k * M * ldc floats).  inject != 0, or a
+// pending FAULT_GEMM_WAIT injection (tests only), makes the CTAs' MMA lanes
+// wait on a barrier nothing completes: every CTA gives up after the wait
+// limit, issues no MMA and sets *status.
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias, float *Cf,
                              __nv_bfloat16 *Cb, int M, int N, int K, int lda, int ldb, int ldc, int relu, int split_k,
-                             float *partials, int *status, cudaStream_t st)
+                             float *partials, int *status, cudaStream_t st, int inject)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (K % GEMM_BK || split_k < 1 || (K / split_k) % GEMM_BK || (lda % 8) || (ldb % 8) ||
         ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (split_k > 1 && !partials))
         return cudaErrorInvalidValue;
-    GemmArgs g{A, B, bias, Cf, Cb, M, N, K, lda, ldb, ldc, relu, split_k, status};
+    if (take_fault(FAULT_GEMM_WAIT)) inject = 1;
+    GemmArgs g{bias, Cf, Cb, M, N, K, ldc, relu, split_k, inject, status};
     if (split_k > 1) {
         g.Cf = partials;
         g.Cb = nullptr;
         g.bias = nullptr;
         g.relu = 0;
     }
-    const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    const int BN = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
     cudaError_t e;
     switch (BN) {
-    case 16: e = gemm_t<16>(g, st); break;
-    case 32: e = gemm_t<32>(g, st); break;
-    case 64: e = gemm_t<64>(g, st); break;
-    default: e = gemm_t<128>(g, st); break;
+    case 16: e = gemm_t<16>(A, B, lda, ldb, g, st); break;
+    case 32: e = gemm_t<32>(A, B, lda, ldb, g, st); break;
+    case 64: e = gemm_t<64>(A, B, lda, ldb, g, st); break;
+    case 128: e = gemm_t<128>(A, B, lda, ldb, g, st); break;
+    default: e = gemm_t<256>(A, B, lda, ldb, g, st); break;
     }
     if (e != cudaSuccess || split_k == 1) return e;
     const int64_t n = (int64_t)M * N;

@@ -252,7 +252,13 @@ cudaError_t proposal_make_input(const float *query, const float *seed_rgb, int H
                                 cudaStream_t st);
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias, float *Cf,
                              __nv_bfloat16 *Cb, int M, int N, int K, int lda, int ldb, int ldc, int relu, int split_k,
-                             float *partials, int *status, cudaStream_t st);
+                             float *partials, int *status, cudaStream_t st, int inject = 0);
+
+// Fault injection for tests (reloc_inject_faults): the number of upcoming
+// GEMM launches whose tensor-core waits are made to run out, and of upcoming
+// device allocations made to fail.  take_fault consumes one if any is set.
+enum { FAULT_GEMM_WAIT = 0, FAULT_ALLOC = 1, FAULT_KINDS = 2 };
+bool take_fault(int kind);
 cudaError_t launch_topk(const float *logits, int B, int C, int k, int32_t *idx, float *margin, cudaStream_t st);
 
 // Record msg as the calling thread's last error; returns st.

@@ -20,9 +20,6 @@
 
 namespace reloc {
 
-cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias, float *Cf,
-                             __nv_bfloat16 *Cb, int M, int N, int K, int lda, int ldb, int ldc, int relu, int split_k,
-                             float *partials, int *status, cudaStream_t st);
 cudaError_t launch_downsample_gray(const float *img, int H, int W, int f, int ch, __nv_bfloat16 *out, cudaStream_t st);
 cudaError_t launch_im2col(const __nv_bfloat16 *x, int B, int H, int W, int C, int Ho, int Wo, int Kp,
                           __nv_bfloat16 *col, cudaStream_t st);

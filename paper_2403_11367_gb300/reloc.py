@@ -159,6 +159,7 @@ SIGNATURES = {
                                    C.POINTER(TrainOptions), _dp, _vp]),
     "reloc_train_reset": (C.c_int, [_vp]),
     "reloc_read_map": (C.c_int, [_vp, _fp, _fp, _fp, _fp, _fp]),
+    "reloc_inject_faults": (C.c_int, [C.c_int, C.c_int]),
 }
 NOALLOC_MAX_VIEWS = 512
 PROPOSAL_H, PROPOSAL_W, PROPOSAL_CLASSES, PROPOSAL_PARAMS = 47, 176, 64, 1916960
@@ -251,6 +252,15 @@ def reloc_ncc_images_noalloc(images, query, scores_out, degenerate_out=None, str
                                         _ptr(query, _F32, shape=(3, H, W), name="query"),
                                         _ptr(scores_out, _F64, numel=V, name="scores_out"),
                                         _ptr(degenerate_out, _I32, numel=V, name="degenerate_out"), _stream(stream)))
+
+
+FAULT_GEMM_WAIT, FAULT_ALLOC = 1, 2
+
+
+def reloc_inject_faults(kind: int, count: int = 1):
+    """Test hook: make the next `count` GEMM launches' tensor-core waits run out
+    (FAULT_GEMM_WAIT) or the next `count` device allocations fail (FAULT_ALLOC)."""
+    _check(lib.reloc_inject_faults(kind, count))
 
 
 def reloc_measure_peaks(device: int = 0) -> dict:

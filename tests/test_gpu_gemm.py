@@ -28,7 +28,8 @@ def bf16(shape, seed):
 
 @pytest.mark.parametrize("M,N,K,split", [(128, 16, 64, 1), (1, 32, 64, 1), (100, 48, 128, 1), (300, 64, 320, 1),
                                          (257, 128, 1152, 1), (64, 200, 256, 1), (130, 1024, 1536, 1),
-                                         (32, 64, 8448 * 64, 128), (96, 320, 4096, 4)])
+                                         (32, 64, 8448 * 64, 128), (96, 320, 4096, 4), (1000, 250, 192, 1),
+                                         (256, 256, 512, 1), (129, 17, 64, 1), (385, 144, 640, 2)])
 def test_gemm_matches_fp64(ctx, M, N, K, split):
     A, a = bf16((M, K), 1 + M)
     B, b = bf16((N, K), 2 + N)
