@@ -169,3 +169,19 @@ def test_learned_localize_fallback_and_topk(R):
         assert np.array_equal(sb[scored], sa[scored])           # same renders, same scores
         assert b.best_score == np.max(sb[scored])
     ctx.set_proposal(False, 8, 0.0)
+
+
+def test_learned_winner_equals_oracle_full_sweep():
+    """Eight held-out driving queries: the GPU's plain sweep and the learned
+    top-k + fallback (shipped weights) pick the FP64 oracle's own full-sweep
+    winner (ties within the NCC tolerance excepted)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from proposal_oracle_check import learned_vs_oracle
+    r = learned_vs_oracle(8)
+    print(r)
+    for i in range(r["queries"]):
+        if r["oracle_top2_margin"][i] < 2e-6:
+            continue
+        assert r["gpu_sweep_winner"][i] == r["oracle_winner"][i], i
+        assert r["learned_winner"][i] == r["oracle_winner"][i], i
