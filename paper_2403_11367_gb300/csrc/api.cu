@@ -727,7 +727,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     float *alp_out = rp ? ctx->talp.as<float>() : (o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr);
     CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
                     o.score ? ctx->partials.as<double>() : nullptr, rgb_out, dep_out, alp_out,
-                    nullptr, 0, d_overflow, st));
+                    nullptr, 0, d_overflow, ctx->flags.as<int>() + 8, st));
     launches += 1;
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
     if (o.target) {
@@ -798,7 +798,8 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
                 CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp, nullptr,
                                 o.brgb ? o.brgb + (int64_t)sb.q0 * 3 * HW : nullptr,
                                 o.bdepth ? o.bdepth + (int64_t)sb.q0 * HW : nullptr,
-                                o.balpha ? o.balpha + (int64_t)sb.q0 * HW : nullptr, vsel, nq, d_overflow, st));
+                                o.balpha ? o.balpha + (int64_t)sb.q0 * HW : nullptr, vsel, nq, d_overflow,
+                                ctx->flags.as<int>() + 8, st));
                 launches += 1;
             }
         }

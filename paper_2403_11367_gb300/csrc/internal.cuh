@@ -168,10 +168,11 @@ cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *b
 // 64-pixel block; optional image export (slot = view) and NCC partials
 // [V][blend_units(cam)][3] = {S_r, S_rr, S_rq} per warp block.
 // view_sel != null: blend only the n_sel views view_sel[0..n_sel), image
-// slot k for view_sel[k].
+// slot k for view_sel[k].  queue: one device int, the launch's work counter
+// (zeroed on the stream before the launch).
 cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                          const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
-                         const int *view_sel, int n_sel, const int *overflow, cudaStream_t st);
+                         const int *view_sel, int n_sel, const int *overflow, int *queue, cudaStream_t st);
 
 // 64-pixel warp blocks of one view: the blend's unit of work and of NCC partials.
 inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w * cam.tile_h / 64); }

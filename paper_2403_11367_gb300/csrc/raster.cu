@@ -306,30 +306,21 @@ __device__ __forceinline__ float step_lt(float a, float b)
     asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
     return d;
 }
-// Register budget: 64 per thread (32 one-warp blocks per SM) for the scoring
-// launches; the export launches (DA) carry depth and alpha sums too and get
-// 72 (28 blocks per SM) rather than spill (same-box A/B: winner export
-// 0.233 -> 0.208 ms).
+// One 64-pixel warp block (unit `unit` of view v, its list range r): the
+// blend and the epilogue (image export to slot out_v, NCC partials).
 template <int TW, int TH, int RPL, bool DA>
-__global__ void __launch_bounds__(32, RPL == 1 ? (DA ? 28 : 32) : 24)
-k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
-        const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
-        float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel,
-        const int *__restrict__ overflow)
+__device__ __forceinline__ void blend_unit(const float4 *__restrict__ rec, const Layout &L,
+                                           const uint32_t *__restrict__ inst_gauss, const CamParams &cam,
+                                           double *__restrict__ partials, float *__restrict__ rgb,
+                                           float *__restrict__ depth, float *__restrict__ alpha, int v, int out_v,
+                                           int unit, int2 r, float4 (*s_rec)[32 * RPL])
 {
     using GM = BlockGeom<TW, TH>;
     constexpr int BW = GM::BW, BH = GM::BH, WPT = GM::WPT;
     constexpr int CH = 32 * RPL;             // records per warp step
-    // kept records compacted: (-qa, Gx, -2 qb, Gy) (-qc, -qc, P0, thr)
+    // kept records compacted in s_rec: (-qa, Gx, -2 qb, Gy) (-qc, -qc, P0, thr)
     // (r, r, g, g) (b, b, z, z)
-    __shared__ float4 s_rec[4][CH];
-
-    // one warp per block: (tile, warp block) units, so a warp that finishes
-    // early frees its slot instead of waiting for the tile's slowest warp
-    const int unit = blockIdx.x;
     const int tile = unit / WPT, warp = unit - tile * WPT;
-    const int v = view_sel ? view_sel[blockIdx.y] : (int)blockIdx.y;
-    const int out_v = blockIdx.y;
     const int tx = tile % cam.ntx, ty = tile / cam.ntx;
     const int lane = threadIdx.x;
     const int bx0p = tx * TW + (warp % GM::NBX) * BW, by0p = ty * TH + (warp / GM::NBX) * BH;
@@ -343,8 +334,6 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     const float DX = (float)(lane % BW) + 0.5f - 0.5f * BW;
     const float dy0 = (float)(2 * (lane / BW)) + 0.5f - 0.5f * BH;
     const f32x2 DY2 = pk(dy0, dy0 + 1.f);
-    int2 r = make_int2(0, 0);
-    if (!*overflow && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + tile];
     const uint32_t *list = inst_gauss + L.io_off[v];
     const float4 *vrec = rec + L.vd_off[v] * 3;
     constexpr float L2E = 1.4426950408889634f;
@@ -517,7 +506,7 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         }
         const double tr = cs_warp_total(sr), trr = cs_warp_total(srr), trq = cs_warp_total(srq);
         if (lane == 0) {
-            double *o = partials + ((int64_t)blockIdx.y * cam.n_tiles * WPT + unit) * 3;
+            double *o = partials + ((int64_t)out_v * cam.n_tiles * WPT + unit) * 3;
             o[0] = tr;
             o[1] = trr;
             o[2] = trq;
@@ -525,30 +514,116 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
     }
 }
 
+// Persistent K6: a grid of resident one-warp blocks (as many as fit on the
+// SMs) takes the launch's units -- (view, tile, 64-pixel block) of every view
+// of every query in the call -- from one queue in view-major order (an atomic
+// ticket per unit).  A warp holds its next ticket, the next unit's view and
+// list range while it blends the current one, so the dependent loads that
+// start a unit are off the critical path, and no block launch separates
+// units (a per-unit grid spent about a quarter of its warp slots idle).  Each
+// unit is processed whole by one warp and writes only its own outputs, so
+// the result does not depend on which warp takes which unit.
+// Register budget: 64 per thread (32 one-warp blocks per SM) for the scoring
+// launches; the export launches (DA) carry depth and alpha sums too and get
+// 72 (28 blocks per SM) rather than spill (same-box A/B: winner export
+// 0.233 -> 0.208 ms).
+template <int TW, int TH, int RPL, bool DA>
+__global__ void __launch_bounds__(32, RPL == 1 ? (DA ? 28 : 32) : 24)
+k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
+        const int2 *__restrict__ ranges, CamParams cam, double *__restrict__ partials, float *__restrict__ rgb,
+        float *__restrict__ depth, float *__restrict__ alpha, const int *__restrict__ view_sel, int n_views,
+        const int *__restrict__ overflow, int *__restrict__ queue)
+{
+    __shared__ float4 s_rec[4][32 * RPL];
+    const int upv = cam.n_tiles * BlockGeom<TW, TH>::WPT;      // units per view
+    const int64_t total = (int64_t)upv * n_views;
+    const bool ovf = *overflow != 0;
+    const int lane = threadIdx.x;
+    // view and list range of unit u (empty past the end or after an overflow)
+    auto locate = [&](int64_t u, int &v, int2 &r) {
+        v = -1;
+        r = make_int2(0, 0);
+        if (u < total) {
+            const int vi = (int)(u / upv), loc = (int)(u - (int64_t)vi * upv);
+            v = view_sel ? view_sel[vi] : vi;
+            if (!ovf && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + loc / BlockGeom<TW, TH>::WPT];
+        }
+    };
+    int64_t u = 0;
+    if (lane == 0) u = atomicAdd(queue, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    int v;
+    int2 r;
+    locate(u, v, r);
+    while (u < total) {
+        // the next unit: ticket, view and range in flight during this one
+        int64_t un = 0;
+        if (lane == 0) un = atomicAdd(queue, 1);
+        un = __shfl_sync(0xffffffffu, un, 0);
+        int vn;
+        int2 rn;
+        locate(un, vn, rn);
+        const int vi = (int)(u / upv);
+        blend_unit<TW, TH, RPL, DA>(rec, L, inst_gauss, cam, partials, rgb, depth, alpha, v < 0 ? 0 : v, vi,
+                                    (int)(u - (int64_t)vi * upv), v < 0 ? make_int2(0, 0) : r, s_rec);
+        __syncwarp();
+        u = un;
+        v = vn;
+        r = rn;
+    }
+}
+
+// resident one-warp blocks per SM of a blend kernel on the current device
+template <typename K>
+static int resident_blocks(K kernel)
+{
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, 0) != cudaSuccess)
+            return 0;
+        cached[dev] = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return cached[dev];
+}
+
 template <int TW, int TH, int RPL>
 static cudaError_t blend_t(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                            const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
-                           const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
+                           const int *view_sel, int n_sel, const int *overflow, int *queue, cudaStream_t st)
 {
-    dim3 grid(cam.n_tiles * (TW * TH / 64), view_sel ? n_sel : L.V);
-    if (depth || alpha)
-        k_blend<TW, TH, RPL, true><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth,
-                                                        alpha, view_sel, overflow);
-    else
-        k_blend<TW, TH, RPL, false><<<grid, 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth,
-                                                         alpha, view_sel, overflow);
+    const int nv = view_sel ? n_sel : L.V;
+    const int64_t units = (int64_t)cam.n_tiles * (TW * TH / 64) * nv;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (depth || alpha) {
+        const int g = resident_blocks(k_blend<TW, TH, RPL, true>);
+        if (g <= 0) return cudaErrorInvalidValue;
+        k_blend<TW, TH, RPL, true><<<(unsigned)min64(units, g), 32, 0, st>>>(rec, L, inst_gauss, ranges, cam, partials,
+                                                                             rgb, depth, alpha, view_sel, nv, overflow,
+                                                                             queue);
+    } else {
+        const int g = resident_blocks(k_blend<TW, TH, RPL, false>);
+        if (g <= 0) return cudaErrorInvalidValue;
+        k_blend<TW, TH, RPL, false><<<(unsigned)min64(units, g), 32, 0, st>>>(rec, L, inst_gauss, ranges, cam,
+                                                                              partials, rgb, depth, alpha, view_sel, nv,
+                                                                              overflow, queue);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                          const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
-                         const int *view_sel, int n_sel, const int *overflow, cudaStream_t st)
+                         const int *view_sel, int n_sel, const int *overflow, int *queue, cudaStream_t st)
 {
     if ((view_sel ? n_sel : L.V) <= 0) return cudaSuccess;
 #define RELOC_BLEND_CASE(W_, H_, R_)                                                                             \
     if (cam.tile_w == W_ && cam.tile_h == H_ && cam.blend_rpl == R_)                                            \
         return blend_t<W_, H_, R_>(rec, L, inst_gauss, ranges, cam, partials, rgb, depth, alpha, view_sel, n_sel, \
-                                   overflow, st);
+                                   overflow, queue, st);
     RELOC_BLEND_CASE(16, 16, 1)
     RELOC_BLEND_CASE(16, 16, 2)
     RELOC_BLEND_CASE(8, 8, 1)
