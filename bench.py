@@ -43,9 +43,9 @@ N_QUERIES = 4
 # particular kernel's instruction mix
 FLOPS_PER_EVAL = 22
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this
-# workload's 64-view k_blend<16,16,1,false> launch of query 0 on the current
-# kernel; None until taken (the roofline's "traffic" is then null)
-BLEND_DRAM_BYTES_PER_LAUNCH = None
+# workload's 64-view k_blend<16,16,1,false> launch of query 0 (715.90 MB +
+# 15.31 MB); to be re-taken whenever that kernel changes (None: not taken)
+BLEND_DRAM_BYTES_PER_LAUNCH = 731_210_000
 WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
             "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
 
@@ -185,8 +185,18 @@ def run_batch_leg(ctx, cam, dev, stream, n_queries=256):
     n_cand = sum(q[3][0] * q[3][1] * q[3][2] for q in qs)
     subs = [r.n_gauss for r in res]
     ctx.set_batch_options(use_graph=False, mem_budget=16 << 30)
+    # the same queries as separate reloc_localize calls, same stream
+    for q in qs[:4]:
+        ctx.localize(q[0], q[1], q[2], q[3], cam, stream=stream, want_scores=False)
+    e0.record(stream)
+    for q in qs:
+        ctx.localize(q[0], q[1], q[2], q[3], cam, stream=stream, want_scores=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_sep = e0.elapsed_time(e1)
     return {"queries": n_queries, "candidates": int(n_cand), "ms": ms,
             "candidates_per_s": n_cand / (ms / 1e3), "queries_per_s": n_queries / (ms / 1e3),
+            "separate_calls_ms": ms_sep, "speedup_vs_separate_calls": ms_sep / ms,
             "subset_min": int(min(subs)), "subset_max": int(max(subs)), "kernel_launches": c.kernel_launches,
             "cuda_graph": True, "tuned": {"tile": [tune.tile_w, tune.tile_h], "rpl": tune.blend_rpl,
                                           "configs_timed": tune.n_tried}}
@@ -926,6 +936,40 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_small_case(leg, dev, stream):
+    """Small cases for ncu captures of one kernel.  blend_small: three
+    16-candidate localize calls of the driving workload's query 0 (its
+    scoring blend is the second k_blend launch).  gemm_small: one 4096^3
+    tensor-core GEMM after one warm-up launch."""
+    import torch
+    from paper_2403_11367_gb300 import reloc as R
+    import scenegen as sg
+    if leg == "gemm_small":
+        ctx = R.Context()
+        gen = torch.Generator(device="cpu").manual_seed(3)
+        A = torch.randn((4096, 4096), generator=gen).to(torch.bfloat16).to(dev)
+        B = torch.randn((4096, 4096), generator=gen).to(torch.bfloat16).to(dev)
+        C = torch.empty((4096, 4096), device=dev)
+        for _ in range(2):
+            ctx.gemm_bf16(A, B, C, stream=stream)
+        torch.cuda.synchronize()
+        return {"gemm": [4096, 4096, 4096], "c00": float(C[0, 0])}
+    g, cam, hidden, seeds = make_workload(0)
+    ctx = R.Context(R.reloc_default_config())
+    ctx.load_map(g)
+    runs, _, _ = ctx.select_block(hidden[0][0], hidden[0][1], RADIUS)
+    img = torch.empty((1, 3, cam.height, cam.width), device=dev)
+    ctx.render(runs, sg.pose_from_xyz_yaw(*hidden[0])[None], cam, rgb=img, stream=stream)
+    q = (img[0] + torch.tensor(sg.image_noise(13, cam.height, cam.width), device=dev)).contiguous()
+    best = []
+    for _ in range(3):
+        res, _ = ctx.localize(q, sg.pose_from_xyz_yaw(*seeds[0]), RADIUS, (4, 2, 2, 0.5, 2.0), cam, stream=stream,
+                              want_scores=False)
+        best.append(res.best_index)
+    torch.cuda.synchronize()
+    return {"views": 16, "best": best}
+
+
 def run_leg(args):
     import torch
     from paper_2403_11367_gb300.build import build
@@ -937,6 +981,8 @@ def run_leg(args):
     stream = torch.cuda.current_stream(dev)
     if args.leg == "map_training":
         out = run_train_leg(cam, dev, stream, steps=args.steps, warmup=args.warmup)
+    elif args.leg in ("blend_small", "gemm_small"):
+        out = run_small_case(args.leg, dev, stream)
     else:
         out = run_ascent_leg(cam, dev, stream)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -950,8 +996,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batching, learned-proposal and precision legs")
-    ap.add_argument("--leg", choices=["map_training", "pose_ascent"],
-                    help="run one self-contained leg alone on cuda:0 and print its JSON object")
+    ap.add_argument("--leg", choices=["map_training", "pose_ascent", "blend_small", "gemm_small"],
+                    help="run one self-contained leg alone on cuda:0 and print its JSON object "
+                         "(blend_small, gemm_small: small cases for ncu captures)")
     args = ap.parse_args()
     if args.leg:
         run_leg(args)
