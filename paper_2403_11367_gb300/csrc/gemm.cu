@@ -10,11 +10,12 @@
 // One CTA of 128 threads computes a 128 x BN tile (BN in {16, 32, ..., 256}),
 // warp-specialised over a ring of GEMM_STAGES shared-memory stages:
 //   - one lane of warp 0 loads the A (128 x 64) and B (BN x 64) tiles of each
-//     K step with TMA (cp.async.bulk.tensor, one 16-byte-wide box per 8-wide
-//     K chunk, so the tiles land in the canonical no-swizzle K-major layout:
-//     8-row x 16-byte core matrices, K-adjacent ones LBO bytes apart, M/N-
-//     adjacent ones 128 bytes apart) and signals the stage's "full" mbarrier
-//     through the copies' transaction count;
+//     K step with TMA (cp.async.bulk.tensor, one box per operand: 64 BF16 =
+//     128 bytes of K by the tile's rows, 128-byte swizzle, so the tiles land
+//     in the canonical K-major SWIZZLE_128B layout: 128-byte rows whose 16-byte
+//     chunks are XOR-permuted by the row within each 8-row, 1024-byte group)
+//     and signals the stage's "full" mbarrier through the copies'
+//     transaction count;
 //   - one lane of warp 1 waits for a full stage, issues its four
 //     tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to
 //     the stage's "empty" mbarrier, which releases the stage to the loader
@@ -57,16 +58,22 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Shared-memory matrix descriptor, no swizzle, K-major (tcgen05 format:
-// start >> 4 in bits 0-13, leading byte offset >> 4 in 16-29, stride byte
-// offset >> 4 in 32-45, version 1 in 46-47, layout type 0 in 61-63).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile (tcgen05
+// format: start >> 4 in bits 0-13, leading byte offset >> 4 in 16-29 (unused
+// for swizzled K-major tiles whose K step fits the 128-byte row; 16), stride
+// byte offset >> 4 in 32-45 (1024: from one 8-row group to the next), the
+// fixed 0b001 in 46-48, base offset 0 (tiles start on 1024-byte
+// boundaries), layout type 2 = 128-byte swizzle in 61-63).  A K step of 16
+// BF16 inside the row advances the start by 32 bytes; the swizzle is applied
+// to the resulting addresses.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -150,7 +157,6 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int kbeg = kz * k_per;
     const int n_k = k_per / GEMM_BK;
     constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;   // power of two >= 32
-    constexpr uint32_t LBO_A = GEMM_BM * 16, LBO_B = BN * 16, SBO = 128;
     constexpr uint32_t IDESC = instr_desc_bf16(GEMM_BM, BN);
 
     if (warp == 0) {
@@ -192,11 +198,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint32_t fb = smem_u32(&bar_full[s]);
             mbar_expect_tx(fb, SM::STAGE);
             const int k0 = kbeg + it * GEMM_BK;
-#pragma unroll
-            for (int kc = 0; kc < GEMM_BK / 8; ++kc) {
-                tma_load_2d(sa + kc * LBO_A, &tmA, k0 + kc * 8, m0, fb);
-                tma_load_2d(sb + kc * LBO_B, &tmB, k0 + kc * 8, n0, fb);
-            }
+            tma_load_2d(sa, &tmA, k0, m0, fb);
+            tma_load_2d(sb, &tmB, k0, n0, fb);
             ++issued;
         }
         // copies still in flight land before the CTA may exit: the last one
@@ -225,9 +228,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint32_t sa = sbase + s * SM::STAGE, sb = sa + SM::A_BYTES;
 #pragma unroll
             for (int j = 0; j < GEMM_BK / 16; ++j) {
-                // K step j covers two core-matrix columns: advance by 2 * LBO
-                const uint64_t da = smem_desc(sa + 2 * j * LBO_A, LBO_A, SBO);
-                const uint64_t db = smem_desc(sb + 2 * j * LBO_B, LBO_B, SBO);
+                // K step j: 16 BF16 = 32 bytes further along the 128-byte rows
+                const uint64_t da = smem_desc_sw128(sa + 32 * j);
+                const uint64_t db = smem_desc_sw128(sb + 32 * j);
                 const uint32_t acc = (it > 0 || j > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\t"
                              "setp.ne.u32 p, %4, 0;\n\t"
@@ -331,18 +334,18 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// Row-major BF16 matrix [rows][ld] (K = cols used), boxes of 8 K-elements
-// (16 bytes) by box_rows rows; rows beyond `rows` and K beyond `cols` read 0.
+// Row-major BF16 matrix [rows][ld] (K = cols used), boxes of 64 K-elements
+// (128 bytes) by box_rows rows, 128-byte swizzle; rows beyond `rows` read 0.
 static cudaError_t make_map(CUtensorMap *map, const __nv_bfloat16 *base, int rows, int cols, int ld, int box_rows)
 {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     const cuuint32_t estride[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dim, stride, box, estride,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
