@@ -95,8 +95,13 @@ def lib():
                                           dp, dp, C.POINTER(C.c_int), dp, dp, dp, u8p, dp, i64p]
             L.orc_param_count.restype = C.c_int64
             L.orc_forward.argtypes = [dp, dp, C.c_int, dp]
+            L.orc_forward_ex.argtypes = [dp, dp, C.c_int, dp, C.c_int]
             L.orc_loss_grad.argtypes = [dp, dp, i32p, C.c_int, dp, dp]
             L.orc_loss_grad.restype = C.c_double
+            L.orc_loss_grad_ex.argtypes = [dp, dp, i32p, C.c_int, dp, dp, C.c_int]
+            L.orc_loss_grad_ex.restype = C.c_double
+            L.orc_bf16_round.argtypes = [C.c_double]
+            L.orc_bf16_round.restype = C.c_double
             L.orc_adam.argtypes = [dp, dp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                    C.c_int]
             L.orc_downsample_gray.argtypes = [fp, C.c_int, C.c_int, C.c_int, dp]
@@ -483,25 +488,32 @@ def cnn_param_count() -> int:
     return int(lib().orc_param_count())
 
 
-def cnn_forward(params, inputs) -> np.ndarray:
-    """logits [B][64] of inputs [B][47][176][2] (FP64)."""
+def bf16_round(x: float) -> float:
+    """Round to nearest even BF16 of the FP32 value of x (the oracle's rounding)."""
+    return float(lib().orc_bf16_round(float(x)))
+
+
+def cnn_forward(params, inputs, act_bf16=False) -> np.ndarray:
+    """logits [B][64] of inputs [B][47][176][2] (FP64); act_bf16: every stored
+    activation rounded to BF16 (the BF16 network's storage format)."""
     p = _c(params, np.float64)
     x = _c(inputs, np.float64)
     B = x.shape[0]
     out = np.zeros((B, 64))
-    lib().orc_forward(_p(p, C.c_double), _p(x, C.c_double), B, _p(out, C.c_double))
+    lib().orc_forward_ex(_p(p, C.c_double), _p(x, C.c_double), B, _p(out, C.c_double), 1 if act_bf16 else 0)
     return out
 
 
-def cnn_loss_grad(params, inputs, labels, want_input_grad=False):
-    """(mean softmax cross-entropy, gradient w.r.t. params [, w.r.t. inputs])."""
+def cnn_loss_grad(params, inputs, labels, want_input_grad=False, act_bf16=False):
+    """(mean softmax cross-entropy, gradient w.r.t. params [, w.r.t. inputs]);
+    act_bf16: activations stored in BF16, the chain rule at those values."""
     p = _c(params, np.float64)
     x = _c(inputs, np.float64)
     y = _c(labels, np.int32)
     g = np.zeros(p.size)
     gi = np.zeros(x.shape) if want_input_grad else None
-    loss = lib().orc_loss_grad(_p(p, C.c_double), _p(x, C.c_double), _p(y, C.c_int32), x.shape[0],
-                               _p(g, C.c_double), _p(gi, C.c_double))
+    loss = lib().orc_loss_grad_ex(_p(p, C.c_double), _p(x, C.c_double), _p(y, C.c_int32), x.shape[0],
+                                  _p(g, C.c_double), _p(gi, C.c_double), 1 if act_bf16 else 0)
     return (float(loss), g, gi) if want_input_grad else (float(loss), g)
 
 

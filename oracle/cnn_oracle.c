@@ -8,6 +8,12 @@
  *   backward by the chain rule; Adam (Kingma and Ba, 2015).
  * Flat parameter layout: per conv layer W then b; FC1 W[1024][1536], b;
  * FC2 W[64][1024], b.  Input [B][47][176][2].
+ *
+ * act_bf16 != 0: every stored activation (each convolution's and FC1's
+ * output after the ReLU) is rounded to BF16 (round to nearest even of the
+ * FP32 value), the storage format of the method's BF16 network; the
+ * backward pass is the chain rule at those stored values (the rounding
+ * passes gradients through unchanged), everything else stays FP64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -21,6 +27,21 @@ static const int CIN[NL] = {2, 32, 64, 64, 128}, COUT[NL] = {32, 64, 64, 128, 12
 #define F1I 1536
 #define F1O 1024
 #define F2O 64
+
+/* BF16 round to nearest even of the FP32 value of x (the standard bit
+ * construction: add 0x7FFF plus the lowest kept bit, truncate 16 bits). */
+double orc_bf16_round(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) != 0x7F800000u) {
+        u += 0x7FFFu + ((u >> 16) & 1u);
+        u &= 0xFFFF0000u;
+        memcpy(&f, &u, 4);
+    }
+    return (double)f;
+}
 
 typedef struct { int H, W, Ho, Wo; } dims;
 static void layer_dims(dims *d)
@@ -76,21 +97,29 @@ void orc_conv3x3s2(const double *x, int H, int W, int Ci, const double *w, const
 /* activations of one sample: a[0] = input, a[l+1] = conv l output, h1, logits */
 typedef struct { double *a[NL + 1]; double *h1, *z; } acts;
 
-static void fwd_one(const double *p, const double *in, acts *A)
+static void round_all(double *a, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) a[i] = orc_bf16_round(a[i]);
+}
+
+static void fwd_one(const double *p, const double *in, acts *A, int act_bf16)
 {
     dims d[NL];
     int64_t wo[7], bo[7];
     layer_dims(d);
     offsets(wo, bo);
     memcpy(A->a[0], in, sizeof(double) * IH * IW * 2);
-    for (int l = 0; l < NL; ++l)
+    for (int l = 0; l < NL; ++l) {
         conv_fwd(A->a[l], d[l].H, d[l].W, CIN[l], p + wo[l], p + bo[l], COUT[l], d[l].Ho, d[l].Wo, A->a[l + 1]);
+        if (act_bf16) round_all(A->a[l + 1], (int64_t)d[l].Ho * d[l].Wo * COUT[l]);
+    }
     const double *x5 = A->a[NL];
     for (int n = 0; n < F1O; ++n) {
         double s = p[bo[5] + n];
         for (int k = 0; k < F1I; ++k) s += p[wo[5] + (int64_t)n * F1I + k] * x5[k];
         A->h1[n] = s > 0 ? s : 0;
     }
+    if (act_bf16) round_all(A->h1, F1O);
     for (int n = 0; n < F2O; ++n) {
         double s = p[bo[6] + n];
         for (int k = 0; k < F1O; ++k) s += p[wo[6] + (int64_t)n * F1O + k] * A->h1[k];
@@ -112,20 +141,26 @@ static acts alloc_acts(void)
 static void free_acts(acts *A) { for (int l = 0; l <= NL; ++l) free(A->a[l]); free(A->h1); free(A->z); }
 
 /* logits [B][64] */
-void orc_forward(const double *p, const double *in, int B, double *logits)
+void orc_forward_ex(const double *p, const double *in, int B, double *logits, int act_bf16)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int b = 0; b < B; ++b) {
         acts A = alloc_acts();
-        fwd_one(p, in + (int64_t)b * IH * IW * 2, &A);
+        fwd_one(p, in + (int64_t)b * IH * IW * 2, &A, act_bf16);
         memcpy(logits + (int64_t)b * F2O, A.z, sizeof(double) * F2O);
         free_acts(&A);
     }
 }
 
+void orc_forward(const double *p, const double *in, int B, double *logits)
+{
+    orc_forward_ex(p, in, B, logits, 0);
+}
+
 /* Mean softmax cross-entropy over the batch and its gradient w.r.t. every
  * parameter (grad, flat layout) and, optionally, the input (grad_in). */
-double orc_loss_grad(const double *p, const double *in, const int32_t *labels, int B, double *grad, double *grad_in)
+double orc_loss_grad_ex(const double *p, const double *in, const int32_t *labels, int B, double *grad, double *grad_in,
+                        int act_bf16)
 {
     const int64_t np = orc_param_count();
     dims d[NL];
@@ -136,7 +171,7 @@ double orc_loss_grad(const double *p, const double *in, const int32_t *labels, i
     double loss = 0;
     for (int b = 0; b < B; ++b) {
         acts A = alloc_acts();
-        fwd_one(p, in + (int64_t)b * IH * IW * 2, &A);
+        fwd_one(p, in + (int64_t)b * IH * IW * 2, &A, act_bf16);
         /* softmax cross-entropy */
         double mx = A.z[0];
         for (int c = 1; c < F2O; ++c) if (A.z[c] > mx) mx = A.z[c];
@@ -200,6 +235,11 @@ double orc_loss_grad(const double *p, const double *in, const int32_t *labels, i
         free_acts(&A);
     }
     return loss;
+}
+
+double orc_loss_grad(const double *p, const double *in, const int32_t *labels, int B, double *grad, double *grad_in)
+{
+    return orc_loss_grad_ex(p, in, labels, B, grad, grad_in, 0);
 }
 
 /* One Adam step (t = step number, 1-based) on n parameters. */

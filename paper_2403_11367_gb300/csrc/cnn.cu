@@ -103,11 +103,12 @@ cudaError_t launch_col2im(const float *dcol, int B, int H, int W, int C, int Ho,
     return cudaGetLastError();
 }
 
-// out[c][r] = in[r][c] for r < R, c < Cc; out is [Cp][Rp] with zero padding
-// (Rp >= R, Cp >= Cc).  in: BF16 or FP32 (converted).
+// out[c][r] = in[r][c] for r < R, c < Cc; out is Cp rows of Rp values (zero
+// padding, Rp >= R, Cp >= Cc) with row stride ldo >= Rp.  in: BF16 or FP32
+// (converted).
 template <typename T>
 __global__ void k_transpose(const T *__restrict__ in, int R, int Cc, int ld_in, __nv_bfloat16 *__restrict__ out, int Rp,
-                            int Cp)
+                            int Cp, int ldo)
 {
     __shared__ float t[32][33];
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -120,15 +121,15 @@ __global__ void k_transpose(const T *__restrict__ in, int R, int Cc, int ld_in, 
     __syncthreads();
     for (int j = threadIdx.y; j < 32; j += 8) {
         const int c = c0 + j, r = r0 + threadIdx.x;
-        if (c < Cp && r < Rp) out[(int64_t)c * Rp + r] = __float2bfloat16_rn(t[threadIdx.x][j]);
+        if (c < Cp && r < Rp) out[(int64_t)c * ldo + r] = __float2bfloat16_rn(t[threadIdx.x][j]);
     }
 }
 
 cudaError_t launch_transpose_bf16(const __nv_bfloat16 *in, int R, int Cc, int ld_in, __nv_bfloat16 *out, int Rp, int Cp,
-                                  cudaStream_t st)
+                                  cudaStream_t st, int ldo)
 {
     dim3 grid((unsigned)ceil_div(Cp, 32), (unsigned)ceil_div(Rp, 32));
-    k_transpose<__nv_bfloat16><<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ld_in, out, Rp, Cp);
+    k_transpose<__nv_bfloat16><<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ld_in, out, Rp, Cp, ldo > 0 ? ldo : Rp);
     return cudaGetLastError();
 }
 
@@ -136,32 +137,51 @@ cudaError_t launch_transpose_f32(const float *in, int R, int Cc, int ld_in, __nv
                                  cudaStream_t st)
 {
     dim3 grid((unsigned)ceil_div(Cp, 32), (unsigned)ceil_div(Rp, 32));
-    k_transpose<float><<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ld_in, out, Rp, Cp);
+    k_transpose<float><<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ld_in, out, Rp, Cp, Rp);
     return cudaGetLastError();
 }
 
 // d (FP32) *= (y > 0), written as BF16 (the gradient through a ReLU).
-__global__ void k_relu_back(const float *__restrict__ d, const __nv_bfloat16 *__restrict__ y, int64_t n,
+// A backward signal carried as two BF16 terms: out [M][2N] holds hi =
+// bf16(x) in columns 0..N-1 and lo = bf16(x - hi) in N..2N-1, so hi + lo
+// keeps ~16 significant bits of x and the GEMMs that contract it (over 2N
+// columns, or 2M rows stacked) accumulate both in FP32.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// ReLU backward of d [M][N] at the stored activations y, split into hi | lo.
+__global__ void k_relu_back(const float *__restrict__ d, const __nv_bfloat16 *__restrict__ y, int64_t M, int N,
                             __nv_bfloat16 *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    out[i] = __float2bfloat16_rn((float)y[i] > 0.f ? d[i] : 0.f);
+    if (i >= M * N) return;
+    const int64_t r = i / N;
+    const int c = (int)(i - r * N);
+    __nv_bfloat16 hi, lo;
+    split_bf16((float)y[i] > 0.f ? d[i] : 0.f, hi, lo);
+    out[r * 2 * N + c] = hi;
+    out[r * 2 * N + N + c] = lo;
 }
 
-cudaError_t launch_relu_back(const float *d, const __nv_bfloat16 *y, int64_t n, __nv_bfloat16 *out, cudaStream_t st)
+cudaError_t launch_relu_back(const float *d, const __nv_bfloat16 *y, int64_t M, int N, __nv_bfloat16 *out,
+                             cudaStream_t st)
 {
-    k_relu_back<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d, y, n, out);
+    const int64_t n = M * N;
+    k_relu_back<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d, y, M, N, out);
     return cudaGetLastError();
 }
 
-// db[c] = sum_r d[r][c] (BF16 input), one block per column, fixed order.
+// db[c] = sum over the R rows of the split signal d [R][2 Cc] (hi + lo), FP32.
 __global__ void k_colsum(const __nv_bfloat16 *__restrict__ d, int R, int Cc, float *__restrict__ db)
 {
     __shared__ float s[256];
     const int c = blockIdx.x;
     float a = 0.f;
-    for (int r = threadIdx.x; r < R; r += 256) a += (float)d[(int64_t)r * Cc + c];
+    for (int r = threadIdx.x; r < R; r += 256)
+        a += (float)d[(int64_t)r * 2 * Cc + c] + (float)d[(int64_t)r * 2 * Cc + Cc + c];
     s[threadIdx.x] = a;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -177,8 +197,8 @@ cudaError_t launch_colsum(const __nv_bfloat16 *d, int R, int Cc, float *db, cuda
     return cudaGetLastError();
 }
 
-// Softmax cross-entropy over C classes, mean over the batch: loss_rows[b],
-// dlogits = (softmax - onehot) / B as FP32 and BF16.  One warp per row.
+// Softmax cross-entropy rows: loss_rows[b], dl = (softmax - onehot) / B in
+// FP32 and split into hi | lo BF16 terms (dlb [B][2C]).
 __global__ void k_softmax_ce(const float *__restrict__ logits, const int32_t *__restrict__ labels, int B, int C,
                              float *__restrict__ loss_rows, float *__restrict__ dl, __nv_bfloat16 *__restrict__ dlb)
 {
@@ -197,7 +217,7 @@ __global__ void k_softmax_ce(const float *__restrict__ logits, const int32_t *__
         const float p = expf(z[c] - mx) / se;
         const float g = (p - (c == y ? 1.f : 0.f)) / (float)B;
         dl[(int64_t)b * C + c] = g;
-        dlb[(int64_t)b * C + c] = __float2bfloat16_rn(g);
+        split_bf16(g, dlb[(int64_t)b * 2 * C + c], dlb[(int64_t)b * 2 * C + C + c]);
     }
     if (lane == 0) loss_rows[b] = logf(se) + mx - z[y];
 }

@@ -26,8 +26,9 @@ cudaError_t launch_im2col(const __nv_bfloat16 *x, int B, int H, int W, int C, in
 cudaError_t launch_col2im(const float *dcol, int B, int H, int W, int C, int Ho, int Wo, int Kp, __nv_bfloat16 *dx_bf,
                           float *dx_f, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const __nv_bfloat16 *in, int R, int Cc, int ld_in, __nv_bfloat16 *out, int Rp, int Cp,
-                                  cudaStream_t st);
-cudaError_t launch_relu_back(const float *d, const __nv_bfloat16 *y, int64_t n, __nv_bfloat16 *out, cudaStream_t st);
+                                  cudaStream_t st, int ldo = 0);
+cudaError_t launch_relu_back(const float *d, const __nv_bfloat16 *y, int64_t M, int N, __nv_bfloat16 *out,
+                             cudaStream_t st);
 cudaError_t launch_colsum(const __nv_bfloat16 *d, int R, int Cc, float *db, cudaStream_t st);
 cudaError_t launch_softmax_ce(const float *logits, const int32_t *labels, int B, int C, float *loss_rows, float *dl,
                               __nv_bfloat16 *dlb, cudaStream_t st);
@@ -241,12 +242,13 @@ static cudaError_t ensure_batch(ProposalNet *P, int B)
     if ((e = P->h1.ensure(2 * (size_t)B * FC1_OUT)) != cudaSuccess) return e;
     if ((e = P->logits.ensure(4 * (size_t)B * FC2_OUT)) != cudaSuccess) return e;
     if ((e = P->dl.ensure(4 * (size_t)B * FC2_OUT)) != cudaSuccess) return e;
-    if ((e = P->dlb.ensure(2 * (size_t)B * FC2_OUT)) != cudaSuccess) return e;
+    // backward signals are carried as hi | lo BF16 pairs: twice the columns
+    if ((e = P->dlb.ensure(2 * 2 * (size_t)B * FC2_OUT)) != cudaSuccess) return e;
     if ((e = P->loss_rows.ensure(4 * (size_t)B)) != cudaSuccess) return e;
-    if ((e = P->tA.ensure(2 * max_tr)) != cudaSuccess) return e;
-    if ((e = P->tB.ensure(2 * max_tr)) != cudaSuccess) return e;
+    if ((e = P->tA.ensure(2 * 2 * max_tr)) != cudaSuccess) return e;
+    if ((e = P->tB.ensure(2 * 2 * max_tr)) != cudaSuccess) return e;
     if ((e = P->dmid.ensure(4 * std::max(max_mid, (size_t)B * FC1_OUT))) != cudaSuccess) return e;
-    if ((e = P->dmid_bf.ensure(2 * std::max(max_mid, (size_t)B * FC1_OUT))) != cudaSuccess) return e;
+    if ((e = P->dmid_bf.ensure(2 * 2 * std::max(max_mid, (size_t)B * FC1_OUT))) != cudaSuccess) return e;
     if ((e = P->dcol.ensure(4 * max_col)) != cudaSuccess) return e;
     if ((e = P->part.ensure(4 * (size_t)32 * 1024 * 1024)) != cudaSuccess) return e;   // split-K partials
     P->cap_b = B;
@@ -292,15 +294,35 @@ static int split_for(int K, int cap)
     return 1;
 }
 
-// weight gradient gW[N][Kc] = dY^T X for dY [M][N] and X [M][Kc] (BF16), M % 64 == 0
+// Backward signals are carried as two BF16 terms, [M][2N] = hi | lo (x ~ hi +
+// lo to ~16 significant bits), so the only BF16 rounding of the backward
+// pass is that of the stored forward activations and weights.
+
+// weight gradient gW[N][Kc] = dY^T X for the split dY [M][2N] and X [M][Kc]
+// (BF16), M % 32 == 0: one GEMM over the 2M stacked rows, hi^T X + lo^T X
 static cudaError_t weight_grad(ProposalNet *P, const __nv_bfloat16 *dY, int M, int N, const __nv_bfloat16 *X, int Kc,
                                float *gW, cudaStream_t st)
 {
     __nv_bfloat16 *tA = P->tA.as<__nv_bfloat16>(), *tB = P->tB.as<__nv_bfloat16>();
-    PK(launch_transpose_bf16(dY, M, N, N, tA, M, N, st));     // [N][M]
-    PK(launch_transpose_bf16(X, M, Kc, Kc, tB, M, Kc, st));   // [Kc][M]
-    const int split = split_for(M, std::max(1, (int)std::min<int64_t>(128, (int64_t)32 * 1024 * 1024 / ((int64_t)N * Kc))));
-    return launch_gemm_bf16(tA, tB, nullptr, gW, nullptr, N, Kc, M, M, M, Kc, 0, split, P->part.as<float>(),
+    const int M2 = 2 * M;
+    PK(launch_transpose_bf16(dY, M, N, 2 * N, tA, M, N, st, M2));          // [N][0, M): hi^T
+    PK(launch_transpose_bf16(dY + N, M, N, 2 * N, tA + M, M, N, st, M2));  // [N][M, 2M): lo^T
+    PK(launch_transpose_bf16(X, M, Kc, Kc, tB, M, Kc, st, M2));             // [Kc][2M]: X^T twice
+    PK(launch_transpose_bf16(X, M, Kc, Kc, tB + M, M, Kc, st, M2));
+    const int split = split_for(M2, std::max(1, (int)std::min<int64_t>(128, (int64_t)32 * 1024 * 1024 / ((int64_t)N * Kc))));
+    return launch_gemm_bf16(tA, tB, nullptr, gW, nullptr, N, Kc, M2, M2, M2, Kc, 0, split, P->part.as<float>(),
+                            P->status.as<int>(), st);
+}
+
+// input gradient dX[M][Kc] (FP32) = dY W for the split dY [M][2N] and the BF16
+// weights W [N][Kc]: one GEMM over 2N, B = [W^T | W^T] ([Kc][2N])
+static cudaError_t input_grad(ProposalNet *P, const __nv_bfloat16 *dY, int M, int N, const __nv_bfloat16 *W, int Kc,
+                              float *dX, cudaStream_t st)
+{
+    __nv_bfloat16 *tB = P->tB.as<__nv_bfloat16>();
+    PK(launch_transpose_bf16(W, N, Kc, Kc, tB, N, Kc, st, 2 * N));
+    PK(launch_transpose_bf16(W, N, Kc, Kc, tB + N, N, Kc, st, 2 * N));
+    return launch_gemm_bf16(dY, tB, nullptr, dX, nullptr, M, Kc, 2 * N, 2 * N, 2 * N, Kc, 0, 1, nullptr,
                             P->status.as<int>(), st);
 }
 
@@ -312,41 +334,31 @@ cudaError_t proposal_train_step(ProposalNet *P, const __nv_bfloat16 *in, const i
     PK(proposal_forward(P, in, B, nullptr, st));
     float *g = P->grad.as<float>();
     __nv_bfloat16 *wbf = P->wbf.as<__nv_bfloat16>();
-    int *status = P->status.as<int>();
     PK(launch_softmax_ce(P->logits.as<float>(), labels, B, FC2_OUT, P->loss_rows.as<float>(), P->dl.as<float>(),
                          P->dlb.as<__nv_bfloat16>(), st));
     if (loss_sum_dev) PK(cudaMemcpyAsync(loss_sum_dev, P->loss_rows.p, 4 * (size_t)B, cudaMemcpyDeviceToDevice, st));
     // FC2
     PK(weight_grad(P, P->dlb.as<__nv_bfloat16>(), B, FC2_OUT, P->h1.as<__nv_bfloat16>(), FC1_OUT, g + P->w_off[6], st));
     PK(launch_colsum(P->dlb.as<__nv_bfloat16>(), B, FC2_OUT, g + P->b_off[6], st));
-    PK(launch_transpose_bf16(wbf + P->wbf_off[6], FC2_OUT, FC1_OUT, FC1_OUT, P->tB.as<__nv_bfloat16>(), FC2_OUT, FC1_OUT, st));
-    PK(launch_gemm_bf16(P->dlb.as<__nv_bfloat16>(), P->tB.as<__nv_bfloat16>(), nullptr, P->dmid.as<float>(), nullptr, B,
-                        FC1_OUT, FC2_OUT, FC2_OUT, FC2_OUT, FC1_OUT, 0, 1, nullptr, status, st));
-    PK(launch_relu_back(P->dmid.as<float>(), P->h1.as<__nv_bfloat16>(), (int64_t)B * FC1_OUT,
-                        P->dmid_bf.as<__nv_bfloat16>(), st));
+    PK(input_grad(P, P->dlb.as<__nv_bfloat16>(), B, FC2_OUT, wbf + P->wbf_off[6], FC1_OUT, P->dmid.as<float>(), st));
+    PK(launch_relu_back(P->dmid.as<float>(), P->h1.as<__nv_bfloat16>(), B, FC1_OUT, P->dmid_bf.as<__nv_bfloat16>(), st));
     // FC1
     const __nv_bfloat16 *x5 = P->y[4].as<__nv_bfloat16>();
     PK(weight_grad(P, P->dmid_bf.as<__nv_bfloat16>(), B, FC1_OUT, x5, FC1_IN, g + P->w_off[5], st));
     PK(launch_colsum(P->dmid_bf.as<__nv_bfloat16>(), B, FC1_OUT, g + P->b_off[5], st));
-    PK(launch_transpose_bf16(wbf + P->wbf_off[5], FC1_OUT, FC1_IN, FC1_IN, P->tB.as<__nv_bfloat16>(), FC1_OUT, FC1_IN, st));
-    PK(launch_gemm_bf16(P->dmid_bf.as<__nv_bfloat16>(), P->tB.as<__nv_bfloat16>(), nullptr, P->dmid.as<float>(), nullptr,
-                        B, FC1_IN, FC1_OUT, FC1_OUT, FC1_OUT, FC1_IN, 0, 1, nullptr, status, st));
+    PK(input_grad(P, P->dmid_bf.as<__nv_bfloat16>(), B, FC1_OUT, wbf + P->wbf_off[5], FC1_IN, P->dmid.as<float>(), st));
     // conv layers, last to first; dmid holds dL/dY_l (FP32, NHWC)
     for (int l = 4; l >= 0; --l) {
         const Conv &c = P->conv[l];
         const int M = B * c.Ho * c.Wo;
-        PK(launch_relu_back(P->dmid.as<float>(), P->y[l].as<__nv_bfloat16>(), (int64_t)M * c.Cout,
+        PK(launch_relu_back(P->dmid.as<float>(), P->y[l].as<__nv_bfloat16>(), M, c.Cout,
                             P->dmid_bf.as<__nv_bfloat16>(), st));
         PK(weight_grad(P, P->dmid_bf.as<__nv_bfloat16>(), M, c.Cout, P->col[l].as<__nv_bfloat16>(), c.Kp,
                        g + P->w_off[l], st));
         PK(launch_colsum(P->dmid_bf.as<__nv_bfloat16>(), M, c.Cout, g + P->b_off[l], st));
         if (l == 0) break;
-        PK(launch_transpose_bf16(wbf + P->wbf_off[l], c.Cout, c.Kp, c.Kp, P->tB.as<__nv_bfloat16>(), c.Cout, c.Kp, st));
-        PK(launch_gemm_bf16(P->dmid_bf.as<__nv_bfloat16>(), P->tB.as<__nv_bfloat16>(), nullptr, P->dcol.as<float>(),
-                            nullptr, M, c.Kp, c.Cout, c.Cout, c.Cout, c.Kp, 0, 1, nullptr, status, st));
-        const Conv &cp = P->conv[l - 1];
+        PK(input_grad(P, P->dmid_bf.as<__nv_bfloat16>(), M, c.Cout, wbf + P->wbf_off[l], c.Kp, P->dcol.as<float>(), st));
         PK(launch_col2im(P->dcol.as<float>(), B, c.H, c.W, c.Cin, c.Ho, c.Wo, c.Kp, nullptr, P->dmid.as<float>(), st));
-        (void)cp;
     }
     if (update) {
         P->steps++;

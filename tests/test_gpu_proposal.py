@@ -2,16 +2,17 @@
 accumulation) against the FP64 CNN oracle run on the same BF16-rounded
 weights and inputs.
 
-Bounds: BF16 keeps 8 significand bits (relative rounding 2^-9); the GPU
-rounds every activation and backward signal to BF16 once per layer (six
-layers deep), so logits and gradients carry ~1% relative error, and an
-occasional ReLU mask flips where a pre-activation is within rounding of 0.
-Forward: relative L2 of the logits <= 3e-2.  Gradients per tensor: cosine
->= 0.998 and relative L2 <= 0.1: the backward signal reaching the first
-convolutions has been rounded to BF16 about seven times (~0.5% per element)
-and a weight gradient is a sum over up to 540,672 (pixel, sample) terms with
-strong cancellation for random labels, which amplifies that noise about
-tenfold.  A step along the GPU gradient must also lower the oracle's loss.
+The GPU network stores its activations in BF16 (8 significand bits) and
+carries every backward signal as two BF16 terms (hi + lo, ~16 bits).  The
+oracle's act_bf16 mode stores the activations the same way (the BF16
+network's definition) and is FP64 otherwise: against it, logits within 2e-3
+relative L2 and every gradient tensor at cosine >= 0.999 and relative L2
+<= 1e-2 (FP32 accumulation and the odd activation rounded the other way at
+a tie).  Against the pure FP64 network (activations not rounded) the BF16
+storage itself shows: logits within 3e-2, gradients at cosine >= 0.998 and
+relative L2 <= 0.1 (the stored activations are rounded six layers deep and a
+weight gradient sums up to 540,672 products with strong cancellation for
+random labels).  A step along the GPU gradient must lower the oracle's loss.
 """
 import math
 
@@ -66,10 +67,12 @@ def test_forward_matches_oracle(R):
     logits = torch.empty((64, 64), device="cuda:0")
     ctx.proposal_forward(xi, logits)
     torch.cuda.synchronize()
-    ref = oracle.cnn_forward(p, x)
-    e = rel_l2(logits.cpu().numpy().astype(np.float64), ref)
-    print("forward logits rel L2", e)
-    assert e <= 3e-2
+    got = logits.cpu().numpy().astype(np.float64)
+    e = rel_l2(got, oracle.cnn_forward(p, x, act_bf16=True))
+    e64 = rel_l2(got, oracle.cnn_forward(p, x))
+    print("forward logits rel L2: BF16-activation oracle", e, "FP64 network", e64)
+    assert e <= 2e-3
+    assert e64 <= 3e-2
 
 
 def test_gradients_match_oracle(R):
@@ -80,14 +83,18 @@ def test_gradients_match_oracle(R):
     labels = (sg.Rng(9).u64(64) % np.uint64(64)).astype(np.int32)
     loss = ctx.proposal_train_step(xi, torch.tensor(labels, device="cuda:0"), 0.0, update=False)
     g = ctx.proposal_get(1).astype(np.float64)
-    loss_ref, g_ref = oracle.cnn_loss_grad(p, x, labels)
-    print("loss", loss, loss_ref)
-    assert abs(loss - loss_ref) <= 1e-2 * loss_ref
+    loss_ref, g_ref = oracle.cnn_loss_grad(p, x, labels, act_bf16=True)
+    loss64, g64 = oracle.cnn_loss_grad(p, x, labels)
+    print("loss", loss, "BF16-activation oracle", loss_ref, "FP64 network", loss64)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    assert abs(loss - loss64) <= 1e-2 * loss64
     for t, (wo, bo, shape) in enumerate(oracle.cnn_offsets()):
         for name, lo, hi in (("W", wo, bo), ("b", bo, bo + shape[0])):
             c, e = cosine(g[lo:hi], g_ref[lo:hi]), rel_l2(g[lo:hi], g_ref[lo:hi])
-            print(f"layer {t} {name}: cosine {c:.6f} rel L2 {e:.3e}")
-            assert c >= 0.998 and e <= 0.1, (t, name, c, e)
+            c64, e64 = cosine(g[lo:hi], g64[lo:hi]), rel_l2(g[lo:hi], g64[lo:hi])
+            print(f"layer {t} {name}: cosine {c:.6f} rel L2 {e:.3e} | FP64 network: cosine {c64:.6f} rel L2 {e64:.3e}")
+            assert c >= 0.999 and e <= 1e-2, (t, name, c, e)
+            assert c64 >= 0.998 and e64 <= 0.1, (t, name, c64, e64)
     # the GPU gradient is a descent direction of the oracle's loss
     eta = 1e-3 / np.linalg.norm(g)
     assert oracle.cnn_loss_grad(p - eta * g, x, labels)[0] < loss_ref

@@ -101,3 +101,78 @@ def test_downsample_gray_matches_numpy():
     ref = img.astype(np.float64).mean(axis=0).reshape(47, 2, 176, 2).mean(axis=(1, 3))
     assert out.shape == (47, 176)
     assert np.allclose(out, ref, atol=1e-12)
+
+
+# ---- BF16 activation storage (the BF16 network's reference) --------------------
+
+def _bf16(a):
+    """torch's FP32 -> BF16 conversion (round to nearest even), as FP64."""
+    torch = pytest.importorskip("torch")
+    return torch.tensor(np.asarray(a, np.float64), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+
+
+def test_bf16_round_ties_to_even_and_matches_torch():
+    # exact ties between two BF16 neighbours go to the even significand
+    assert oracle.bf16_round(1 + 2 ** -8) == 1.0
+    assert oracle.bf16_round(1 + 3 * 2 ** -8) == 1 + 2 ** -6
+    assert oracle.bf16_round(-(1 + 2 ** -8)) == -1.0
+    assert oracle.bf16_round(1 + 2 ** -8 + 2 ** -20) == 1 + 2 ** -7
+    assert oracle.bf16_round(0.0) == 0.0 and oracle.bf16_round(3.0e38) == float(_bf16([3.0e38])[0])
+    vals = sg.Rng(5).normal(2000, 0.0, 3.0) * np.exp(sg.Rng(6).uniform(2000, -20, 20))
+    got = np.array([oracle.bf16_round(v) for v in vals])
+    assert np.array_equal(got, _bf16(vals))
+
+
+def _forward_composed(p, x):
+    """The network layer by layer from the oracle's single-layer convolution,
+    every stored activation rounded to BF16; returns (x5, h1, logits)."""
+    offs = oracle.cnn_offsets()
+    outs = []
+    for xb in x:
+        a = xb
+        for l in range(5):
+            wo, bo, shape = offs[l]
+            a = _bf16(oracle.conv3x3s2(a, p[wo:bo].reshape(shape), p[bo:bo + shape[0]]))
+        x5 = a.reshape(-1)
+        wo, bo, shape = offs[5]
+        h1 = _bf16(np.maximum(p[wo:bo].reshape(shape) @ x5 + p[bo:bo + shape[0]], 0.0))
+        wo, bo, shape = offs[6]
+        z = p[wo:bo].reshape(shape) @ h1 + p[bo:bo + shape[0]]
+        outs.append((x5, h1, z))
+    return outs
+
+
+def test_bf16_activation_forward_is_the_rounded_composition(net):
+    p, x, y = net
+    z = oracle.cnn_forward(p, x, act_bf16=True)
+    ref = np.stack([o[2] for o in _forward_composed(p, x)])
+    assert np.abs(z - ref).max() <= 1e-9 * np.abs(ref).max()
+    # and the rounding matters: the plain forward differs
+    assert np.abs(oracle.cnn_forward(p, x) - ref).max() > 1e-6
+
+
+def test_bf16_activation_gradient_is_the_chain_rule_at_stored_values(net):
+    """The last two layers' weight gradients in closed form at the rounded
+    activations: dL/dW2 = dz h1^T, dL/dW1 = (W2^T dz * [h1 > 0]) x5^T."""
+    p, x, y = net
+    loss, g = oracle.cnn_loss_grad(p, x, y, act_bf16=True)
+    offs = oracle.cnn_offsets()
+    w2o, b2o, s2 = offs[6]
+    w1o, b1o, s1 = offs[5]
+    W2 = p[w2o:b2o].reshape(s2)
+    gW2 = np.zeros(s2)
+    gW1 = np.zeros(s1)
+    ref_loss = 0.0
+    for (x5, h1, z), lab in zip(_forward_composed(p, x), y):
+        e = np.exp(z - z.max())
+        pr = e / e.sum()
+        ref_loss += (np.log(e.sum()) + z.max() - z[lab]) / len(y)
+        dz = pr.copy()
+        dz[lab] -= 1.0
+        dz /= len(y)
+        gW2 += np.outer(dz, h1)
+        dh = (W2.T @ dz) * (h1 > 0)
+        gW1 += np.outer(dh, x5)
+    assert abs(loss - ref_loss) <= 1e-12 * ref_loss
+    assert np.abs(g[w2o:b2o].reshape(s2) - gW2).max() <= 1e-12 * np.abs(gW2).max()
+    assert np.abs(g[w1o:b1o].reshape(s1) - gW1).max() <= 1e-12 * np.abs(gW1).max()
