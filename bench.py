@@ -205,9 +205,11 @@ def run_batch_leg(ctx, cam, dev, stream, n_queries=256):
 WEIGHTS = os.path.join(ROOT, "paper_2403_11367_gb300", "weights", "proposal_street.bin")
 
 
-def run_learned_leg(ctx, cam, dev, stream, n_queries=256):
+def run_learned_leg(ctx, cam, dev, stream, g_map, n_queries=256):
     """Learned proposal (top-k + margin fallback) vs the plain 64-candidate
-    sweep on the same queries: queries/s of both, recall of the plain winner."""
+    sweep on the same queries: queries/s of both, recall of the plain winner;
+    and the learned + batched + BF16-storage form against the plain FP32
+    per-query path."""
     import numpy as np
     import torch
     import scenegen as sg
@@ -246,6 +248,41 @@ def run_learned_leg(ctx, cam, dev, stream, n_queries=256):
     ctx.set_batch_options(use_graph=False, mem_budget=16 << 30)
     out["recall_vs_full_sweep"] = float(np.mean(np.array(best["plain"]) == np.array(best["learned"])))
     out["speedup"] = out["queries_per_s_learned"] / out["queries_per_s_plain"]
+
+    # the three patterns together -- learned proposal, one batched graph-captured
+    # call, BF16 attribute storage -- against the plain FP32 method run per query
+    # (one reloc_localize call per query, full 64-candidate sweep)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for q in qs[:4]:
+        ctx.localize(q[0], q[1], q[2], q[3], cam, stream=stream, want_scores=False)
+    e0.record(stream)
+    per_query = [ctx.localize(q[0], q[1], q[2], q[3], cam, stream=stream, want_scores=False)[0].best_index
+                 for q in qs]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    from paper_2403_11367_gb300 import reloc as R
+    cb = R.Context(R.reloc_default_config())
+    cb.load_map(g_map, R.BF16)
+    cb.proposal_init(0)
+    cb.proposal_set_params(np.fromfile(WEIGHTS, dtype="<f4"))
+    cb.set_batch_options(use_graph=True, mem_budget=24 << 30)
+    cb.set_proposal(True, meta["top_k"], meta["tau"])
+    cb.localize_batch(qs, cam, stream=stream, want_scores=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res, _ = cb.localize_batch(qs, cam, stream=stream, want_scores=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_comb = e0.elapsed_time(e1)
+    cb.close()
+    out["combined"] = {
+        "form": "learned top-k + margin fallback, one batched graph-captured call, BF16 attribute storage",
+        "baseline": "plain FP32, one reloc_localize per query (64-candidate sweep)",
+        "queries_per_s": n_queries / (ms_comb / 1e3), "queries_per_s_plain_fp32_per_query": n_queries / (ms_plain / 1e3),
+        "speedup": ms_plain / ms_comb,
+        "candidates_scored_per_query": float(np.mean([r.n_scored for r in res])),
+        "winner_agreement_vs_plain_fp32": float(np.mean(np.array([r.best_index for r in res]) == np.array(per_query)))}
     return out
 
 
@@ -854,7 +891,7 @@ def run_ours(args):
     precision = run_precision_leg(g, cam, dev, stream, queries, seed_poses, ref_scores, ref_best,
                                   orc[0] if orc else None) if not args.no_batch else None
     batch = run_batch_leg(ctx, cam, dev, stream) if not args.no_batch else None
-    learned = run_learned_leg(ctx, cam, dev, stream) if not args.no_batch else None
+    learned = run_learned_leg(ctx, cam, dev, stream, g) if not args.no_batch else None
     random_search = run_random_leg(ctx, cam, dev, stream) if not args.no_batch else None
     refine = run_refine_leg(ctx, cam, dev, stream) if not args.no_batch else None
     ascent = run_ascent_leg(cam, dev, stream) if not args.no_batch else None

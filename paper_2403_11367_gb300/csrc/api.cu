@@ -129,7 +129,7 @@ struct reloc_ctx {
     std::vector<int64_t> order;
     BlockIndex blocks;
     // workspace (sized for the largest sub-batch of a call)
-    DevBuf gidx, tables, rec, rect, ntiles, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums, dtot;
+    DevBuf gidx, tables, rec, rect, dkey, k1a, v1a, k1b, v1b, hist1, chunk_sums, dtot;
     DevBuf srect, bhist, inst, ranges, partials, qpart, qstats;
     // per-call results (all views / queries of the call)
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
@@ -247,7 +247,7 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
 {
     if (!ctx) return RELOC_OK;
     cudaSetDevice(ctx->device);
-    DevBuf *bufs[] = {&ctx->mean, &ctx->attr, &ctx->gidx, &ctx->tables, &ctx->rec, &ctx->rect, &ctx->ntiles,
+    DevBuf *bufs[] = {&ctx->mean, &ctx->attr, &ctx->gidx, &ctx->tables, &ctx->rec, &ctx->rect,
                       &ctx->dkey, &ctx->k1a, &ctx->v1a, &ctx->k1b, &ctx->v1b, &ctx->hist1, &ctx->chunk_sums,
                       &ctx->srect, &ctx->bhist, &ctx->inst, &ctx->ranges, &ctx->partials,
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
@@ -659,8 +659,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     if (sb.pblk > 0) {
         CK(launch_project(ctx->mean.as<float>(), ctx->mean.as<float>() + ctx->n, ctx->mean.as<float>() + 2 * ctx->n,
                           ctx->attr.p, ctx->precision, ctx->sh_degree, ctx->n, ctx->gidx.as<uint32_t>(), L, sb.pblk,
-                          sb.d_views, cp, ctx->rec.as<float4>(), ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(),
-                          ctx->dkey.as<uint32_t>(), st));
+                          sb.d_views, cp, ctx->rec.as<float4>(), ctx->rect.as<uint2>(), ctx->dkey.as<uint32_t>(), st));
         launches += 1;
     }
     stage_mark(ctx, sbi, RELOC_STAGE_DEPTH_SORT, st, capturing);
@@ -683,7 +682,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         // pass 0: dense (view, Gaussian) arrays; culled pairs are dropped
         p.keys_in = ctx->dkey.as<uint32_t>();
         p.vals_in = nullptr;
-        p.filt = ctx->ntiles.as<uint32_t>();
+        p.drop_culled = 1;
         p.len = nullptr;
         p.keys_out = ka;
         p.vals_out = va;
@@ -691,7 +690,7 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
         p.shift = 0;
         CK(launch_radix_pass(p, st));
         launches += 3;
-        p.filt = nullptr;
+        p.drop_culled = 0;
         p.len = nvis;
         p.len_out = nullptr;
         for (int pass = 1; pass < 4; ++pass) {
@@ -860,7 +859,6 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->gidx.ensure(4 * (size_t)S_tot));
         CKS(ctx->rec.ensure(48 * (size_t)VS));
         CKS(ctx->rect.ensure(8 * (size_t)VS));
-        CKS(ctx->ntiles.ensure(4 * (size_t)VS));
         CKS(ctx->dkey.ensure(4 * (size_t)VS));
         CKS(ctx->k1a.ensure(4 * (size_t)VS));
         CKS(ctx->v1a.ensure(4 * (size_t)VS));
@@ -1674,14 +1672,17 @@ extern "C" reloc_status reloc_stage_times(reloc_ctx *ctx, double *ms_out, int64_
 
 // --------------------------------------------------------------- debug ----
 
-__global__ void k_unpack_rect(const uint2 *__restrict__ rc, int64_t n, int32_t *__restrict__ out)
+// rectangles of visible pairs (the projection writes none for culled pairs,
+// whose depth key is 0xFFFFFFFF)
+__global__ void k_unpack_rect(const uint2 *__restrict__ rc, const uint32_t *__restrict__ dkey, int64_t n,
+                              int32_t *__restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint2 r = rc[i];
-    if (r.x == 0xFFFFFFFFu) {
+    if (dkey[i] == 0xFFFFFFFFu) {
         out[4 * i] = out[4 * i + 1] = out[4 * i + 2] = out[4 * i + 3] = -1;
     } else {
+        const uint2 r = rc[i];
         out[4 * i] = (int32_t)(r.x & 0xFFFF);
         out[4 * i + 1] = (int32_t)(r.y & 0xFFFF);
         out[4 * i + 2] = (int32_t)(r.x >> 16);
@@ -1702,7 +1703,8 @@ extern "C" reloc_status reloc_export_debug(reloc_ctx *ctx, float *records_dev, i
     if (records_dev && VS > 0)
         CK(cudaMemcpyAsync(records_dev, ctx->rec.p, 48 * (size_t)VS, cudaMemcpyDeviceToDevice, st));
     if (rects_dev && VS > 0) {
-        k_unpack_rect<<<(unsigned)ceil_div(VS, 256), 256, 0, st>>>(ctx->rect.as<uint2>(), VS, rects_dev);
+        k_unpack_rect<<<(unsigned)ceil_div(VS, 256), 256, 0, st>>>(ctx->rect.as<uint2>(), ctx->dkey.as<uint32_t>(), VS,
+                                                                  rects_dev);
         CK(cudaGetLastError());
     }
     if (inst_tiles_dev && VI)

@@ -106,7 +106,7 @@ cudaError_t launch_gather_subset(const int64_t *run_begin, const int64_t *run_of
 cudaError_t launch_project(const float *mx, const float *my, const float *mz, const void *attr,
                            int precision, int sh_degree, int64_t n_map, const uint32_t *gidx,
                            const Layout &L, int n_blocks, const ViewParams *views, const CamParams &cam,
-                           float4 *rec, uint2 *rect, uint32_t *ntiles, uint32_t *dkey, cudaStream_t st);
+                           float4 *rec, uint2 *rect, uint32_t *dkey, cudaStream_t st);
 
 // Stable LSD radix sort pass over segments (views).  Segment s holds
 // seg_off[s+1] - seg_off[s] slots at seg_off[s], of which len[s] are valid
@@ -114,7 +114,10 @@ cudaError_t launch_project(const float *mx, const float *my, const float *mz, co
 // filt != 0 and implicit values (the index in the segment); len_out receives
 // the kept counts.  hist: RADIX words per chunk.
 struct RadixPass {
-    const uint32_t *keys_in, *vals_in, *filt, *len;
+    // drop_culled: pass over dense (view, Gaussian) arrays, dropping keys of
+    // 0xFFFFFFFF (culled pairs; visible depth keys are positive finite floats)
+    const uint32_t *keys_in, *vals_in, *len;
+    int drop_culled;
     uint32_t *keys_out, *vals_out, *len_out, *hist;
     uint32_t *dtot;    // per (segment, digit) totals of the pass, zeroed by the caller
     const int64_t *seg_off;

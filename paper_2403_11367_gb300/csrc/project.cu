@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 k_project(const float *__restrict__ mx, const float *__restrict__ my, const float *__restrict__ mz,
           const T *__restrict__ attr, int64_t n_map, const uint32_t *__restrict__ gidx, Layout L,
           const ViewParams *__restrict__ views, CamParams cam, float4 *__restrict__ rec,
-          uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles, uint32_t *__restrict__ dkey)
+          uint2 *__restrict__ rect, uint32_t *__restrict__ dkey)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ ViewParams s_view[PROJ_VIEW_BATCH];
@@ -273,8 +273,9 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
                     }
                 }
             }
-            rect[o] = rc;
-            ntiles[o] = nt;
+            if (nt) rect[o] = rc;
+            // the depth key doubles as the visibility flag (0xFFFFFFFF: culled, and
+            // no rectangle written); visible depths are positive and finite
             dkey[o] = nt ? __float_as_uint(tz) : 0xFFFFFFFFu;
         }
     }
@@ -284,14 +285,14 @@ template <typename T>
 static cudaError_t project_t(const float *mx, const float *my, const float *mz, const T *attr, int sh_degree,
                              int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
                              const ViewParams *views, const CamParams &cam, float4 *rec, uint2 *rect,
-                             uint32_t *ntiles, uint32_t *dkey, cudaStream_t st)
+                             uint32_t *dkey, cudaStream_t st)
 {
     dim3 grid((unsigned)n_blocks);
     switch (sh_degree) {
-    case 0: k_project<T, 0><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
-    case 1: k_project<T, 1><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
-    case 2: k_project<T, 2><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
-    case 3: k_project<T, 3><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, ntiles, dkey); break;
+    case 0: k_project<T, 0><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, dkey); break;
+    case 1: k_project<T, 1><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, dkey); break;
+    case 2: k_project<T, 2><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, dkey); break;
+    case 3: k_project<T, 3><<<grid, PROJ_THREADS, 0, st>>>(mx, my, mz, attr, n_map, gidx, L, views, cam, rec, rect, dkey); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -299,14 +300,14 @@ static cudaError_t project_t(const float *mx, const float *my, const float *mz, 
 
 cudaError_t launch_project(const float *mx, const float *my, const float *mz, const void *attr, int precision,
                            int sh_degree, int64_t n_map, const uint32_t *gidx, const Layout &L, int n_blocks,
-                           const ViewParams *views, const CamParams &cam, float4 *rec, uint2 *rect, uint32_t *ntiles,
+                           const ViewParams *views, const CamParams &cam, float4 *rec, uint2 *rect,
                            uint32_t *dkey, cudaStream_t st)
 {
     if (n_blocks <= 0) return cudaSuccess;
     switch (precision) {
-    case 0: return project_t(mx, my, mz, (const float *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
-    case 1: return project_t(mx, my, mz, (const __half *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
-    case 2: return project_t(mx, my, mz, (const __nv_bfloat16 *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, ntiles, dkey, st);
+    case 0: return project_t(mx, my, mz, (const float *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, dkey, st);
+    case 1: return project_t(mx, my, mz, (const __half *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, dkey, st);
+    case 2: return project_t(mx, my, mz, (const __nv_bfloat16 *)attr, sh_degree, n_map, gidx, L, n_blocks, views, cam, rec, rect, dkey, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
         d[r] = RADIX;
         if (idx < n) {
             const uint32_t k = p.keys_in[base + idx];
-            const bool keep = p.filt ? p.filt[base + idx] != 0 : true;
+            const bool keep = !p.drop_culled || k != 0xFFFFFFFFu;
             d[r] = keep ? (k >> p.shift) & p.mask : (uint32_t)RADIX;
         }
     }
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
         if (vld[r]) {
             key[r] = p.keys_in[base + idx];
             val[r] = p.vals_in ? p.vals_in[base + idx] : (uint32_t)(begin + idx);
-            if (p.filt) vld[r] = p.filt[base + idx] != 0;
+            if (p.drop_culled) vld[r] = key[r] != 0xFFFFFFFFu;
         }
     }
 #pragma unroll
