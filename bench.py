@@ -63,23 +63,24 @@ def stage_rooflines(stage_ms, S, V, n_vis, n_inst, n_eval_per_view, fp32_peak, e
     kernels happen to move).  S subset Gaussians, V views, n_vis visible
     (view, Gaussian) pairs, n_inst tile instances.
       project     HBM: attributes read once per Gaussian (236 B, SH3 FP32) +
-                  16 B per (view, Gaussian) (rectangle, tile count, depth key)
-                  + a 48-byte record per visible pair
-      depth_sort  HBM: first pass reads key + tile count of every pair twice
-                  (16 B) and writes the visible pairs (8 B); three more passes
-                  read the key for counting and key + value for scattering
-                  and write key + value (20 B per visible pair each)
+                  the depth key of every (view, Gaussian) pair (4 B; culled
+                  pairs marked) + the tile rectangle and 48-byte record of
+                  each visible pair (56 B)
+      depth_sort  HBM: the first pass reads the key of every pair twice (count
+                  and scatter, 8 B) and writes the visible pairs (8 B); three
+                  more passes read the key for counting and key + value for
+                  scattering and write key + value (20 B per visible pair each)
       tile_count  HBM: depth-ordered index (4 B) and rectangle (8 B) read,
       + tile_emit rectangle written (8 B), read back with the index (12 B),
                   each instance written once (4 B)
-      blend       FP32: 24 flop per included (pixel, Gaussian) pair (oracle
-                  count), against the measured FP32 FMA peak; plus one
+      blend       FP32: 22 operations per evaluated (pixel, Gaussian) pair
+                  (oracle count), against the measured FP32 FMA peak; plus one
                   exponential per pair against the measured ex2 rate"""
     gb = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9
     out = {}
-    b = S * 236 + S * V * 16 + n_vis * 48
+    b = S * 236 + S * V * 4 + n_vis * 56
     out["project"] = {"bound": "hbm", "bytes": b, "achieved_gbs": gb(b, stage_ms["project"])}
-    b = S * V * 16 + n_vis * 8 + 3 * 20 * n_vis
+    b = S * V * 8 + n_vis * 8 + 3 * 20 * n_vis
     out["depth_sort"] = {"bound": "hbm", "bytes": b, "achieved_gbs": gb(b, stage_ms["depth_sort"])}
     b = n_vis * (4 + 8 + 8 + 12) + n_inst * 4
     ms = stage_ms["tile_count"] + stage_ms["tile_emit"]
