@@ -39,6 +39,19 @@ def z_ref(g, poses, cam):
     return max([1.0] + zs)
 
 
+def compare_rgb(rgb, ref, tol_rgb=TOL_RGB):
+    """compare_images for a colour-only render (V,3,H,W): unflagged pixels
+    within the tolerance, flagged ones within it plus the oracle's bound."""
+    mask = ref["flags"] == 0
+    e_rgb = np.abs(rgb - ref["rgb"]).max(axis=1)
+    stats = dict(flagged=float(1 - mask.mean()), rgb=float(e_rgb[mask].max(initial=0)),
+                 rgb_flagged=float(e_rgb[~mask].max(initial=0)),
+                 flagged_excess=float(np.max(e_rgb - ref["bound"], initial=0)))
+    assert stats["rgb"] <= tol_rgb, stats
+    assert np.all(e_rgb <= tol_rgb + ref["bound"]), stats
+    return stats
+
+
 def compare_images(rgb, depth, alpha, ref, zr, tol_rgb=TOL_RGB, tol_depth_rel=TOL_DEPTH_REL):
     """rgb (V,3,H,W), depth/alpha (V,H,W) numpy from the GPU; ref: oracle.render_views output.
 

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from parity import TOL_NCC, compare_images, replay_tile_lists, z_ref
+from parity import TOL_NCC, compare_images, compare_rgb, replay_tile_lists, z_ref
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +45,15 @@ def gpu_render(ctx, ranges, poses, cam):
     torch.cuda.synchronize()
     return rgb.cpu().numpy().astype(np.float64), depth.cpu().numpy().astype(np.float64), \
         alpha.cpu().numpy().astype(np.float64)
+
+
+def gpu_render_rgb(ctx, ranges, poses, cam):
+    """Colour only (no depth or alpha): the blend variant of the scoring
+    launches, which carries no depth and weight sums."""
+    rgb = torch.empty((len(poses), 3, cam.height, cam.width), device=torch.device("cuda:0"))
+    ctx.render(ranges, poses, cam, rgb)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy().astype(np.float64)
 
 
 def ordered(ctx, g):
@@ -229,7 +238,7 @@ def test_block_select_matches_oracle(R):
 
 # ------------------------------------------------------------ edge cases ----
 
-@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (16, 16), (8, 16)])
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (16, 16), (8, 16), (16, 8), (32, 16)])
 def test_ragged_image_and_tile_shapes(R, tiny, tile):
     cam = sg.Camera(101, 37, 40.0, 40.0, 50.5, 18.5)
     ctx = make_ctx(R, tiny.gaussians, tile_w=tile[0], tile_h=tile[1])
@@ -239,6 +248,8 @@ def test_ragged_image_and_tile_shapes(R, tiny, tile):
     prm = oracle.params(tile_w=tile[0], tile_h=tile[1])
     ref = oracle.render_views(g, poses, cam, prm)
     compare_images(rgb, depth, alpha, ref, z_ref(g, poses, cam))
+    # colour only (the scoring launches' variant), ragged in x and y here
+    compare_rgb(gpu_render_rgb(ctx, full_range(ctx), poses, cam), ref)
     rec, rect, it, ig, cnt, rg = export(ctx, 3, g.n, cam, tile)
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, tile[0], tile[1])
 
@@ -319,8 +330,9 @@ def needle_scene():
 
 def test_thin_footprints_match_oracle_across_block_shapes(R):
     """Needle-like footprints against the FP64 oracle, pixel by pixel, with
-    16x16 tiles (two records per lane as well), 8x8, 32x8 and 8x16 tiles (warp
-    blocks of 16x4, 8x8, 32x2, 8x8 pixels): RGB and alpha within 1e-4 and depth
+    16x16 tiles (two records per lane as well), 8x8, 32x8, 8x16 and 32x16 tiles
+    (warp blocks of 16x4, 8x8, 16x4, 8x8 and 16x4 pixels; colour-only renders
+    as well): RGB and alpha within 1e-4 and depth
     within 1e-4 z_ref on unflagged pixels, flagged pixels within the oracle's
     bound, NCC within 2e-6 of the oracle's.  The records' principal axes
     reproduce the oracle's quadratic form at the ends of both axes.  Besides,
@@ -333,7 +345,7 @@ def test_thin_footprints_match_oracle_across_block_shapes(R):
     g, cam, poses, q_np = needle_scene()
     q = torch.tensor(q_np, device="cuda:0").contiguous()
     base = ref = None
-    for tile, rpl in (((16, 16), 1), ((16, 16), 2), ((8, 8), 1), ((32, 8), 1), ((8, 16), 1)):
+    for tile, rpl in (((16, 16), 1), ((16, 16), 2), ((8, 8), 1), ((32, 8), 1), ((8, 16), 1), ((32, 16), 1)):
         ctx = make_ctx(R, g, tile_w=tile[0], tile_h=tile[1], blend_rpl=rpl)
         go = ordered(ctx, g)
         imgs = gpu_render(ctx, full_range(ctx), poses, cam)
@@ -343,6 +355,9 @@ def test_thin_footprints_match_oracle_across_block_shapes(R):
             ref = oracle.render_views(go, poses, cam, query=q_np.astype(np.float64))
             zr = z_ref(go, poses, cam)
         stats = compare_images(*imgs, ref, zr)
+        rgb_only = gpu_render_rgb(ctx, full_range(ctx), poses, cam)
+        compare_rgb(rgb_only, ref)
+        assert np.abs(rgb_only - imgs[0]).max() <= 2e-5, (tile, rpl, float(np.abs(rgb_only - imgs[0]).max()))
         assert np.abs(sc - ref["scores"]).max() <= TOL_NCC, (tile, rpl, float(np.abs(sc - ref["scores"]).max()))
         if base is None:
             base = imgs, sc
@@ -455,6 +470,7 @@ def test_street_sh3_reduced_camera(R, street_small):
     ref = oracle.render_views(sub, poses, cam)
     st = compare_images(rgb, depth, alpha, ref, z_ref(sub, poses, cam))
     print("street sh3 704x188", st)
+    print("street sh3 704x188 colour only", compare_rgb(gpu_render_rgb(ctx, runs, poses, cam), ref))
     rec, rect, it, ig, cnt, rg = export(ctx, len(poses), ng, cam)
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
 
@@ -521,3 +537,5 @@ def test_street_full_size_sampled(R):
     rgb, depth, alpha = gpu_render(ctx, runs, poses[pick], cam)
     two = oracle.render_views(sub, poses[pick], cam)
     print("full-size sampled views", compare_images(rgb, depth, alpha, two, z_ref(sub, poses[pick], cam)))
+    # the same views in colour only (the scoring launches' variant)
+    print("full-size sampled views, colour only", compare_rgb(gpu_render_rgb(ctx, runs, poses[pick], cam), two))
