@@ -386,6 +386,44 @@ def test_overflow_grow_and_retry_is_exact(R, tiny):
         assert np.array_equal(x, y)
 
 
+def far_scene():
+    """300 Gaussians 2-12 m in front of a 64x48 camera and 60 at 15-60 km
+    (scale z/40, about a pixel): depths over four and a half decades, so the
+    visible depth keys differ in every byte of the float32 pattern."""
+    r = sg.Rng(77)
+    zn, zf = r.uniform(300, 2.0, 12.0), r.uniform(60, 15000.0, 60000.0)
+    z = np.concatenate([zn, zf])
+    n = len(z)
+    mean = np.stack([r.uniform(n, -0.55, 0.55) * z, r.uniform(n, -0.4, 0.4) * z, z], 1)
+    scale = np.concatenate([np.exp(r.uniform(3 * 300, math.log(0.05), math.log(0.4))).reshape(300, 3),
+                            np.repeat((zf / 40.0)[:, None], 3, 1)])
+    quat = r.normal(4 * n).reshape(n, 4)
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    opacity = r.uniform(n, 0.3, 0.95)
+    rgb = r.uniform(3 * n).reshape(n, 1, 3)
+    g = sg.Gaussians(mean.astype(np.float32), scale.astype(np.float32), quat.astype(np.float32),
+                     opacity.astype(np.float32), rgb.astype(np.float32), 0)
+    W = np.eye(4)
+    W[:3, :3] = _rot(1, 0.05)
+    W[:3, 3] = (0.3, 0.2, 0.0)
+    return g, sg.Camera(64, 48, 50.0, 50.0, 32.0, 24.0), np.stack([np.eye(4), W])
+
+
+def test_depths_over_four_decades(R):
+    """Visible depths from 2 m to 60 km (the far Gaussians all on screen):
+    images against the oracle and the tile lists bit for bit, so every byte
+    of the depth sort's keys orders them."""
+    g, cam, poses = far_scene()
+    ctx = make_ctx(R, g)
+    go = ordered(ctx, g)
+    ref = oracle.render_views(go, poses, cam)
+    assert ref["counts"][:, 0].min() == 360
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), poses, cam)
+    compare_images(rgb, depth, alpha, ref, z_ref(go, poses, cam))
+    rec, rect, it, ig, cnt, rg = export(ctx, len(poses), go.n, cam)
+    replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
+
+
 def test_repeat_calls_are_deterministic(R, tiny):
     ctx = make_ctx(R, tiny.gaussians)
     q = torch.rand((3, tiny.camera.height, tiny.camera.width), device="cuda:0", generator=None)
