@@ -421,10 +421,12 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
 //
 // k_tile_emit_reg<KT>: rows of at most 32*KT tiles.  The row is cut into KT
 // bands of 32 tiles with one queue each (a pair straddling a band edge goes
-// to both); lane l keeps the slot of its tile in band b in register slot[b],
-// so draining band b's queue costs one predicated store per pair, with no
-// divergence and no dependent shared-memory round trip (the row through the
-// horizon takes most pairs of every chunk).
+// to both, with the mask of the band's lanes it covers, formed once by the
+// lane that queues it); lane l keeps the slot of its tile in band b in
+// register slot[b], so draining band b's queue costs one bit test and one
+// predicated store per pair, with no divergence and no dependent
+// shared-memory round trip (the row through the horizon takes most pairs of
+// every chunk).
 // k_tile_emit_smem: any row width, one queue, slots in shared memory.
 constexpr int EMIT_STAGE = BIN_CHUNK_MIN;             // a whole chunk of the usual size: one barrier
 
@@ -485,14 +487,14 @@ k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__
             if (x < ntx) slot[b] = (uint32_t)R[x].x + h[x];
         }
     }
-    // band b's queue: pairs covering tile lane + 32 b go to out[slot[b]++]
-    auto drain = [&](const uint2 *qb, int cnt_q, int b, uint32_t &sl) {
-        const uint32_t xl = (uint32_t)(lane + 32 * b);
+    // band b's queue holds (Gaussian, lanes of the band its rectangle covers):
+    // lane l writes the Gaussian to out[slot[b]++] if its bit is set
+    const uint32_t mybit = 1u << lane;
+    auto drain = [&](const uint2 *qb, int cnt_q, uint32_t &sl) {
 #pragma unroll 4
         for (int j = 0; j < cnt_q; ++j) {
             const uint2 e = qb[j];
-            const uint32_t x0 = e.y & 0xFFFFu;
-            if (xl - x0 <= (e.y >> 16) - x0) {         // x0 <= x <= x1
+            if (e.y & mybit) {
                 out[sl] = e.x;
                 ++sl;
             }
@@ -520,18 +522,24 @@ k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__
             }
             if (__ballot_sync(0xffffffffu, in_row) == 0) continue;
             const uint32_t gi = in_row ? s_g[i] : 0u;
-            const int b0 = (int)((rc.x & 0xFFFFu) >> 5), b1 = (int)(rc.x >> 21);
+            const int x0 = (int)(rc.x & 0xFFFFu), x1 = (int)(rc.x >> 16);
+            const int b0 = x0 >> 5, b1 = x1 >> 5;
 #pragma unroll
             for (int b = 0; b < KT; ++b) {
                 const bool p = in_row && b0 <= b && b <= b1;
                 const unsigned mask = __ballot_sync(0xffffffffu, p);
                 if (mask == 0) continue;
                 uint2 *qb = q + b * 64;
-                if (p) qb[qn[b] + __popc(mask & lt)] = make_uint2(gi, rc.x);
+                if (p) {
+                    // lanes lo..hi of band b: tiles 32 b + lo .. 32 b + hi
+                    const int lo = max(x0 - 32 * b, 0), hi = min(x1 - 32 * b, 31);
+                    const uint32_t lanes = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+                    qb[qn[b] + __popc(mask & lt)] = make_uint2(gi, lanes);
+                }
                 qn[b] += __popc(mask);
                 if (qn[b] >= 32) {
                     __syncwarp();
-                    drain(qb, qn[b], b, slot[b]);
+                    drain(qb, qn[b], slot[b]);
                     qn[b] = 0;
                     __syncwarp();
                 }
@@ -542,7 +550,7 @@ k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__
         __syncwarp();
 #pragma unroll
         for (int b = 0; b < KT; ++b)
-            if (qn[b] > 0) drain(q + b * 64, qn[b], b, slot[b]);
+            if (qn[b] > 0) drain(q + b * 64, qn[b], slot[b]);
     }
 }
 
