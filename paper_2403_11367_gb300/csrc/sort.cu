@@ -64,20 +64,27 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_tmp,
 // ------------------------------------------------------------ upsweep ------
 // Per chunk digit counts -> hist[s][d][k] (digit-major inside a segment, so
 // one exclusive scan of the segment's block gives every chunk's offsets).
+// Each key adds 1 to its warp's own histogram with a shared-memory atomic;
+// the warps' histograms are summed at the end.  (Merging a warp's equal
+// digits first with __match_any_sync, one atomic per distinct digit, kept
+// the MIO queue full: the depth sort took 0.66 instead of 0.51 ms per
+// 64-candidate query, on the exponent byte too, where few values recur.)
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
 {
-    __shared__ uint32_t s_h[RADIX];
+    constexpr int NW = SORT_THREADS / 32;
+    __shared__ uint32_t s_h[NW][RADIX];
     const int c = blockIdx.x;
     const int s = find_segment(p.chunk_base, p.n_seg, c);
     const int k = c - p.chunk_base[s], cps = p.chunk_base[s + 1] - p.chunk_base[s];
-    s_h[threadIdx.x] = 0;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s_h[w][threadIdx.x] = 0;
     __syncthreads();
     const int64_t cap = p.seg_off[s + 1] - p.seg_off[s];
     const int64_t seg_len = p.len ? min64(p.len[s], cap) : cap;
     const int64_t begin = (int64_t)k * SORT_CHUNK;
     const int n = (int)max64(0, min64(SORT_CHUNK, seg_len - begin));
     const int64_t base = p.seg_off[s] + begin;
-    const unsigned lt = lanemask_lt();
     // all of this thread's loads first (independent, in flight together), then the counts
     uint32_t d[SORT_IPT];
 #pragma unroll
@@ -91,12 +98,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_upsweep(RadixPass p)
         }
     }
 #pragma unroll
-    for (int r = 0; r < SORT_IPT; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-        if (d[r] != (uint32_t)RADIX && (peers & lt) == 0) atomicAdd(&s_h[d[r]], (uint32_t)__popc(peers));
-    }
+    for (int r = 0; r < SORT_IPT; ++r)
+        if (d[r] != (uint32_t)RADIX) atomicAdd(&s_h[warp][d[r]], 1u);
     __syncthreads();
-    const uint32_t cnt = s_h[threadIdx.x];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt += s_h[w][threadIdx.x];
     p.hist[(int64_t)RADIX * p.chunk_base[s] + (int64_t)threadIdx.x * cps + k] = cnt;
     if (cnt) atomicAdd(p.dtot + (int64_t)RADIX * s + threadIdx.x, cnt);
 }
