@@ -419,23 +419,27 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
 // ------------------------------------------------------ K4 tile emission ----
 // A warp per (chunk, tile row).  The block stages the chunk's depth-ordered
 // (rectangle, Gaussian) pairs in shared memory; each warp picks, in order,
-// the pairs whose rectangle covers its row (ballot + popc into per-warp
-// queues) and, per queued pair, writes the Gaussian into each covered tile's
-// list at that tile's running slot.  Lane l owns the tiles x = l (mod 32) of
-// the row, so a tile's slot counter is only ever touched by one thread, and
-// the pairs are handled in depth order: every list comes out ordered by
-// (depth, index) without a sort over the instances.
+// the pairs whose rectangle covers its row (ballot + popc into a per-warp
+// queue of (Gaussian, column span) entries) and writes every queued pair into
+// each covered tile's list at that tile's running slot.  The pairs are taken
+// in depth order, so every list comes out ordered by (depth, index) without a
+// sort over the instances.
 //
-// k_tile_emit_reg<KT>: rows of at most 32*KT tiles.  The row is cut into KT
-// bands of 32 tiles with one queue each (a pair straddling a band edge goes
-// to both, with the mask of the band's lanes it covers, formed once by the
-// lane that queues it); lane l keeps the slot of its tile in band b in
-// register slot[b], so draining band b's queue costs one bit test and one
-// predicated store per pair, with no divergence and no dependent
-// shared-memory round trip (the row through the horizon takes most pairs of
-// every chunk).
-// k_tile_emit_smem: any row width, one queue, slots in shared memory.
+// k_tile_emit_flat: rows of at most EMIT_FLAT_MAX_NTX tiles.  32 queued pairs
+// are written at a time with no loop over tiles or column bands: queued pair
+// e (lane e) XORs its lane bit into a difference array along the row at x0
+// and at x1 + 1, so the array's inclusive XOR prefix is, for every tile x,
+// the mask M[x] of the queued pairs covering x.  Pair e's slot in tile x is
+// cnt[x] + popc(M[x] & bits below e) -- its rank among the chunk's pairs
+// covering x, in depth order -- so the instances can be written in any order
+// (lane e writes its pair's first EMIT_JCAP columns; the columns of wider
+// spans are spread over the lanes), and then cnt[x] += popc(M[x]).
+// k_tile_emit_smem: any row width, slots in shared memory, a lane per
+// column of each queued pair.
 constexpr int EMIT_STAGE = BIN_CHUNK_MIN;             // a whole chunk of the usual size: one barrier
+constexpr int EMIT_FLAT_MAX_NTX = 256;
+constexpr int EMIT_Q = 64;                            // queue entries per warp
+constexpr int EMIT_JCAP = 4;                          // columns a pair's own lane writes
 
 struct EmitChunk {
     int v, n;
@@ -459,16 +463,20 @@ __device__ __forceinline__ EmitChunk emit_chunk(const uint32_t *n_vis, const uin
     return ch;
 }
 
-template <int KT>
-__global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
-k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
-                const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
-                const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
-                uint32_t *__restrict__ inst_gauss)
+template <int CPL>
+__global__ void __launch_bounds__(TILE_EMIT_WARPS * 32, 6)
+k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
+                 const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
+                 const uint32_t *__restrict__ bhist, const int2 *__restrict__ ranges, Layout L, CamParams cp,
+                 uint32_t *__restrict__ inst_gauss)
 {
+    static_assert(CPL % 4 == 0, "columns per lane in 16-byte groups");
+    constexpr int NC = 32 * CPL;                        // columns a warp's arrays hold (>= ntx)
     __shared__ uint2 s_rc[EMIT_STAGE];
     __shared__ uint32_t s_g[EMIT_STAGE];
-    extern __shared__ uint2 s_qb[];                     // [TILE_EMIT_WARPS][KT][64]
+    __shared__ uint2 s_q[TILE_EMIT_WARPS][EMIT_Q];
+    __shared__ __align__(16) uint32_t s_cnt[TILE_EMIT_WARPS][NC];
+    __shared__ __align__(16) uint32_t s_m[TILE_EMIT_WARPS][NC + 4];   // x1 + 1 <= ntx <= NC
     const EmitChunk ch = emit_chunk(n_vis, n_inst, L, cp);
     if (ch.skip) return;
     const int v = ch.v, n = ch.n;
@@ -476,40 +484,102 @@ k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__
     const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
     const bool active = row < cp.nty;
     const int ntx = cp.ntx;
-    uint2 *q = s_qb + warp * KT * 64;
+    uint2 *q = s_q[warp];
     uint32_t *out = inst_gauss + L.io_off[v];
-    uint32_t slot[KT];
-    int qn[KT];
-#pragma unroll
-    for (int b = 0; b < KT; ++b) {
-        qn[b] = 0;
-        slot[b] = 0;
-    }
+    uint32_t *cnt = s_cnt[warp];
+    uint32_t *M = s_m[warp];
     if (active) {
         const uint32_t *h = bhist + (int64_t)cp.n_tiles * blockIdx.x + (int64_t)row * ntx;
         const int2 *R = ranges + (int64_t)v * cp.n_tiles + (int64_t)row * ntx;
-#pragma unroll
-        for (int b = 0; b < KT; ++b) {
-            const int x = lane + 32 * b;
-            if (x < ntx) slot[b] = (uint32_t)R[x].x + h[x];
-        }
+        for (int x = lane; x < NC; x += 32) cnt[x] = x < ntx ? (uint32_t)R[x].x + h[x] : 0u;
+        for (int x = lane; x < NC + 4; x += 32) M[x] = 0u;
     }
-    // band b's queue holds (Gaussian, lanes of the band its rectangle covers):
-    // lane l writes the Gaussian to out[slot[b]++] if its bit is set
-    const uint32_t mybit = 1u << lane;
-    auto drain = [&](const uint2 *qb, int cnt_q, uint32_t &sl) {
-#pragma unroll 4
-        for (int j = 0; j < cnt_q; ++j) {
-            const uint2 e = qb[j];
-            if (e.y & mybit) {
-                out[sl] = e.x;
-                ++sl;
+    const unsigned lt = lanemask_lt();
+    // writes the first ne (1..32) queued pairs
+    auto drain = [&](int ne) {
+        __syncwarp();
+        uint32_t gv = 0u;
+        int x0 = 0, w = 0;
+        if (lane < ne) {
+            const uint2 e = q[lane];
+            gv = e.x;
+            x0 = (int)(e.y & 0xFFFFu);
+            w = (int)(e.y >> 16) - x0 + 1;
+            atomicXor(&M[x0], 1u << lane);
+            atomicXor(&M[x0 + w], 1u << lane);
+        }
+        __syncwarp();
+        // inclusive XOR prefix along the row: lane l holds columns CPL l ..
+        // CPL l + CPL - 1 in registers, one warp scan of the lanes' totals
+        uint32_t m[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; k += 4) {
+            const uint4 t = *reinterpret_cast<const uint4 *>(M + CPL * lane + k);
+            m[k] = t.x; m[k + 1] = t.y; m[k + 2] = t.z; m[k + 3] = t.w;
+        }
+#pragma unroll
+        for (int k = 1; k < CPL; ++k) m[k] ^= m[k - 1];
+        uint32_t inc = m[CPL - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc ^= t;
+        }
+        const uint32_t ex = inc ^ m[CPL - 1];
+#pragma unroll
+        for (int k = 0; k < CPL; k += 4) {
+            m[k] ^= ex; m[k + 1] ^= ex; m[k + 2] ^= ex; m[k + 3] ^= ex;
+            *reinterpret_cast<uint4 *>(M + CPL * lane + k) = make_uint4(m[k], m[k + 1], m[k + 2], m[k + 3]);
+        }
+        __syncwarp();
+        const int wl = min(w, EMIT_JCAP);
+        for (int j = 0; j < wl; ++j) {
+            const int x = x0 + j;
+            out[cnt[x] + __popc(M[x] & lt)] = gv;
+        }
+        // columns past EMIT_JCAP: instance I of the concatenated remainders
+        // belongs to the pair whose inclusive prefix first exceeds I
+        const int rw = max(w - EMIT_JCAP, 0);
+        if (__any_sync(0xffffffffu, rw > 0)) {
+            int incl = rw;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int base = 0; base < total; base += 32) {
+                const int I = base + lane;
+                int e = 0;                              // the number of pairs with incl <= I
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const int t = __shfl_sync(0xffffffffu, incl, e + s - 1);
+                    if (t <= I) e += s;
+                }
+                const int start = __shfl_sync(0xffffffffu, incl - rw, e);
+                const int xe = __shfl_sync(0xffffffffu, x0, e);
+                const uint32_t ge = __shfl_sync(0xffffffffu, gv, e);
+                if (I < total) {
+                    const int x = xe + EMIT_JCAP + (I - start);
+                    out[cnt[x] + __popc(M[x] & ((1u << e) - 1u))] = ge;
+                }
             }
         }
+        __syncwarp();
+        // cnt[x] += popc(M[x]) from the registers; M back to zero
+#pragma unroll
+        for (int k = 0; k < CPL; k += 4) {
+            uint4 c = *reinterpret_cast<const uint4 *>(cnt + CPL * lane + k);
+            c.x += __popc(m[k]); c.y += __popc(m[k + 1]); c.z += __popc(m[k + 2]); c.w += __popc(m[k + 3]);
+            *reinterpret_cast<uint4 *>(cnt + CPL * lane + k) = c;
+            *reinterpret_cast<uint4 *>(M + CPL * lane + k) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (lane == 0) M[NC] = 0u;
+        __syncwarp();
     };
     const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
     const uint2 *sr = srect + L.vd_off[v] + ch.begin;
-    const unsigned lt = lanemask_lt();
+    int qn = 0;
     for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
         const int m = min(EMIT_STAGE, n - s0);
         __syncthreads();
@@ -521,44 +591,24 @@ k_tile_emit_reg(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__
         if (!active) continue;
         for (int i0 = 0; i0 < m; i0 += 32) {
             const int i = i0 + lane;
-            bool in_row = false;
+            bool p = false;
             uint2 rc = make_uint2(0u, 0u);
             if (i < m) {
                 rc = s_rc[i];
-                in_row = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
+                p = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
             }
-            if (__ballot_sync(0xffffffffu, in_row) == 0) continue;
-            const uint32_t gi = in_row ? s_g[i] : 0u;
-            const int x0 = (int)(rc.x & 0xFFFFu), x1 = (int)(rc.x >> 16);
-            const int b0 = x0 >> 5, b1 = x1 >> 5;
-#pragma unroll
-            for (int b = 0; b < KT; ++b) {
-                const bool p = in_row && b0 <= b && b <= b1;
-                const unsigned mask = __ballot_sync(0xffffffffu, p);
-                if (mask == 0) continue;
-                uint2 *qb = q + b * 64;
-                if (p) {
-                    // lanes lo..hi of band b: tiles 32 b + lo .. 32 b + hi
-                    const int lo = max(x0 - 32 * b, 0), hi = min(x1 - 32 * b, 31);
-                    const uint32_t lanes = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
-                    qb[qn[b] + __popc(mask & lt)] = make_uint2(gi, lanes);
-                }
-                qn[b] += __popc(mask);
-                if (qn[b] >= 32) {
-                    __syncwarp();
-                    drain(qb, qn[b], slot[b]);
-                    qn[b] = 0;
-                    __syncwarp();
-                }
+            const unsigned mask = __ballot_sync(0xffffffffu, p);
+            if (p) q[qn + __popc(mask & lt)] = make_uint2(s_g[i], rc.x);
+            qn += __popc(mask);
+            if (qn >= 32) {                             // at most 63 queued
+                drain(32);
+                qn -= 32;
+                if (lane < qn) q[lane] = q[32 + lane];
+                __syncwarp();
             }
         }
     }
-    if (active) {
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < KT; ++b)
-            if (qn[b] > 0) drain(q + b * 64, qn[b], slot[b]);
-    }
+    if (active && qn > 0) drain(qn);
 }
 
 __global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
@@ -636,16 +686,18 @@ k_tile_emit_smem(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
     }
 }
 
-template <int KT>
-static cudaError_t tile_emit_t(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
-                               const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
-                               const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
+cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
+                             const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
+                             const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
 {
-    dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
-    if (KT > 0) {
-        const size_t smem = sizeof(uint2) * TILE_EMIT_WARPS * (KT > 0 ? KT : 1) * 64;
-        k_tile_emit_reg<(KT > 0 ? KT : 1)><<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(
-            sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, inst_gauss);
+    if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
+    const dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
+    if (cp.ntx <= 128) {
+        k_tile_emit_flat<4><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
+                                                                  L, cp, inst_gauss);
+    } else if (cp.ntx <= EMIT_FLAT_MAX_NTX) {
+        k_tile_emit_flat<8><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
+                                                                  L, cp, inst_gauss);
     } else {
         const size_t smem = 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
         k_tile_emit_smem<<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
@@ -654,32 +706,9 @@ static cudaError_t tile_emit_t(const uint32_t *sorted_g, const uint2 *srect, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const uint32_t *n_vis,
-                             const uint32_t *n_inst, const uint32_t *bhist, const int2 *ranges, const Layout &L,
-                             const CamParams &cp, int n_chunks, uint32_t *inst_gauss, cudaStream_t st)
-{
-    if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
-    const int kt = (int)ceil_div(cp.ntx, 32);
-#define TILE_EMIT_CASE(K) \
-    if (kt <= K) return tile_emit_t<K>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, n_chunks, inst_gauss, st)
-    TILE_EMIT_CASE(1);
-    TILE_EMIT_CASE(2);
-    TILE_EMIT_CASE(3);
-    TILE_EMIT_CASE(4);
-    TILE_EMIT_CASE(6);
-    TILE_EMIT_CASE(8);
-#undef TILE_EMIT_CASE
-    return tile_emit_t<0>(sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, n_chunks, inst_gauss, st);
-}
-
 cudaError_t configure_tile_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_emit_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TILE_EMIT_SMEM_MAX);
-    if (e == cudaSuccess)   // band queues of the widest register variant: 8 x 8 warps x 64 pairs x 8 B
-        e = cudaFuncSetAttribute(k_tile_emit_reg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(uint2) * TILE_EMIT_WARPS * 8 * 64);
-    return e;
+    return cudaFuncSetAttribute(k_tile_emit_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_EMIT_SMEM_MAX);
 }
 
 // Tile id of every instance of one view, from its ranges (debug export).

@@ -254,6 +254,27 @@ def test_ragged_image_and_tile_shapes(R, tiny, tile):
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, tile[0], tile[1])
 
 
+@pytest.mark.parametrize("width", [2048, 2056])
+def test_wide_rows_tile_lists(R, tiny, width):
+    """Rows of 256 tiles of 8 x 8 (the widest the lane-mask emission takes)
+    and of 257 (the emission with slot counters per column): tile lists bit
+    for bit against the oracle's replay, images against the oracle.  The long
+    focal length gives spans of up to tens of tiles, so the emission's
+    spreading of wide spans over the lanes is exercised too."""
+    cam = sg.Camera(width, 24, 300.0, 300.0, width / 2.0, 12.0)
+    ctx = make_ctx(R, tiny.gaussians, tile_w=8, tile_h=8)
+    g = ordered(ctx, tiny.gaussians)
+    poses = tiny.candidate_poses[:2]
+    rgb, depth, alpha = gpu_render(ctx, full_range(ctx), poses, cam)
+    ref = oracle.render_views(g, poses, cam, oracle.params(tile_w=8, tile_h=8))
+    compare_images(rgb, depth, alpha, ref, z_ref(g, poses, cam))
+    rec, rect, it, ig, cnt, rg = export(ctx, 2, g.n, cam, (8, 8))
+    widths = (rect[..., 2] - rect[..., 0] + 1)[rect[..., 0] >= 0]
+    assert widths.max() > 8
+    n = replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 8, 8)
+    assert n == ctx.last_counts().n_instances
+
+
 def test_no_dilation_uses_fp64_inverse(R, tiny):
     # eps2d = 0: tiny footprints have det(Sigma') < 1e-6 and take the FP64 path
     ctx = make_ctx(R, tiny.gaussians, eps2d=0.0)
