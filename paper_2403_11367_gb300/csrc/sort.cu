@@ -438,7 +438,7 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
 // column of each queued pair.
 constexpr int EMIT_STAGE = BIN_CHUNK_MIN;             // a whole chunk of the usual size: one barrier
 constexpr int EMIT_FLAT_MAX_NTX = 256;
-constexpr int EMIT_Q = 64;                            // queue entries per warp
+constexpr int EMIT_Q = 256;                           // queue ring entries per warp (>= 31 + 128)
 constexpr int EMIT_JCAP = 4;                          // columns a pair's own lane writes
 
 struct EmitChunk {
@@ -463,7 +463,9 @@ __device__ __forceinline__ EmitChunk emit_chunk(const uint32_t *n_vis, const uin
     return ch;
 }
 
-template <int CPL>
+// RMASK (grids of at most 32 tile rows): each staged pair carries the bit
+// mask of the rows its rectangle covers, so a warp's row test is one AND.
+template <int CPL, bool RMASK>
 __global__ void __launch_bounds__(TILE_EMIT_WARPS * 32, 6)
 k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
                  const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
@@ -472,9 +474,10 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
 {
     static_assert(CPL % 4 == 0, "columns per lane in 16-byte groups");
     constexpr int NC = 32 * CPL;                        // columns a warp's arrays hold (>= ntx)
-    __shared__ uint2 s_rc[EMIT_STAGE];
+    __shared__ uint32_t s_y[EMIT_STAGE];                // row mask (RMASK) or y0 | y1 << 16
+    __shared__ uint32_t s_x[EMIT_STAGE];                // x0 | x1 << 16
     __shared__ uint32_t s_g[EMIT_STAGE];
-    __shared__ uint2 s_q[TILE_EMIT_WARPS][EMIT_Q];
+    __shared__ uint16_t s_q[TILE_EMIT_WARPS][EMIT_Q];   // ring of staged-pair indices
     __shared__ __align__(16) uint32_t s_cnt[TILE_EMIT_WARPS][NC];
     __shared__ __align__(16) uint32_t s_m[TILE_EMIT_WARPS][NC + 4];   // x1 + 1 <= ntx <= NC
     const EmitChunk ch = emit_chunk(n_vis, n_inst, L, cp);
@@ -484,7 +487,7 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
     const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
     const bool active = row < cp.nty;
     const int ntx = cp.ntx;
-    uint2 *q = s_q[warp];
+    uint16_t *q = s_q[warp];
     uint32_t *out = inst_gauss + L.io_off[v];
     uint32_t *cnt = s_cnt[warp];
     uint32_t *M = s_m[warp];
@@ -495,19 +498,22 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
         for (int x = lane; x < NC + 4; x += 32) M[x] = 0u;
     }
     const unsigned lt = lanemask_lt();
-    // writes the first ne (1..32) queued pairs
+    uint32_t head = 0, tail = 0;                        // queued: [head, tail), mod EMIT_Q
+    // writes the ne (1..32) pairs at the head of the queue
     auto drain = [&](int ne) {
         __syncwarp();
         uint32_t gv = 0u;
         int x0 = 0, w = 0;
         if (lane < ne) {
-            const uint2 e = q[lane];
-            gv = e.x;
-            x0 = (int)(e.y & 0xFFFFu);
-            w = (int)(e.y >> 16) - x0 + 1;
+            const int i = q[(head + lane) % EMIT_Q];
+            const uint32_t xs = s_x[i];
+            gv = s_g[i];
+            x0 = (int)(xs & 0xFFFFu);
+            w = (int)(xs >> 16) - x0 + 1;
             atomicXor(&M[x0], 1u << lane);
             atomicXor(&M[x0 + w], 1u << lane);
         }
+        head += ne;
         __syncwarp();
         // inclusive XOR prefix along the row: lane l holds columns CPL l ..
         // CPL l + CPL - 1 in registers, one warp scan of the lanes' totals
@@ -579,36 +585,55 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
     };
     const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
     const uint2 *sr = srect + L.vd_off[v] + ch.begin;
-    int qn = 0;
+    const uint32_t rowbit = 1u << (row & 31);
     for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
         const int m = min(EMIT_STAGE, n - s0);
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += TILE_EMIT_WARPS * 32) {
-            s_rc[j] = sr[s0 + j];
+            const uint2 rc = sr[s0 + j];
+            if (RMASK) {
+                const uint32_t y0 = rc.y & 0xFFFFu, y1 = rc.y >> 16;     // y0 <= y1 <= 31
+                s_y[j] = ((2u << y1) - 1u) & (0xFFFFFFFFu << y0);
+            } else {
+                s_y[j] = rc.y;
+            }
+            s_x[j] = rc.x;
             s_g[j] = g[s0 + j];
         }
         __syncthreads();
         if (!active) continue;
-        for (int i0 = 0; i0 < m; i0 += 32) {
-            const int i = i0 + lane;
-            bool p = false;
-            uint2 rc = make_uint2(0u, 0u);
-            if (i < m) {
-                rc = s_rc[i];
-                p = (int)(rc.y & 0xFFFFu) <= row && row <= (int)(rc.y >> 16);
+        // 128 pairs per step: four ballots, queued in pair order; the queue
+        // is written out 32 pairs at a time and emptied before the stage is
+        // replaced (one call site of the drain)
+        int i0 = 0;
+        while (true) {
+            const uint32_t qn = tail - head;            // at most 31 + 128
+            if (qn >= 32u || (i0 >= m && qn > 0u)) {
+                drain((int)min(qn, 32u));
+                continue;
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, p);
-            if (p) q[qn + __popc(mask & lt)] = make_uint2(s_g[i], rc.x);
-            qn += __popc(mask);
-            if (qn >= 32) {                             // at most 63 queued
-                drain(32);
-                qn -= 32;
-                if (lane < qn) q[lane] = q[32 + lane];
-                __syncwarp();
+            if (i0 >= m) break;
+            bool p[4];
+            unsigned b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u + lane;
+                p[u] = false;
+                if (i < m) {
+                    const uint32_t y = s_y[i];
+                    p[u] = RMASK ? (y & rowbit) != 0u
+                                 : (int)(y & 0xFFFFu) <= row && row <= (int)(y >> 16);
+                }
+                b[u] = __ballot_sync(0xffffffffu, p[u]);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (p[u]) q[(tail + __popc(b[u] & lt)) % EMIT_Q] = (uint16_t)(i0 + 32 * u + lane);
+                tail += __popc(b[u]);
+            }
+            i0 += 128;
         }
     }
-    if (active && qn > 0) drain(qn);
 }
 
 __global__ void __launch_bounds__(TILE_EMIT_WARPS * 32)
@@ -692,12 +717,21 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 {
     if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
     const dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
+    const bool rm = cp.nty <= 32;
     if (cp.ntx <= 128) {
-        k_tile_emit_flat<4><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
-                                                                  L, cp, inst_gauss);
+        if (rm)
+            k_tile_emit_flat<4, true><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
+                                                                            ranges, L, cp, inst_gauss);
+        else
+            k_tile_emit_flat<4, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
+                                                                             ranges, L, cp, inst_gauss);
     } else if (cp.ntx <= EMIT_FLAT_MAX_NTX) {
-        k_tile_emit_flat<8><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
-                                                                  L, cp, inst_gauss);
+        if (rm)
+            k_tile_emit_flat<8, true><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
+                                                                            ranges, L, cp, inst_gauss);
+        else
+            k_tile_emit_flat<8, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
+                                                                             ranges, L, cp, inst_gauss);
     } else {
         const size_t smem = 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
         k_tile_emit_smem<<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
