@@ -443,7 +443,7 @@ constexpr int EMIT_JCAP = 4;                          // columns a pair's own la
 
 struct EmitChunk {
     int v, n;
-    int64_t begin;
+    int64_t begin, nv;
     bool skip;
 };
 
@@ -456,6 +456,7 @@ __device__ __forceinline__ EmitChunk emit_chunk(const uint32_t *n_vis, const uin
     const int k = c - L.cb_base[ch.v];
     const int64_t S = L.vd_off[ch.v + 1] - L.vd_off[ch.v];
     const int64_t nv = min64(n_vis[ch.v], S);
+    ch.nv = nv;
     ch.begin = (int64_t)k * cp.bin_chunk;
     ch.skip = ch.begin >= nv ||                                             // past the visible list
               (int64_t)n_inst[ch.v] > L.io_off[ch.v + 1] - L.io_off[ch.v];   // overflow: nothing emitted
@@ -465,7 +466,12 @@ __device__ __forceinline__ EmitChunk emit_chunk(const uint32_t *n_vis, const uin
 
 // RMASK (grids of at most 32 tile rows): each staged pair carries the bit
 // mask of the rows its rectangle covers, so a warp's row test is one AND.
-template <int CPL, bool RMASK>
+// DYN (with RMASK, chunks of at most one stage): one block per chunk, whose
+// warps take the chunk's rows from a counter, heaviest row first (the row
+// through the horizon holds several times the average row's instances, and
+// a block of fixed rows lives as long as its heaviest one).  Otherwise a
+// block per (chunk, 8 rows), a warp per row.
+template <int CPL, bool RMASK, bool DYN>
 __global__ void __launch_bounds__(TILE_EMIT_WARPS * 32, 6)
 k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict__ srect,
                  const uint32_t *__restrict__ n_vis, const uint32_t *__restrict__ n_inst,
@@ -473,6 +479,7 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
                  uint32_t *__restrict__ inst_gauss)
 {
     static_assert(CPL % 4 == 0, "columns per lane in 16-byte groups");
+    static_assert(!DYN || RMASK, "dynamic rows need the 32-row mask");
     constexpr int NC = 32 * CPL;                        // columns a warp's arrays hold (>= ntx)
     __shared__ uint32_t s_y[EMIT_STAGE];                // row mask (RMASK) or y0 | y1 << 16
     __shared__ uint32_t s_x[EMIT_STAGE];                // x0 | x1 << 16
@@ -480,25 +487,29 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
     __shared__ uint16_t s_q[TILE_EMIT_WARPS][EMIT_Q];   // ring of staged-pair indices
     __shared__ __align__(16) uint32_t s_cnt[TILE_EMIT_WARPS][NC];
     __shared__ __align__(16) uint32_t s_m[TILE_EMIT_WARPS][NC + 4];   // x1 + 1 <= ntx <= NC
+    __shared__ uint32_t s_load[32];                     // DYN: the chunk's instances per row
+    __shared__ int s_order[32];                         // DYN: rows, heaviest first
+    __shared__ int s_next;
     const EmitChunk ch = emit_chunk(n_vis, n_inst, L, cp);
     if (ch.skip) return;
     const int v = ch.v, n = ch.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
-    const bool active = row < cp.nty;
     const int ntx = cp.ntx;
     uint16_t *q = s_q[warp];
     uint32_t *out = inst_gauss + L.io_off[v];
     uint32_t *cnt = s_cnt[warp];
     uint32_t *M = s_m[warp];
-    if (active) {
-        const uint32_t *h = bhist + (int64_t)cp.n_tiles * blockIdx.x + (int64_t)row * ntx;
-        const int2 *R = ranges + (int64_t)v * cp.n_tiles + (int64_t)row * ntx;
-        for (int x = lane; x < NC; x += 32) cnt[x] = x < ntx ? (uint32_t)R[x].x + h[x] : 0u;
-        for (int x = lane; x < NC + 4; x += 32) M[x] = 0u;
-    }
+    const uint32_t *hc = bhist + (int64_t)cp.n_tiles * blockIdx.x;
+    const int2 *Rv = ranges + (int64_t)v * cp.n_tiles;
     const unsigned lt = lanemask_lt();
     uint32_t head = 0, tail = 0;                        // queued: [head, tail), mod EMIT_Q
+    // slot counters of a row: the tiles' list starts plus the chunk's offsets
+    auto init_row = [&](int row) {
+        const uint32_t *h = hc + (int64_t)row * ntx;
+        const int2 *R = Rv + (int64_t)row * ntx;
+        for (int x = lane; x < NC; x += 32) cnt[x] = x < ntx ? (uint32_t)R[x].x + h[x] : 0u;
+        for (int x = lane; x < NC + 4; x += 32) M[x] = 0u;
+    };
     // writes the ne (1..32) pairs at the head of the queue
     auto drain = [&](int ne) {
         __syncwarp();
@@ -583,28 +594,11 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
         if (lane == 0) M[NC] = 0u;
         __syncwarp();
     };
-    const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
-    const uint2 *sr = srect + L.vd_off[v] + ch.begin;
-    const uint32_t rowbit = 1u << (row & 31);
-    for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
-        const int m = min(EMIT_STAGE, n - s0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < m; j += TILE_EMIT_WARPS * 32) {
-            const uint2 rc = sr[s0 + j];
-            if (RMASK) {
-                const uint32_t y0 = rc.y & 0xFFFFu, y1 = rc.y >> 16;     // y0 <= y1 <= 31
-                s_y[j] = ((2u << y1) - 1u) & (0xFFFFFFFFu << y0);
-            } else {
-                s_y[j] = rc.y;
-            }
-            s_x[j] = rc.x;
-            s_g[j] = g[s0 + j];
-        }
-        __syncthreads();
-        if (!active) continue;
-        // 128 pairs per step: four ballots, queued in pair order; the queue
-        // is written out 32 pairs at a time and emptied before the stage is
-        // replaced (one call site of the drain)
+    // one row over the m staged pairs: 128 pairs per step (four ballots),
+    // queued in pair order, written out 32 at a time and emptied at the end
+    // (before the stage is replaced; one call site of the drain)
+    auto scan_row = [&](int row, int m) {
+        const uint32_t rowbit = 1u << (row & 31);
         int i0 = 0;
         while (true) {
             const uint32_t qn = tail - head;            // at most 31 + 128
@@ -632,6 +626,68 @@ k_tile_emit_flat(const uint32_t *__restrict__ sorted_g, const uint2 *__restrict_
                 tail += __popc(b[u]);
             }
             i0 += 128;
+        }
+    };
+    const uint32_t *g = sorted_g + L.vd_off[v] + ch.begin;
+    const uint2 *sr = srect + L.vd_off[v] + ch.begin;
+    auto stage = [&](int s0, int m) {
+        for (int j = threadIdx.x; j < m; j += TILE_EMIT_WARPS * 32) {
+            const uint2 rc = sr[s0 + j];
+            if (RMASK) {
+                const uint32_t y0 = rc.y & 0xFFFFu, y1 = rc.y >> 16;     // y0 <= y1 <= 31
+                s_y[j] = ((2u << y1) - 1u) & (0xFFFFFFFFu << y0);
+            } else {
+                s_y[j] = rc.y;
+            }
+            s_x[j] = rc.x;
+            s_g[j] = g[s0 + j];
+        }
+    };
+    if (DYN) {
+        const int nty = cp.nty;                         // <= 32; n <= EMIT_STAGE
+        if (threadIdx.x < 32) s_load[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_next = 0;
+        stage(0, n);
+        __syncthreads();
+        // the chunk's instances per row: its tiles' offsets up to the next
+        // chunk's (the exclusive prefix over the view's chunks), or up to the
+        // tile's total for the view's last chunk
+        const bool last = ch.begin + cp.bin_chunk >= ch.nv;
+        for (int t = threadIdx.x; t < nty * ntx; t += TILE_EMIT_WARPS * 32) {
+            const uint32_t nxt = last ? (uint32_t)(Rv[t].y - Rv[t].x) : hc[(int64_t)cp.n_tiles + t];
+            const uint32_t c = nxt - hc[t];
+            if (c) atomicAdd(&s_load[t / ntx], c);
+        }
+        __syncthreads();
+        if (warp == 0) {                                // heaviest row first, ties by row
+            const uint32_t ld = lane < nty ? s_load[lane] : 0u;
+            int rank = 0;
+            for (int k = 0; k < nty; ++k) {
+                const uint32_t o = __shfl_sync(0xffffffffu, ld, k);
+                rank += (o > ld || (o == ld && k < lane)) ? 1 : 0;
+            }
+            if (lane < nty) s_order[rank] = lane;
+        }
+        __syncthreads();
+        while (true) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= nty) break;
+            const int row = s_order[k];
+            init_row(row);
+            scan_row(row, n);
+        }
+    } else {
+        const int row = blockIdx.y * TILE_EMIT_WARPS + warp;
+        const bool active = row < cp.nty;
+        if (active) init_row(row);
+        for (int s0 = 0; s0 < n; s0 += EMIT_STAGE) {
+            const int m = min(EMIT_STAGE, n - s0);
+            __syncthreads();
+            stage(s0, m);
+            __syncthreads();
+            if (active) scan_row(row, m);
         }
     }
 }
@@ -717,21 +773,23 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 {
     if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
     const dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
-    const bool rm = cp.nty <= 32;
+    const bool rm = cp.nty <= 32, dyn = rm && cp.bin_chunk <= EMIT_STAGE;
+    const dim3 grid1(n_chunks, 1);
+#define EMIT_FLAT(CPL_)                                                                                         \
+    if (dyn)                                                                                                    \
+        k_tile_emit_flat<CPL_, true, true><<<grid1, TILE_EMIT_WARPS * 32, 0, st>>>(                             \
+            sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, inst_gauss);                                  \
+    else if (rm)                                                                                                \
+        k_tile_emit_flat<CPL_, true, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(                             \
+            sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, inst_gauss);                                  \
+    else                                                                                                        \
+        k_tile_emit_flat<CPL_, false, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(                            \
+            sorted_g, srect, n_vis, n_inst, bhist, ranges, L, cp, inst_gauss)
     if (cp.ntx <= 128) {
-        if (rm)
-            k_tile_emit_flat<4, true><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
-                                                                            ranges, L, cp, inst_gauss);
-        else
-            k_tile_emit_flat<4, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
-                                                                             ranges, L, cp, inst_gauss);
+        EMIT_FLAT(4);
     } else if (cp.ntx <= EMIT_FLAT_MAX_NTX) {
-        if (rm)
-            k_tile_emit_flat<8, true><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
-                                                                            ranges, L, cp, inst_gauss);
-        else
-            k_tile_emit_flat<8, false><<<grid, TILE_EMIT_WARPS * 32, 0, st>>>(sorted_g, srect, n_vis, n_inst, bhist,
-                                                                             ranges, L, cp, inst_gauss);
+        EMIT_FLAT(8);
+#undef EMIT_FLAT
     } else {
         const size_t smem = 4 * (size_t)TILE_EMIT_WARPS * cp.ntx;
         k_tile_emit_smem<<<grid, TILE_EMIT_WARPS * 32, smem, st>>>(sorted_g, srect, n_vis, n_inst, bhist, ranges,
