@@ -133,6 +133,7 @@ struct reloc_ctx {
     DevBuf srect, bhist, inst, ranges, partials, qpart, qstats;
     // per-call results (all views / queries of the call)
     DevBuf nvis, ninst, scores, degen, best, best_score, view_sel, flags;
+    DevBuf bqueue;                       // the blend's work counter and heavy-tile list
     DevBuf hq, hrgb, hdepth;
     DevBuf pnp_X, pnp_out;
     DevBuf gbuf, gcoef, gpart, gpose;    // NCC pose gradients
@@ -251,7 +252,7 @@ extern "C" reloc_status reloc_destroy(reloc_ctx *ctx)
                       &ctx->dkey, &ctx->k1a, &ctx->v1a, &ctx->k1b, &ctx->v1b, &ctx->hist1, &ctx->chunk_sums,
                       &ctx->srect, &ctx->bhist, &ctx->inst, &ctx->ranges, &ctx->partials,
                       &ctx->qpart, &ctx->qstats, &ctx->nvis, &ctx->ninst, &ctx->scores, &ctx->degen,
-                      &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->hq, &ctx->hrgb,
+                      &ctx->best, &ctx->best_score, &ctx->view_sel, &ctx->flags, &ctx->bqueue, &ctx->hq, &ctx->hrgb,
                       &ctx->hdepth, &ctx->prop_in, &ctx->prop_seed, &ctx->prop_logits, &ctx->prop_idx,
                       &ctx->prop_mrg, &ctx->prop_loss, &ctx->pnp_X, &ctx->pnp_out, &ctx->gbuf, &ctx->gcoef,
                       &ctx->gpart, &ctx->gpose};
@@ -726,8 +727,8 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
     float *alp_out = rp ? ctx->talp.as<float>() : (o.alpha ? o.alpha + (int64_t)sb.v0 * HW : nullptr);
     CK(launch_blend(ctx->rec.as<float4>(), L, fgauss, ctx->ranges.as<int2>(), cp,
                     o.score ? ctx->partials.as<double>() : nullptr, rgb_out, dep_out, alp_out,
-                    nullptr, 0, d_overflow, ctx->flags.as<int>() + 8, st));
-    launches += 1;
+                    nullptr, 0, d_overflow, ctx->bqueue.as<int>(), st));
+    launches += blend_launches(L.V);
     stage_mark(ctx, sbi, RELOC_STAGE_SCORE, st, capturing);
     if (o.target) {
         // map training: the image loss and dL/dC, then back through the blend and the projection
@@ -798,8 +799,8 @@ static reloc_status enqueue_subbatch(reloc_ctx *ctx, SubBatch &sb, int sbi, cons
                                 o.brgb ? o.brgb + (int64_t)sb.q0 * 3 * HW : nullptr,
                                 o.bdepth ? o.bdepth + (int64_t)sb.q0 * HW : nullptr,
                                 o.balpha ? o.balpha + (int64_t)sb.q0 * HW : nullptr, vsel, nq, d_overflow,
-                                ctx->flags.as<int>() + 8, st));
-                launches += 1;
+                                ctx->bqueue.as<int>(), st));
+                launches += blend_launches(nq);
             }
         }
     }
@@ -902,6 +903,7 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
         CKS(ctx->best_score.ensure(8 * (size_t)Q));
         CKS(ctx->view_sel.ensure(4 * (size_t)Q));
         CKS(ctx->flags.ensure(64));
+        CKS(ctx->bqueue.ensure(4 * (size_t)blend_queue_ints(cp, std::max<int64_t>(V, Qm))));
         CKS(ctx->tables.ensure(tab));
         // pinned staging: tables, then readback
         const size_t rb_off = align256(tab);

@@ -171,14 +171,21 @@ cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *b
 // 64-pixel block; optional image export (slot = view) and NCC partials
 // [V][blend_units(cam)][3] = {S_r, S_rr, S_rq} per warp block.
 // view_sel != null: blend only the n_sel views view_sel[0..n_sel), image
-// slot k for view_sel[k].  queue: one device int, the launch's work counter
-// (zeroed on the stream before the launch).
+// slot k for view_sel[k].  queue: blend_queue_ints(cam, n) device ints for n
+// views, the launch's work counter and list of heavy tiles (zeroed on the
+// stream as needed).  blend_launches(n) launches.
 cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *inst_gauss, const int2 *ranges,
                          const CamParams &cam, double *partials, float *rgb, float *depth, float *alpha,
                          const int *view_sel, int n_sel, const int *overflow, int *queue, cudaStream_t st);
 
 // 64-pixel warp blocks of one view: the blend's unit of work and of NCC partials.
 inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w * cam.tile_h / 64); }
+// Work-queue ints of a blend launch over n views.
+inline int64_t blend_queue_ints(const CamParams &cam, int64_t n) { return 4 + n * cam.n_tiles; }
+// Kernel launches of a blend over n views: the heavy-tile listing runs for
+// launches of several views (a one-view launch ends on its longest unit
+// whatever the order).
+__host__ __device__ __forceinline__ int blend_launches(int64_t n) { return n >= 4 ? 2 : 1; }
 
 // K7: NCC per view from its n_units partials and its query's statistics;
 // coef (may be null): [V][4] = 1/sqrt(var_r var_q), NCC/var_r, mean r, mean q.

@@ -516,17 +516,39 @@ __device__ __forceinline__ void blend_unit(const float4 *__restrict__ rec, const
 
 // Persistent K6: a grid of resident one-warp blocks (as many as fit on the
 // SMs) takes the launch's units -- (view, tile, 64-pixel block) of every view
-// of every query in the call -- from one queue in view-major order (an atomic
-// ticket per unit).  A warp holds its next ticket, the next unit's view and
-// list range while it blends the current one, so the dependent loads that
-// start a unit are off the critical path, and no block launch separates
-// units (a per-unit grid spent about a quarter of its warp slots idle).  Each
-// unit is processed whole by one warp and writes only its own outputs, so
-// the result does not depend on which warp takes which unit.
+// of every query in the call -- from one queue (an atomic ticket per unit).
+// The units of heavy tiles (lists of at least BLEND_HEAVY records, listed by
+// k_blend_heavy: the horizon's tiles, whose units run up to twenty times the
+// mean) are handed out first, the rest in view-major order (the heavy ones
+// skipped there), so that no long unit starts near the end of the launch.
+// A warp holds its next ticket, the next unit's view and list range while it
+// blends the current one, so the dependent loads that start a unit are off
+// the critical path, and no block launch separates units (a per-unit grid
+// spent about a quarter of its warp slots idle).  Each unit is processed
+// whole by one warp and writes only its own outputs, so the result does not
+// depend on which warp takes which unit, nor on the order of the heavy list.
 // Register budget: 64 per thread (32 one-warp blocks per SM) for the scoring
 // launches; the export launches (DA) carry depth and alpha sums too and get
 // 72 (28 blocks per SM) rather than spill (same-box A/B: winner export
 // 0.233 -> 0.208 ms).
+constexpr int BLEND_HEAVY = 1024;
+constexpr int BQ_LIST = 4;                       // queue[0] ticket, [1] heavy count, list from [4]
+
+// queue[BQ_LIST + k] = vi * n_tiles + tile for each (view slot, tile) whose
+// list holds at least BLEND_HEAVY records; queue[1] counts them (zeroed on
+// the stream before the launch).  Nothing is listed after an overflow.
+__global__ void k_blend_heavy(const int2 *__restrict__ ranges, const int *__restrict__ view_sel, int n_views,
+                              int n_tiles, const int *__restrict__ overflow, int *__restrict__ queue)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_views * n_tiles || *overflow != 0) return;
+    const int vi = (int)(i / n_tiles), t = (int)(i - (int64_t)vi * n_tiles);
+    const int v = view_sel ? view_sel[vi] : vi;
+    if (v < 0) return;
+    const int2 r = ranges[(int64_t)v * n_tiles + t];
+    if (r.y - r.x >= BLEND_HEAVY) queue[BQ_LIST + atomicAdd(queue + 1, 1)] = (int)i;
+}
+
 template <int TW, int TH, int RPL, bool DA>
 __global__ void __launch_bounds__(32, RPL == 1 ? (DA ? 28 : 32) : 24)
 k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ inst_gauss,
@@ -535,9 +557,14 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         const int *__restrict__ overflow, int *__restrict__ queue)
 {
     __shared__ float4 s_rec[4][32 * RPL];
-    const int upv = cam.n_tiles * BlockGeom<TW, TH>::WPT;      // units per view
+    constexpr int WPT = BlockGeom<TW, TH>::WPT;
+    const int upv = cam.n_tiles * WPT;                          // units per view
     const int64_t total = (int64_t)upv * n_views;
     const bool ovf = *overflow != 0;
+    // heavy units, handed out first (and skipped in order) when the launch
+    // listed them
+    const bool listed = blend_launches(n_views) > 1;
+    const int64_t hh = listed ? (int64_t)queue[1] * WPT : 0;
     const int lane = threadIdx.x;
     // view and list range of unit u (empty past the end or after an overflow)
     auto locate = [&](int64_t u, int &v, int2 &r) {
@@ -546,23 +573,36 @@ k_blend(const float4 *__restrict__ rec, Layout L, const uint32_t *__restrict__ i
         if (u < total) {
             const int vi = (int)(u / upv), loc = (int)(u - (int64_t)vi * upv);
             v = view_sel ? view_sel[vi] : vi;
-            if (!ovf && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + loc / BlockGeom<TW, TH>::WPT];
+            if (!ovf && v >= 0) r = ranges[(int64_t)v * cam.n_tiles + loc / WPT];
         }
     };
-    int64_t u = 0;
-    if (lane == 0) u = atomicAdd(queue, 1);
-    u = __shfl_sync(0xffffffffu, u, 0);
+    // the next unit of the queue: the heavy list's, then the rest in order
+    auto next = [&](int64_t &u, int &v, int2 &r) {
+        while (true) {
+            int64_t t = 0;
+            if (lane == 0) t = atomicAdd(queue, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t < hh) {
+                const int h = queue[BQ_LIST + (int)(t / WPT)];
+                u = (int64_t)(h / cam.n_tiles) * upv + (int64_t)(h % cam.n_tiles) * WPT + (int)(t % WPT);
+                locate(u, v, r);
+                return;
+            }
+            u = t - hh;
+            locate(u, v, r);
+            if (u >= total || !listed || r.y - r.x < BLEND_HEAVY) return;
+        }
+    };
+    int64_t u;
     int v;
     int2 r;
-    locate(u, v, r);
+    next(u, v, r);
     while (u < total) {
         // the next unit: ticket, view and range in flight during this one
-        int64_t un = 0;
-        if (lane == 0) un = atomicAdd(queue, 1);
-        un = __shfl_sync(0xffffffffu, un, 0);
+        int64_t un;
         int vn;
         int2 rn;
-        locate(un, vn, rn);
+        next(un, vn, rn);
         const int vi = (int)(u / upv);
         blend_unit<TW, TH, RPL, DA>(rec, L, inst_gauss, cam, partials, rgb, depth, alpha, v < 0 ? 0 : v, vi,
                                     (int)(u - (int64_t)vi * upv), v < 0 ? make_int2(0, 0) : r, s_rec);
@@ -597,8 +637,13 @@ static cudaError_t blend_t(const float4 *rec, const Layout &L, const uint32_t *i
 {
     const int nv = view_sel ? n_sel : L.V;
     const int64_t units = (int64_t)cam.n_tiles * (TW * TH / 64) * nv;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (blend_launches(nv) > 1) {
+        const int64_t nt = (int64_t)nv * cam.n_tiles;
+        k_blend_heavy<<<(unsigned)ceil_div(nt, 256), 256, 0, st>>>(ranges, view_sel, nv, cam.n_tiles, overflow,
+                                                                   queue);
+    }
     if (depth || alpha) {
         const int g = resident_blocks(k_blend<TW, TH, RPL, true>);
         if (g <= 0) return cudaErrorInvalidValue;

@@ -535,6 +535,29 @@ def test_street_sh3_reduced_camera(R, street_small):
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
 
 
+def test_blend_same_per_view_whatever_the_view_count(R, street_small):
+    """The blend's work order (tiles whose lists hold 1024 records or more
+    first in launches of four views or more, list order in launches of fewer)
+    decides only which warp takes a unit: every view renders bit for bit the
+    same alone, in threes and among eight.  32 x 16 tiles give this street
+    lists longer than 1024 records."""
+    cam = sg.street_camera(704, 188, 276.0)
+    hidden, seeds = sg.street_queries(2, seed=12)
+    ctx = make_ctx(R, street_small, tile_w=32, tile_h=16)
+    runs, ng, nb = ctx.select_block(seeds[0][0], seeds[0][1], 40.0)
+    poses = sg.street_grid_poses(seeds[0], 2, 2, 2, 0.5, 2.0)
+    rgb8, d8, a8 = gpu_render(ctx, runs, poses, cam)
+    rg = export(ctx, len(poses), ng, cam, (32, 16))[5]
+    assert (rg[..., 1] - rg[..., 0]).max() >= 1024
+    for sel in ([0], [3], [1, 5, 6]):
+        rgb, d, a = gpu_render(ctx, runs, poses[sel], cam)
+        assert np.array_equal(rgb, rgb8[sel]) and np.array_equal(d, d8[sel]) and np.array_equal(a, a8[sel]), sel
+    # colour only (the scoring launches' variant) too
+    c8 = gpu_render_rgb(ctx, runs, poses, cam)
+    for sel in ([2], [0, 4, 7]):
+        assert np.array_equal(gpu_render_rgb(ctx, runs, poses[sel], cam), c8[sel]), sel
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 def test_half_precision_storage(R, street_small, precision):
     """FP16/BF16 attribute storage (means FP32): parity with the oracle fed the
