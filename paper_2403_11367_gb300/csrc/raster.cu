@@ -22,47 +22,43 @@ __device__ __forceinline__ double warp_sum_d(double x)
     return x;
 }
 
-// Compensated FP32 sums (Ogita, Rump and Oishi, "Accurate sum and dot
-// product", 2005: Sum2 and Dot2).  A sum is carried as hi + lo; TwoSum gives
-// the exact rounding error of each addition and TwoProd (one FMA) that of
-// each product, and the errors are summed into lo, so the result is as if
-// computed in twice the working precision and then rounded.  The _rn
-// intrinsics keep the compiler from fusing or reordering these steps.
+// Compensated FP32 sums by error-free extraction (Rump, Ogita and Oishi,
+// "Accurate floating-point summation part I: faithful rounding", 2008): with
+// SIGMA = 1.5 * 2^10, h = fl(x + SIGMA) - SIGMA is x rounded to a multiple of
+// 2^-13 (exactly, for |x| < 2^9) and x - h is exact.  A sum is carried as
+// hi + lo: the extracted parts h are added into hi, where every partial sum
+// is a multiple of 2^-13 below 2^11 -- at most 2^24 grid steps, so each
+// addition is exact (a warp block sums 192 samples of magnitude up to 4: the
+// colours, their squares and their products with the query, with room to
+// spare) -- and the remainders x - h (at most 2^-14 each) into lo, whose
+// rounding errors are 2^-37 of the samples' size.  A product a b adds its
+// exact rounding error fma(a, b, -ab) to lo as well.  Both parts cross the
+// warp butterfly as plain sums (hi exactly), and hi + lo is combined in
+// FP64.  The _rn intrinsics keep the compiler from fusing or reordering
+// these steps.
+constexpr float CS_SIGMA = 1536.f;
 struct CSum {
     float hi, lo;
 };
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 __device__ __forceinline__ void cs_add(CSum &c, float x)
 {
-    float s, e;
-    two_sum(c.hi, x, s, e);
-    c.hi = s;
-    c.lo = __fadd_rn(c.lo, e);
+    const float h = __fsub_rn(__fadd_rn(x, CS_SIGMA), CS_SIGMA);
+    c.hi = __fadd_rn(c.hi, h);
+    c.lo = __fadd_rn(c.lo, __fsub_rn(x, h));
 }
 __device__ __forceinline__ void cs_add_prod(CSum &c, float a, float b)
 {
     const float p = __fmul_rn(a, b);
-    const float pe = __fmaf_rn(a, b, -p);           // a b - p, exactly
-    float s, e;
-    two_sum(c.hi, p, s, e);
-    c.hi = s;
-    c.lo = __fadd_rn(c.lo, __fadd_rn(e, pe));
+    cs_add(c, p);
+    c.lo = __fadd_rn(c.lo, __fmaf_rn(a, b, -p));      // a b - p, exactly
 }
 // butterfly over the warp: every lane ends with the warp's total
 __device__ __forceinline__ double cs_warp_total(CSum c)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const float h = __shfl_xor_sync(0xffffffffu, c.hi, o), l = __shfl_xor_sync(0xffffffffu, c.lo, o);
-        float s, e;
-        two_sum(c.hi, h, s, e);
-        c.hi = s;
-        c.lo = __fadd_rn(__fadd_rn(c.lo, l), e);
+        c.hi = __fadd_rn(c.hi, __shfl_xor_sync(0xffffffffu, c.hi, o));
+        c.lo = __fadd_rn(c.lo, __shfl_xor_sync(0xffffffffu, c.lo, o));
     }
     return (double)c.hi + (double)c.lo;
 }
