@@ -43,9 +43,9 @@ N_QUERIES = 4
 # particular kernel's instruction mix
 FLOPS_PER_EVAL = 22
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this
-# workload's 64-view k_blend<16,16,1,false> launch of query 0 (715.90 MB +
-# 15.31 MB); to be re-taken whenever that kernel changes (None: not taken)
-BLEND_DRAM_BYTES_PER_LAUNCH = 731_210_000
+# workload's 64-view k_blend<16,16,1,false> launch of query 0 (2174.55 MB +
+# 14.79 MB); to be re-taken whenever that kernel changes (None: not taken)
+BLEND_DRAM_BYTES_PER_LAUNCH = 2_189_346_816
 WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
             "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
 

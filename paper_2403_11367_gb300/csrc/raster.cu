@@ -114,17 +114,30 @@ __global__ void __launch_bounds__(QS_THREADS) k_query_stats(Layout L, int64_t HW
     }
 }
 
-__global__ void k_query_stats_final(const double *part, int Q, double *qstats)
+// A block per query: its QS_BLOCKS partials summed by a fixed tree (one per
+// thread, then a warp and a block reduction), so the sums are deterministic.
+constexpr int QSF_THREADS = 160;                 // >= QS_BLOCKS, whole warps
+static_assert(QSF_THREADS >= QS_BLOCKS && QSF_THREADS % 32 == 0, "one partial per thread");
+__global__ void __launch_bounds__(QSF_THREADS) k_query_stats_final(const double *part, double *qstats)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= Q) return;
+    __shared__ double s[2][QSF_THREADS / 32];
+    const int q = blockIdx.x, k = threadIdx.x;
     double A = 0, B = 0;
-    for (int k = 0; k < QS_BLOCKS; ++k) {
-        A += part[2 * ((int64_t)q * QS_BLOCKS + k)];
-        B += part[2 * ((int64_t)q * QS_BLOCKS + k) + 1];
+    if (k < QS_BLOCKS) {
+        A = part[2 * ((int64_t)q * QS_BLOCKS + k)];
+        B = part[2 * ((int64_t)q * QS_BLOCKS + k) + 1];
     }
-    qstats[2 * q] = A;
-    qstats[2 * q + 1] = B;
+    A = warp_sum_d(A);
+    B = warp_sum_d(B);
+    if ((k & 31) == 0) { s[0][k >> 5] = A; s[1][k >> 5] = B; }
+    __syncthreads();
+    if (k == 0) {
+        A = 0;
+        B = 0;
+        for (int w = 0; w < QSF_THREADS / 32; ++w) { A += s[0][w]; B += s[1][w]; }
+        qstats[2 * q] = A;
+        qstats[2 * q + 1] = B;
+    }
 }
 
 cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *block_scratch, double *qstats,
@@ -132,7 +145,7 @@ cudaError_t launch_query_stats(const Layout &L, int64_t HW, bool gray, double *b
 {
     if (L.Q <= 0) return cudaSuccess;
     k_query_stats<<<dim3(QS_BLOCKS, L.Q), QS_THREADS, 0, st>>>(L, HW, gray ? 1 : 0, block_scratch);
-    k_query_stats_final<<<(L.Q + 127) / 128, 128, 0, st>>>(block_scratch, L.Q, qstats);
+    k_query_stats_final<<<L.Q, QSF_THREADS, 0, st>>>(block_scratch, qstats);
     return cudaGetLastError();
 }
 

@@ -339,42 +339,71 @@ k_tile_count(const uint32_t *__restrict__ sorted_g, const uint32_t *__restrict__
 
 // Per view: bhist[chunk][tile] becomes the exclusive prefix over the view's
 // chunks (each chunk's first slot inside a tile's list, relative to the
-// tile's start), a thread per (view, tile), totals -> ranges[v][tile].y; then
-// a block per view scans the totals in tile order into ranges[v][tile] =
-// [begin, end) (empty tiles [0, 0)) and n_inst[v].
-constexpr int TCOL_THREADS = 128;
+// tile's start), totals -> ranges[v][tile].y; then a block per view scans
+// the totals in tile order into ranges[v][tile] = [begin, end) (empty tiles
+// [0, 0)) and n_inst[v].  The chunk prefix: a block per (view, 32 tiles),
+// eight threads per tile, each holding up to TCOL_SEG of the tile's chunks in
+// registers (all its loads in flight at once), so a view's ~80 chunks are
+// scanned as eight short runs plus a prefix over the eight run totals.
+constexpr int TCOL_TILES = 32;
+constexpr int TCOL_SEGS = 8;
+constexpr int TCOL_THREADS = TCOL_TILES * TCOL_SEGS;
+constexpr int TCOL_SEG = 16;                         // chunks per run in registers
 constexpr int TSCAN_THREADS = 1024;
 
-__global__ void __launch_bounds__(TCOL_THREADS)
+__global__ void __launch_bounds__(TCOL_THREADS, 4)
 k_tile_chunk_scan(const uint32_t *__restrict__ n_vis, Layout L, CamParams cp, uint32_t *__restrict__ bhist,
                   int2 *__restrict__ ranges)
 {
+    __shared__ uint32_t s_run[TCOL_SEGS][TCOL_TILES];
     const int v = blockIdx.y;
-    const int t = blockIdx.x * TCOL_THREADS + threadIdx.x;
+    const int tl = threadIdx.x % TCOL_TILES, sg = threadIdx.x / TCOL_TILES;
+    const int t = blockIdx.x * TCOL_TILES + tl;
     const int nt = cp.n_tiles;
-    if (t >= nt) return;
     const int64_t S = L.vd_off[v + 1] - L.vd_off[v];
     const int64_t nv = min64(n_vis[v], S);
     const int nch = (int)ceil_div(nv, cp.bin_chunk);
     uint32_t *h = bhist + (int64_t)nt * L.cb_base[v] + t;
-    uint32_t run = 0;
-    int c = 0;
-    for (; c + 8 <= nch; c += 8) {                      // eight independent loads in flight
-        uint32_t x[8];
+    const int per = (int)ceil_div(nch, TCOL_SEGS);      // chunks of this thread's run
+    const int c0 = sg * per, c1 = min(nch, c0 + per);
+    uint32_t sum = 0;
+    if (per <= TCOL_SEG) {                              // uniform over the block
+        uint32_t x[TCOL_SEG];
+        uint32_t *hp = h + (int64_t)c0 * nt;
+        const int m = t < nt ? c1 - c0 : 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = h[(int64_t)(c + j) * nt];
+        for (int j = 0; j < TCOL_SEG; ++j) x[j] = j < m ? hp[(int64_t)j * nt] : 0u;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            h[(int64_t)(c + j) * nt] = run;
-            run += x[j];
-        }
+        for (int j = 0; j < TCOL_SEG; ++j) sum += x[j];
+        s_run[sg][tl] = sum;
+        __syncthreads();
+        if (t >= nt) return;
+        uint32_t run = 0;
+        for (int k = 0; k < sg; ++k) run += s_run[k][tl];
+#pragma unroll
+        for (int j = 0; j < TCOL_SEG; ++j)
+            if (j < m) {
+                hp[(int64_t)j * nt] = run;
+                run += x[j];
+            }
+        if (sg == TCOL_SEGS - 1) ranges[(int64_t)v * nt + t].y = (int)run;
+        return;
     }
-    for (; c < nch; ++c) {
+    // long views (more than TCOL_SEGS * TCOL_SEG chunks) or tiles past the
+    // grid: runs summed first, then rewritten
+    if (t < nt)
+        for (int c = c0; c < c1; ++c) sum += h[(int64_t)c * nt];
+    s_run[sg][tl] = sum;
+    __syncthreads();
+    if (t >= nt) return;
+    uint32_t run = 0;
+    for (int k = 0; k < sg; ++k) run += s_run[k][tl];
+    for (int c = c0; c < c1; ++c) {
         const uint32_t x = h[(int64_t)c * nt];
         h[(int64_t)c * nt] = run;
         run += x;
     }
-    ranges[(int64_t)v * nt + t].y = (int)run;
+    if (sg == TCOL_SEGS - 1) ranges[(int64_t)v * nt + t].y = (int)run;
 }
 
 __global__ void __launch_bounds__(TSCAN_THREADS)
@@ -410,7 +439,7 @@ cudaError_t launch_tile_count(const uint32_t *sorted_g, const uint32_t *n_vis, c
         const size_t smem = 4 * (size_t)(band_rows + 1) * W;
         k_tile_count<<<n_chunks, BIN_THREADS, smem, st>>>(sorted_g, n_vis, rect, L, cp, band_rows, srect, bhist);
     }
-    k_tile_chunk_scan<<<dim3((unsigned)ceil_div(cp.n_tiles, TCOL_THREADS), L.V), TCOL_THREADS, 0, st>>>(
+    k_tile_chunk_scan<<<dim3((unsigned)ceil_div(cp.n_tiles, TCOL_TILES), L.V), TCOL_THREADS, 0, st>>>(
         n_vis, L, cp, bhist, ranges);
     k_tile_scan<<<L.V, TSCAN_THREADS, 0, st>>>(L, cp, ranges, n_inst, overflow);
     return cudaGetLastError();
@@ -440,6 +469,7 @@ constexpr int EMIT_STAGE = BIN_CHUNK_MIN;             // a whole chunk of the us
 constexpr int EMIT_FLAT_MAX_NTX = 256;
 constexpr int EMIT_Q = 256;                           // queue ring entries per warp (>= 31 + 128)
 constexpr int EMIT_JCAP = 4;                          // columns a pair's own lane writes
+constexpr int EMIT_DYN_MIN_CHUNKS = 1024;             // about a full wave of eight-warp blocks
 
 struct EmitChunk {
     int v, n;
@@ -773,7 +803,9 @@ cudaError_t launch_tile_emit(const uint32_t *sorted_g, const uint2 *srect, const
 {
     if (n_chunks <= 0 || L.V <= 0) return cudaSuccess;
     const dim3 grid(n_chunks, (unsigned)ceil_div(cp.nty, TILE_EMIT_WARPS));
-    const bool rm = cp.nty <= 32, dyn = rm && cp.bin_chunk <= EMIT_STAGE;
+    // a block per chunk needs enough chunks to fill the GPU (a one-view launch
+    // has ~80); fewer take a block per (chunk, eight rows)
+    const bool rm = cp.nty <= 32, dyn = rm && cp.bin_chunk <= EMIT_STAGE && n_chunks >= EMIT_DYN_MIN_CHUNKS;
     const dim3 grid1(n_chunks, 1);
 #define EMIT_FLAT(CPL_)                                                                                         \
     if (dyn)                                                                                                    \
