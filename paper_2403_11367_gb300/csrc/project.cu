@@ -176,6 +176,7 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
         m[3] = r10 * s0; m[4] = r11 * s1; m[5] = r12 * s2;
         m[6] = r20 * s0; m[7] = r21 * s1; m[8] = r22 * s2;
     }
+    const float lopac = __log2f(opac);           // the record's log2 o, once per Gaussian
     const float cut2 = cam.cut;
     const float inv_tw = 1.0f / cam.tile_w, inv_th = 1.0f / cam.tile_h;
 
@@ -200,11 +201,14 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
             uint32_t nt = 0;
             uint2 rc = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
             if (tz > cam.near_plane) {
-                // Jacobian of the projection (FOV clamp in J only)
-                float xz = fminf(fmaxf(tx / tz, -cam.limx), cam.limx);
-                float yz = fminf(fmaxf(ty / tz, -cam.limy), cam.limy);
-                float j00 = cam.fx / tz, j02 = -cam.fx * xz / tz;
-                float j11 = cam.fy / tz, j12 = -cam.fy * yz / tz;
+                // Jacobian of the projection (FOV clamp in J only), from one
+                // IEEE-rounded reciprocal of the depth (the pixel position
+                // below keeps its IEEE divisions)
+                const float iz = __frcp_rn(tz);
+                float xz = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
+                float yz = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
+                float j00 = cam.fx * iz, j02 = -cam.fx * xz * iz;
+                float j11 = cam.fy * iz, j12 = -cam.fy * yz * iz;
                 // T = J R_w (2x3)
                 float t00 = j00 * P.R[0] + j02 * P.R[6], t01 = j00 * P.R[1] + j02 * P.R[7], t02 = j00 * P.R[2] + j02 * P.R[8];
                 float t10 = j11 * P.R[3] + j12 * P.R[6], t11 = j11 * P.R[4] + j12 * P.R[7], t12 = j11 * P.R[5] + j12 * P.R[8];
@@ -267,7 +271,7 @@ k_project(const float *__restrict__ mx, const float *__restrict__ my, const floa
                         // log2(o) - (alpha' . d)^2 - (beta' . d)^2
                         constexpr float KAPPA = 0.8493218002880191f;
                         float4 *rp = rec + 3 * o;
-                        rp[0] = make_float4(u, vpx, tz, __log2f(opac));
+                        rp[0] = make_float4(u, vpx, tz, lopac);
                         rp[1] = make_float4(KAPPA * ab[0], KAPPA * ab[1], KAPPA * ab[2], KAPPA * ab[3]);
                         rp[2] = make_float4(cr, cg, cbl, 0.f);
                     }
