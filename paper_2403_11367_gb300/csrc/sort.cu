@@ -152,10 +152,11 @@ k_digit_scan(uint32_t *hist, const uint32_t *__restrict__ dtot, const int32_t *_
 
 // ------------------------------------------------------------ scatter ------
 // Stable scatter of one chunk.  Warp w owns the contiguous items
-// [w*512, (w+1)*512) and ranks them round by round with __match_any_sync, so
-// ranks follow input order; per-warp digit counters then give each warp's
-// offset inside the block.  Items are staged digit-sorted in shared memory
-// and written out in runs (coalesced).
+// [w*256, (w+1)*256) and ranks them round by round (the lanes sharing a
+// digit from nine ballots, one per bit of the digit), so ranks follow input
+// order; per-warp digit counters then give each warp's offset inside the
+// block.  Items are staged digit-sorted in shared memory and written out in
+// runs (coalesced).
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
 {
     constexpr int NW = SORT_THREADS / 32;
@@ -201,7 +202,15 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(RadixPass p)
         const bool valid = vld[r];
         const uint32_t kk = key[r], vv = val[r];
         const uint32_t d = valid ? (kk >> p.shift) & p.mask : (uint32_t)RADIX;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes holding the same digit (or both invalid): the intersection of
+        // nine ballots, one per bit of d (0..RADIX)
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const bool set = ((d >> b) & 1u) != 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, set);
+            peers &= set ? bal : ~bal;
+        }
         uint32_t before = 0;
         if (valid) before = s_wcnt[warp][d];
         __syncwarp();
