@@ -2,7 +2,7 @@
 
 Workload (one "step" = one query through the whole path): the driving-scale
 street -- 2M Gaussians, SH degree 3, FP32 attributes, 20 m blocks; each query
-selects the blocks within 40 m of its coarse pose (~280k Gaussians), renders
+selects the blocks within 40 m of its coarse pose (~280k-320k Gaussians), renders
 64 candidate poses (4 x 4 x 4 grid, 0.5 m / 2 deg) at 1408x376, scores each
 against the query image by NCC, takes the argmax and exports the winner's RGB
 and depth.  Metric: candidate views rendered + NCC-scored per second.
@@ -46,7 +46,7 @@ FLOPS_PER_EVAL = 22
 # workload's 64-view k_blend<16,16,1,false> launch of query 0 (2174.55 MB +
 # 14.79 MB); to be re-taken whenever that kernel changes (None: not taken)
 BLEND_DRAM_BYTES_PER_LAUNCH = 2_189_346_816
-WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k/query), "
+WORKLOAD = ("driving street: 2M Gaussians SH3 FP32, 20 m blocks, 40 m radius (~280k-320k/query), "
             "1408x376 fx=fy=552, 64 candidates (4x4x4 grid 0.5 m / 2 deg), 16x16 tiles")
 
 
