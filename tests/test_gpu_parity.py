@@ -254,14 +254,16 @@ def test_ragged_image_and_tile_shapes(R, tiny, tile):
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, tile[0], tile[1])
 
 
-@pytest.mark.parametrize("width,height", [(2048, 24), (2056, 24), (120, 272)])
+@pytest.mark.parametrize("width,height", [(2048, 24), (2056, 24), (120, 272), (1408, 376)])
 def test_wide_rows_tile_lists(R, tiny, width, height):
     """Rows of 256 tiles of 8 x 8 (the widest the XOR-mask emission takes),
-    of 257 (the emission with slot counters per column), and 34 tile rows
-    (more than a 32-bit row mask holds): tile lists bit for bit against the
-    oracle's replay, images against the oracle.  The long focal length gives
-    spans of up to tens of tiles, so the emission's spreading of wide spans
-    over the lanes is exercised too."""
+    of 257 (the emission with slot counters per column), 34 tile rows (more
+    than a 32-bit row mask holds), and 176 x 47 = 8272 tiles (over 8192: the
+    binning chunks double to 4096 Gaussians and the emission stages each
+    chunk in two halves): tile lists bit for bit against the oracle's
+    replay, images against the oracle.  The long focal length gives spans of
+    up to tens of tiles, so the emission's spreading of wide spans over the
+    lanes is exercised too."""
     cam = sg.Camera(width, height, 300.0, 300.0, width / 2.0, height / 2.0)
     ctx = make_ctx(R, tiny.gaussians, tile_w=8, tile_h=8)
     g = ordered(ctx, tiny.gaussians)
