@@ -537,6 +537,24 @@ def test_street_sh3_reduced_camera(R, street_small):
     replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
 
 
+def test_tile_lists_bit_exact_block_per_chunk(R):
+    """8 views of the 2M-Gaussian street (~320k Gaussians selected) at
+    704x188: over 1024 binning chunks, so the emission takes a block per
+    chunk whose warps take the tile rows heaviest first; every view's tile
+    lists bit for bit against the oracle's replay."""
+    g = sg.street_gaussians(2_000_000, seed=11, sh_degree=3)
+    cam = sg.street_camera(704, 188, 276.0)
+    hidden, seeds = sg.street_queries(1, seed=12)
+    ctx = make_ctx(R, g)
+    runs, ng, nb = ctx.select_block(seeds[0][0], seeds[0][1], 40.0)
+    poses = sg.street_grid_poses(seeds[0], 2, 2, 2, 0.5, 2.0)
+    assert len(poses) * math.ceil(ng / 2048) >= 1024
+    gpu_render_rgb(ctx, runs, poses, cam)
+    rec, rect, it, ig, cnt, rg = export(ctx, len(poses), ng, cam)
+    n = replay_tile_lists(rec, rect, it, ig, cnt, rg, cam.width, cam.height, 16, 16)
+    assert n == ctx.last_counts().n_instances
+
+
 def test_blend_same_per_view_whatever_the_view_count(R, street_small):
     """The blend's work order (tiles whose lists hold 1024 records or more
     first in launches of four views or more, list order in launches of fewer)
