@@ -547,11 +547,13 @@ static void plan_batches(const reloc_ctx *ctx, const std::vector<QuerySpec> &qs,
         SubBatch sb;
         sb.q0 = q;
         sb.v0 = vglob;
-        int64_t bytes = 0;
+        int64_t bytes = 0, units = 0;
         while (q < Q) {
             const int64_t b = query_bytes(qs[q].S, qs[q].V, caps[q], cp);
-            if (q > sb.q0 && bytes + b > ctx->mem_budget) break;
+            const int64_t un = (int64_t)qs[q].V * blend_units(cp);
+            if (q > sb.q0 && (bytes + b > ctx->mem_budget || units + un > BLEND_MAX_UNITS)) break;
             bytes += b;
+            units += un;
             vglob += qs[q].V;
             ++q;
         }
@@ -833,6 +835,10 @@ static reloc_status run_batch(reloc_ctx *ctx, std::vector<QuerySpec> &qs, const 
     if (Vtot > (1 << 24)) return fail(RELOC_EINVAL, "too many views in one call");
     CamParams cp;
     CKS(make_cam(ctx, cam, cp));
+    for (auto &q : qs)
+        if ((int64_t)q.V * blend_units(cp) > BLEND_MAX_UNITS)
+            return fail(RELOC_EINVAL, "a query's %d views of %d x %d pixels exceed %lld blend units", q.V, cp.width,
+                        cp.height, (long long)BLEND_MAX_UNITS);
     CK(cudaSetDevice(ctx->device));
     ctx->last_valid = false;
     const int64_t HW = (int64_t)cp.width * cp.height;

@@ -180,6 +180,10 @@ cudaError_t launch_blend(const float4 *rec, const Layout &L, const uint32_t *ins
 
 // 64-pixel warp blocks of one view: the blend's unit of work and of NCC partials.
 inline int blend_units(const CamParams &cam) { return cam.n_tiles * (cam.tile_w * cam.tile_h / 64); }
+// Units (64-pixel blocks over all views) of one blend launch at most: the
+// work queue's tickets (heavy units counted twice) and its heavy-tile
+// entries stay far inside int32.  Sub-batches are cut to respect it.
+constexpr int64_t BLEND_MAX_UNITS = (int64_t)1 << 29;
 // Work-queue ints of a blend launch over n views.
 inline int64_t blend_queue_ints(const CamParams &cam, int64_t n) { return 4 + n * cam.n_tiles; }
 // Kernel launches of a blend over n views: the heavy-tile listing runs for

@@ -470,6 +470,12 @@ def test_invalid_arguments_fail_cleanly(R, tiny):
     with pytest.raises(R.RelocError) as e:
         empty.render([], tiny.candidate_poses[:1], tiny.camera)
     assert e.value.status == R.ENOMAP
+    # 4096 views of 16000 x 9000 pixels: more 64-pixel blend units than one
+    # launch's work queue counts (2^29), refused before any allocation
+    huge = sg.Camera(16000, 9000, 8000.0, 8000.0, 8000.0, 4500.0)
+    with pytest.raises(R.RelocError) as e:
+        ctx.render(full_range(ctx), np.repeat(tiny.candidate_poses[:1], 4096, axis=0), huge)
+    assert e.value.status == R.EINVAL
     # the context still works after errors
     gpu_render(ctx, full_range(ctx), tiny.candidate_poses[:1], tiny.camera)
 
